@@ -1,0 +1,22 @@
+"""CPU FP64 oracle for finite-temperature TD-DMRG carrier mobility.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path (the CUDA library and its
+Python binding) may import, call or link anything in this package.  Only the
+test-suite, the package smoke check and the CPU-baseline leg of the benchmark
+use it.
+
+The oracle is written from the paper (Li, Ren & Shuai, "Finite temperature
+TD-DMRG for the carrier mobility of organic semiconductors"):
+
+* ``model``  -- multi-mode Holstein(-Peierls) chain, Eq. 1 and Eq. 10, the current
+  operator (Eq. 3), their MPOs and an independent dense construction.
+* ``ed``     -- exact diagonalisation in the one-carrier sector: C(t) of Eq. 6
+  through the eigenbasis, Z, <H>, the Kubo mobility of Eq. 2.
+* ``tdvp``   -- a plain FP64 purified-MPS TD-DMRG (Eq. 4-6, Eq. S1) with the
+  one-site projector-splitting integrator the paper uses for both imaginary
+  and real time.
+* ``kubo``   -- quadrature of Eq. 2 and the hopping-limit closed form of Eq. 7.
+
+Every function is slow and literal on purpose.  It shares no code, tables or
+helpers with the CUDA path.
+"""

@@ -1,0 +1,50 @@
+"""Kubo mobility (Eq. 2) and the hopping-limit correlation function (Eq. 7).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
+"""
+import numpy as np
+
+
+def mobility(t: np.ndarray, C: np.ndarray, kT: float) -> float:
+    """mu = 1/(2 kT) int_{-t_max}^{t_max} C(t) dt  (Eq. 2, e0 = 1, cut off at t_max).
+
+    With C(-t) = C(t)^* the integral is 2 int_0^{t_max} Re C dt; the trapezoid rule is
+    used on the given grid (which must start at t = 0)."""
+    t = np.asarray(t, dtype=float)
+    C = np.asarray(C)
+    if t[0] != 0.0:
+        raise ValueError("grid must start at t = 0")
+    integral = 0.0
+    for i in range(len(t) - 1):
+        integral += 0.5 * (t[i + 1] - t[i]) * (C[i].real + C[i + 1].real)
+    return float(2.0 * integral / (2.0 * kT))
+
+
+def bose(omega: float, kT: float) -> float:
+    return 1.0 / np.expm1(omega / kT)
+
+
+def fgr_correlation(t, V, omega, g, kT, n_neighbours=2):
+    """Hopping-limit C(t) for this model's C(t) convention (derived form of Eq. 7).
+
+    Eq. 7 prints C/R^2 = V^2 exp{-sum g^2 [2n+1 - n e^{-iwt} - (n+1) e^{iwt}]}.  For the
+    current of Eq. 3 on a periodic chain, to second order in V, a hop from molecule n
+    relaxes the modes of both molecules, each carrier has two neighbours, and
+    C(t) = Tr[rho e^{iHt} j e^{-iHt} j] carries the opposite time phase:
+        C(t)/V^2 = 2 exp{-sum_m 2 g_m^2 [2n_m+1 - n_m e^{i w_m t} - (n_m+1) e^{-i w_m t}]}."""
+    t = np.atleast_1d(np.asarray(t, dtype=float))
+    expo = np.zeros(t.shape, dtype=complex)
+    for w, gm in zip(omega, g):
+        n = bose(w, kT)
+        expo += 2.0 * gm * gm * (2 * n + 1 - n * np.exp(1j * w * t) - (n + 1) * np.exp(-1j * w * t))
+    return n_neighbours * V * V * np.exp(-expo)
+
+
+def free_band_correlation(N: int, V: float, beta: float) -> float:
+    """g = 0: C(t) is constant, C = sum_k p_k (2 V sin k)^2, k = 2 pi m / N,
+    p_k ~ exp(-beta 2 V cos k) (band of Eq. 1 without phonons)."""
+    ks = 2.0 * np.pi * np.arange(N) / N
+    eps = 2.0 * V * np.cos(ks)
+    p = np.exp(-beta * (eps - eps.min()))
+    p /= p.sum()
+    return float(np.sum(p * (2.0 * V * np.sin(ks)) ** 2))

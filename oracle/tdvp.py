@@ -53,7 +53,9 @@ def gauge_qr(Y: np.ndarray, extra: Optional[np.ndarray] = None,
     columns of ``extra`` (m x p candidate directions, e.g. what the Hamiltonian couples the
     current state into) and then by the unit vectors e_0, e_1, ..., each projected against
     everything already in Q and taken when its residual norm exceeds complete_tol times its
-    own norm.  R = Q^H Y.
+    own norm.  R = Q^H Y, except that the rows of completed positions are set to zero
+    (their entries are residuals below rank_tol * ||Y||_F, which the Gram-Schmidt
+    coefficients of the skipped columns do not carry).
     """
     m, n = Y.shape
     assert m >= n
@@ -81,9 +83,11 @@ def gauge_qr(Y: np.ndarray, extra: Optional[np.ndarray] = None,
             yield e
 
     gen = candidates()
+    completed = []
     for j in range(n):
         if j in have:
             continue
+        completed.append(j)
         while True:
             c = next(gen, None)
             if c is None:
@@ -100,6 +104,7 @@ def gauge_qr(Y: np.ndarray, extra: Optional[np.ndarray] = None,
                 have.append(j)
                 break
     R = Q.conj().T @ Y
+    R[completed, :] = 0.0
     return Q, R
 
 

@@ -1,0 +1,165 @@
+/*
+ * tdmrg.h -- C ABI of the GB300 finite-temperature TD-DMRG library (libtdmrg.so).
+ *
+ * The library computes the current-current correlation function of a periodic
+ * multi-mode Holstein(-Peierls) chain with one carrier and the Kubo mobility from it
+ * (Li, Ren & Shuai, "Finite temperature TD-DMRG for the carrier mobility of organic
+ * semiconductors"):
+ *
+ *   H     = V sum_n (c+_{n+1} c_n + h.c.) + sum_{n,m} w_m b+_{nm} b_{nm}
+ *           + sum_{n,m} g_m w_m (b+_{nm} + b_{nm}) c+_n c_n                      (Eq. 1)
+ *   j     = (V / i) sum_n (c+_{n+1} c_n - c+_n c_{n+1})            (Eq. 3, e0 = R = 1)
+ *   Psi_b = exp(-beta H / 2) |I>,  |I> = sum_i |i>_P |i>_Q            (Eq. 4-5)
+ *   C(t)  = <Psi_b| e^{iHt} j e^{-iHt} j |Psi_b> / Z                     (Eq. 6)
+ *   mu    = 1/(2 kT) int C(t) dt                                          (Eq. 2)
+ *
+ * Both propagations use the one-site TDVP projector-splitting integrator on a purified
+ * MPS (Eq. S1), every step of it in CUDA kernels for sm_103a.  Units: hbar = kB = e0 = R = 1.
+ *
+ * Conventions for every function:
+ *  - return TDMRG_OK (0) on success, a negative TDMRG_ERR_* code otherwise; the message of
+ *    the last failure is available from tdmrg_last_error(h) (a string owned by the handle,
+ *    valid until the next call on it) or tdmrg_last_global_error() when no handle exists;
+ *  - host pointers are owned by the caller and only read/written during the call;
+ *  - the handle owns all device memory it allocates (cudaMalloc on the current device);
+ *    tdmrg_model_destroy frees it;
+ *  - all work is issued on the handle's stream (default: the legacy default stream);
+ *    functions that return results to host memory synchronise that stream;
+ *  - no exception crosses the ABI; a handle is not thread safe.
+ */
+#ifndef TDMRG_H
+#define TDMRG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TDMRG_OK             0
+#define TDMRG_ERR_ARG       -1   /* invalid argument (sizes, grids, order of calls)      */
+#define TDMRG_ERR_CUDA      -2   /* a CUDA runtime call failed                           */
+#define TDMRG_ERR_OOM       -3   /* device allocation failed                             */
+#define TDMRG_ERR_NONFINITE -4   /* NaN/Inf detected in a norm after a half-sweep        */
+#define TDMRG_ERR_NOCONV    -5   /* Krylov exponential did not converge (estimate > 1e3 tol) */
+#define TDMRG_ERR_TIMEOUT   -6   /* a bounded device-side wait (grid barrier) gave up    */
+#define TDMRG_ERR_STATE     -7   /* call out of order (e.g. correlation before prepare)  */
+
+#define TDMRG_PREC_C128        0 /* every contraction in complex FP64                    */
+#define TDMRG_PREC_C64_3XTF32  1 /* H_eff / environment contractions as complex FP32 via
+                                    3xTF32 split products on the tensor cores; Lanczos
+                                    orthogonalisation, small exponential, QR and all norms
+                                    and traces stay FP64                                   */
+
+typedef struct tdmrg_model tdmrg_model;
+
+/* Build the chain of Eq. 1: N >= 3 molecules on a ring, `modes` intramolecular modes per
+ * molecule with frequencies omega[modes], dimensionless couplings g[modes] and nmax[modes]
+ * harmonic-oscillator levels (2 <= nmax <= 32), transfer integral V.  Builds the MPOs of
+ * H (bond dimension 7) and j (bond dimension 6) on the host and uploads them.
+ * Site order along the MPS: e_1, v_{1,1..modes}, e_2, ... (plus p_n with a Peierls mode). */
+int tdmrg_model_create(int N, int modes, const double* omega, const double* g, double V,
+                       const int* nmax, tdmrg_model** out);
+
+/* Holstein-Peierls extension (Eq. 10): one bond mode p_n (frequency omega_p, nmax_p levels)
+ * per bond, modulating the transfer integral as V (1 + alpha (b_p + b_p^+)); the current
+ * operator becomes j = i[H, P] (Eq. 3 with V -> V (1 + alpha x_p)).  Call before
+ * tdmrg_thermal_prepare. */
+int tdmrg_model_set_peierls(tdmrg_model* h, double alpha, double omega_p, int nmax_p);
+
+/* TDMRG_PREC_C128 (default) or TDMRG_PREC_C64_3XTF32. */
+int tdmrg_model_set_precision(tdmrg_model* h, int precision);
+
+/* Krylov exponential control: stop when beta_k |(exp(tau T_k) e_1)_k| < tol (default 1e-13
+ * for C128, 1e-7 for 3xTF32), at most kmax (<= 32) vectors; fixed_k > 0 forces exactly that
+ * many vectors (smooth map for finite differences). */
+int tdmrg_model_set_krylov(tdmrg_model* h, double tol, int kmax, int fixed_k);
+
+/* Work stream (a cudaStream_t passed as void*; NULL = legacy default stream). */
+int tdmrg_model_set_stream(tdmrg_model* h, void* stream);
+
+int tdmrg_model_destroy(tdmrg_model* h);
+
+/* Imaginary-time preparation of Psi_beta (Eq. 5): |I> restricted to the one-carrier sector,
+ * bond dimensions M_k = min(M, prod of local dims on either side), right-canonicalised, then
+ * round(beta / (2 dtau)) symmetric projector-splitting steps of exp(-dtau H), normalised
+ * after each step.  beta must be an even multiple of dtau.  Stores log Z. */
+int tdmrg_thermal_prepare(tdmrg_model* h, double beta, double dtau, int M);
+
+/* C(t) of Eq. 6 on t_grid[nt] (host, ascending, t_grid[0] = 0, every point an integer
+ * multiple of dt).  Forms j|Psi_b> (MPO applied by one-site variational fitting at the
+ * bond dimensions of Psi_b) and propagates both states with steps dt.  Writes C_out[2*nt]
+ * (host, interleaved re, im).  Requires tdmrg_thermal_prepare. */
+int tdmrg_correlation(tdmrg_model* h, const double* t_grid, int nt, double dt, double* C_out);
+
+/* Stepping interface under tdmrg_correlation: realtime_init forms Psi_1 = Psi_b and
+ * Psi_2 = j Psi_b; realtime_step advances both by nsteps steps dt; realtime_observe writes
+ * the current C (C_out[2] host) and, if obs is not NULL, obs[3] = {<Psi1|Psi1>, <Psi2|Psi2>,
+ * <Psi1|H|Psi1>}. */
+int tdmrg_realtime_init(tdmrg_model* h);
+int tdmrg_realtime_step(tdmrg_model* h, int nsteps, double dt);
+int tdmrg_realtime_observe(tdmrg_model* h, double* C_out, double* obs);
+
+/* Kubo mobility of Eq. 2 with the cut-off t_max = t_grid[nt-1]:
+ * mu = (1 / (2 kT)) * 2 int_0^{t_max} Re C dt by the trapezoid rule (C(-t) = C(t)^*).
+ * t_grid[nt], C[2*nt] host; pure host arithmetic, no handle needed. */
+int tdmrg_mobility(const double* t_grid, const double* C, int nt, double kT, double* mu_out);
+
+/* log Z = log Tr[exp(-beta H) P_1] accumulated by tdmrg_thermal_prepare. */
+int tdmrg_get_logz(const tdmrg_model* h, double* logz);
+
+/* Counters since the last reset: stats[0] site updates, [1] H_eff matvecs, [2] algorithmic
+ * H_eff flops, [3] Krylov vectors, [4] bond matvecs, [5] gauge QRs, [6] completions,
+ * [7] environment updates.  n = number of entries wanted (<= 8). */
+int tdmrg_get_stats(const tdmrg_model* h, double* stats, int n);
+int tdmrg_reset_stats(tdmrg_model* h);
+
+const char* tdmrg_last_error(const tdmrg_model* h);
+const char* tdmrg_last_global_error(void);
+
+/* ----------------------------------------------------------------------------------
+ * Kernel-level entry points (device pointers, complex FP64 interleaved re/im, row-major).
+ * They run one hot-path contraction in isolation, for parity tests and measurement.
+ * Arguments are sizes and device pointers owned by the caller; nothing is allocated
+ * except where noted; the call returns after the work is enqueued on `stream`.
+ * ---------------------------------------------------------------------------------- */
+
+/* Effective Hamiltonian of one site (K1):
+ *   out[a,s,t,b] = sum L[w,a,y] W[w,v,s,u] A[y,u,t,c] R[v,b,c]
+ * L: Dl x Ml x Ml, R: Dr x Mr x Mr, A/out: Ml x (d*d) x Mr, W: Dl x Dr x d x d (dense, host
+ * pointer, complex interleaved).  Workspace X, Y: device buffers of at least
+ * max(Dl, Dr) * Ml * d*d * Mr complex entries each.  precision: TDMRG_PREC_*.  For
+ * TDMRG_PREC_C64_3XTF32 the scratch `ws32` must hold 8 * (Dl*Ml*Ml + max(Dl,Dr)*Ml*d*d*Mr
+ * + Dr*Mr*Mr) floats (pass NULL for C128).  Returns after enqueueing on `stream`. */
+int tdmrg_kernel_heff(int Ml, int Mr, int d, int Dl, int Dr, const double* W_host,
+                      const void* L, const void* R, const void* A, void* out,
+                      void* X, void* Y, void* ws32, int precision, void* stream);
+
+/* Left environment update (K5):
+ *   Lout[v,b,c] = sum conj(bra[a,s,t,b]) L[w,a,y] W[w,v,s,u] ket[y,u,t,c]
+ * bra: Ml1 x d*d x Mr1, ket: Ml2 x d*d x Mr2, L: Dl x Ml1 x Ml2, Lout: Dr x Mr1 x Mr2.
+ * X, Y: workspace of max(Dl,Dr) * Ml2 * d*d * Mr2 complex entries. */
+int tdmrg_kernel_env_left(int Ml1, int Mr1, int Ml2, int Mr2, int d, int Dl, int Dr,
+                          const double* W_host, const void* L, const void* bra,
+                          const void* ket, void* Lout, void* X, void* Y, void* stream);
+
+/* Gauge QR (K4): Y (m x n row-major, m >= n) = Q R with the deterministic completion
+ * described for the oracle: accepted columns are Gram-Schmidt residuals (twice) above
+ * 1e-12 ||Y||_F; skipped positions are filled from the columns of E (m x p row-major, may
+ * be NULL with p = 0) then unit vectors, each taken when its residual exceeds 1e-2 of its
+ * norm.  Q (m x n) and R (n x n) row-major outputs; R rows of completed positions are 0.
+ * status (device int, may be NULL): set to 1 if the bounded grid barrier timed out. */
+int tdmrg_kernel_gauge_qr(int m, int n, const void* Y, int p, const void* E, void* Q,
+                          void* R, int* status, void* stream);
+
+/* Krylov exponential (K2/K3) of a dense Hermitian matrix H (n x n, device):
+ * out = exp(tau H) v with tau = tau_re + i tau_im, Lanczos with full re-orthogonalisation
+ * in FP64 and the small exponential on the device.  kused (host, may be NULL) receives
+ * the number of Krylov vectors.  Allocates its own workspace (freed before return);
+ * synchronises `stream`. */
+int tdmrg_kernel_krylov_dense(int n, const void* H, const void* v, void* out, double tau_re,
+                              double tau_im, double tol, int kmax, int* kused, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TDMRG_H */

@@ -1,0 +1,235 @@
+"""ctypes binding of libtdmrg.so (argument marshalling only).
+
+Every function of ``include/tdmrg.h`` is exposed under the same name; ``Model`` wraps the
+handle.  There is no fallback: if the library is missing or cannot be loaded, importing the
+binding raises, and every failing call raises ``TdmrgError`` with the library's message.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libtdmrg.so")
+
+PREC_C128 = 0
+PREC_C64_3XTF32 = 1
+
+ERRORS = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_OOM", -4: "ERR_NONFINITE",
+          -5: "ERR_NOCONV", -6: "ERR_TIMEOUT", -7: "ERR_STATE"}
+
+
+class TdmrgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+
+
+_lib = None
+
+_d = ctypes.c_double
+_i = ctypes.c_int
+_p = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+_SIGS = {
+    "tdmrg_model_create": [_i, _i, _dp, _dp, _d, _ip, ctypes.POINTER(_p)],
+    "tdmrg_model_set_peierls": [_p, _d, _d, _i],
+    "tdmrg_model_set_precision": [_p, _i],
+    "tdmrg_model_set_krylov": [_p, _d, _i, _i],
+    "tdmrg_model_set_stream": [_p, _p],
+    "tdmrg_model_destroy": [_p],
+    "tdmrg_thermal_prepare": [_p, _d, _d, _i],
+    "tdmrg_correlation": [_p, _dp, _i, _d, _dp],
+    "tdmrg_realtime_init": [_p],
+    "tdmrg_realtime_step": [_p, _i, _d],
+    "tdmrg_realtime_observe": [_p, _dp, _dp],
+    "tdmrg_mobility": [_dp, _dp, _i, _d, _dp],
+    "tdmrg_get_logz": [_p, _dp],
+    "tdmrg_get_stats": [_p, _dp, _i],
+    "tdmrg_reset_stats": [_p],
+    "tdmrg_kernel_heff": [_i, _i, _i, _i, _i, _dp, _p, _p, _p, _p, _p, _p, _p, _i, _p],
+    "tdmrg_kernel_env_left": [_i, _i, _i, _i, _i, _i, _i, _dp, _p, _p, _p, _p, _p, _p, _p],
+    "tdmrg_kernel_gauge_qr": [_i, _i, _p, _i, _p, _p, _p, _p, _p],
+    "tdmrg_kernel_krylov_dense": [_i, _p, _p, _p, _d, _d, _d, _i, _ip, _p],
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load libtdmrg.so (raises OSError if it is missing: build it first)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError("libtdmrg.so not found at %s; run __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    for name, args in _SIGS.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.tdmrg_last_error.argtypes = [_p]
+    lib.tdmrg_last_error.restype = ctypes.c_char_p
+    lib.tdmrg_last_global_error.argtypes = []
+    lib.tdmrg_last_global_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def declared_symbols(header: str) -> list:
+    """Names of the functions declared in include/tdmrg.h."""
+    import re
+    text = open(header).read()
+    return sorted(set(re.findall(r"\b(tdmrg_[a-z0-9_]+)\s*\(", text)))
+
+
+def _check(rc, handle=None):
+    if rc != 0:
+        lib = load()
+        msg = lib.tdmrg_last_error(handle) if handle else lib.tdmrg_last_global_error()
+        raise TdmrgError(rc, (msg or b"").decode())
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+class Model:
+    """One chain (Eq. 1 / Eq. 10) and its TD-DMRG state, living on the current CUDA device."""
+
+    def __init__(self, N, omega, g, nmax, V, peierls=None, precision=PREC_C128, krylov=None,
+                 stream=None):
+        lib = load()
+        om = np.ascontiguousarray(omega, dtype=np.float64)
+        gg = np.ascontiguousarray(g, dtype=np.float64)
+        nm = np.ascontiguousarray(nmax, dtype=np.int32)
+        h = ctypes.c_void_p()
+        _check(lib.tdmrg_model_create(int(N), int(om.size), _dptr(om), _dptr(gg), float(V),
+                                      nm.ctypes.data_as(_ip), ctypes.byref(h)))
+        self._h = h
+        self._lib = lib
+        if peierls is not None:
+            alpha, omega_p, nmax_p = peierls
+            _check(lib.tdmrg_model_set_peierls(h, float(alpha), float(omega_p), int(nmax_p)), h)
+        if precision != PREC_C128:
+            _check(lib.tdmrg_model_set_precision(h, int(precision)), h)
+        if krylov is not None:
+            tol, kmax, fixed = krylov
+            _check(lib.tdmrg_model_set_krylov(h, float(tol), int(kmax), int(fixed)), h)
+        if stream is not None:
+            _check(lib.tdmrg_model_set_stream(h, _stream_ptr(stream)), h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.tdmrg_model_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def thermal_prepare(self, beta, dtau, M):
+        _check(self._lib.tdmrg_thermal_prepare(self._h, float(beta), float(dtau), int(M)), self._h)
+
+    def correlation(self, t_grid, dt):
+        t = np.ascontiguousarray(t_grid, dtype=np.float64)
+        out = np.zeros(2 * t.size)
+        _check(self._lib.tdmrg_correlation(self._h, _dptr(t), int(t.size), float(dt), _dptr(out)),
+               self._h)
+        return out[0::2] + 1j * out[1::2]
+
+    def realtime_init(self):
+        _check(self._lib.tdmrg_realtime_init(self._h), self._h)
+
+    def realtime_step(self, nsteps, dt):
+        _check(self._lib.tdmrg_realtime_step(self._h, int(nsteps), float(dt)), self._h)
+
+    def realtime_observe(self, with_obs=False):
+        c = np.zeros(2)
+        obs = np.zeros(3)
+        _check(self._lib.tdmrg_realtime_observe(self._h, _dptr(c),
+                                                _dptr(obs) if with_obs else None), self._h)
+        return (complex(c[0], c[1]), obs) if with_obs else complex(c[0], c[1])
+
+    def logz(self):
+        v = ctypes.c_double()
+        _check(self._lib.tdmrg_get_logz(self._h, ctypes.byref(v)), self._h)
+        return v.value
+
+    def stats(self):
+        s = np.zeros(8)
+        _check(self._lib.tdmrg_get_stats(self._h, _dptr(s), 8), self._h)
+        keys = ["site_updates", "matvecs", "heff_flops", "krylov_vectors", "bond_matvecs", "qrs",
+                "completions", "env_updates"]
+        return dict(zip(keys, s.tolist()))
+
+    def reset_stats(self):
+        _check(self._lib.tdmrg_reset_stats(self._h), self._h)
+
+
+def mobility(t_grid, C, kT):
+    """Eq. 2 through tdmrg_mobility."""
+    lib = load()
+    t = np.ascontiguousarray(t_grid, dtype=np.float64)
+    c = np.empty(2 * t.size)
+    c[0::2] = np.real(C)
+    c[1::2] = np.imag(C)
+    mu = ctypes.c_double()
+    _check(lib.tdmrg_mobility(_dptr(t), _dptr(c), int(t.size), float(kT), ctypes.byref(mu)))
+    return mu.value
+
+
+# --- kernel-level entry points (device pointers from torch tensors) -------------------------
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def kernel_heff(L, W, R, A, out, X, Y, d, precision=PREC_C128, ws32=None, stream=None):
+    """out = H_eff A for one site; L, R, A, out, X, Y complex128 CUDA tensors, W numpy complex."""
+    lib = load()
+    Dl, Ml, _ = L.shape
+    Dr, Mr, _ = R.shape
+    Wc = np.ascontiguousarray(W, dtype=np.complex128).view(np.float64)
+    _check(lib.tdmrg_kernel_heff(Ml, Mr, d, Dl, Dr, _dptr(Wc), _ptr(L), _ptr(R), _ptr(A),
+                                 _ptr(out), _ptr(X), _ptr(Y), _ptr(ws32), int(precision),
+                                 _stream_ptr(stream)))
+
+
+def kernel_env_left(L, W, bra, ket, Lout, X, Y, d, stream=None):
+    lib = load()
+    Dl = L.shape[0]
+    Dr = Lout.shape[0]
+    Ml1, _, Mr1 = bra.shape
+    Ml2, _, Mr2 = ket.shape
+    Wc = np.ascontiguousarray(W, dtype=np.complex128).view(np.float64)
+    _check(lib.tdmrg_kernel_env_left(Ml1, Mr1, Ml2, Mr2, d, Dl, Dr, _dptr(Wc), _ptr(L),
+                                     _ptr(bra), _ptr(ket), _ptr(Lout), _ptr(X), _ptr(Y),
+                                     _stream_ptr(stream)))
+
+
+def kernel_gauge_qr(Y, Q, R, E=None, status=None, stream=None):
+    lib = load()
+    m, n = Y.shape
+    p = 0 if E is None else E.shape[1]
+    _check(lib.tdmrg_kernel_gauge_qr(m, n, _ptr(Y), p, _ptr(E), _ptr(Q), _ptr(R), _ptr(status),
+                                     _stream_ptr(stream)))
+
+
+def kernel_krylov_dense(H, v, out, tau, tol=1e-13, kmax=32, stream=None):
+    lib = load()
+    k = ctypes.c_int()
+    _check(lib.tdmrg_kernel_krylov_dense(H.shape[0], _ptr(H), _ptr(v), _ptr(out),
+                                         float(np.real(tau)), float(np.imag(tau)), float(tol),
+                                         int(kmax), ctypes.byref(k), _stream_ptr(stream)))
+    return k.value

@@ -1,0 +1,673 @@
+// TDVP engine: device storage, the contraction building blocks and the one-site
+// projector-splitting sweep (imaginary and real time), the variational application of the
+// current MPO and the MPS-MPO-MPS overlap.
+#include "engine.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "../../include/tdmrg.h"
+
+namespace tdmrg {
+
+namespace {
+constexpr long long NOSPLIT = 1LL << 60;
+const cplx ONE = {1.0, 0.0};
+const cplx ZERO = {0.0, 0.0};
+
+MatRef mref(const cplx* p, long long rs, long long cs, long long sb = 0, long long sr = 0,
+            int conj = 0) {
+  MatRef r;
+  r.p = p;
+  r.rs = rs;
+  r.cs = cs;
+  r.sb = sb;
+  r.sr = sr;
+  r.conj = conj;
+  return r;
+}
+QrRef qref(const cplx* p, long long rs, long long cs, long long cb, long long cbs, int conj) {
+  QrRef r;
+  r.p = p;
+  r.rs = rs;
+  r.cs = cs;
+  r.cb = cb;
+  r.cbs = cbs;
+  r.conj = conj;
+  return r;
+}
+}  // namespace
+
+void throw_cuda(cudaError_t e, const char* what, int line) {
+  const int code = (e == cudaErrorMemoryAllocation) ? TDMRG_ERR_OOM : TDMRG_ERR_CUDA;
+  throw Failure{code, std::string(cudaGetErrorString(e)) + " in " + what + " (engine.cu:" +
+                          std::to_string(line) + ")"};
+}
+
+// ------------------------------------------------------------------------------------
+// contraction building blocks
+// ------------------------------------------------------------------------------------
+void heff_f64(const Ctx& c, const DevMpoSite& W, int Ml, int Mr, int D, int d, const cplx* Lenv,
+              const cplx* Renv, const cplx* in, cplx* out, const int* skip) {
+  const long long per = (long long)Ml * D * Mr;
+  // X[(w,a)][(s,c)] = sum_y L[w,a,y] in[y,(s,c)]
+  CK(zgemm(W.Dl * Ml, D * Mr, Ml, 1, 1, ONE, mref(Lenv, Ml, 1), mref(in, (long long)D * Mr, 1),
+           ZERO, c.X, (long long)D * Mr, 0, skip, c.st));
+  // Y[v][a][s][t][c] = sum_{w,u} W[w,v,s,u] X[w][a][u][t][c]
+  CK(mpo_mix(W.lr, Ml, d, Mr, c.X, per, c.Y, per, skip, c.st));
+  // out[(a,s)][b] = sum_{v,c} Y[v][(a,s)][c] R[v][b][c]
+  CK(zgemm(Ml * D, Mr, Mr, 1, W.Dr, ONE, mref(c.Y, Mr, 1, 0, per),
+           mref(Renv, 1, Mr, 0, (long long)Mr * Mr), ZERO, out, Mr, 0, skip, c.st));
+}
+
+void left_partial_f64(const Ctx& c, const DevMpoSite& W, int Ml1, int Ml2, int D, int d, int Mr2,
+                      const cplx* Lenv, const cplx* ket, cplx* Y, const int* skip) {
+  const long long per = (long long)Ml1 * D * Mr2;
+  CK(zgemm(W.Dl * Ml1, D * Mr2, Ml2, 1, 1, ONE, mref(Lenv, Ml2, 1),
+           mref(ket, (long long)D * Mr2, 1), ZERO, c.X, (long long)D * Mr2, 0, skip, c.st));
+  CK(mpo_mix(W.lr, Ml1, d, Mr2, c.X, per, Y, per, skip, c.st));
+}
+
+void right_partial_f64(const Ctx& c, const DevMpoSite& W, int Ml2, int D, int d, int Mr1, int Mr2,
+                       const cplx* Renv, const cplx* ket, cplx* Y, const int* skip) {
+  const long long per = (long long)Ml2 * D * Mr1;
+  // X[v][(y,s)][b] = sum_c ket[(y,s)][c] R[v][b][c]
+  CK(zgemm(Ml2 * D, Mr1, Mr2, W.Dr, 1, ONE, mref(ket, Mr2, 1),
+           mref(Renv, 1, Mr2, (long long)Mr1 * Mr2), ZERO, c.X, Mr1, per, skip, c.st));
+  CK(mpo_mix(W.rl, Ml2, d, Mr1, c.X, per, Y, per, skip, c.st));
+}
+
+void env_left_f64(const Ctx& c, const DevMpoSite& W, int Ml1, int Mr1, int Ml2, int Mr2, int D,
+                  int d, const cplx* Lenv, const cplx* bra, const cplx* ket, cplx* Lout) {
+  left_partial_f64(c, W, Ml1, Ml2, D, d, Mr2, Lenv, ket, c.Y, nullptr);
+  const long long per = (long long)Ml1 * D * Mr2;
+  // Lout[v][b][c] = sum_{(a,s)} conj(bra[(a,s)][b]) Y[v][(a,s)][c]
+  CK(zgemm(Mr1, Mr2, Ml1 * D, W.Dr, 1, ONE, mref(bra, 1, Mr1, 0, 0, 1), mref(c.Y, Mr2, 1, per),
+           ZERO, Lout, Mr2, (long long)Mr1 * Mr2, nullptr, c.st));
+}
+
+void env_right_f64(const Ctx& c, const DevMpoSite& W, int Ml1, int Mr1, int Ml2, int Mr2, int D,
+                   int d, const cplx* Renv, const cplx* bra, const cplx* ket, cplx* Rout) {
+  right_partial_f64(c, W, Ml2, D, d, Mr1, Mr2, Renv, ket, c.Y, nullptr);
+  const long long per = (long long)Ml2 * D * Mr1;
+  // Rout[w][a][y] = sum_{(s,b)} conj(bra[a][(s,b)]) Y[w][y][(s,b)]
+  CK(zgemm(Ml1, Ml2, D * Mr1, W.Dl, 1, ONE, mref(bra, (long long)D * Mr1, 1, 0, 0, 1),
+           mref(c.Y, 1, (long long)D * Mr1, per), ZERO, Rout, Ml2, (long long)Ml1 * Ml2,
+           nullptr, c.st));
+}
+
+void bond_f64(const Ctx& c, int M, int Dw, const cplx* Lenv, const cplx* Renv, const cplx* in,
+              cplx* out, const int* skip) {
+  const long long mm = (long long)M * M;
+  CK(zgemm(Dw * M, M, M, 1, 1, ONE, mref(Lenv, M, 1), mref(in, M, 1), ZERO, c.X, M, 0, skip,
+           c.st));
+  CK(zgemm(M, M, M, 1, Dw, ONE, mref(c.X, M, 1, 0, mm), mref(Renv, 1, M, 0, mm), ZERO, out, M,
+           0, skip, c.st));
+}
+
+// ------------------------------------------------------------------------------------
+// MPO upload
+// ------------------------------------------------------------------------------------
+void Engine::upload_mpo(const std::vector<MpoSite>& W, DevMpo& out) {
+  free_mpo(out);
+  out.s.resize(W.size());
+  out.maxD = 1;
+  for (size_t k = 0; k < W.size(); ++k) {
+    const MpoSite& h = W[k];
+    DevMpoSite& s = out.s[k];
+    s.Dl = h.Dl;
+    s.Dr = h.Dr;
+    s.d = h.d;
+    s.nblk = (int)h.blocks.size();
+    s.host = h.blocks;
+    out.maxD = std::max(out.maxD, std::max(h.Dl, h.Dr));
+    const int nb = s.nblk, d = h.d;
+    // host staging: lr tables then rl tables
+    std::vector<int> ilr_start(h.Dr + 1, 0), ilr_chan(nb), irl_start(h.Dl + 1, 0), irl_chan(nb);
+    std::vector<cplx> olr((size_t)nb * d * d), orl((size_t)nb * d * d);
+    {
+      int pos = 0;
+      for (int wo = 0; wo < h.Dr; ++wo) {
+        ilr_start[wo] = pos;
+        for (const auto& b : h.blocks)
+          if (b.wr == wo) {
+            ilr_chan[pos] = b.wl;
+            for (int e = 0; e < d * d; ++e) olr[(size_t)pos * d * d + e] = {b.op[e].real(), b.op[e].imag()};
+            ++pos;
+          }
+      }
+      ilr_start[h.Dr] = pos;
+      pos = 0;
+      for (int wo = 0; wo < h.Dl; ++wo) {
+        irl_start[wo] = pos;
+        for (const auto& b : h.blocks)
+          if (b.wl == wo) {
+            irl_chan[pos] = b.wr;
+            for (int e = 0; e < d * d; ++e) orl[(size_t)pos * d * d + e] = {b.op[e].real(), b.op[e].imag()};
+            ++pos;
+          }
+      }
+      irl_start[h.Dl] = pos;
+    }
+    const size_t ops_bytes = sizeof(cplx) * (size_t)nb * d * d;
+    const size_t int_bytes = sizeof(int) * (size_t)(h.Dr + 1 + nb + h.Dl + 1 + nb);
+    const size_t total = 2 * ops_bytes + int_bytes + 64;
+    char* mem = nullptr;
+    CK(cudaMalloc(&mem, total));
+    s.mem = mem;
+    cplx* d_olr = reinterpret_cast<cplx*>(mem);
+    cplx* d_orl = d_olr + (size_t)nb * d * d;
+    int* ip = reinterpret_cast<int*>(d_orl + (size_t)nb * d * d);
+    int* d_lrs = ip;
+    int* d_lrc = d_lrs + h.Dr + 1;
+    int* d_rls = d_lrc + nb;
+    int* d_rlc = d_rls + h.Dl + 1;
+    if (nb > 0) {
+      CK(cudaMemcpy(d_olr, olr.data(), ops_bytes, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(d_orl, orl.data(), ops_bytes, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(d_lrc, ilr_chan.data(), sizeof(int) * nb, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(d_rlc, irl_chan.data(), sizeof(int) * nb, cudaMemcpyHostToDevice));
+    }
+    CK(cudaMemcpy(d_lrs, ilr_start.data(), sizeof(int) * (h.Dr + 1), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_rls, irl_start.data(), sizeof(int) * (h.Dl + 1), cudaMemcpyHostToDevice));
+    s.lr = MixTable{h.Dr, d_lrs, d_lrc, d_olr};
+    s.rl = MixTable{h.Dl, d_rls, d_rlc, d_orl};
+  }
+}
+
+void Engine::free_mpo(DevMpo& m) {
+  for (auto& s : m.s)
+    if (s.mem) cudaFree(s.mem);
+  m.s.clear();
+}
+
+// ------------------------------------------------------------------------------------
+// construction / workspace
+// ------------------------------------------------------------------------------------
+Engine::Engine(const ModelParams& p) : P(p) {
+  sites_ = chain_sites(P);
+  rebuild_mpos();
+  CK(cudaMalloc(&status_, sizeof(int) * 4));
+  CK(cudaMemset(status_, 0, sizeof(int) * 4));
+  CK(cudaMalloc(&lz_, sizeof(LzState)));
+  CK(cudaMalloc(&scal_, sizeof(double) * 8));
+  CK(cudaMalloc(&part_c_, sizeof(cplx) * (KMAX + 1) * NBLK));
+  CK(cudaMalloc(&part_d_, sizeof(double) * NBLK));
+  CK(cudaMallocHost(&h_pinned_, sizeof(int) * 4));
+  CK(cudaMallocHost(&h_pinned_d_, sizeof(double) * 4));
+}
+
+Engine::~Engine() {
+  free_mps(psi_b_);
+  free_mps(psi1_);
+  free_mps(psi2_);
+  free_mpo(H_);
+  free_mpo(J_);
+  free_mpo(I_);
+  cplx* bufs[] = {X_, Y_, V_, Kout_, T1_, Cb_, Rb_, Ex_, env_tmp_[0], env_tmp_[1], part_c_};
+  for (cplx* b : bufs)
+    if (b) cudaFree(b);
+  if (part_d_) cudaFree(part_d_);
+  if (scal_) cudaFree(scal_);
+  if (lz_) cudaFree(lz_);
+  if (status_) cudaFree(status_);
+  if (qr_.part) cudaFree(qr_.part);
+  if (qr_.partn) cudaFree(qr_.partn);
+  if (qr_.bar) cudaFree(qr_.bar);
+  if (h_pinned_) cudaFreeHost(h_pinned_);
+  if (h_pinned_d_) cudaFreeHost(h_pinned_d_);
+}
+
+void Engine::rebuild_mpos() {
+  sites_ = chain_sites(P);
+  upload_mpo(hamiltonian_mpo(P), H_);
+  upload_mpo(current_mpo(P), J_);
+  upload_mpo(identity_mpo(P), I_);
+  prepared_ = false;
+  rt_ready_ = false;
+}
+
+void Engine::set_precision(int p) {
+  if (p != TDMRG_PREC_C128) throw Failure{TDMRG_ERR_ARG, "precision not available in this build"};
+  precision_ = p;
+}
+
+void Engine::set_krylov(double tol, int kmax, int fixed_k) {
+  if (!(tol > 0.0) || kmax < 1 || kmax > KMAX || fixed_k < 0 || fixed_k > KMAX)
+    throw Failure{TDMRG_ERR_ARG, "krylov: need tol > 0, 1 <= kmax <= 32, 0 <= fixed_k <= 32"};
+  ktol_ = tol;
+  kmax_ = kmax;
+  fixed_k_ = fixed_k;
+}
+
+void Engine::ensure_workspace(long long maxsite, long long maxxy, int maxbond, int maxm) {
+  if (maxsite > ws_site_) {
+    for (cplx** b : {&V_, &Kout_, &T1_}) {
+      if (*b) cudaFree(*b);
+      *b = nullptr;
+    }
+    CK(cudaMalloc(&V_, sizeof(cplx) * (size_t)(KMAX + 1) * maxsite));
+    CK(cudaMalloc(&Kout_, sizeof(cplx) * (size_t)maxsite));
+    CK(cudaMalloc(&T1_, sizeof(cplx) * (size_t)maxsite));
+    ws_site_ = maxsite;
+  }
+  if (maxxy > ws_xy_) {
+    for (cplx** b : {&X_, &Y_}) {
+      if (*b) cudaFree(*b);
+      *b = nullptr;
+    }
+    CK(cudaMalloc(&X_, sizeof(cplx) * (size_t)maxxy));
+    CK(cudaMalloc(&Y_, sizeof(cplx) * (size_t)maxxy));
+    ws_xy_ = maxxy;
+  }
+  if (maxbond > ws_bond_) {
+    for (cplx** b : {&Cb_, &Rb_}) {
+      if (*b) cudaFree(*b);
+      *b = nullptr;
+    }
+    CK(cudaMalloc(&Cb_, sizeof(cplx) * (size_t)maxbond * maxbond));
+    CK(cudaMalloc(&Rb_, sizeof(cplx) * (size_t)maxbond * maxbond));
+    ws_bond_ = maxbond;
+  }
+  if (maxm > ws_m_) {
+    if (qr_.part) cudaFree(qr_.part);
+    if (qr_.partn) cudaFree(qr_.partn);
+    if (qr_.bar) cudaFree(qr_.bar);
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    qr_.gmax = sms;
+    qr_.nmax = maxm;
+    CK(cudaMalloc(&qr_.part, sizeof(cplx) * 2 * (size_t)sms * maxm));
+    CK(cudaMalloc(&qr_.partn, sizeof(double) * 2 * (size_t)sms));
+    CK(cudaMalloc(&qr_.bar, sizeof(unsigned) * 2));
+    ws_m_ = maxm;
+  }
+}
+
+long long Engine::env_size(const DevMps& s, int k, int Dw, bool left) const {
+  const long long M = left ? s.Mb[k] : s.Mb[k + 1];
+  return (long long)Dw * M * M;
+}
+
+void Engine::alloc_mps(DevMps& s, int M) {
+  free_mps(s);
+  const int L = (int)sites_.size();
+  s.Mb = bond_dimensions(sites_, M);
+  s.D.resize(L);
+  s.d.resize(L);
+  s.A.assign(L, nullptr);
+  s.Lenv.assign(L, nullptr);
+  s.Renv.assign(L, nullptr);
+  for (int k = 0; k < L; ++k) {
+    s.d[k] = sites_[k].d;
+    s.D[k] = sites_[k].d * sites_[k].d;
+    CK(cudaMalloc(&s.A[k], sizeof(cplx) * (size_t)s.size(k)));
+    CK(cudaMalloc(&s.Lenv[k], sizeof(cplx) * (size_t)env_size(s, k, H_.s[k].Dl, true)));
+    CK(cudaMalloc(&s.Renv[k], sizeof(cplx) * (size_t)env_size(s, k, H_.s[k].Dr, false)));
+  }
+  long long maxsite = 1, maxxy = 1, maxenv = 1;
+  int maxbond = 1;
+  const int Dmax = std::max(H_.maxD, J_.maxD);
+  for (int k = 0; k < L; ++k) {
+    maxsite = std::max(maxsite, s.size(k));
+    maxxy = std::max(maxxy, (long long)Dmax * s.size(k));
+    maxbond = std::max(maxbond, s.Mb[k + 1]);
+    maxenv = std::max(maxenv, env_size(s, k, Dmax, true));
+    maxenv = std::max(maxenv, env_size(s, k, Dmax, false));
+  }
+  maxxy = std::max(maxxy, (long long)Dmax * maxbond * maxbond);
+  ensure_workspace(maxsite, maxxy, maxbond, maxbond);
+  if (maxenv > env_tmp_size_) {
+    for (int i = 0; i < 2; ++i) {
+      if (env_tmp_[i]) cudaFree(env_tmp_[i]);
+      CK(cudaMalloc(&env_tmp_[i], sizeof(cplx) * (size_t)maxenv));
+    }
+    env_tmp_size_ = maxenv;
+  }
+}
+
+void Engine::free_mps(DevMps& s) {
+  for (auto* p : s.A)
+    if (p) cudaFree(p);
+  for (auto* p : s.Lenv)
+    if (p) cudaFree(p);
+  for (auto* p : s.Renv)
+    if (p) cudaFree(p);
+  s.A.clear();
+  s.Lenv.clear();
+  s.Renv.clear();
+}
+
+void Engine::copy_mps(const DevMps& src, DevMps& dst) {
+  if (dst.A.size() != src.A.size() || dst.Mb != src.Mb) {
+    free_mps(dst);
+    dst.Mb = src.Mb;
+    dst.D = src.D;
+    dst.d = src.d;
+    const int L = src.L();
+    dst.A.assign(L, nullptr);
+    dst.Lenv.assign(L, nullptr);
+    dst.Renv.assign(L, nullptr);
+    for (int k = 0; k < L; ++k) {
+      CK(cudaMalloc(&dst.A[k], sizeof(cplx) * (size_t)src.size(k)));
+      CK(cudaMalloc(&dst.Lenv[k], sizeof(cplx) * (size_t)env_size(src, k, H_.s[k].Dl, true)));
+      CK(cudaMalloc(&dst.Renv[k], sizeof(cplx) * (size_t)env_size(src, k, H_.s[k].Dr, false)));
+    }
+  }
+  for (int k = 0; k < src.L(); ++k)
+    CK(cudaMemcpyAsync(dst.A[k], src.A[k], sizeof(cplx) * (size_t)src.size(k),
+                       cudaMemcpyDeviceToDevice, st_));
+}
+
+void Engine::set_ones(cplx* p) {
+  static const cplx one = {1.0, 0.0};
+  CK(cudaMemcpyAsync(p, &one, sizeof(cplx), cudaMemcpyHostToDevice, st_));
+}
+
+// ------------------------------------------------------------------------------------
+// numerics helpers
+// ------------------------------------------------------------------------------------
+double Engine::norm2_dev(const cplx* x, long long n) {
+  CK(znorm2(n, x, scal_, part_d_, NBLK, nullptr, st_));
+  CK(cudaMemcpyAsync(h_pinned_d_, scal_, sizeof(double), cudaMemcpyDeviceToHost, st_));
+  CK(cudaStreamSynchronize(st_));
+  return h_pinned_d_[0];
+}
+
+void Engine::scale_dev(cplx* x, long long n, double f) {
+  h_pinned_d_[1] = f;
+  CK(cudaMemcpyAsync(scal_ + 1, h_pinned_d_ + 1, sizeof(double), cudaMemcpyHostToDevice, st_));
+  CK(zscale_by(n, x, scal_ + 1, nullptr, st_));
+  CK(cudaStreamSynchronize(st_));
+}
+
+void Engine::check_status() {
+  CK(cudaMemcpyAsync(h_pinned_ + 1, status_, sizeof(int), cudaMemcpyDeviceToHost, st_));
+  CK(cudaStreamSynchronize(st_));
+  if (h_pinned_[1] == 1) throw Failure{TDMRG_ERR_TIMEOUT, "gauge QR grid barrier timed out"};
+  if (h_pinned_[1] == 2) throw Failure{TDMRG_ERR_CUDA, "gauge QR ran out of completion vectors"};
+}
+
+void Engine::gauge_qr_dev(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cplx* R) {
+  CK(gauge_qr(m, n, Y, p, E, Q, R, qr_, status_, st_));
+  stats.qrs += 1;
+}
+
+void Engine::absorb_left(const cplx* C, int M, cplx* A, long long ncols) {
+  CK(zgemm(M, (int)ncols, M, 1, 1, ONE, mref(C, M, 1), mref(A, ncols, 1), ZERO, T1_, ncols, 0,
+           nullptr, st_));
+  CK(cudaMemcpyAsync(A, T1_, sizeof(cplx) * (size_t)M * ncols, cudaMemcpyDeviceToDevice, st_));
+}
+
+void Engine::absorb_right(cplx* A, long long nrows, const cplx* C, int M) {
+  CK(zgemm((int)nrows, M, M, 1, 1, ONE, mref(A, M, 1), mref(C, M, 1), ZERO, T1_, M, 0, nullptr,
+           st_));
+  CK(cudaMemcpyAsync(A, T1_, sizeof(cplx) * (size_t)M * nrows, cudaMemcpyDeviceToDevice, st_));
+}
+
+// ------------------------------------------------------------------------------------
+// gauge shifts
+// ------------------------------------------------------------------------------------
+// center (Ml*D x Mr) = Q Cbond; Q -> A_k; L_{k+1} updated.  Completion candidates are the
+// columns of the left part of H_eff applied to the center.
+void Engine::shift_right(DevMps& s, int k, const cplx* center, cplx* Cbond) {
+  const DevMpoSite& W = H_.s[k];
+  const int Ml = s.Mb[k], Mr = s.Mb[k + 1], D = s.D[k], d = s.d[k];
+  left_partial_f64(ctx(), W, Ml, Ml, D, d, Mr, s.Lenv[k], center, Y_, nullptr);
+  gauge_qr_dev(Ml * D, Mr, qref(center, Mr, 1, NOSPLIT, 0, 0), W.Dr * Mr,
+               qref(Y_, Mr, 1, Mr, (long long)Ml * D * Mr, 0), s.A[k], Cbond);
+  env_left_f64(ctx(), W, Ml, Mr, Ml, Mr, D, d, s.Lenv[k], s.A[k], s.A[k], s.Lenv[k + 1]);
+  stats.env_updates += 1;
+}
+
+// center (Ml x D*Mr) = Cbond Q; Q -> A_k; R_{k-1} updated.  Works on Y = center^H.
+void Engine::shift_left(DevMps& s, int k, const cplx* center, cplx* Cbond) {
+  const DevMpoSite& W = H_.s[k];
+  const int Ml = s.Mb[k], Mr = s.Mb[k + 1], D = s.D[k], d = s.d[k];
+  right_partial_f64(ctx(), W, Ml, D, d, Mr, Mr, s.Renv[k], center, Y_, nullptr);
+  gauge_qr_dev(D * Mr, Ml, qref(center, 1, (long long)D * Mr, NOSPLIT, 0, 1), W.Dl * Ml,
+               qref(Y_, 1, (long long)D * Mr, NOSPLIT, 0, 1), T1_, Rb_);
+  CK(ztranspose(D * Mr, Ml, T1_, s.A[k], 1, st_));
+  CK(ztranspose(Ml, Ml, Rb_, Cbond, 1, st_));
+  env_right_f64(ctx(), W, Ml, Mr, Ml, Mr, D, d, s.Renv[k], s.A[k], s.A[k], s.Renv[k - 1]);
+  stats.env_updates += 1;
+}
+
+void Engine::right_canonicalize(DevMps& s) {
+  const int L = s.L();
+  set_ones(s.Lenv[0]);
+  set_ones(s.Renv[L - 1]);
+  for (int k = L - 1; k > 0; --k) {
+    shift_left(s, k, s.A[k], Cb_);
+    absorb_right(s.A[k - 1], (long long)s.Mb[k - 1] * s.D[k - 1], Cb_, s.Mb[k]);
+  }
+}
+
+void Engine::build_right_envs(DevMps& s) {
+  const int L = s.L();
+  set_ones(s.Lenv[0]);
+  set_ones(s.Renv[L - 1]);
+  for (int k = L - 1; k > 0; --k) {
+    const int Ml = s.Mb[k], Mr = s.Mb[k + 1];
+    env_right_f64(ctx(), H_.s[k], Ml, Mr, Ml, Mr, s.D[k], s.d[k], s.Renv[k], s.A[k], s.A[k],
+                  s.Renv[k - 1]);
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// the projector-splitting step
+// ------------------------------------------------------------------------------------
+void Engine::site_update(DevMps& s, int k, double hr, double hi) {
+  const DevMpoSite& W = H_.s[k];
+  const int Ml = s.Mb[k], Mr = s.Mb[k + 1], D = s.D[k], d = s.d[k];
+  const double flops = 8.0 * W.Dl * Ml * (double)Ml * D * Mr + 8.0 * W.Dr * Ml * (double)D * Mr * Mr;
+  const cplx* Le = s.Lenv[k];
+  const cplx* Re = s.Renv[k];
+  Ctx c = ctx();
+  krylov(s.size(k), s.A[k], Kout_, hr, hi, [&](const cplx* in, cplx* out, const int* skip) {
+    heff_f64(c, W, Ml, Mr, D, d, Le, Re, in, out, skip);
+    stats.matvecs += 1;
+    stats.heff_flops += flops;
+  });
+  stats.site_updates += 1;
+}
+
+void Engine::tdvp_step(DevMps& s, double tr, double ti) {
+  const double hr = 0.5 * tr, hi = 0.5 * ti;
+  const int L = s.L();
+  Ctx c = ctx();
+  for (int k = 0; k < L; ++k) {
+    site_update(s, k, hr, hi);
+    if (k < L - 1) {
+      shift_right(s, k, Kout_, Cb_);
+      const int M = s.Mb[k + 1], Dw = H_.s[k].Dr;
+      const cplx* Le = s.Lenv[k + 1];
+      const cplx* Re = s.Renv[k];
+      krylov((long long)M * M, Cb_, Rb_, -hr, -hi, [&](const cplx* in, cplx* out, const int* sk) {
+        bond_f64(c, M, Dw, Le, Re, in, out, sk);
+        stats.bond_matvecs += 1;
+      });
+      absorb_left(Rb_, M, s.A[k + 1], (long long)s.D[k + 1] * s.Mb[k + 2]);
+    } else {
+      CK(cudaMemcpyAsync(s.A[k], Kout_, sizeof(cplx) * (size_t)s.size(k),
+                         cudaMemcpyDeviceToDevice, st_));
+    }
+  }
+  for (int k = L - 1; k >= 0; --k) {
+    site_update(s, k, hr, hi);
+    if (k > 0) {
+      shift_left(s, k, Kout_, Cb_);
+      const int M = s.Mb[k], Dw = H_.s[k].Dl;
+      const cplx* Le = s.Lenv[k];
+      const cplx* Re = s.Renv[k - 1];
+      krylov((long long)M * M, Cb_, Rb_, -hr, -hi, [&](const cplx* in, cplx* out, const int* sk) {
+        bond_f64(c, M, Dw, Le, Re, in, out, sk);
+        stats.bond_matvecs += 1;
+      });
+      absorb_right(s.A[k - 1], (long long)s.Mb[k - 1] * s.D[k - 1], Rb_, M);
+    } else {
+      CK(cudaMemcpyAsync(s.A[k], Kout_, sizeof(cplx) * (size_t)s.size(k),
+                         cudaMemcpyDeviceToDevice, st_));
+    }
+  }
+  check_status();
+}
+
+// ------------------------------------------------------------------------------------
+// observables and the application of j
+// ------------------------------------------------------------------------------------
+Cx Engine::overlap(const DevMps& bra, const DevMpo& W, const DevMps& ket) {
+  const int L = bra.L();
+  int cur = 0;
+  set_ones(env_tmp_[0]);
+  for (int k = 0; k < L; ++k) {
+    env_left_f64(ctx(), W.s[k], bra.Mb[k], bra.Mb[k + 1], ket.Mb[k], ket.Mb[k + 1], bra.D[k],
+                 bra.d[k], env_tmp_[cur], bra.A[k], ket.A[k], env_tmp_[cur ^ 1]);
+    cur ^= 1;
+  }
+  cplx r;
+  CK(cudaMemcpyAsync(&r, env_tmp_[cur], sizeof(cplx), cudaMemcpyDeviceToHost, st_));
+  CK(cudaStreamSynchronize(st_));
+  return Cx(r.x, r.y);
+}
+
+// phi ~ W|psi> at psi's bond dimensions by one-site variational fitting; psi has its center
+// at site 0 and right-orthonormal sites 1..L-1; phi starts as a copy of psi.
+void Engine::fit_apply(const DevMpo& W, const DevMps& psi, DevMps& phi, int sweeps) {
+  copy_mps(psi, phi);
+  const int L = psi.L();
+  std::vector<cplx*> Lf(L, nullptr), Rf(L, nullptr);
+  struct Guard {
+    std::vector<cplx*>& a;
+    std::vector<cplx*>& b;
+    ~Guard() {
+      for (auto* p : a)
+        if (p) cudaFree(p);
+      for (auto* p : b)
+        if (p) cudaFree(p);
+    }
+  } guard{Lf, Rf};
+  for (int k = 0; k < L; ++k) {
+    CK(cudaMalloc(&Lf[k], sizeof(cplx) * (size_t)env_size(psi, k, W.s[k].Dl, true)));
+    CK(cudaMalloc(&Rf[k], sizeof(cplx) * (size_t)env_size(psi, k, W.s[k].Dr, false)));
+  }
+  set_ones(Lf[0]);
+  set_ones(Rf[L - 1]);
+  Ctx c = ctx();
+  for (int k = L - 1; k > 0; --k) {
+    const int Ml = psi.Mb[k], Mr = psi.Mb[k + 1];
+    env_right_f64(c, W.s[k], Ml, Mr, Ml, Mr, psi.D[k], psi.d[k], Rf[k], phi.A[k], psi.A[k],
+                  Rf[k - 1]);
+  }
+  for (int sw = 0; sw < sweeps; ++sw) {
+    for (int k = 0; k < L; ++k) {
+      const int Ml = psi.Mb[k], Mr = psi.Mb[k + 1], D = psi.D[k], d = psi.d[k];
+      heff_f64(c, W.s[k], Ml, Mr, D, d, Lf[k], Rf[k], psi.A[k], Kout_, nullptr);
+      if (k < L - 1) {
+        left_partial_f64(c, W.s[k], Ml, Ml, D, d, Mr, Lf[k], psi.A[k], Y_, nullptr);
+        gauge_qr_dev(Ml * D, Mr, qref(Kout_, Mr, 1, NOSPLIT, 0, 0), W.s[k].Dr * Mr,
+                     qref(Y_, Mr, 1, Mr, (long long)Ml * D * Mr, 0), phi.A[k], Rb_);
+        env_left_f64(c, W.s[k], Ml, Mr, Ml, Mr, D, d, Lf[k], phi.A[k], psi.A[k], Lf[k + 1]);
+      } else {
+        CK(cudaMemcpyAsync(phi.A[k], Kout_, sizeof(cplx) * (size_t)psi.size(k),
+                           cudaMemcpyDeviceToDevice, st_));
+      }
+    }
+    for (int k = L - 1; k >= 0; --k) {
+      const int Ml = psi.Mb[k], Mr = psi.Mb[k + 1], D = psi.D[k], d = psi.d[k];
+      heff_f64(c, W.s[k], Ml, Mr, D, d, Lf[k], Rf[k], psi.A[k], Kout_, nullptr);
+      if (k > 0) {
+        right_partial_f64(c, W.s[k], Ml, D, d, Mr, Mr, Rf[k], psi.A[k], Y_, nullptr);
+        gauge_qr_dev(D * Mr, Ml, qref(Kout_, 1, (long long)D * Mr, NOSPLIT, 0, 1),
+                     W.s[k].Dl * Ml, qref(Y_, 1, (long long)D * Mr, NOSPLIT, 0, 1), T1_, Rb_);
+        CK(ztranspose(D * Mr, Ml, T1_, phi.A[k], 1, st_));
+        env_right_f64(c, W.s[k], Ml, Mr, Ml, Mr, D, d, Rf[k], phi.A[k], psi.A[k], Rf[k - 1]);
+      } else {
+        CK(cudaMemcpyAsync(phi.A[k], Kout_, sizeof(cplx) * (size_t)psi.size(k),
+                           cudaMemcpyDeviceToDevice, st_));
+      }
+    }
+  }
+  check_status();
+}
+
+// ------------------------------------------------------------------------------------
+// public flow
+// ------------------------------------------------------------------------------------
+void Engine::thermal_prepare(double beta, double dtau, int M) {
+  if (!(beta > 0.0) || !(dtau > 0.0) || M < 2)
+    throw Failure{TDMRG_ERR_ARG, "thermal_prepare: need beta > 0, dtau > 0, M >= 2"};
+  const double nsf = beta / (2.0 * dtau);
+  const long long nsteps = std::llround(nsf);
+  if (std::fabs(nsteps * 2.0 * dtau - beta) > 1e-9 * std::max(1.0, beta) || nsteps < 1)
+    throw Failure{TDMRG_ERR_ARG, "thermal_prepare: beta must be an even multiple of dtau"};
+  prepared_ = false;
+  rt_ready_ = false;
+  CK(cudaMemsetAsync(status_, 0, sizeof(int), st_));
+  alloc_mps(psi_b_, M);
+  // |I> on the one-carrier sector
+  const auto ent = identity_state_entries(P);
+  int* d_ent = nullptr;
+  size_t maxe = 0;
+  for (auto& e : ent) maxe = std::max(maxe, e.size());
+  CK(cudaMalloc(&d_ent, sizeof(int) * std::max<size_t>(maxe, 1)));
+  for (int k = 0; k < psi_b_.L(); ++k) {
+    CK(cudaMemcpy(d_ent, ent[k].data(), sizeof(int) * ent[k].size(), cudaMemcpyHostToDevice));
+    CK(zfill_identity_mps(psi_b_.A[k], psi_b_.Mb[k], psi_b_.D[k], psi_b_.Mb[k + 1], d_ent,
+                          (int)ent[k].size() / 3, st_));
+    CK(cudaStreamSynchronize(st_));
+  }
+  cudaFree(d_ent);
+  right_canonicalize(psi_b_);
+  check_status();
+  double n2 = norm2_dev(psi_b_.A[0], psi_b_.size(0));
+  logZ_ = std::log(n2);
+  scale_dev(psi_b_.A[0], psi_b_.size(0), 1.0 / std::sqrt(n2));
+  for (long long i = 0; i < nsteps; ++i) {
+    tdvp_step(psi_b_, -dtau, 0.0);
+    n2 = norm2_dev(psi_b_.A[0], psi_b_.size(0));
+    if (!std::isfinite(n2) || n2 <= 0.0)
+      throw Failure{TDMRG_ERR_NONFINITE, "non-finite norm in imaginary-time step"};
+    logZ_ += std::log(n2);
+    scale_dev(psi_b_.A[0], psi_b_.size(0), 1.0 / std::sqrt(n2));
+  }
+  prepared_ = true;
+}
+
+void Engine::realtime_init() {
+  if (!prepared_) throw Failure{TDMRG_ERR_STATE, "realtime_init before thermal_prepare"};
+  copy_mps(psi_b_, psi1_);
+  build_right_envs(psi1_);
+  fit_apply(J_, psi_b_, psi2_, 2);
+  build_right_envs(psi2_);
+  CK(cudaStreamSynchronize(st_));
+  rt_ready_ = true;
+}
+
+void Engine::realtime_step(int nsteps, double dt) {
+  if (!rt_ready_) throw Failure{TDMRG_ERR_STATE, "realtime_step before realtime_init"};
+  if (nsteps < 0 || !(dt > 0.0)) throw Failure{TDMRG_ERR_ARG, "realtime_step: need dt > 0"};
+  for (int i = 0; i < nsteps; ++i) {
+    tdvp_step(psi1_, 0.0, -dt);
+    tdvp_step(psi2_, 0.0, -dt);
+  }
+}
+
+void Engine::realtime_observe(double* C, double* obs) {
+  if (!rt_ready_) throw Failure{TDMRG_ERR_STATE, "realtime_observe before realtime_init"};
+  const Cx c = overlap(psi1_, J_, psi2_);
+  if (!std::isfinite(c.real()) || !std::isfinite(c.imag()))
+    throw Failure{TDMRG_ERR_NONFINITE, "non-finite C(t)"};
+  C[0] = c.real();
+  C[1] = c.imag();
+  if (obs) {
+    obs[0] = overlap(psi1_, I_, psi1_).real();
+    obs[1] = overlap(psi2_, I_, psi2_).real();
+    obs[2] = overlap(psi1_, H_, psi1_).real();
+  }
+}
+
+}  // namespace tdmrg

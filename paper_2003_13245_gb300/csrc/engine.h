@@ -1,0 +1,190 @@
+// TDVP engine: device MPS/MPO storage and the one-site projector-splitting sweep.
+#pragma once
+#include <string>
+#include <vector>
+
+#include "model.h"
+#include "tdmrg_internal.cuh"
+
+namespace tdmrg {
+
+constexpr int NBLK = 1024;   // partial-sum blocks of the two-stage reductions
+
+struct Failure {
+  int code;
+  std::string msg;
+};
+
+// device copy of one site of an MPO: mixing tables for both contraction directions
+struct DevMpoSite {
+  int Dl = 0, Dr = 0, d = 0, nblk = 0;
+  MixTable lr{}, rl{};               // lr: in = wl, out = wr;  rl: in = wr, out = wl
+  void* mem = nullptr;               // one allocation holding all tables
+  std::vector<MpoBlock> host;
+};
+
+struct DevMpo {
+  std::vector<DevMpoSite> s;
+  int maxD = 1;
+};
+
+struct DevMps {
+  std::vector<int> Mb;               // bond dims, L + 1 entries
+  std::vector<int> D;                // local (fused P,Q) dims d^2
+  std::vector<int> d;
+  std::vector<cplx*> A;              // site tensors [Ml][D][Mr]
+  std::vector<cplx*> Lenv, Renv;     // environments for the Hamiltonian MPO
+  int L() const { return (int)A.size(); }
+  long long size(int k) const { return (long long)Mb[k] * D[k] * Mb[k + 1]; }
+};
+
+// Contraction building blocks, FP64.  X and Y are workspaces of at least
+// max(Dl, Dr) * (left dim) * D * (right dim) entries.  All enqueue on `st`.
+struct Ctx {
+  cudaStream_t st;
+  cplx* X;
+  cplx* Y;
+};
+// out[a,s,t,b] = sum L[w,a,y] W[w,v,s,u] in[y,u,t,c] R[v,b,c]  (bra dims = ket dims)
+void heff_f64(const Ctx& c, const DevMpoSite& W, int Ml, int Mr, int D, int d, const cplx* Lenv,
+              const cplx* Renv, const cplx* in, cplx* out, const int* skip);
+// Y[v][a][s][t][c] = sum L[w,a,y] W[w,v,s,u] ket[y,u,t,c]   (a < Ml1, y < Ml2, c < Mr2)
+void left_partial_f64(const Ctx& c, const DevMpoSite& W, int Ml1, int Ml2, int D, int d,
+                      int Mr2, const cplx* Lenv, const cplx* ket, cplx* Y, const int* skip);
+// Y[w][y][s][t][b] = sum W[w,v,s,u] ket[y,u,t,c] R[v,b,c]     (y < Ml2, b < Mr1, c < Mr2)
+void right_partial_f64(const Ctx& c, const DevMpoSite& W, int Ml2, int D, int d, int Mr1,
+                       int Mr2, const cplx* Renv, const cplx* ket, cplx* Y, const int* skip);
+void env_left_f64(const Ctx& c, const DevMpoSite& W, int Ml1, int Mr1, int Ml2, int Mr2, int D,
+                  int d, const cplx* Lenv, const cplx* bra, const cplx* ket, cplx* Lout);
+void env_right_f64(const Ctx& c, const DevMpoSite& W, int Ml1, int Mr1, int Ml2, int Mr2, int D,
+                   int d, const cplx* Renv, const cplx* bra, const cplx* ket, cplx* Rout);
+// out = sum_w L_w in R_w^T (zero-site effective Hamiltonian of a bond of dimension M)
+void bond_f64(const Ctx& c, int M, int Dw, const cplx* Lenv, const cplx* Renv, const cplx* in,
+              cplx* out, const int* skip);
+
+void throw_cuda(cudaError_t e, const char* what, int line);
+#define CK(x)                                                 \
+  do {                                                        \
+    cudaError_t e__ = (x);                                    \
+    if (e__ != cudaSuccess) ::tdmrg::throw_cuda(e__, #x, __LINE__); \
+  } while (0)
+
+struct Stats {
+  double site_updates = 0, matvecs = 0, heff_flops = 0, krylov_vectors = 0, bond_matvecs = 0,
+         qrs = 0, completions = 0, env_updates = 0;
+};
+
+class Engine {
+ public:
+  explicit Engine(const ModelParams& P);
+  ~Engine();
+
+  void set_precision(int p);
+  void set_krylov(double tol, int kmax, int fixed_k);
+  void set_stream(cudaStream_t s) { st_ = s; }
+  void rebuild_mpos();
+  void thermal_prepare(double beta, double dtau, int M);
+  void realtime_init();
+  void realtime_step(int nsteps, double dt);
+  void realtime_observe(double* C, double* obs);
+  double logz() const { return logZ_; }
+  bool prepared() const { return prepared_; }
+  bool rt_ready() const { return rt_ready_; }
+  Stats stats;
+  ModelParams P;
+
+  void ensure_workspace(long long maxsite, long long maxxy, int maxbond, int maxm);
+  static void upload_mpo(const std::vector<MpoSite>& W, DevMpo& out);
+  static void free_mpo(DevMpo& m);
+  cudaStream_t stream() const { return st_; }
+  cplx* X() { return X_; }
+  cplx* Y() { return Y_; }
+
+  // Lanczos exponential exp(tau M) v for a matvec callback (device pointers)
+  template <class F>
+  int krylov(long long n, const cplx* v, cplx* out, double tr, double ti, F&& matvec);
+  void gauge_qr_dev(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cplx* R);
+
+ private:
+  void alloc_mps(DevMps& s, int M);
+  void free_mps(DevMps& s);
+  void copy_mps(const DevMps& src, DevMps& dst);
+  void right_canonicalize(DevMps& s);
+  void build_right_envs(DevMps& s);
+  void tdvp_step(DevMps& s, double tr, double ti);
+  void site_update(DevMps& s, int k, double hr, double hi);
+  void shift_right(DevMps& s, int k, const cplx* center, cplx* Cbond);
+  void shift_left(DevMps& s, int k, const cplx* center, cplx* Cbond);
+  Ctx ctx() const { return Ctx{st_, X_, Y_}; }
+  void absorb_left(const cplx* C, int M, cplx* A, long long ncols);
+  void absorb_right(cplx* A, long long nrows, const cplx* C, int M);
+  void set_ones(cplx* p);
+  double norm2_dev(const cplx* x, long long n);
+  void scale_dev(cplx* x, long long n, double f);
+  Cx overlap(const DevMps& bra, const DevMpo& W, const DevMps& ket);
+  void fit_apply(const DevMpo& W, const DevMps& psi, DevMps& phi, int sweeps);
+  void check_status();
+  long long env_size(const DevMps& s, int k, int Dw, bool left) const;
+
+  cudaStream_t st_ = 0;
+  int precision_ = 0;
+  double ktol_ = 1e-13;
+  int kmax_ = 32, fixed_k_ = 0;
+  bool prepared_ = false, rt_ready_ = false;
+  double logZ_ = 0.0;
+  std::vector<SiteInfo> sites_;
+  DevMpo H_, J_, I_;
+  DevMps psi_b_, psi1_, psi2_;
+
+  // workspace
+  long long ws_site_ = 0, ws_xy_ = 0;
+  int ws_bond_ = 0, ws_m_ = 0;
+  cplx *X_ = nullptr, *Y_ = nullptr, *V_ = nullptr, *Kout_ = nullptr, *T1_ = nullptr;
+  cplx *Cb_ = nullptr, *Rb_ = nullptr, *Ex_ = nullptr;
+  cplx* part_c_ = nullptr;
+  double* part_d_ = nullptr;
+  double* scal_ = nullptr;          // device scalars
+  LzState* lz_ = nullptr;
+  QrScratch qr_{};
+  int* status_ = nullptr;
+  int* h_pinned_ = nullptr;
+  double* h_pinned_d_ = nullptr;
+  cplx* env_tmp_[2] = {nullptr, nullptr};
+  long long env_tmp_size_ = 0;
+};
+
+// Lanczos with full re-orthogonalisation (two classical Gram-Schmidt passes) in FP64; the
+// small exponential and the stopping test run on the device; the host only polls the flag.
+template <class F>
+inline int Engine::krylov(long long n, const cplx* v, cplx* out, double tr, double ti, F&& matvec) {
+  const int cap0 = fixed_k_ > 0 ? fixed_k_ : kmax_;
+  const int kcap = (int)std::min<long long>(cap0, n);
+  LzState* S = lz_;
+  const int* done = &S->done;
+  CK(znorm2(n, v, scal_, part_d_, NBLK, nullptr, st_));
+  CK(lz_start(S, scal_, st_));
+  CK(cudaMemcpyAsync(V_, v, sizeof(cplx) * (size_t)n, cudaMemcpyDeviceToDevice, st_));
+  CK(zscale_by(n, V_, &S->inv, done, st_));
+  int used = 0;
+  for (int j = 0; j < kcap; ++j) {
+    cplx* q = V_ + (size_t)j * n;
+    cplx* w = V_ + (size_t)(j + 1) * n;
+    matvec(q, w, done);
+    CK(zdots(n, j + 1, V_, n, w, S->h1, part_c_, NBLK, done, st_));
+    CK(zsub_multi(n, j + 1, V_, n, S->h1, w, done, st_));
+    CK(zdots(n, j + 1, V_, n, w, S->h2, part_c_, NBLK, done, st_));
+    CK(zsub_multi(n, j + 1, V_, n, S->h2, w, done, st_));
+    CK(znorm2(n, w, &S->nrm2, part_d_, NBLK, done, st_));
+    CK(lz_small_exp(S, j, tr, ti, ktol_, kcap, fixed_k_ > 0 ? 1 : 0, st_));
+    CK(zscale_by(n, w, &S->inv, done, st_));
+    used = j + 1;
+    CK(cudaMemcpyAsync(h_pinned_, done, sizeof(int), cudaMemcpyDeviceToHost, st_));
+    CK(cudaStreamSynchronize(st_));
+    if (h_pinned_[0]) break;
+  }
+  stats.krylov_vectors += used;
+  CK(zcombine(n, S, V_, n, out, st_));
+  return used;
+}
+
+}  // namespace tdmrg

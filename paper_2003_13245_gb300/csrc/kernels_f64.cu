@@ -1,0 +1,754 @@
+// FP64 kernels of the TDVP sweep: strided batched complex GEMM (the contractions of H_eff,
+// the environment updates and the bond step), sparse MPO channel mixing, Lanczos
+// reductions, the small Krylov exponential and the cooperative gauge QR.
+#include "tdmrg_internal.cuh"
+
+#include <cooperative_groups.h>
+#include <cmath>
+
+namespace tdmrg {
+
+__device__ __forceinline__ cplx cmul(cplx a, cplx b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ cplx cmulc(cplx a, cplx b) {   // conj(a) * b
+  return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ void cfma(cplx& acc, cplx a, cplx b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+__device__ __forceinline__ cplx cadd(cplx a, cplx b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ cplx csub(cplx a, cplx b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ cplx cconj_if(cplx a, int c) { return c ? make_double2(a.x, -a.y) : a; }
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// ------------------------------------------------------------------------------------
+// complex GEMM: 64 x 64 output tile, 16-deep k slices, 256 threads, 4 x 4 outputs/thread
+// ------------------------------------------------------------------------------------
+constexpr int GT = 64;
+constexpr int GK = 16;
+
+__global__ void __launch_bounds__(256) zgemm_kernel(int m, int n, int k, int nred, cplx alpha,
+                                                    MatRef A, MatRef B, cplx beta, cplx* C,
+                                                    long long ldc, long long sc,
+                                                    const int* skip) {
+  if (skip && *skip) return;
+  __shared__ cplx As[GK][GT + 1];
+  __shared__ cplx Bs[GK][GT + 1];
+  const int t = threadIdx.x;
+  const int tx = t & 15, ty = t >> 4;
+  const int bm = blockIdx.y * GT, bn = blockIdx.x * GT;
+  const long long b = blockIdx.z;
+  cplx acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_double2(0.0, 0.0);
+
+  const bool a_kcontig = (A.cs == 1);
+  const bool b_kcontig = (B.rs == 1);
+  for (int r = 0; r < nred; ++r) {
+    const cplx* Ap = A.p + b * A.sb + (long long)r * A.sr;
+    const cplx* Bp = B.p + b * B.sb + (long long)r * B.sr;
+    for (int k0 = 0; k0 < k; k0 += GK) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        int i, kk;
+        if (a_kcontig) { kk = t & 15; i = (t >> 4) + 16 * q; }
+        else { i = t & 63; kk = (t >> 6) + 4 * q; }
+        const int gi = bm + i, gk = k0 + kk;
+        cplx v = make_double2(0.0, 0.0);
+        if (gi < m && gk < k) v = cconj_if(Ap[gi * A.rs + gk * A.cs], A.conj);
+        As[kk][i] = v;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        int j, kk;
+        if (b_kcontig) { kk = t & 15; j = (t >> 4) + 16 * q; }
+        else { j = t & 63; kk = (t >> 6) + 4 * q; }
+        const int gj = bn + j, gk = k0 + kk;
+        cplx v = make_double2(0.0, 0.0);
+        if (gj < n && gk < k) v = cconj_if(Bp[gk * B.rs + gj * B.cs], B.conj);
+        Bs[kk][j] = v;
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int kk = 0; kk < GK; ++kk) {
+        cplx av[4], bv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) cfma(acc[i][j], av[i], bv[j]);
+      }
+      __syncthreads();
+    }
+  }
+  cplx* Cb = C + b * sc;
+  const bool use_beta = (beta.x != 0.0 || beta.y != 0.0);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gi = bm + ty + 16 * i;
+    if (gi >= m) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gj = bn + tx + 16 * j;
+      if (gj >= n) continue;
+      cplx v = cmul(alpha, acc[i][j]);
+      if (use_beta) v = cadd(v, cmul(beta, Cb[gi * ldc + gj]));
+      Cb[gi * ldc + gj] = v;
+    }
+  }
+}
+
+cudaError_t zgemm(int m, int n, int k, int nbatch, int nred, cplx alpha, MatRef A, MatRef B,
+                  cplx beta, cplx* C, long long ldc, long long sc, const int* skip,
+                  cudaStream_t s) {
+  if (m <= 0 || n <= 0 || nbatch <= 0) return cudaSuccess;
+  dim3 grid((n + GT - 1) / GT, (m + GT - 1) / GT, nbatch);
+  zgemm_kernel<<<grid, 256, 0, s>>>(m, n, k, nred, alpha, A, B, beta, C, ldc, sc, skip);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
+// MPO channel mixing
+// ------------------------------------------------------------------------------------
+__global__ void mpo_mix_kernel(int Dout, int Ma, int d, int Mb, const int* start,
+                               const int* chan, const cplx* ops, const cplx* X, long long xs,
+                               cplx* Y, long long ys, const int* skip) {
+  if (skip && *skip) return;
+  const long long per = (long long)Ma * d * d * Mb;
+  const long long total = per * Dout;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    long long r = e;
+    const int b = (int)(r % Mb); r /= Mb;
+    const int tau = (int)(r % d); r /= d;
+    const int sig = (int)(r % d); r /= d;
+    const int a = (int)(r % Ma);
+    const int wo = (int)(r / Ma);
+    cplx acc = make_double2(0.0, 0.0);
+    for (int blk = start[wo]; blk < start[wo + 1]; ++blk) {
+      const cplx* op = ops + (long long)blk * d * d + sig * d;
+      const cplx* x = X + chan[blk] * xs + ((long long)a * d * d + tau) * Mb + b;
+      for (int u = 0; u < d; ++u) {
+        const cplx o = op[u];
+        if (o.x != 0.0 || o.y != 0.0) cfma(acc, o, x[(long long)u * d * Mb]);
+      }
+    }
+    Y[wo * ys + (e - (long long)wo * per)] = acc;
+  }
+}
+
+cudaError_t mpo_mix(const MixTable& T, int Ma, int d, int Mb, const cplx* X, long long xs,
+                    cplx* Y, long long ys, const int* skip, cudaStream_t s) {
+  const long long total = (long long)T.Dout * Ma * d * d * Mb;
+  if (total <= 0) return cudaSuccess;
+  long long blocks = (total + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  mpo_mix_kernel<<<(int)blocks, 256, 0, s>>>(T.Dout, Ma, d, Mb, T.start, T.chan, T.ops, X, xs,
+                                              Y, ys, skip);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
+// reductions (two stages, fixed order: deterministic)
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ cplx block_sum_c(cplx v, cplx* sh) {
+  double re = warp_sum(v.x), im = warp_sum(v.y);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = make_double2(re, im);
+  __syncthreads();
+  cplx out = make_double2(0.0, 0.0);
+  if (threadIdx.x < 32) {
+    cplx x = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : make_double2(0.0, 0.0);
+    out.x = warp_sum(x.x);
+    out.y = warp_sum(x.y);
+  }
+  __syncthreads();
+  return out;
+}
+
+__global__ void zdots_partial_kernel(long long n, const cplx* V, long long ldv, const cplx* w,
+                                     cplx* partial, const int* skip) {
+  if (skip && *skip) return;
+  __shared__ cplx sh[32];
+  const int vec = blockIdx.y;
+  const cplx* v = V + vec * ldv;
+  cplx acc = make_double2(0.0, 0.0);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const cplx a = v[e], b = w[e];
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(-a.y, b.x, acc.y);
+  }
+  cplx s = block_sum_c(acc, sh);
+  if (threadIdx.x == 0) partial[vec * gridDim.x + blockIdx.x] = s;
+}
+
+__global__ void reduce_partial_c_kernel(int nvec, int nblk, const cplx* partial, cplx* out,
+                                        const int* skip) {
+  if (skip && *skip) return;
+  __shared__ cplx sh[32];
+  for (int vec = 0; vec < nvec; ++vec) {
+    cplx acc = make_double2(0.0, 0.0);
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) acc = cadd(acc, partial[vec * nblk + i]);
+    cplx s = block_sum_c(acc, sh);
+    if (threadIdx.x == 0) out[vec] = s;
+  }
+}
+
+cudaError_t zdots(long long n, int nvec, const cplx* V, long long ldv, const cplx* w, cplx* out,
+                  cplx* partial, int nblk, const int* skip, cudaStream_t s) {
+  int g = (int)((n + 255) / 256);
+  if (g > nblk) g = nblk;
+  if (g < 1) g = 1;
+  zdots_partial_kernel<<<dim3(g, nvec), 256, 0, s>>>(n, V, ldv, w, partial, skip);
+  reduce_partial_c_kernel<<<1, 256, 0, s>>>(nvec, g, partial, out, skip);
+  return cudaGetLastError();
+}
+
+__global__ void zsub_multi_kernel(long long n, int nvec, const cplx* V, long long ldv,
+                                  const cplx* h, cplx* w, const int* skip) {
+  if (skip && *skip) return;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    cplx acc = w[e];
+    for (int i = 0; i < nvec; ++i) {
+      const cplx q = V[i * ldv + e], c = h[i];
+      acc.x -= q.x * c.x - q.y * c.y;
+      acc.y -= q.x * c.y + q.y * c.x;
+    }
+    w[e] = acc;
+  }
+}
+
+cudaError_t zsub_multi(long long n, int nvec, const cplx* V, long long ldv, const cplx* h,
+                       cplx* w, const int* skip, cudaStream_t s) {
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  zsub_multi_kernel<<<(int)blocks, 256, 0, s>>>(n, nvec, V, ldv, h, w, skip);
+  return cudaGetLastError();
+}
+
+__global__ void znorm2_partial_kernel(long long n, const cplx* x, double* partial,
+                                      const int* skip) {
+  if (skip && *skip) return;
+  __shared__ cplx sh[32];
+  double acc = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const cplx a = x[e];
+    acc = fma(a.x, a.x, acc);
+    acc = fma(a.y, a.y, acc);
+  }
+  cplx s = block_sum_c(make_double2(acc, 0.0), sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s.x;
+}
+
+__global__ void reduce_partial_d_kernel(int nblk, const double* partial, double* out,
+                                        const int* skip) {
+  if (skip && *skip) return;
+  __shared__ cplx sh[32];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) acc += partial[i];
+  cplx s = block_sum_c(make_double2(acc, 0.0), sh);
+  if (threadIdx.x == 0) *out = s.x;
+}
+
+cudaError_t znorm2(long long n, const cplx* x, double* out, double* partial, int nblk,
+                   const int* skip, cudaStream_t s) {
+  int g = (int)((n + 255) / 256);
+  if (g > nblk) g = nblk;
+  if (g < 1) g = 1;
+  znorm2_partial_kernel<<<g, 256, 0, s>>>(n, x, partial, skip);
+  reduce_partial_d_kernel<<<1, 256, 0, s>>>(g, partial, out, skip);
+  return cudaGetLastError();
+}
+
+__global__ void zscale_by_kernel(long long n, cplx* x, const double* factor, const int* skip) {
+  if (skip && *skip) return;
+  const double f = *factor;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    x[e].x *= f;
+    x[e].y *= f;
+  }
+}
+
+cudaError_t zscale_by(long long n, cplx* x, const double* factor, const int* skip,
+                      cudaStream_t s) {
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  zscale_by_kernel<<<(int)blocks, 256, 0, s>>>(n, x, factor, skip);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
+// Lanczos bookkeeping and the small exponential exp(tau T_k) e_1 (one warp, FP64).
+// T_k is real symmetric tridiagonal; the exponential is evaluated by its Taylor series
+// with scaling: s = ceil(|tau| ||T||_inf / 0.5) sub-steps, each summed until the term
+// falls below 1e-18 of the partial sum (Moler & Van Loan, "Nineteen dubious ways", method
+// 1 with scaling).  Lane i holds row i.
+// ------------------------------------------------------------------------------------
+__global__ void lz_start_kernel(LzState* S, const double* nrm2) {
+  if (threadIdx.x == 0) {
+    const double b0 = sqrt(*nrm2);
+    S->b0 = b0;
+    S->inv = b0 > 0.0 ? 1.0 / b0 : 0.0;
+    S->k = 0;
+    S->done = (b0 == 0.0) ? 1 : 0;
+    S->noconv = 0;
+    S->err = 0.0;
+    if (b0 == 0.0) {
+      for (int i = 0; i < KMAX; ++i) S->c[i] = make_double2(0.0, 0.0);
+    }
+  }
+}
+
+cudaError_t lz_start(LzState* S, const double* nrm2, cudaStream_t s) {
+  lz_start_kernel<<<1, 32, 0, s>>>(S, nrm2);
+  return cudaGetLastError();
+}
+
+__global__ void lz_small_exp_kernel(LzState* S, int j, double tr, double ti, double tol,
+                                    int kcap, int fixed) {
+  if (S->done) return;
+  const int lane = threadIdx.x;
+  const int k = j + 1;
+  const double aj = S->h1[j].x + S->h2[j].x;       // alpha_j = Re <q_j, H q_j>
+  const double nb = sqrt(S->nrm2);                  // beta_{j+1}
+  // row `lane` of T_k: diagonal alpha_lane, off-diagonals beta_lane (left), beta_{lane+1}
+  const double a = lane < j ? S->alpha[lane] : (lane == j ? aj : 0.0);
+  const double bl = (lane >= 1 && lane < k) ? S->beta[lane] : 0.0;
+  const double br = (lane + 1 < k) ? S->beta[lane + 1] : 0.0;
+  __syncwarp();
+  if (lane == 0) {
+    S->alpha[j] = aj;
+    S->beta[j + 1] = nb;
+  }
+  const double rowsum = fabs(a) + fabs(bl) + fabs(br);
+  const double tnorm = warp_max(rowsum);
+  // scale used for the breakdown test: entries of T_k only
+  const double scale = warp_max(fmax(fabs(a), fabs(bl)));
+  const double tabs = sqrt(tr * tr + ti * ti);
+  int nsub = (int)ceil(tabs * tnorm / 0.5);
+  if (nsub < 1) nsub = 1;
+  const double sr = tr / nsub, si = ti / nsub;
+  double yr = (lane == 0) ? 1.0 : 0.0, yi = 0.0;
+  for (int st = 0; st < nsub; ++st) {
+    double tr_ = yr, ti_ = yi, ar = yr, ai = yi;
+    for (int q = 1; q <= 60; ++q) {
+      const double ur = __shfl_up_sync(0xffffffffu, tr_, 1);
+      const double ui = __shfl_up_sync(0xffffffffu, ti_, 1);
+      const double dr = __shfl_down_sync(0xffffffffu, tr_, 1);
+      const double di = __shfl_down_sync(0xffffffffu, ti_, 1);
+      const double xr = a * tr_ + (lane >= 1 ? bl * ur : 0.0) + (lane < 31 ? br * dr : 0.0);
+      const double xi = a * ti_ + (lane >= 1 ? bl * ui : 0.0) + (lane < 31 ? br * di : 0.0);
+      // term <- (tau / nsub) * (T term) / q
+      tr_ = (sr * xr - si * xi) / q;
+      ti_ = (sr * xi + si * xr) / q;
+      ar += tr_;
+      ai += ti_;
+      const double tm = warp_max(fabs(tr_) + fabs(ti_));
+      const double am = warp_max(fabs(ar) + fabs(ai));
+      if (tm <= 1e-18 * am) break;
+    }
+    yr = ar;
+    yi = ai;
+  }
+  const double ylr = __shfl_sync(0xffffffffu, yr, k - 1);
+  const double yli = __shfl_sync(0xffffffffu, yi, k - 1);
+  const double err = nb * sqrt(ylr * ylr + yli * yli);
+  const bool breakdown = nb <= 1e-12 * fmax(scale, 1e-300);
+  const bool done = breakdown || k >= kcap || (!fixed && err < tol);
+  if (done) {
+    if (lane < k) S->c[lane] = make_double2(S->b0 * yr, S->b0 * yi);
+    if (lane == 0) {
+      S->k = k;
+      S->err = err;
+      S->noconv = (!breakdown && !fixed && err > 1e3 * tol) ? 1 : 0;
+      __threadfence();
+      S->done = 1;
+    }
+  } else if (lane == 0) {
+    S->inv = 1.0 / nb;
+  }
+}
+
+cudaError_t lz_small_exp(LzState* S, int j, double tau_re, double tau_im, double tol, int kcap,
+                         int fixed, cudaStream_t s) {
+  lz_small_exp_kernel<<<1, 32, 0, s>>>(S, j, tau_re, tau_im, tol, kcap, fixed);
+  return cudaGetLastError();
+}
+
+__global__ void zcombine_kernel(long long n, const LzState* S, const cplx* V, long long ldv,
+                                cplx* out) {
+  const int k = S->k;
+  __shared__ cplx c[KMAX];
+  if (threadIdx.x < KMAX) c[threadIdx.x] = S->c[threadIdx.x];
+  __syncthreads();
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    cplx acc = make_double2(0.0, 0.0);
+    for (int i = 0; i < k; ++i) cfma(acc, c[i], V[i * ldv + e]);
+    out[e] = acc;
+  }
+}
+
+cudaError_t zcombine(long long n, const LzState* S, const cplx* V, long long ldv, cplx* out,
+                     cudaStream_t s) {
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  zcombine_kernel<<<(int)blocks, 256, 0, s>>>(n, S, V, ldv, out);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
+// Gauge QR: Gram-Schmidt (twice) column by column with skipped columns and deterministic
+// completion.  One cooperative launch; CTA g owns a contiguous block of rows of Y, Q and
+// of the working vector, so the only cross-CTA traffic is the partial dot products and
+// norms, exchanged through double-buffered global arrays and a bounded grid barrier.
+// ------------------------------------------------------------------------------------
+constexpr long long BARRIER_TIMEOUT_CYCLES = 4000000000LL;   // about 2 s at 2 GHz
+constexpr int QR_THREADS = 256;
+
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* status) {
+  __syncthreads();
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = bar + 1;
+    volatile int* vstat = status;
+    const unsigned gen = *vgen;
+    __threadfence();
+    const unsigned prev = atomicAdd(bar, 1u);
+    int ok = 1;
+    if (prev == nblocks - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == gen) {
+        if (*vstat) { ok = 0; break; }
+        if (clock64() - t0 > BARRIER_TIMEOUT_CYCLES) {
+          atomicExch(status, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__device__ __forceinline__ cplx qr_load(const QrRef& Y, long long r, long long c) {
+  const long long off = r * Y.rs + (c % Y.cb) * Y.cs + (c / Y.cb) * Y.cbs;
+  return cconj_if(Y.p[off], Y.conj);
+}
+
+struct QrKernelArgs {
+  int m, n, p;
+  QrRef Y, E;
+  cplx* Q;
+  cplx* R;
+  cplx* part;
+  double* partn;
+  unsigned* bar;
+  int* status;
+  double rank_tol, complete_tol;
+};
+
+// dots of v (own rows) against the columns of Q listed as accepted and < lim, reduced over
+// all CTAs into h (shared); then v -= Q h; hacc += h.
+__device__ bool qr_pass(const QrKernelArgs& A, int r0, int nr, int lim, cplx* v, cplx* h,
+                        cplx* hacc, const unsigned char* acc, int& buf, unsigned G) {
+  const int n = A.n;
+  const int g = blockIdx.x;
+  for (int i = threadIdx.x; i < lim; i += blockDim.x) {
+    cplx s = make_double2(0.0, 0.0);
+    if (acc[i]) {
+      for (int r = 0; r < nr; ++r) {
+        const cplx q = A.Q[(long long)(r0 + r) * n + i];
+        const cplx x = v[r];
+        s.x = fma(q.x, x.x, s.x);
+        s.x = fma(q.y, x.y, s.x);
+        s.y = fma(q.x, x.y, s.y);
+        s.y = fma(-q.y, x.x, s.y);
+      }
+    }
+    A.part[((long long)buf * G + g) * n + i] = s;
+  }
+  if (!grid_barrier(A.bar, G, A.status)) return false;
+  for (int i = threadIdx.x; i < lim; i += blockDim.x) {
+    cplx s = make_double2(0.0, 0.0);
+    if (acc[i])
+      for (unsigned gg = 0; gg < G; ++gg) s = cadd(s, A.part[((long long)buf * G + gg) * n + i]);
+    h[i] = s;
+    hacc[i] = cadd(hacc[i], s);
+  }
+  buf ^= 1;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int r = warp; r < nr; r += nw) {
+    double sr = 0.0, si = 0.0;
+    for (int i = lane; i < lim; i += 32) {
+      const cplx q = A.Q[(long long)(r0 + r) * n + i];
+      const cplx c = h[i];
+      sr += q.x * c.x - q.y * c.y;
+      si += q.x * c.y + q.y * c.x;
+    }
+    sr = warp_sum(sr);
+    si = warp_sum(si);
+    if (lane == 0) v[r] = make_double2(v[r].x - sr, v[r].y - si);
+  }
+  __syncthreads();
+  return true;
+}
+
+__device__ bool qr_norm(const QrKernelArgs& A, int nr, const cplx* v, double& out, int& buf,
+                        unsigned G, double* red) {
+  double s = 0.0;
+  for (int r = threadIdx.x; r < nr; r += blockDim.x) s += v[r].x * v[r].x + v[r].y * v[r].y;
+  s = warp_sum(s);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    A.partn[buf * G + blockIdx.x] = t;
+  }
+  if (!grid_barrier(A.bar, G, A.status)) return false;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (unsigned gg = 0; gg < G; ++gg) t += A.partn[buf * G + gg];
+    red[32] = t;
+  }
+  __syncthreads();
+  out = sqrt(red[32]);
+  buf ^= 1;
+  __syncthreads();
+  return true;
+}
+
+__global__ void __launch_bounds__(QR_THREADS) gauge_qr_kernel(QrKernelArgs A) {
+  extern __shared__ unsigned char smem[];
+  const int m = A.m, n = A.n;
+  const unsigned G = gridDim.x;
+  const int rows = (m + G - 1) / G;
+  const int r0 = blockIdx.x * rows;
+  const int nr = max(0, min(m, r0 + rows) - r0);
+  cplx* v = reinterpret_cast<cplx*>(smem);
+  cplx* h = v + rows;
+  cplx* hacc = h + n;
+  double* red = reinterpret_cast<double*>(hacc + n);            // 33 doubles
+  unsigned char* acc = reinterpret_cast<unsigned char*>(red + 34);
+  int buf = 0;
+
+  for (long long e = threadIdx.x; e < (long long)nr * n; e += blockDim.x)
+    A.Q[(long long)r0 * n + e] = make_double2(0.0, 0.0);
+  if (blockIdx.x == 0)
+    for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x)
+      A.R[e] = make_double2(0.0, 0.0);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc[i] = 0;
+  // ||Y||_F
+  double ynorm2 = 0.0;
+  for (long long e = threadIdx.x; e < (long long)nr * n; e += blockDim.x) {
+    const cplx y = qr_load(A.Y, r0 + e / n, e % n);
+    ynorm2 += y.x * y.x + y.y * y.y;
+  }
+  // reuse qr_norm's reduction through a fake vector: do it inline
+  ynorm2 = warp_sum(ynorm2);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ynorm2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    A.partn[buf * G + blockIdx.x] = t;
+  }
+  if (!grid_barrier(A.bar, G, A.status)) return;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (unsigned gg = 0; gg < G; ++gg) t += A.partn[buf * G + gg];
+    red[33] = t;
+  }
+  __syncthreads();
+  const double thr = A.rank_tol * sqrt(red[33]);
+  buf ^= 1;
+  __syncthreads();
+
+  // accepted columns
+  for (int j = 0; j < n; ++j) {
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) v[r] = qr_load(A.Y, r0 + r, j);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) hacc[i] = make_double2(0.0, 0.0);
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass)
+      if (!qr_pass(A, r0, nr, j, v, h, hacc, acc, buf, G)) return;
+    double nrm;
+    if (!qr_norm(A, nr, v, nrm, buf, G, red)) return;
+    const bool take = nrm > thr;
+    if (take) {
+      const double inv = 1.0 / nrm;
+      for (int r = threadIdx.x; r < nr; r += blockDim.x)
+        A.Q[(long long)(r0 + r) * n + j] = make_double2(v[r].x * inv, v[r].y * inv);
+    }
+    if (blockIdx.x == 0) {
+      for (int i = threadIdx.x; i < j; i += blockDim.x) A.R[(long long)i * n + j] = hacc[i];
+      if (threadIdx.x == 0 && take) A.R[(long long)j * n + j] = make_double2(nrm, 0.0);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && take) acc[j] = 1;
+    __syncthreads();
+  }
+  // completion of skipped positions
+  long long cand = 0;
+  for (int j = 0; j < n; ++j) {
+    if (acc[j]) continue;
+    bool found = false;
+    while (!found) {
+      if (cand >= (long long)A.p + m) {
+        if (threadIdx.x == 0 && blockIdx.x == 0) atomicExch(A.status, 2);
+        return;
+      }
+      double n0;
+      if (cand < A.p) {
+        for (int r = threadIdx.x; r < nr; r += blockDim.x) v[r] = qr_load(A.E, r0 + r, cand);
+        __syncthreads();
+        if (!qr_norm(A, nr, v, n0, buf, G, red)) return;
+      } else {
+        const long long unit = cand - A.p;
+        for (int r = threadIdx.x; r < nr; r += blockDim.x)
+          v[r] = make_double2((r0 + r) == unit ? 1.0 : 0.0, 0.0);
+        __syncthreads();
+        n0 = 1.0;
+      }
+      ++cand;
+      if (n0 == 0.0) continue;
+      for (int pass = 0; pass < 2; ++pass)
+        if (!qr_pass(A, r0, nr, n, v, h, hacc, acc, buf, G)) return;
+      double nc;
+      if (!qr_norm(A, nr, v, nc, buf, G, red)) return;
+      if (nc > A.complete_tol * n0) {
+        const double inv = 1.0 / nc;
+        for (int r = threadIdx.x; r < nr; r += blockDim.x)
+          A.Q[(long long)(r0 + r) * n + j] = make_double2(v[r].x * inv, v[r].y * inv);
+        __syncthreads();
+        if (threadIdx.x == 0) acc[j] = 1;
+        __syncthreads();
+        found = true;
+      }
+    }
+  }
+}
+
+static int g_qr_coop_blocks = -1;
+
+int gauge_qr_grid(int m) {
+  if (g_qr_coop_blocks < 0) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // shared memory is at most ~20 KB: one CTA per SM is always co-resident
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gauge_qr_kernel, QR_THREADS, 48 * 1024);
+    if (per < 1) per = 1;
+    g_qr_coop_blocks = sms;   // one CTA per SM keeps the barrier cheap
+  }
+  int g = (m + 63) / 64;
+  if (g > g_qr_coop_blocks) g = g_qr_coop_blocks;
+  if (g < 1) g = 1;
+  return g;
+}
+
+cudaError_t gauge_qr(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cplx* R,
+                     const QrScratch& W, int* status, cudaStream_t s) {
+  const int G = gauge_qr_grid(m);
+  if (G > W.gmax || n > W.nmax) return cudaErrorInvalidValue;
+  const int rows = (m + G - 1) / G;
+  const size_t smem = (size_t)rows * sizeof(cplx) + 2 * (size_t)n * sizeof(cplx) +
+                      34 * sizeof(double) + (size_t)n + 16;
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(gauge_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+    attr_set = true;
+  }
+  cudaError_t e = cudaMemsetAsync(W.bar, 0, 2 * sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  QrKernelArgs a;
+  a.m = m; a.n = n; a.p = p;
+  a.Y = Y; a.E = E;
+  if (p == 0) { a.E = Y; }
+  a.Q = Q; a.R = R;
+  a.part = W.part; a.partn = W.partn; a.bar = W.bar; a.status = status;
+  a.rank_tol = 1e-12;
+  a.complete_tol = 1e-2;
+  void* args[] = {&a};
+  return cudaLaunchCooperativeKernel((const void*)gauge_qr_kernel, dim3(G), dim3(QR_THREADS),
+                                     args, smem, s);
+}
+
+// ------------------------------------------------------------------------------------
+// small helpers
+// ------------------------------------------------------------------------------------
+__global__ void ztranspose_kernel(int m, int n, const cplx* src, cplx* dst, int conj) {
+  __shared__ cplx tile[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int yy = threadIdx.y; yy < 32; yy += 8) {
+    const int i = by + yy, j = bx + threadIdx.x;
+    if (i < m && j < n) tile[yy][threadIdx.x] = cconj_if(src[(long long)i * n + j], conj);
+  }
+  __syncthreads();
+  for (int yy = threadIdx.y; yy < 32; yy += 8) {
+    const int j = bx + yy, i = by + threadIdx.x;
+    if (i < m && j < n) dst[(long long)j * m + i] = tile[threadIdx.x][yy];
+  }
+}
+
+cudaError_t ztranspose(int m, int n, const cplx* src, cplx* dst, int conj, cudaStream_t s) {
+  dim3 grid((n + 31) / 32, (m + 31) / 32);
+  ztranspose_kernel<<<grid, dim3(32, 8), 0, s>>>(m, n, src, dst, conj);
+  return cudaGetLastError();
+}
+
+// entries: triples (a, s, b) of unit coefficients; the tensor is zeroed first by the caller
+__global__ void fill_entries_kernel(cplx* A, int D, int Mr, const int* entries, int nent) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nent; e += gridDim.x * blockDim.x) {
+    const int a = entries[3 * e], s = entries[3 * e + 1], b = entries[3 * e + 2];
+    A[((long long)a * D + s) * Mr + b] = make_double2(1.0, 0.0);
+  }
+}
+
+cudaError_t zfill_identity_mps(cplx* A, int Ml, int D, int Mr, const int* entries, int nent,
+                               cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(A, 0, sizeof(cplx) * (size_t)Ml * D * Mr, s);
+  if (e != cudaSuccess) return e;
+  if (nent > 0) fill_entries_kernel<<<(nent + 255) / 256, 256, 0, s>>>(A, D, Mr, entries, nent);
+  return cudaGetLastError();
+}
+
+}  // namespace tdmrg

@@ -1,0 +1,93 @@
+// Internal declarations shared by the CUDA translation units of libtdmrg.
+// Complex numbers are double2 {re, im} (FP64 path); every tensor is row-major.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace tdmrg {
+
+typedef double2 cplx;
+
+constexpr int KMAX = 32;            // largest Krylov dimension
+
+// Strided view of a matrix operand: element (i, j) = p[i * rs + j * cs] (conjugated if conj),
+// batch b / reduction term r shift the pointer by b * sb + r * sr.
+struct MatRef {
+  const cplx* p;
+  long long rs, cs, sb, sr;
+  int conj;
+};
+
+// C_b = alpha * sum_{r < nred} op(A_{b,r}) op(B_{b,r}) + beta * C_b, b < nbatch.
+// C row-major with leading dimension ldc and batch stride sc.
+cudaError_t zgemm(int m, int n, int k, int nbatch, int nred, cplx alpha, MatRef A, MatRef B,
+                  cplx beta, cplx* C, long long ldc, long long sc, const int* skip,
+                  cudaStream_t s);
+
+// Sparse MPO mixing over the channel and the physical (P) level of a site:
+// Y[wo][a][s][t][b] = sum_{blocks of wo} sum_u op[s][u] X[wi][a][u][t][b].
+struct MixTable {
+  int Dout;
+  const int* start;      // Dout + 1
+  const int* chan;       // input channel of each block
+  const cplx* ops;       // d x d per block
+};
+cudaError_t mpo_mix(const MixTable& T, int Ma, int d, int Mb, const cplx* X, long long xs,
+                    cplx* Y, long long ys, const int* skip, cudaStream_t s);
+
+// Lanczos scalars living on the device.
+struct LzState {
+  cplx h1[KMAX + 1];
+  cplx h2[KMAX + 1];
+  double alpha[KMAX];
+  double beta[KMAX + 1];
+  cplx c[KMAX];
+  double nrm2;
+  double b0;
+  double inv;
+  double err;
+  int k;
+  int done;
+  int noconv;
+  int pad;
+};
+
+// partial[vec][blk] = sum_{e in chunk blk} conj(V[vec][e]) * w[e]
+cudaError_t zdots(long long n, int nvec, const cplx* V, long long ldv, const cplx* w,
+                  cplx* out, cplx* partial, int nblk, const int* skip, cudaStream_t s);
+cudaError_t zsub_multi(long long n, int nvec, const cplx* V, long long ldv, const cplx* h,
+                       cplx* w, const int* skip, cudaStream_t s);
+cudaError_t znorm2(long long n, const cplx* x, double* out, double* partial, int nblk,
+                   const int* skip, cudaStream_t s);
+cudaError_t zscale_by(long long n, cplx* x, const double* factor, const int* skip,
+                      cudaStream_t s);
+cudaError_t lz_start(LzState* S, const double* nrm2, cudaStream_t s);
+cudaError_t lz_small_exp(LzState* S, int j, double tau_re, double tau_im, double tol,
+                         int kcap, int fixed, cudaStream_t s);
+cudaError_t zcombine(long long n, const LzState* S, const cplx* V, long long ldv, cplx* out,
+                     cudaStream_t s);
+
+// Gauge QR (cooperative kernel). Y(r, c) and E(r, c) are read through the refs; E columns are
+// split in blocks: E(r, c) = p[r*rs + (c % cb) * cs + (c / cb) * cbs].
+struct QrRef {
+  const cplx* p;
+  long long rs, cs, cb, cbs;
+  int conj;
+};
+struct QrScratch {
+  cplx* part;          // 2 * gmax * nmax
+  double* partn;       // 2 * gmax
+  unsigned* bar;       // 2
+  int gmax;
+  int nmax;
+};
+cudaError_t gauge_qr(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cplx* R,
+                     const QrScratch& W, int* status, cudaStream_t s);
+int gauge_qr_grid(int m);
+
+// dst[j][i] = conj?(src[i][j]) for an m x n source.
+cudaError_t ztranspose(int m, int n, const cplx* src, cplx* dst, int conj, cudaStream_t s);
+cudaError_t zfill_identity_mps(cplx* A, int Ml, int D, int Mr, const int* entries, int nent,
+                               cudaStream_t s);
+
+}  // namespace tdmrg

@@ -1,0 +1,117 @@
+"""Kernel-level parity: each hot-path contraction through the C ABI against the oracle's
+plain FP64 implementation on the same seeded inputs (sizes span several 64-wide tiles and
+ragged tails)."""
+import numpy as np
+import pytest
+
+from tests.inputs import random_complex, random_mpo_site
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2003_13245_gb300.build import build_library
+    build_library()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+HEFF_CASES = [
+    # Ml, Mr, d, Dl, Dr
+    (1, 4, 2, 1, 7),
+    (4, 16, 4, 7, 7),
+    (37, 53, 3, 7, 7),
+    (64, 64, 2, 7, 7),
+    (96, 70, 4, 6, 6),
+    (130, 129, 2, 7, 1),
+]
+
+
+@pytest.mark.parametrize("Ml,Mr,d,Dl,Dr", HEFF_CASES)
+def test_heff_matches_oracle(Ml, Mr, d, Dl, Dr):
+    from oracle import tdvp
+    from paper_2003_13245_gb300 import binding
+    rng = np.random.default_rng(1000 + Ml + Mr)
+    L = random_complex(rng, (Dl, Ml, Ml))
+    R = random_complex(rng, (Dr, Mr, Mr))
+    W = random_mpo_site(rng, Dl, Dr, d)
+    A = random_complex(rng, (Ml, d * d, Mr))
+    ref = tdvp.heff(L, W, R, A, d)
+    n = Ml * d * d * Mr
+    X = torch.zeros(max(Dl, Dr) * n, dtype=torch.complex128, device="cuda")
+    Y = torch.zeros_like(X)
+    out = torch.zeros(n, dtype=torch.complex128, device="cuda")
+    binding.kernel_heff(dev(L), W, dev(R), dev(A), out, X, Y, d)
+    got = out.cpu().numpy().reshape(ref.shape)
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("Ml1,Mr1,Ml2,Mr2,d,Dl,Dr", [
+    (1, 4, 1, 4, 2, 1, 7), (16, 64, 16, 64, 2, 7, 7), (33, 47, 29, 51, 3, 7, 6), (70, 70, 70, 70, 4, 6, 1)])
+def test_env_left_matches_oracle(Ml1, Mr1, Ml2, Mr2, d, Dl, Dr):
+    from oracle import tdvp
+    from paper_2003_13245_gb300 import binding
+    rng = np.random.default_rng(77 + Ml1 + Mr2)
+    L = random_complex(rng, (Dl, Ml1, Ml2))
+    W = random_mpo_site(rng, Dl, Dr, d)
+    bra = random_complex(rng, (Ml1, d * d, Mr1))
+    ket = random_complex(rng, (Ml2, d * d, Mr2))
+    ref = tdvp.update_left(L, bra, W, ket, d)
+    X = torch.zeros(max(Dl, Dr) * Ml1 * d * d * Mr2, dtype=torch.complex128, device="cuda")
+    Y = torch.zeros_like(X)
+    out = torch.zeros((Dr, Mr1, Mr2), dtype=torch.complex128, device="cuda")
+    binding.kernel_env_left(dev(L), W, dev(bra), dev(ket), out, X, Y, d)
+    assert np.abs(out.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("m,n,rank,p", [(12, 5, 5, 0), (300, 64, 64, 0), (1000, 130, 97, 40),
+                                        (64, 64, 30, 0), (4096, 128, 128, 0), (256, 70, 3, 300)])
+def test_gauge_qr_matches_oracle(m, n, rank, p):
+    """Full-rank and rank-deficient (with and without completion candidates) gauge QR."""
+    from oracle import tdvp
+    from paper_2003_13245_gb300 import binding
+    rng = np.random.default_rng(m * 7 + n)
+    Y = random_complex(rng, (m, rank)) @ random_complex(rng, (rank, n))
+    if rank < n:
+        Y[:, rng.choice(n, size=min(n - rank, 5), replace=False)] = 0.0
+    E = random_complex(rng, (m, p)) if p else None
+    Qr, Rr = tdvp.gauge_qr(Y, E)
+    # the C ABI zeroes R rows of completed positions (the oracle returns Q^H Y there)
+    Q = torch.zeros((m, n), dtype=torch.complex128, device="cuda")
+    R = torch.zeros((n, n), dtype=torch.complex128, device="cuda")
+    binding.kernel_gauge_qr(dev(Y), Q, R, dev(E) if E is not None else None)
+    Qg, Rg = Q.cpu().numpy(), R.cpu().numpy()
+    assert np.abs(Qg.conj().T @ Qg - np.eye(n)).max() < 1e-12
+    assert np.abs(Qg @ Rg - Y).max() <= 1e-10 * np.abs(Y).max()
+    # the same columns are taken and the same completion vectors are chosen
+    if rank == n:
+        assert np.abs(Qg - Qr).max() < 1e-9
+    else:
+        acc = np.abs(np.diag(Rr)) > 0
+        assert np.array_equal(np.abs(np.diag(Rg)) > 0, acc)
+        # accepted columns are well defined up to rounding amplified by small residuals
+        assert np.abs(np.abs(np.einsum("ij,ij->j", Qg.conj(), Qr)) - 1).max() < 1e-6
+
+
+@pytest.mark.parametrize("tau", [-0.3j, -0.05, 0.05, -2.0j])
+def test_krylov_dense_matches_expm(tau):
+    import scipy.linalg
+    from paper_2003_13245_gb300 import binding
+    rng = np.random.default_rng(3)
+    n = 100
+    A = random_complex(rng, (n, n))
+    H = (A + A.conj().T) / 8
+    v = random_complex(rng, (n,))
+    ref = scipy.linalg.expm(tau * H) @ v
+    out = torch.zeros(n, dtype=torch.complex128, device="cuda")
+    k = binding.kernel_krylov_dense(dev(H), dev(v), out, tau, tol=1e-14, kmax=32)
+    got = out.cpu().numpy()
+    assert 1 <= k <= 32
+    assert np.abs(got - ref).max() / np.abs(ref).max() < 1e-11

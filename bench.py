@@ -1,0 +1,318 @@
+#!/usr/bin/env python
+"""Throughput of the finite-temperature TD-DMRG hot path on one GB300 (or N replicas).
+
+Workload (one "step"): one second-order one-site TDVP projector-splitting step dt of both
+real-time states (e^{-iHt}|Psi_b> and e^{-iHt} j|Psi_b>) plus the C(t) overlap of Eq. 6, on
+the periodic Holstein chain N=16 with two modes per molecule, (w, g, nmax) = (0.2, 1.5, 8) and
+(1.0, 0.8, 4), V = 0.5, kBT = 2, bond dimension M = 128, dt = dtau = 0.05: 4 x 48 = 192 site
+updates per step.  The thermal state (Eq. 5) and j|Psi_b> are prepared before the timed region.
+
+Metric: TDVP site-updates/s (higher is better).  Prints one JSON line (rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision c128|c64]
+    python bench.py --impl reference ...      # the CPU oracle on the same workload
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="holstein-N16-2mode-M128", N=16, omega=[0.2, 1.0], g=[1.5, 0.8],
+                nmax=[8, 4], V=0.5, kT=2.0, dtau=0.05, M=128, dt=0.05)
+FP64_PEAK_TFLOPS = 1.25          # GB300 dense FP64 (nominal; no FP64 figure is measured)
+METRIC = "TDVP site-updates/s (real-time, both states, N=16 2-mode Holstein chain, M=128)"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default="c128", choices=["c128", "c64"])
+    p.add_argument("--cpu-seconds", type=float, default=20.0,
+                   help="CPU time budget of the oracle sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------------------
+# CPU oracle sample (cpu_baseline leg and --impl reference)
+# ----------------------------------------------------------------------------------------
+class _Budget(Exception):
+    pass
+
+
+def oracle_sample(budget_s):
+    """Site updates/s of the FP64 CPU oracle on the same chain and bond dimension: the
+    right-canonicalised |I> (not timed), then imaginary-time site updates until the budget."""
+    from oracle import tdvp
+    from oracle.model import HolsteinModel, mpo_hamiltonian
+    w = WORKLOAD
+    m = HolsteinModel(N=w["N"], omega=w["omega"], g=w["g"], nmax=w["nmax"], V=w["V"])
+    psi = tdvp.PurifiedMPS(m, tdvp.identity_state(m, w["M"]), mpo_hamiltonian(m))
+    psi.right_canonicalize()
+    count = [0]
+    t0 = time.perf_counter()
+
+    def tick():
+        count[0] += 1
+        if time.perf_counter() - t0 > budget_s:
+            raise _Budget()
+
+    try:
+        while True:
+            psi.step(-w["dtau"], tdvp.KrylovOpts(), on_site=tick)
+    except _Budget:
+        pass
+    el = time.perf_counter() - t0
+    return count[0], el
+
+
+def cpu_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads") for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    return os.cpu_count()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    per = max(3.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_sample(per / 4)
+    units, secs = 0, 0.0
+    for _ in range(args.steps):
+        u, s = oracle_sample(per)
+        units += u
+        secs += s
+    v = units / secs
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "site-updates/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"], **{k: WORKLOAD[k] for k in
+                                                         ("N", "omega", "g", "nmax", "V", "kT", "M", "dt")}},
+            "cpu_baseline": {"value": v, "unit": "site-updates/s", "cores": cpu_threads(),
+                             "kind": "oracle",
+                             "sample": "FP64 numpy oracle, imaginary-time site updates of the "
+                                       "same chain at M=128 from the right-canonicalised |I>, "
+                                       "%.0f s per step" % per},
+            "e2e": {"value": v, "unit": "site-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------------------
+# GPU run
+# ----------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the library has no CPU path)")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    from paper_2003_13245_gb300.build import build_library
+    if rank == 0:
+        build_library()
+    barrier()
+    from paper_2003_13245_gb300 import Model, PREC_C128, PREC_C64_3XTF32
+    prec = PREC_C128 if args.precision == "c128" else PREC_C64_3XTF32
+    w = WORKLOAD
+    stream = torch.cuda.Stream()
+    launches0 = None
+
+    # ---- end-to-end region starts: host parameters -> device ----
+    torch.cuda.synchronize()
+    t_e2e0 = time.perf_counter()
+    m = Model(w["N"], w["omega"], w["g"], w["nmax"], w["V"], precision=prec, stream=stream)
+    m.thermal_prepare(1.0 / w["kT"], w["dtau"], w["M"])
+    m.realtime_init()
+    for _ in range(args.warmup):
+        m.realtime_step(1, w["dt"])
+        m.realtime_observe()
+    pre = m.stats()
+    m.reset_stats()
+    barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    Cs = []
+    for _ in range(args.steps):
+        m.realtime_step(1, w["dt"])
+        Cs.append(m.realtime_observe())
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_e2e1 = time.perf_counter()
+    barrier()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    st = m.stats()
+    m.close()
+
+    site_updates = st["site_updates"]
+    total_units = site_updates
+    ms_max = ms
+    e2e_units = site_updates + pre["site_updates"]
+    e2e_s = t_e2e1 - t_e2e0
+    if dist is not None:
+        t = torch.tensor([ms, site_updates, e2e_s, e2e_units], dtype=torch.float64, device="cuda")
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = t.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        ms_max, total_units = mx[0].item(), sm[1].item()
+        e2e_s, e2e_units = mx[2].item(), sm[3].item()
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    value = total_units / (ms_max / 1e3)
+    heff_tflops = st["heff_flops"] / (st["heff_ms"] / 1e3) / 1e12 if st["heff_ms"] > 0 else None
+    if prec == PREC_C128:
+        roof = {"bound": "alu", "achieved": heff_tflops, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": heff_tflops / FP64_PEAK_TFLOPS if heff_tflops else None,
+                "traffic": None,
+                "kernel": "zgemm_kernel (H_eff contractions, FP64 DFMA)",
+                "peak_source": "nominal GB300 dense FP64 rate (no measured FP64 peak)",
+                "per_launch": "algorithmic H_eff flops 8*(Dl*Ml^2*d^2*Mr + Dr*Ml*d^2*Mr^2) "
+                              "per matvec / event-timed matvec duration"}
+    else:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        tf32 = peaks["bf16_tflops"] / 2.0
+        roof = {"bound": "tensor", "achieved": heff_tflops, "peak": tf32, "unit": "TFLOP/s",
+                "frac": heff_tflops / tf32 if heff_tflops else None, "traffic": None}
+    steps_total = args.steps + args.warmup
+    line = {
+        "metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c128" if prec == PREC_C128 else "c64-3xtf32", "data": "synthetic",
+        "config": {"workload": w["name"], "N": w["N"], "modes": len(w["omega"]),
+                   "omega": w["omega"], "g": w["g"], "nmax": w["nmax"], "V": w["V"],
+                   "kT": w["kT"], "M": w["M"], "dt": w["dt"], "sites": 48,
+                   "site_updates_per_step": site_updates / args.steps,
+                   "parallelism": "replicas x%d" % world,
+                   "l2": "inputs larger than L2: site tensors + environments of both states "
+                         "exceed 129 MB"},
+        "roofline": roof,
+        "heff": {"tflops": heff_tflops, "matvecs": st["matvecs"], "flops": st["heff_flops"]},
+        "e2e": {"value": e2e_units / e2e_s, "unit": "site-updates/s",
+                "h2d_bytes_per_step": (pre["h2d_bytes"] + st["h2d_bytes"]) / steps_total,
+                "d2h_bytes_per_step": (pre["d2h_bytes"] + st["d2h_bytes"]) / steps_total,
+                "region": "model_create from host parameters -> thermal_prepare -> "
+                          "realtime_init -> warmup + timed steps, C(t) read to host each step"},
+        "gpu_launches": int(st["launches"]),
+        "clocks": clocks,
+        "C_last": [Cs[-1].real, Cs[-1].imag] if Cs else None,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        u, s = oracle_sample(args.cpu_seconds)
+        line["cpu_baseline"] = {"value": u / s, "unit": "site-updates/s", "cores": cpu_threads(),
+                                "kind": "oracle",
+                                "sample": "FP64 numpy oracle: %d imaginary-time site updates of "
+                                          "the same chain at M=128 from the right-canonicalised "
+                                          "|I> in %.1f s" % (u, s)}
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.steps < 1 or args.warmup < 0:
+        raise SystemExit("need --steps >= 1")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -107,8 +107,11 @@ int tdmrg_mobility(const double* t_grid, const double* C, int nt, double kT, dou
 int tdmrg_get_logz(const tdmrg_model* h, double* logz);
 
 /* Counters since the last reset: stats[0] site updates, [1] H_eff matvecs, [2] algorithmic
- * H_eff flops, [3] Krylov vectors, [4] bond matvecs, [5] gauge QRs, [6] completions,
- * [7] environment updates.  n = number of entries wanted (<= 8). */
+ * H_eff flops (8 real flops per complex multiply-add of the two dense contractions),
+ * [3] Krylov vectors, [4] bond matvecs, [5] gauge QRs, [6] completions, [7] environment
+ * updates, [8] event-timed milliseconds of the site H_eff matvecs, [9] host-to-device and
+ * [10] device-to-host bytes copied by the library, [11] kernels launched by the library
+ * (process-wide counter, relative to this handle's last reset).  n = entries wanted (<= 12). */
 int tdmrg_get_stats(const tdmrg_model* h, double* stats, int n);
 int tdmrg_reset_stats(tdmrg_model* h);
 
@@ -124,14 +127,24 @@ const char* tdmrg_last_global_error(void);
 
 /* Effective Hamiltonian of one site (K1):
  *   out[a,s,t,b] = sum L[w,a,y] W[w,v,s,u] A[y,u,t,c] R[v,b,c]
- * L: Dl x Ml x Ml, R: Dr x Mr x Mr, A/out: Ml x (d*d) x Mr, W: Dl x Dr x d x d (dense, host
- * pointer, complex interleaved).  Workspace X, Y: device buffers of at least
- * max(Dl, Dr) * Ml * d*d * Mr complex entries each.  precision: TDMRG_PREC_*.  For
- * TDMRG_PREC_C64_3XTF32 the scratch `ws32` must hold 8 * (Dl*Ml*Ml + max(Dl,Dr)*Ml*d*d*Mr
- * + Dr*Mr*Mr) floats (pass NULL for C128).  Returns after enqueueing on `stream`. */
+ * L: Dl x Ml x Ml, R: Dr x Mr x Mr, A/out: Ml x (d*d) x Mr (complex FP64), W: Dl x Dr x d x d
+ * (dense, host pointer, complex interleaved).  TDMRG_PREC_C128: X, Y are device workspaces of
+ * max(Dl, Dr) * Ml * d*d * Mr complex entries each (ws32 unused).  TDMRG_PREC_C64_3XTF32:
+ * both contractions run on the tensor cores with 3xTF32 split operands; ws32 is a device
+ * workspace of tdmrg_heff_workspace_floats(...) floats (X, Y unused).  Synchronises `stream`;
+ * ERR_TIMEOUT if a bounded pipeline wait gave up. */
 int tdmrg_kernel_heff(int Ml, int Mr, int d, int Dl, int Dr, const double* W_host,
                       const void* L, const void* R, const void* A, void* out,
                       void* X, void* Y, void* ws32, int precision, void* stream);
+
+/* Size in floats of the 3xTF32 workspace of tdmrg_kernel_heff (-1 for invalid sizes). */
+long long tdmrg_heff_workspace_floats(int Ml, int Mr, int d, int Dl, int Dr);
+
+/* One tensor-core complex contraction C[m][n] = sum_k opA(A[m][k]) opB(B[n][k]) with opX =
+ * conjugation when conjX, A: M x K, B: N x K, C: M x N (complex FP64, row-major, device).
+ * The operands are split into 3xTF32 planes (allocated and freed inside); synchronises. */
+int tdmrg_kernel_zgemm_tc(int M, int N, int K, const void* A, const void* B, int conjA, int conjB,
+                          void* C, void* stream);
 
 /* Left environment update (K5):
  *   Lout[v,b,c] = sum conj(bra[a,s,t,b]) L[w,a,y] W[w,v,s,u] ket[y,u,t,c]

@@ -61,17 +61,25 @@ def gauge_qr(Y: np.ndarray, extra: Optional[np.ndarray] = None,
     assert m >= n
     thr = rank_tol * np.linalg.norm(Y)
     Q = np.zeros((m, n), dtype=complex)
-    have = []
-    for j in range(n):
-        r = Y[:, j].astype(complex)
+    B = np.zeros((m, n), dtype=complex)      # the columns of Q taken so far, in the order taken
+    nb = 0
+    have = set()
+
+    def residual(v):
         for _ in range(2):
-            if have:
-                Qa = Q[:, have]
-                r = r - Qa @ (Qa.conj().T @ r)
+            if nb:
+                Bv = B[:, :nb]
+                v = v - Bv @ (Bv.conj().T @ v)
+        return v
+
+    for j in range(n):
+        r = residual(Y[:, j].astype(complex))
         nr = np.linalg.norm(r)
         if nr > thr:
             Q[:, j] = r / nr
-            have.append(j)
+            B[:, nb] = Q[:, j]
+            nb += 1
+            have.add(j)
 
     def candidates():
         if extra is not None:
@@ -95,13 +103,13 @@ def gauge_qr(Y: np.ndarray, extra: Optional[np.ndarray] = None,
             n0 = np.linalg.norm(c)
             if n0 == 0.0:
                 continue
-            for _ in range(2):
-                Qa = Q[:, have]
-                c = c - Qa @ (Qa.conj().T @ c)
+            c = residual(c)
             nc = np.linalg.norm(c)
             if nc > complete_tol * n0:
                 Q[:, j] = c / nc
-                have.append(j)
+                B[:, nb] = Q[:, j]
+                nb += 1
+                have.add(j)
                 break
     R = Q.conj().T @ Y
     R[completed, :] = 0.0
@@ -333,13 +341,16 @@ class PurifiedMPS:
     def norm(self) -> float:
         return float(np.linalg.norm(self.A[0]))   # center at site 0
 
-    def step(self, tau: complex, kopts: KrylovOpts, stats=None):
-        """One second-order projector-splitting step exp(tau H) (tau = -i dt or -dtau)."""
+    def step(self, tau: complex, kopts: KrylovOpts, stats=None, on_site=None):
+        """One second-order projector-splitting step exp(tau H) (tau = -i dt or -dtau).
+
+        ``on_site`` (optional) is called after every site update (used to time a bounded
+        sample of site updates)."""
         h = 0.5 * tau
         L = self.L
         # left to right
         for k in range(L):
-            self._site(k, h, kopts, stats)
+            self._site(k, h, kopts, stats, on_site)
             if k < L - 1:
                 C = self._shift_right(k)
                 Lk, Rk = self.Lenv[k + 1], self.Renv[k]
@@ -348,7 +359,7 @@ class PurifiedMPS:
                 self.A[k + 1] = np.einsum("ab,bsc->asc", C, self.A[k + 1])
         # right to left
         for k in range(L - 1, -1, -1):
-            self._site(k, h, kopts, stats)
+            self._site(k, h, kopts, stats, on_site)
             if k > 0:
                 C = self._shift_left(k)
                 Lk, Rk = self.Lenv[k], self.Renv[k - 1]
@@ -356,12 +367,14 @@ class PurifiedMPS:
                                    kopts.kmax, kopts.fixed_k)
                 self.A[k - 1] = np.einsum("asb,bc->asc", self.A[k - 1], C)
 
-    def _site(self, k, h, kopts, stats):
+    def _site(self, k, h, kopts, stats, on_site=None):
         Lk, Rk, Wk, dk = self.Lenv[k], self.Renv[k], self.W[k], self.d[k]
         self.A[k], used = krylov_expm(lambda x: heff(Lk, Wk, Rk, x, dk), self.A[k], h,
                                       kopts.tol, kopts.kmax, kopts.fixed_k)
         if stats is not None:
             stats.append(used)
+        if on_site is not None:
+            on_site()
 
 
 def overlap(bra: List[np.ndarray], Ws: List[np.ndarray], ket: List[np.ndarray], d: List[int]) -> complex:

@@ -53,6 +53,7 @@ _SIGS = {
     "tdmrg_kernel_env_left": [_i, _i, _i, _i, _i, _i, _i, _dp, _p, _p, _p, _p, _p, _p, _p],
     "tdmrg_kernel_gauge_qr": [_i, _i, _p, _i, _p, _p, _p, _p, _p],
     "tdmrg_kernel_krylov_dense": [_i, _p, _p, _p, _d, _d, _d, _i, _ip, _p],
+    "tdmrg_kernel_zgemm_tc": [_i, _i, _i, _p, _p, _i, _i, _p, _p],
 }
 
 
@@ -68,6 +69,8 @@ def load(path: str = LIB_PATH):
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = ctypes.c_int
+    lib.tdmrg_heff_workspace_floats.argtypes = [_i, _i, _i, _i, _i]
+    lib.tdmrg_heff_workspace_floats.restype = ctypes.c_longlong
     lib.tdmrg_last_error.argtypes = [_p]
     lib.tdmrg_last_error.restype = ctypes.c_char_p
     lib.tdmrg_last_global_error.argtypes = []
@@ -167,10 +170,10 @@ class Model:
         return v.value
 
     def stats(self):
-        s = np.zeros(8)
-        _check(self._lib.tdmrg_get_stats(self._h, _dptr(s), 8), self._h)
+        s = np.zeros(12)
+        _check(self._lib.tdmrg_get_stats(self._h, _dptr(s), 12), self._h)
         keys = ["site_updates", "matvecs", "heff_flops", "krylov_vectors", "bond_matvecs", "qrs",
-                "completions", "env_updates"]
+                "completions", "env_updates", "heff_ms", "h2d_bytes", "d2h_bytes", "launches"]
         return dict(zip(keys, s.tolist()))
 
     def reset_stats(self):
@@ -204,6 +207,19 @@ def kernel_heff(L, W, R, A, out, X, Y, d, precision=PREC_C128, ws32=None, stream
     _check(lib.tdmrg_kernel_heff(Ml, Mr, d, Dl, Dr, _dptr(Wc), _ptr(L), _ptr(R), _ptr(A),
                                  _ptr(out), _ptr(X), _ptr(Y), _ptr(ws32), int(precision),
                                  _stream_ptr(stream)))
+
+
+def heff_workspace_floats(Ml, Mr, d, Dl, Dr):
+    return int(load().tdmrg_heff_workspace_floats(Ml, Mr, d, Dl, Dr))
+
+
+def kernel_zgemm_tc(A, B, C, conjA=0, conjB=0, stream=None):
+    """C = opA(A) opB(B)^T on the tensor cores (3xTF32); complex128 CUDA tensors."""
+    lib = load()
+    M, K = A.shape
+    N = B.shape[0]
+    _check(lib.tdmrg_kernel_zgemm_tc(M, N, K, _ptr(A), _ptr(B), int(conjA), int(conjB), _ptr(C),
+                                     _stream_ptr(stream)))
 
 
 def kernel_env_left(L, W, bra, ket, Lout, X, Y, d, stream=None):

@@ -9,6 +9,7 @@
 
 #include "../../include/tdmrg.h"
 #include "engine.h"
+#include "tc.cuh"
 
 using tdmrg::Engine;
 using tdmrg::Failure;
@@ -211,15 +212,18 @@ int tdmrg_get_logz(const tdmrg_model* h, double* logz) {
 int tdmrg_get_stats(const tdmrg_model* h, double* stats, int n) {
   if (!h || !stats || n < 0) return fail(nullptr, TDMRG_ERR_ARG, "NULL argument");
   const auto& s = h->eng->stats;
-  const double v[8] = {s.site_updates, s.matvecs, s.heff_flops, s.krylov_vectors,
-                       s.bond_matvecs, s.qrs, s.completions, s.env_updates};
-  for (int i = 0; i < n && i < 8; ++i) stats[i] = v[i];
+  const double v[12] = {s.site_updates, s.matvecs, s.heff_flops, s.krylov_vectors,
+                        s.bond_matvecs, s.qrs, s.completions, s.env_updates, s.heff_ms,
+                        s.h2d_bytes, s.d2h_bytes,
+                        (double)tdmrg::launch_count() - s.launches_at_reset};
+  for (int i = 0; i < n && i < 12; ++i) stats[i] = v[i];
   return TDMRG_OK;
 }
 
 int tdmrg_reset_stats(tdmrg_model* h) {
   if (!h) return fail(nullptr, TDMRG_ERR_ARG, "NULL handle");
   h->eng->stats = tdmrg::Stats();
+  h->eng->stats.launches_at_reset = (double)tdmrg::launch_count();
   return TDMRG_OK;
 }
 
@@ -229,19 +233,74 @@ const char* tdmrg_last_global_error(void) { return g_err.c_str(); }
 // ---------------------------------------------------------------------------------------
 // kernel-level entry points
 // ---------------------------------------------------------------------------------------
+long long tdmrg_heff_workspace_floats(int Ml, int Mr, int d, int Dl, int Dr) {
+  if (Ml < 1 || Mr < 1 || d < 1 || Dl < 1 || Dr < 1) return -1;
+  return tdmrg::heff_tc_floats(Ml, Mr, d * d, Dl, Dr);
+}
+
 int tdmrg_kernel_heff(int Ml, int Mr, int d, int Dl, int Dr, const double* W_host, const void* L,
                       const void* R, const void* A, void* out, void* X, void* Y, void* ws32,
                       int precision, void* stream) {
-  (void)ws32;
-  if (Ml < 1 || Mr < 1 || d < 1 || Dl < 1 || Dr < 1 || !W_host || !L || !R || !A || !out || !X || !Y)
+  if (Ml < 1 || Mr < 1 || d < 1 || Dl < 1 || Dr < 1 || !W_host || !L || !R || !A || !out)
     return fail(nullptr, TDMRG_ERR_ARG, "heff: bad arguments");
-  if (precision != TDMRG_PREC_C128) return fail(nullptr, TDMRG_ERR_ARG, "heff: precision not built");
+  if (precision == TDMRG_PREC_C128 && (!X || !Y))
+    return fail(nullptr, TDMRG_ERR_ARG, "heff: C128 needs the X and Y workspaces");
+  if (precision == TDMRG_PREC_C64_3XTF32 && !ws32)
+    return fail(nullptr, TDMRG_ERR_ARG, "heff: 3xTF32 needs the ws32 workspace");
+  if (precision != TDMRG_PREC_C128 && precision != TDMRG_PREC_C64_3XTF32)
+    return fail(nullptr, TDMRG_ERR_ARG, "heff: unknown precision");
   return guarded(nullptr, [&] {
     TempMpo W(Dl, Dr, d, W_host);
-    tdmrg::Ctx c{(cudaStream_t)stream, (tdmrg::cplx*)X, (tdmrg::cplx*)Y};
-    tdmrg::heff_f64(c, W.m.s[0], Ml, Mr, d * d, d, (const tdmrg::cplx*)L, (const tdmrg::cplx*)R,
-                    (const tdmrg::cplx*)A, (tdmrg::cplx*)out, nullptr);
-    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    cudaStream_t s = (cudaStream_t)stream;
+    if (precision == TDMRG_PREC_C128) {
+      tdmrg::Ctx c{s, (tdmrg::cplx*)X, (tdmrg::cplx*)Y};
+      tdmrg::heff_f64(c, W.m.s[0], Ml, Mr, d * d, d, (const tdmrg::cplx*)L,
+                      (const tdmrg::cplx*)R, (const tdmrg::cplx*)A, (tdmrg::cplx*)out, nullptr);
+    } else {
+      int* st = nullptr;
+      CK(cudaMalloc(&st, sizeof(int)));
+      CK(cudaMemsetAsync(st, 0, sizeof(int), s));
+      tdmrg::TcWork w = tdmrg::heff_tc_carve((float*)ws32, Ml, Mr, d * d, Dl, Dr, st);
+      tdmrg::heff_tc_envs(s, w, Ml, Mr, Dl, Dr, (const tdmrg::cplx*)L, (const tdmrg::cplx*)R);
+      tdmrg::heff_tc(s, w, W.m.s[0], Ml, Mr, d * d, d, (const tdmrg::cplx*)A, (tdmrg::cplx*)out);
+      int hs = 0;
+      CK(cudaMemcpyAsync(&hs, st, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      cudaFree(st);
+      if (hs) throw Failure{TDMRG_ERR_TIMEOUT, "tensor-core pipeline wait timed out"};
+    }
+    CK(cudaStreamSynchronize(s));
+  });
+}
+
+int tdmrg_kernel_zgemm_tc(int M, int N, int K, const void* A, const void* B, int conjA, int conjB,
+                          void* C, void* stream) {
+  if (M < 1 || N < 1 || K < 1 || !A || !B || !C) return fail(nullptr, TDMRG_ERR_ARG, "zgemm_tc: bad arguments");
+  return guarded(nullptr, [&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    tdmrg::TcOperand a{nullptr, M, K, tdmrg::pad4(K), 1}, b{nullptr, N, K, tdmrg::pad4(K), 1};
+    int* st = nullptr;
+    CK(cudaMalloc(&a.p, sizeof(float) * a.floats()));
+    CK(cudaMalloc(&b.p, sizeof(float) * b.floats()));
+    CK(cudaMalloc(&st, sizeof(int)));
+    struct F {
+      void* x[3];
+      ~F() {
+        for (void* p : x)
+          if (p) cudaFree(p);
+      }
+    } f{{a.p, b.p, st}};
+    CK(cudaMemsetAsync(st, 0, sizeof(int), s));
+    CK(tdmrg::split_f64((const tdmrg::cplx*)A, 0, K, 1, 0, a, s));
+    CK(tdmrg::split_f64((const tdmrg::cplx*)B, 0, K, 1, 0, b, s));
+    tdmrg::TcGemm g{};
+    g.M = M; g.N = N; g.K = K; g.nred = 1; g.nbatch = 1; g.conjA = conjA; g.conjB = conjB;
+    g.out_mode = 0; g.C = C; g.ldc = N; g.status = st;
+    CK(tdmrg::tc_gemm(a, b, g, s));
+    int hs = 0;
+    CK(cudaMemcpyAsync(&hs, st, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hs) throw Failure{TDMRG_ERR_TIMEOUT, "tensor-core pipeline wait timed out"};
   });
 }
 

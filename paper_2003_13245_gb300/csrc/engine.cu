@@ -2,6 +2,7 @@
 // projector-splitting sweep (imaginary and real time), the variational application of the
 // current MPO and the MPS-MPO-MPS overlap.
 #include "engine.h"
+#include "tc.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -108,6 +109,201 @@ void bond_f64(const Ctx& c, int M, int Dw, const cplx* Lenv, const cplx* Renv, c
 }
 
 // ------------------------------------------------------------------------------------
+// mixed-precision H_eff on the tensor cores
+// ------------------------------------------------------------------------------------
+namespace {
+long long r4(long long x) { return (x + 3) & ~3LL; }
+}
+
+long long heff_tc_floats(int Ml, int Mr, int D, int Dl, int Dr) {
+  return 4 * r4((long long)Dl * Ml * pad4(Ml)) + 4 * r4((long long)Dr * Mr * pad4(Mr)) +
+         4 * r4((long long)D * Mr * pad4(Ml)) + 2 * r4((long long)Dl * Ml * D * Mr) +
+         4 * r4((long long)Dr * Ml * D * pad4(Mr)) + 64;
+}
+
+TcWork heff_tc_carve(float* base, int Ml, int Mr, int D, int Dl, int Dr, int* status) {
+  TcWork w;
+  float* p = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(base) + 15) & ~(uintptr_t)15);
+  w.Lp = p;
+  p += 4 * r4((long long)Dl * Ml * pad4(Ml));
+  w.Rp = p;
+  p += 4 * r4((long long)Dr * Mr * pad4(Mr));
+  w.Bt = p;
+  p += 4 * r4((long long)D * Mr * pad4(Ml));
+  w.X = p;
+  p += 2 * r4((long long)Dl * Ml * D * Mr);
+  w.Yp = p;
+  w.status = status;
+  return w;
+}
+
+void heff_tc_envs(cudaStream_t st, const TcWork& w, int Ml, int Mr, int Dl, int Dr,
+                  const cplx* Lenv, const cplx* Renv) {
+  TcOperand Lp{w.Lp, Dl * Ml, Ml, pad4(Ml), 1};
+  TcOperand Rp{w.Rp, Mr, Mr, pad4(Mr), Dr};
+  CK(split_f64(Lenv, 0, Ml, 1, 0, Lp, st));
+  CK(split_f64(Renv, (long long)Mr * Mr, Mr, 1, 0, Rp, st));
+}
+
+void heff_tc(cudaStream_t st, const TcWork& w, const DevMpoSite& W, int Ml, int Mr, int D, int d,
+             const cplx* in, cplx* out) {
+  const int Dl = W.Dl, Dr = W.Dr;
+  TcOperand Lp{w.Lp, Dl * Ml, Ml, pad4(Ml), 1};
+  TcOperand Rp{w.Rp, Mr, Mr, pad4(Mr), Dr};
+  TcOperand Bt{w.Bt, D * Mr, Ml, pad4(Ml), 1};
+  TcOperand Yp{w.Yp, Ml * D, Mr, pad4(Mr), Dr};
+  const long long xplane = (long long)Dl * Ml * D * Mr;
+  // B operand of the first contraction: in^T (rows (s,b), K = a')
+  CK(split_f64_t(in, 0, (long long)D * Mr, 0, Bt, st));
+  // X[(w,a)][(s,b)] = sum_y L[w,a,y] in[y,(s,b)]   -> FP32 planar
+  TcGemm g1{};
+  g1.M = Dl * Ml; g1.N = D * Mr; g1.K = Ml; g1.nred = 1; g1.nbatch = 1;
+  g1.out_mode = 1; g1.C = w.X; g1.ldc = (long long)D * Mr; g1.sbc = 0; g1.plane = xplane;
+  g1.status = w.status;
+  CK(tc_gemm(Lp, Bt, g1, st));
+  // Y[v][(a,s)][b] = sum W X  -> split planes
+  CK(mix_split(W.lr, Ml, d, Mr, w.X, (long long)Ml * D * Mr, xplane, Yp, 0, st));
+  // out[(a,s)][b] = sum_{v,c} Y[v][(a,s)][c] R[v][b][c]   -> FP64
+  TcGemm g2{};
+  g2.M = Ml * D; g2.N = Mr; g2.K = Mr; g2.nred = Dr; g2.nbatch = 1; g2.a_red = 1; g2.b_red = 1;
+  g2.out_mode = 0; g2.C = out; g2.ldc = Mr; g2.sbc = 0; g2.status = w.status;
+  CK(tc_gemm(Yp, Rp, g2, st));
+}
+
+// building blocks with engine-owned buffers
+void heff_tc_prepare(cudaStream_t st, const TcBufs& b, int Ml, int Mr, int Dl, int Dr,
+                     const cplx* Lenv, const cplx* Renv) {
+  TcOperand Lp{b.envA, Dl * Ml, Ml, pad4(Ml), 1};
+  TcOperand Rp{b.envB, Mr, Mr, pad4(Mr), Dr};
+  CK(split_f64(Lenv, 0, Ml, 1, 0, Lp, st));
+  CK(split_f64(Renv, (long long)Mr * Mr, Mr, 1, 0, Rp, st));
+}
+
+namespace {
+// X[(w,a)][(s,c)] = sum_y L[w,a,y] ket[y,(s,c)] into b.x32 (FP32 planar), L planes in b.envA
+void left_x_tc(cudaStream_t st, const TcBufs& b, int Dl, int Ml1, int Ml2, int D, int Mr2,
+               const cplx* ket) {
+  TcOperand Lp{b.envA, Dl * Ml1, Ml2, pad4(Ml2), 1};
+  TcOperand Bt{b.siteA, D * Mr2, Ml2, pad4(Ml2), 1};
+  CK(split_f64_t(ket, 0, (long long)D * Mr2, 0, Bt, st));
+  TcGemm g{};
+  g.M = Dl * Ml1; g.N = D * Mr2; g.K = Ml2; g.nred = 1; g.nbatch = 1;
+  g.out_mode = 1; g.C = b.x32; g.ldc = (long long)D * Mr2; g.sbc = 0;
+  g.plane = (long long)Dl * Ml1 * D * Mr2; g.status = b.status;
+  CK(tc_gemm(Lp, Bt, g, st));
+}
+
+// X[v][(y,s)][b] = sum_c ket[(y,s)][c] R[v][b][c] into b.x32, R planes in b.envB
+void right_x_tc(cudaStream_t st, const TcBufs& b, int Dr, int Ml2, int D, int Mr1, int Mr2,
+                const cplx* ket) {
+  TcOperand Kp{b.siteA, Ml2 * D, Mr2, pad4(Mr2), 1};
+  TcOperand Rp{b.envB, Mr1, Mr2, pad4(Mr2), Dr};
+  CK(split_f64(ket, 0, Mr2, 1, 0, Kp, st));
+  TcGemm g{};
+  g.M = Ml2 * D; g.N = Mr1; g.K = Mr2; g.nred = 1; g.nbatch = Dr; g.b_bat = 1;
+  g.out_mode = 1; g.C = b.x32; g.ldc = Mr1; g.sbc = (long long)Ml2 * D * Mr1;
+  g.plane = (long long)Dr * Ml2 * D * Mr1; g.status = b.status;
+  CK(tc_gemm(Kp, Rp, g, st));
+}
+}  // namespace
+
+void heff_tc_apply(cudaStream_t st, const TcBufs& b, const DevMpoSite& W, int Ml, int Mr, int D,
+                   int d, const cplx* in, cplx* out) {
+  left_x_tc(st, b, W.Dl, Ml, Ml, D, Mr, in);
+  TcOperand Yp{b.mix, Ml * D, Mr, pad4(Mr), W.Dr};
+  CK(mix_split(W.lr, Ml, d, Mr, b.x32, (long long)Ml * D * Mr, (long long)W.Dl * Ml * D * Mr, Yp, 0,
+               st));
+  TcOperand Rp{b.envB, Mr, Mr, pad4(Mr), W.Dr};
+  TcGemm g{};
+  g.M = Ml * D; g.N = Mr; g.K = Mr; g.nred = W.Dr; g.nbatch = 1; g.a_red = 1; g.b_red = 1;
+  g.out_mode = 0; g.C = out; g.ldc = Mr; g.status = b.status;
+  CK(tc_gemm(Yp, Rp, g, st));
+}
+
+void left_partial_tc(cudaStream_t st, const TcBufs& b, const DevMpoSite& W, int Ml1, int Ml2, int D,
+                     int d, int Mr2, const cplx* Lenv, const cplx* ket, cplx* Yout) {
+  TcOperand Lp{b.envA, W.Dl * Ml1, Ml2, pad4(Ml2), 1};
+  CK(split_f64(Lenv, 0, Ml2, 1, 0, Lp, st));
+  left_x_tc(st, b, W.Dl, Ml1, Ml2, D, Mr2, ket);
+  TcOperand Yp{b.mix, Ml1 * D, Mr2, pad4(Mr2), W.Dr};
+  CK(mix_split(W.lr, Ml1, d, Mr2, b.x32, (long long)Ml1 * D * Mr2,
+               (long long)W.Dl * Ml1 * D * Mr2, Yp, 0, st));
+  CK(planes_to_f64(Yp, Yout, st));
+}
+
+void right_partial_tc(cudaStream_t st, const TcBufs& b, const DevMpoSite& W, int Ml2, int D, int d,
+                      int Mr1, int Mr2, const cplx* Renv, const cplx* ket, cplx* Yout) {
+  TcOperand Rp{b.envB, Mr1, Mr2, pad4(Mr2), W.Dr};
+  CK(split_f64(Renv, (long long)Mr1 * Mr2, Mr2, 1, 0, Rp, st));
+  right_x_tc(st, b, W.Dr, Ml2, D, Mr1, Mr2, ket);
+  TcOperand Yp{b.mix, Ml2, D * Mr1, pad4(D * Mr1), W.Dl};
+  CK(mix_split(W.rl, Ml2, d, Mr1, b.x32, (long long)Ml2 * D * Mr1,
+               (long long)W.Dr * Ml2 * D * Mr1, Yp, 2, st));
+  CK(planes_to_f64(Yp, Yout, st));
+}
+
+void env_left_tc(cudaStream_t st, const TcBufs& b, const DevMpoSite& W, int Ml1, int Mr1, int Ml2,
+                 int Mr2, int D, int d, const cplx* Lenv, const cplx* bra, const cplx* ket,
+                 cplx* Lout) {
+  TcOperand Lp{b.envA, W.Dl * Ml1, Ml2, pad4(Ml2), 1};
+  CK(split_f64(Lenv, 0, Ml2, 1, 0, Lp, st));
+  left_x_tc(st, b, W.Dl, Ml1, Ml2, D, Mr2, ket);
+  // Y^T[v][c][(a,s)]
+  TcOperand Yt{b.mix, Mr2, Ml1 * D, pad4(Ml1 * D), W.Dr};
+  CK(mix_split(W.lr, Ml1, d, Mr2, b.x32, (long long)Ml1 * D * Mr2,
+               (long long)W.Dl * Ml1 * D * Mr2, Yt, 1, st));
+  // bra^T[b][(a,s)]
+  TcOperand Bt{b.siteB, Mr1, Ml1 * D, pad4(Ml1 * D), 1};
+  CK(split_f64_t(bra, 0, Mr1, 0, Bt, st));
+  TcGemm g{};
+  g.M = Mr1; g.N = Mr2; g.K = Ml1 * D; g.nred = 1; g.nbatch = W.Dr; g.b_bat = 1; g.conjA = 1;
+  g.out_mode = 0; g.C = Lout; g.ldc = Mr2; g.sbc = (long long)Mr1 * Mr2; g.status = b.status;
+  CK(tc_gemm(Bt, Yt, g, st));
+}
+
+void env_right_tc(cudaStream_t st, const TcBufs& b, const DevMpoSite& W, int Ml1, int Mr1, int Ml2,
+                  int Mr2, int D, int d, const cplx* Renv, const cplx* bra, const cplx* ket,
+                  cplx* Rout) {
+  TcOperand Rp{b.envB, Mr1, Mr2, pad4(Mr2), W.Dr};
+  CK(split_f64(Renv, (long long)Mr1 * Mr2, Mr2, 1, 0, Rp, st));
+  right_x_tc(st, b, W.Dr, Ml2, D, Mr1, Mr2, ket);
+  // Y[w][y][(s,b)]
+  TcOperand Yp{b.mix, Ml2, D * Mr1, pad4(D * Mr1), W.Dl};
+  CK(mix_split(W.rl, Ml2, d, Mr1, b.x32, (long long)Ml2 * D * Mr1,
+               (long long)W.Dr * Ml2 * D * Mr1, Yp, 2, st));
+  TcOperand Bp{b.siteB, Ml1, D * Mr1, pad4(D * Mr1), 1};
+  CK(split_f64(bra, 0, (long long)D * Mr1, 1, 0, Bp, st));
+  TcGemm g{};
+  g.M = Ml1; g.N = Ml2; g.K = D * Mr1; g.nred = 1; g.nbatch = W.Dl; g.b_bat = 1; g.conjA = 1;
+  g.out_mode = 0; g.C = Rout; g.ldc = Ml2; g.sbc = (long long)Ml1 * Ml2; g.status = b.status;
+  CK(tc_gemm(Bp, Yp, g, st));
+}
+
+void bond_tc_prepare(cudaStream_t st, const TcBufs& b, int M, int Dw, const cplx* Lenv,
+                     const cplx* Renv) {
+  TcOperand Lp{b.envA, Dw * M, M, pad4(M), 1};
+  TcOperand Rp{b.envB, M, M, pad4(M), Dw};
+  CK(split_f64(Lenv, 0, M, 1, 0, Lp, st));
+  CK(split_f64(Renv, (long long)M * M, M, 1, 0, Rp, st));
+}
+
+void bond_tc_apply(cudaStream_t st, const TcBufs& b, int M, int Dw, const cplx* in, cplx* out) {
+  TcOperand Lp{b.envA, Dw * M, M, pad4(M), 1};
+  TcOperand Rp{b.envB, M, M, pad4(M), Dw};
+  TcOperand Ct{b.siteA, M, M, pad4(M), 1};
+  CK(split_f64_t(in, 0, M, 0, Ct, st));
+  TcOperand Xp{b.mix, M, M, pad4(M), Dw};
+  TcGemm g1{};
+  g1.M = Dw * M; g1.N = M; g1.K = M; g1.nred = 1; g1.nbatch = 1;
+  g1.out_mode = 2; g1.C = b.mix; g1.ldc = pad4(M); g1.plane = Xp.plane(); g1.status = b.status;
+  CK(tc_gemm(Lp, Ct, g1, st));
+  TcGemm g2{};
+  g2.M = M; g2.N = M; g2.K = M; g2.nred = Dw; g2.nbatch = 1; g2.a_red = 1; g2.b_red = 1;
+  g2.out_mode = 0; g2.C = out; g2.ldc = M; g2.status = b.status;
+  CK(tc_gemm(Xp, Rp, g2, st));
+}
+
+// ------------------------------------------------------------------------------------
 // MPO upload
 // ------------------------------------------------------------------------------------
 void Engine::upload_mpo(const std::vector<MpoSite>& W, DevMpo& out) {
@@ -197,6 +393,7 @@ Engine::Engine(const ModelParams& p) : P(p) {
   CK(cudaMalloc(&part_d_, sizeof(double) * NBLK));
   CK(cudaMallocHost(&h_pinned_, sizeof(int) * 4));
   CK(cudaMallocHost(&h_pinned_d_, sizeof(double) * 4));
+  for (auto& e : ev_) CK(cudaEventCreate(&e));
 }
 
 Engine::~Engine() {
@@ -218,6 +415,10 @@ Engine::~Engine() {
   if (qr_.bar) cudaFree(qr_.bar);
   if (h_pinned_) cudaFreeHost(h_pinned_);
   if (h_pinned_d_) cudaFreeHost(h_pinned_d_);
+  for (auto& e : ev_)
+    if (e) cudaEventDestroy(e);
+  for (float* p : {tcb_.envA, tcb_.envB, tcb_.siteA, tcb_.siteB, tcb_.x32, tcb_.mix})
+    if (p) cudaFree(p);
 }
 
 void Engine::rebuild_mpos() {
@@ -230,14 +431,21 @@ void Engine::rebuild_mpos() {
 }
 
 void Engine::set_precision(int p) {
-  if (p != TDMRG_PREC_C128) throw Failure{TDMRG_ERR_ARG, "precision not available in this build"};
-  precision_ = p;
+  if (p != TDMRG_PREC_C128 && p != TDMRG_PREC_C64_3XTF32)
+    throw Failure{TDMRG_ERR_ARG, "unknown precision"};
+  if (p != precision_) {
+    precision_ = p;
+    if (!ktol_user_) ktol_ = (p == TDMRG_PREC_C128) ? 1e-13 : 1e-7;
+    prepared_ = false;
+    rt_ready_ = false;
+  }
 }
 
 void Engine::set_krylov(double tol, int kmax, int fixed_k) {
   if (!(tol > 0.0) || kmax < 1 || kmax > KMAX || fixed_k < 0 || fixed_k > KMAX)
     throw Failure{TDMRG_ERR_ARG, "krylov: need tol > 0, 1 <= kmax <= 32, 0 <= fixed_k <= 32"};
   ktol_ = tol;
+  ktol_user_ = true;
   kmax_ = kmax;
   fixed_k_ = fixed_k;
 }
@@ -320,6 +528,7 @@ void Engine::alloc_mps(DevMps& s, int M) {
   }
   maxxy = std::max(maxxy, (long long)Dmax * maxbond * maxbond);
   ensure_workspace(maxsite, maxxy, maxbond, maxbond);
+  if (mixed()) alloc_tc(s);
   if (maxenv > env_tmp_size_) {
     for (int i = 0; i < 2; ++i) {
       if (env_tmp_[i]) cudaFree(env_tmp_[i]);
@@ -327,6 +536,52 @@ void Engine::alloc_mps(DevMps& s, int M) {
     }
     env_tmp_size_ = maxenv;
   }
+}
+
+void Engine::alloc_tc(const DevMps& s) {
+  const int Dmax = std::max(H_.maxD, J_.maxD);
+  long long site = 1, env = 1, x = 1;
+  for (int k = 0; k < s.L(); ++k) {
+    const long long Ml = s.Mb[k], Mr = s.Mb[k + 1], D = s.D[k];
+    const long long cands[4] = {D * Mr * pad4((int)Ml), Ml * D * pad4((int)Mr),
+                                Mr * pad4((int)(Ml * D)), Ml * pad4((int)(D * Mr))};
+    for (long long c : cands) site = std::max(site, c);
+    env = std::max(env, (long long)Dmax * Ml * pad4((int)Ml));
+    env = std::max(env, (long long)Dmax * Mr * pad4((int)Mr));
+    x = std::max(x, (long long)Dmax * Ml * D * Mr);
+  }
+  if (site > tc_site_ || env > tc_env_ || x > tc_x_) {
+    for (float** p : {&tcb_.envA, &tcb_.envB, &tcb_.siteA, &tcb_.siteB, &tcb_.x32, &tcb_.mix}) {
+      if (*p) cudaFree(*p);
+      *p = nullptr;
+    }
+    CK(cudaMalloc(&tcb_.envA, sizeof(float) * 4 * env));
+    CK(cudaMalloc(&tcb_.envB, sizeof(float) * 4 * env));
+    CK(cudaMalloc(&tcb_.siteA, sizeof(float) * 4 * site));
+    CK(cudaMalloc(&tcb_.siteB, sizeof(float) * 4 * site));
+    CK(cudaMalloc(&tcb_.x32, sizeof(float) * 2 * x));
+    CK(cudaMalloc(&tcb_.mix, sizeof(float) * 4 * (long long)Dmax * site));
+    tc_site_ = site;
+    tc_env_ = env;
+    tc_x_ = x;
+  }
+  tcb_.status = status_ + 2;
+}
+
+void Engine::env_left_any(const DevMpoSite& W, int Ml1, int Mr1, int Ml2, int Mr2, int D, int d,
+                          const cplx* Lenv, const cplx* bra, const cplx* ket, cplx* Lout) {
+  if (mixed())
+    env_left_tc(st_, tcb_, W, Ml1, Mr1, Ml2, Mr2, D, d, Lenv, bra, ket, Lout);
+  else
+    env_left_f64(ctx(), W, Ml1, Mr1, Ml2, Mr2, D, d, Lenv, bra, ket, Lout);
+}
+
+void Engine::env_right_any(const DevMpoSite& W, int Ml1, int Mr1, int Ml2, int Mr2, int D, int d,
+                           const cplx* Renv, const cplx* bra, const cplx* ket, cplx* Rout) {
+  if (mixed())
+    env_right_tc(st_, tcb_, W, Ml1, Mr1, Ml2, Mr2, D, d, Renv, bra, ket, Rout);
+  else
+    env_right_f64(ctx(), W, Ml1, Mr1, Ml2, Mr2, D, d, Renv, bra, ket, Rout);
 }
 
 void Engine::free_mps(DevMps& s) {
@@ -365,6 +620,7 @@ void Engine::copy_mps(const DevMps& src, DevMps& dst) {
 void Engine::set_ones(cplx* p) {
   static const cplx one = {1.0, 0.0};
   CK(cudaMemcpyAsync(p, &one, sizeof(cplx), cudaMemcpyHostToDevice, st_));
+  stats.h2d_bytes += sizeof(cplx);
 }
 
 // ------------------------------------------------------------------------------------
@@ -374,21 +630,25 @@ double Engine::norm2_dev(const cplx* x, long long n) {
   CK(znorm2(n, x, scal_, part_d_, NBLK, nullptr, st_));
   CK(cudaMemcpyAsync(h_pinned_d_, scal_, sizeof(double), cudaMemcpyDeviceToHost, st_));
   CK(cudaStreamSynchronize(st_));
+  stats.d2h_bytes += sizeof(double);
   return h_pinned_d_[0];
 }
 
 void Engine::scale_dev(cplx* x, long long n, double f) {
   h_pinned_d_[1] = f;
   CK(cudaMemcpyAsync(scal_ + 1, h_pinned_d_ + 1, sizeof(double), cudaMemcpyHostToDevice, st_));
+  stats.h2d_bytes += sizeof(double);
   CK(zscale_by(n, x, scal_ + 1, nullptr, st_));
   CK(cudaStreamSynchronize(st_));
 }
 
 void Engine::check_status() {
-  CK(cudaMemcpyAsync(h_pinned_ + 1, status_, sizeof(int), cudaMemcpyDeviceToHost, st_));
+  CK(cudaMemcpyAsync(h_pinned_ + 1, status_, 3 * sizeof(int), cudaMemcpyDeviceToHost, st_));
   CK(cudaStreamSynchronize(st_));
+  stats.d2h_bytes += 3 * sizeof(int);
   if (h_pinned_[1] == 1) throw Failure{TDMRG_ERR_TIMEOUT, "gauge QR grid barrier timed out"};
   if (h_pinned_[1] == 2) throw Failure{TDMRG_ERR_CUDA, "gauge QR ran out of completion vectors"};
+  if (h_pinned_[3] != 0) throw Failure{TDMRG_ERR_TIMEOUT, "tensor-core pipeline wait timed out"};
 }
 
 void Engine::gauge_qr_dev(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cplx* R) {
@@ -416,10 +676,13 @@ void Engine::absorb_right(cplx* A, long long nrows, const cplx* C, int M) {
 void Engine::shift_right(DevMps& s, int k, const cplx* center, cplx* Cbond) {
   const DevMpoSite& W = H_.s[k];
   const int Ml = s.Mb[k], Mr = s.Mb[k + 1], D = s.D[k], d = s.d[k];
-  left_partial_f64(ctx(), W, Ml, Ml, D, d, Mr, s.Lenv[k], center, Y_, nullptr);
+  if (mixed())
+    left_partial_tc(st_, tcb_, W, Ml, Ml, D, d, Mr, s.Lenv[k], center, Y_);
+  else
+    left_partial_f64(ctx(), W, Ml, Ml, D, d, Mr, s.Lenv[k], center, Y_, nullptr);
   gauge_qr_dev(Ml * D, Mr, qref(center, Mr, 1, NOSPLIT, 0, 0), W.Dr * Mr,
                qref(Y_, Mr, 1, Mr, (long long)Ml * D * Mr, 0), s.A[k], Cbond);
-  env_left_f64(ctx(), W, Ml, Mr, Ml, Mr, D, d, s.Lenv[k], s.A[k], s.A[k], s.Lenv[k + 1]);
+  env_left_any(W, Ml, Mr, Ml, Mr, D, d, s.Lenv[k], s.A[k], s.A[k], s.Lenv[k + 1]);
   stats.env_updates += 1;
 }
 
@@ -427,12 +690,15 @@ void Engine::shift_right(DevMps& s, int k, const cplx* center, cplx* Cbond) {
 void Engine::shift_left(DevMps& s, int k, const cplx* center, cplx* Cbond) {
   const DevMpoSite& W = H_.s[k];
   const int Ml = s.Mb[k], Mr = s.Mb[k + 1], D = s.D[k], d = s.d[k];
-  right_partial_f64(ctx(), W, Ml, D, d, Mr, Mr, s.Renv[k], center, Y_, nullptr);
+  if (mixed())
+    right_partial_tc(st_, tcb_, W, Ml, D, d, Mr, Mr, s.Renv[k], center, Y_);
+  else
+    right_partial_f64(ctx(), W, Ml, D, d, Mr, Mr, s.Renv[k], center, Y_, nullptr);
   gauge_qr_dev(D * Mr, Ml, qref(center, 1, (long long)D * Mr, NOSPLIT, 0, 1), W.Dl * Ml,
                qref(Y_, 1, (long long)D * Mr, NOSPLIT, 0, 1), T1_, Rb_);
   CK(ztranspose(D * Mr, Ml, T1_, s.A[k], 1, st_));
   CK(ztranspose(Ml, Ml, Rb_, Cbond, 1, st_));
-  env_right_f64(ctx(), W, Ml, Mr, Ml, Mr, D, d, s.Renv[k], s.A[k], s.A[k], s.Renv[k - 1]);
+  env_right_any(W, Ml, Mr, Ml, Mr, D, d, s.Renv[k], s.A[k], s.A[k], s.Renv[k - 1]);
   stats.env_updates += 1;
 }
 
@@ -452,7 +718,7 @@ void Engine::build_right_envs(DevMps& s) {
   set_ones(s.Renv[L - 1]);
   for (int k = L - 1; k > 0; --k) {
     const int Ml = s.Mb[k], Mr = s.Mb[k + 1];
-    env_right_f64(ctx(), H_.s[k], Ml, Mr, Ml, Mr, s.D[k], s.d[k], s.Renv[k], s.A[k], s.A[k],
+    env_right_any(H_.s[k], Ml, Mr, Ml, Mr, s.D[k], s.d[k], s.Renv[k], s.A[k], s.A[k],
                   s.Renv[k - 1]);
   }
 }
@@ -467,11 +733,26 @@ void Engine::site_update(DevMps& s, int k, double hr, double hi) {
   const cplx* Le = s.Lenv[k];
   const cplx* Re = s.Renv[k];
   Ctx c = ctx();
+  int nev = 0;
+  const bool mx = mixed();
+  if (mx) heff_tc_prepare(st_, tcb_, Ml, Mr, W.Dl, W.Dr, Le, Re);
   krylov(s.size(k), s.A[k], Kout_, hr, hi, [&](const cplx* in, cplx* out, const int* skip) {
-    heff_f64(c, W, Ml, Mr, D, d, Le, Re, in, out, skip);
+    CK(cudaEventRecord(ev_[2 * nev], st_));
+    if (mx)
+      heff_tc_apply(st_, tcb_, W, Ml, Mr, D, d, in, out);
+    else
+      heff_f64(c, W, Ml, Mr, D, d, Le, Re, in, out, skip);
+    CK(cudaEventRecord(ev_[2 * nev + 1], st_));
+    ++nev;
     stats.matvecs += 1;
     stats.heff_flops += flops;
   });
+  // every recorded matvec completed before the Krylov loop's last poll
+  for (int i = 0; i < nev; ++i) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ev_[2 * i], ev_[2 * i + 1]));
+    stats.heff_ms += ms;
+  }
   stats.site_updates += 1;
 }
 
@@ -486,8 +767,12 @@ void Engine::tdvp_step(DevMps& s, double tr, double ti) {
       const int M = s.Mb[k + 1], Dw = H_.s[k].Dr;
       const cplx* Le = s.Lenv[k + 1];
       const cplx* Re = s.Renv[k];
+      if (mixed()) bond_tc_prepare(st_, tcb_, M, Dw, Le, Re);
       krylov((long long)M * M, Cb_, Rb_, -hr, -hi, [&](const cplx* in, cplx* out, const int* sk) {
-        bond_f64(c, M, Dw, Le, Re, in, out, sk);
+        if (mixed())
+          bond_tc_apply(st_, tcb_, M, Dw, in, out);
+        else
+          bond_f64(c, M, Dw, Le, Re, in, out, sk);
         stats.bond_matvecs += 1;
       });
       absorb_left(Rb_, M, s.A[k + 1], (long long)s.D[k + 1] * s.Mb[k + 2]);
@@ -503,8 +788,12 @@ void Engine::tdvp_step(DevMps& s, double tr, double ti) {
       const int M = s.Mb[k], Dw = H_.s[k].Dl;
       const cplx* Le = s.Lenv[k];
       const cplx* Re = s.Renv[k - 1];
+      if (mixed()) bond_tc_prepare(st_, tcb_, M, Dw, Le, Re);
       krylov((long long)M * M, Cb_, Rb_, -hr, -hi, [&](const cplx* in, cplx* out, const int* sk) {
-        bond_f64(c, M, Dw, Le, Re, in, out, sk);
+        if (mixed())
+          bond_tc_apply(st_, tcb_, M, Dw, in, out);
+        else
+          bond_f64(c, M, Dw, Le, Re, in, out, sk);
         stats.bond_matvecs += 1;
       });
       absorb_right(s.A[k - 1], (long long)s.Mb[k - 1] * s.D[k - 1], Rb_, M);
@@ -524,13 +813,14 @@ Cx Engine::overlap(const DevMps& bra, const DevMpo& W, const DevMps& ket) {
   int cur = 0;
   set_ones(env_tmp_[0]);
   for (int k = 0; k < L; ++k) {
-    env_left_f64(ctx(), W.s[k], bra.Mb[k], bra.Mb[k + 1], ket.Mb[k], ket.Mb[k + 1], bra.D[k],
-                 bra.d[k], env_tmp_[cur], bra.A[k], ket.A[k], env_tmp_[cur ^ 1]);
+    env_left_any(W.s[k], bra.Mb[k], bra.Mb[k + 1], ket.Mb[k], ket.Mb[k + 1], bra.D[k], bra.d[k],
+                 env_tmp_[cur], bra.A[k], ket.A[k], env_tmp_[cur ^ 1]);
     cur ^= 1;
   }
   cplx r;
   CK(cudaMemcpyAsync(&r, env_tmp_[cur], sizeof(cplx), cudaMemcpyDeviceToHost, st_));
   CK(cudaStreamSynchronize(st_));
+  stats.d2h_bytes += sizeof(cplx);
   return Cx(r.x, r.y);
 }
 
@@ -559,18 +849,31 @@ void Engine::fit_apply(const DevMpo& W, const DevMps& psi, DevMps& phi, int swee
   Ctx c = ctx();
   for (int k = L - 1; k > 0; --k) {
     const int Ml = psi.Mb[k], Mr = psi.Mb[k + 1];
-    env_right_f64(c, W.s[k], Ml, Mr, Ml, Mr, psi.D[k], psi.d[k], Rf[k], phi.A[k], psi.A[k],
+    env_right_any(W.s[k], Ml, Mr, Ml, Mr, psi.D[k], psi.d[k], Rf[k], phi.A[k], psi.A[k],
                   Rf[k - 1]);
   }
+  const bool mx = mixed();
+  auto heff_any = [&](int k, const cplx* in, cplx* out) {
+    const int Ml = psi.Mb[k], Mr = psi.Mb[k + 1];
+    if (mx) {
+      heff_tc_prepare(st_, tcb_, Ml, Mr, W.s[k].Dl, W.s[k].Dr, Lf[k], Rf[k]);
+      heff_tc_apply(st_, tcb_, W.s[k], Ml, Mr, psi.D[k], psi.d[k], in, out);
+    } else {
+      heff_f64(c, W.s[k], Ml, Mr, psi.D[k], psi.d[k], Lf[k], Rf[k], in, out, nullptr);
+    }
+  };
   for (int sw = 0; sw < sweeps; ++sw) {
     for (int k = 0; k < L; ++k) {
       const int Ml = psi.Mb[k], Mr = psi.Mb[k + 1], D = psi.D[k], d = psi.d[k];
-      heff_f64(c, W.s[k], Ml, Mr, D, d, Lf[k], Rf[k], psi.A[k], Kout_, nullptr);
+      heff_any(k, psi.A[k], Kout_);
       if (k < L - 1) {
-        left_partial_f64(c, W.s[k], Ml, Ml, D, d, Mr, Lf[k], psi.A[k], Y_, nullptr);
+        if (mx)
+          left_partial_tc(st_, tcb_, W.s[k], Ml, Ml, D, d, Mr, Lf[k], psi.A[k], Y_);
+        else
+          left_partial_f64(c, W.s[k], Ml, Ml, D, d, Mr, Lf[k], psi.A[k], Y_, nullptr);
         gauge_qr_dev(Ml * D, Mr, qref(Kout_, Mr, 1, NOSPLIT, 0, 0), W.s[k].Dr * Mr,
                      qref(Y_, Mr, 1, Mr, (long long)Ml * D * Mr, 0), phi.A[k], Rb_);
-        env_left_f64(c, W.s[k], Ml, Mr, Ml, Mr, D, d, Lf[k], phi.A[k], psi.A[k], Lf[k + 1]);
+        env_left_any(W.s[k], Ml, Mr, Ml, Mr, D, d, Lf[k], phi.A[k], psi.A[k], Lf[k + 1]);
       } else {
         CK(cudaMemcpyAsync(phi.A[k], Kout_, sizeof(cplx) * (size_t)psi.size(k),
                            cudaMemcpyDeviceToDevice, st_));
@@ -578,13 +881,16 @@ void Engine::fit_apply(const DevMpo& W, const DevMps& psi, DevMps& phi, int swee
     }
     for (int k = L - 1; k >= 0; --k) {
       const int Ml = psi.Mb[k], Mr = psi.Mb[k + 1], D = psi.D[k], d = psi.d[k];
-      heff_f64(c, W.s[k], Ml, Mr, D, d, Lf[k], Rf[k], psi.A[k], Kout_, nullptr);
+      heff_any(k, psi.A[k], Kout_);
       if (k > 0) {
-        right_partial_f64(c, W.s[k], Ml, D, d, Mr, Mr, Rf[k], psi.A[k], Y_, nullptr);
+        if (mx)
+          right_partial_tc(st_, tcb_, W.s[k], Ml, D, d, Mr, Mr, Rf[k], psi.A[k], Y_);
+        else
+          right_partial_f64(c, W.s[k], Ml, D, d, Mr, Mr, Rf[k], psi.A[k], Y_, nullptr);
         gauge_qr_dev(D * Mr, Ml, qref(Kout_, 1, (long long)D * Mr, NOSPLIT, 0, 1),
                      W.s[k].Dl * Ml, qref(Y_, 1, (long long)D * Mr, NOSPLIT, 0, 1), T1_, Rb_);
         CK(ztranspose(D * Mr, Ml, T1_, phi.A[k], 1, st_));
-        env_right_f64(c, W.s[k], Ml, Mr, Ml, Mr, D, d, Rf[k], phi.A[k], psi.A[k], Rf[k - 1]);
+        env_right_any(W.s[k], Ml, Mr, Ml, Mr, D, d, Rf[k], phi.A[k], psi.A[k], Rf[k - 1]);
       } else {
         CK(cudaMemcpyAsync(phi.A[k], Kout_, sizeof(cplx) * (size_t)psi.size(k),
                            cudaMemcpyDeviceToDevice, st_));
@@ -616,6 +922,7 @@ void Engine::thermal_prepare(double beta, double dtau, int M) {
   CK(cudaMalloc(&d_ent, sizeof(int) * std::max<size_t>(maxe, 1)));
   for (int k = 0; k < psi_b_.L(); ++k) {
     CK(cudaMemcpy(d_ent, ent[k].data(), sizeof(int) * ent[k].size(), cudaMemcpyHostToDevice));
+    stats.h2d_bytes += sizeof(int) * ent[k].size();
     CK(zfill_identity_mps(psi_b_.A[k], psi_b_.Mb[k], psi_b_.D[k], psi_b_.Mb[k + 1], d_ent,
                           (int)ent[k].size() / 3, st_));
     CK(cudaStreamSynchronize(st_));

@@ -62,6 +62,52 @@ void env_right_f64(const Ctx& c, const DevMpoSite& W, int Ml1, int Mr1, int Ml2,
 void bond_f64(const Ctx& c, int M, int Dw, const cplx* Lenv, const cplx* Renv, const cplx* in,
               cplx* out, const int* skip);
 
+// Mixed-precision (3xTF32 tensor-core) H_eff: split planes of the environments are made once
+// per site update (heff_tc_envs), the matvec splits its FP64 input, runs the two contractions
+// on tcgen05 and writes FP64.
+struct TcWork {
+  float* Lp = nullptr;     // 4 * Dl*Ml * pad4(Ml)
+  float* Rp = nullptr;     // 4 * Dr*Mr * pad4(Mr)
+  float* Bt = nullptr;     // 4 * D*Mr * pad4(Ml)
+  float* X = nullptr;      // 2 * Dl*Ml*D*Mr
+  float* Yp = nullptr;     // 4 * Dr*Ml*D * pad4(Mr)
+  int* status = nullptr;
+};
+// Buffers of the mixed-precision contractions (float counts are set by the engine)
+struct TcBufs {
+  float* envA = nullptr;   // split planes of a left environment
+  float* envB = nullptr;   // split planes of a right environment
+  float* siteA = nullptr;  // split planes of a site-sized operand
+  float* siteB = nullptr;
+  float* x32 = nullptr;    // FP32 planar intermediate (MPO channel x site)
+  float* mix = nullptr;    // split planes of an MPO-channel x site operand
+  int* status = nullptr;
+};
+void heff_tc_prepare(cudaStream_t st, const TcBufs& b, int Ml, int Mr, int Dl, int Dr,
+                     const cplx* Lenv, const cplx* Renv);
+void heff_tc_apply(cudaStream_t st, const TcBufs& b, const DevMpoSite& W, int Ml, int Mr, int D,
+                   int d, const cplx* in, cplx* out);
+void left_partial_tc(cudaStream_t st, const TcBufs& b, const DevMpoSite& W, int Ml1, int Ml2, int D,
+                     int d, int Mr2, const cplx* Lenv, const cplx* ket, cplx* Yout);
+void right_partial_tc(cudaStream_t st, const TcBufs& b, const DevMpoSite& W, int Ml2, int D, int d,
+                      int Mr1, int Mr2, const cplx* Renv, const cplx* ket, cplx* Yout);
+void env_left_tc(cudaStream_t st, const TcBufs& b, const DevMpoSite& W, int Ml1, int Mr1, int Ml2,
+                 int Mr2, int D, int d, const cplx* Lenv, const cplx* bra, const cplx* ket,
+                 cplx* Lout);
+void env_right_tc(cudaStream_t st, const TcBufs& b, const DevMpoSite& W, int Ml1, int Mr1, int Ml2,
+                  int Mr2, int D, int d, const cplx* Renv, const cplx* bra, const cplx* ket,
+                  cplx* Rout);
+void bond_tc_prepare(cudaStream_t st, const TcBufs& b, int M, int Dw, const cplx* Lenv,
+                     const cplx* Renv);
+void bond_tc_apply(cudaStream_t st, const TcBufs& b, int M, int Dw, const cplx* in, cplx* out);
+
+long long heff_tc_floats(int Ml, int Mr, int D, int Dl, int Dr);
+TcWork heff_tc_carve(float* base, int Ml, int Mr, int D, int Dl, int Dr, int* status);
+void heff_tc_envs(cudaStream_t st, const TcWork& w, int Ml, int Mr, int Dl, int Dr,
+                  const cplx* Lenv, const cplx* Renv);
+void heff_tc(cudaStream_t st, const TcWork& w, const DevMpoSite& W, int Ml, int Mr, int D, int d,
+             const cplx* in, cplx* out);
+
 void throw_cuda(cudaError_t e, const char* what, int line);
 #define CK(x)                                                 \
   do {                                                        \
@@ -72,6 +118,9 @@ void throw_cuda(cudaError_t e, const char* what, int line);
 struct Stats {
   double site_updates = 0, matvecs = 0, heff_flops = 0, krylov_vectors = 0, bond_matvecs = 0,
          qrs = 0, completions = 0, env_updates = 0;
+  double heff_ms = 0;                 // event-timed duration of the site H_eff matvecs
+  double h2d_bytes = 0, d2h_bytes = 0;
+  double launches_at_reset = 0;
 };
 
 class Engine {
@@ -116,6 +165,12 @@ class Engine {
   void shift_right(DevMps& s, int k, const cplx* center, cplx* Cbond);
   void shift_left(DevMps& s, int k, const cplx* center, cplx* Cbond);
   Ctx ctx() const { return Ctx{st_, X_, Y_}; }
+  bool mixed() const { return precision_ != 0; }
+  void env_left_any(const DevMpoSite& W, int Ml1, int Mr1, int Ml2, int Mr2, int D, int d,
+                    const cplx* Lenv, const cplx* bra, const cplx* ket, cplx* Lout);
+  void env_right_any(const DevMpoSite& W, int Ml1, int Mr1, int Ml2, int Mr2, int D, int d,
+                     const cplx* Renv, const cplx* bra, const cplx* ket, cplx* Rout);
+  void alloc_tc(const DevMps& s);
   void absorb_left(const cplx* C, int M, cplx* A, long long ncols);
   void absorb_right(cplx* A, long long nrows, const cplx* C, int M);
   void set_ones(cplx* p);
@@ -129,6 +184,7 @@ class Engine {
   cudaStream_t st_ = 0;
   int precision_ = 0;
   double ktol_ = 1e-13;
+  bool ktol_user_ = false;
   int kmax_ = 32, fixed_k_ = 0;
   bool prepared_ = false, rt_ready_ = false;
   double logZ_ = 0.0;
@@ -150,6 +206,9 @@ class Engine {
   int* h_pinned_ = nullptr;
   double* h_pinned_d_ = nullptr;
   cplx* env_tmp_[2] = {nullptr, nullptr};
+  cudaEvent_t ev_[2 * KMAX + 2] = {};
+  TcBufs tcb_{};
+  long long tc_site_ = 0, tc_env_ = 0, tc_x_ = 0;
   long long env_tmp_size_ = 0;
 };
 
@@ -180,6 +239,7 @@ inline int Engine::krylov(long long n, const cplx* v, cplx* out, double tr, doub
     used = j + 1;
     CK(cudaMemcpyAsync(h_pinned_, done, sizeof(int), cudaMemcpyDeviceToHost, st_));
     CK(cudaStreamSynchronize(st_));
+    stats.d2h_bytes += sizeof(int);
     if (h_pinned_[0]) break;
   }
   stats.krylov_vectors += used;

@@ -8,6 +8,10 @@
 
 namespace tdmrg {
 
+static long long g_launches = 0;
+long long launch_count() { return g_launches; }
+void count_launch(int n) { g_launches += n; }
+
 __device__ __forceinline__ cplx cmul(cplx a, cplx b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -120,6 +124,7 @@ cudaError_t zgemm(int m, int n, int k, int nbatch, int nred, cplx alpha, MatRef 
                   cudaStream_t s) {
   if (m <= 0 || n <= 0 || nbatch <= 0) return cudaSuccess;
   dim3 grid((n + GT - 1) / GT, (m + GT - 1) / GT, nbatch);
+  count_launch();
   zgemm_kernel<<<grid, 256, 0, s>>>(m, n, k, nred, alpha, A, B, beta, C, ldc, sc, skip);
   return cudaGetLastError();
 }
@@ -160,6 +165,7 @@ cudaError_t mpo_mix(const MixTable& T, int Ma, int d, int Mb, const cplx* X, lon
   if (total <= 0) return cudaSuccess;
   long long blocks = (total + 255) / 256;
   if (blocks > 152 * 32) blocks = 152 * 32;
+  count_launch();
   mpo_mix_kernel<<<(int)blocks, 256, 0, s>>>(T.Dout, Ma, d, Mb, T.start, T.chan, T.ops, X, xs,
                                               Y, ys, skip);
   return cudaGetLastError();
@@ -219,6 +225,7 @@ cudaError_t zdots(long long n, int nvec, const cplx* V, long long ldv, const cpl
   int g = (int)((n + 255) / 256);
   if (g > nblk) g = nblk;
   if (g < 1) g = 1;
+  count_launch(2);
   zdots_partial_kernel<<<dim3(g, nvec), 256, 0, s>>>(n, V, ldv, w, partial, skip);
   reduce_partial_c_kernel<<<1, 256, 0, s>>>(nvec, g, partial, out, skip);
   return cudaGetLastError();
@@ -244,6 +251,7 @@ cudaError_t zsub_multi(long long n, int nvec, const cplx* V, long long ldv, cons
   long long blocks = (n + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
+  count_launch();
   zsub_multi_kernel<<<(int)blocks, 256, 0, s>>>(n, nvec, V, ldv, h, w, skip);
   return cudaGetLastError();
 }
@@ -278,6 +286,7 @@ cudaError_t znorm2(long long n, const cplx* x, double* out, double* partial, int
   int g = (int)((n + 255) / 256);
   if (g > nblk) g = nblk;
   if (g < 1) g = 1;
+  count_launch(2);
   znorm2_partial_kernel<<<g, 256, 0, s>>>(n, x, partial, skip);
   reduce_partial_d_kernel<<<1, 256, 0, s>>>(g, partial, out, skip);
   return cudaGetLastError();
@@ -298,6 +307,7 @@ cudaError_t zscale_by(long long n, cplx* x, const double* factor, const int* ski
   long long blocks = (n + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
+  count_launch();
   zscale_by_kernel<<<(int)blocks, 256, 0, s>>>(n, x, factor, skip);
   return cudaGetLastError();
 }
@@ -325,6 +335,7 @@ __global__ void lz_start_kernel(LzState* S, const double* nrm2) {
 }
 
 cudaError_t lz_start(LzState* S, const double* nrm2, cudaStream_t s) {
+  count_launch();
   lz_start_kernel<<<1, 32, 0, s>>>(S, nrm2);
   return cudaGetLastError();
 }
@@ -396,6 +407,7 @@ __global__ void lz_small_exp_kernel(LzState* S, int j, double tr, double ti, dou
 
 cudaError_t lz_small_exp(LzState* S, int j, double tau_re, double tau_im, double tol, int kcap,
                          int fixed, cudaStream_t s) {
+  count_launch();
   lz_small_exp_kernel<<<1, 32, 0, s>>>(S, j, tau_re, tau_im, tol, kcap, fixed);
   return cudaGetLastError();
 }
@@ -419,6 +431,7 @@ cudaError_t zcombine(long long n, const LzState* S, const cplx* V, long long ldv
   long long blocks = (n + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
+  count_launch();
   zcombine_kernel<<<(int)blocks, 256, 0, s>>>(n, S, V, ldv, out);
   return cudaGetLastError();
 }
@@ -708,6 +721,7 @@ cudaError_t gauge_qr(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cplx* R,
   a.rank_tol = 1e-12;
   a.complete_tol = 1e-2;
   void* args[] = {&a};
+  count_launch();
   return cudaLaunchCooperativeKernel((const void*)gauge_qr_kernel, dim3(G), dim3(QR_THREADS),
                                      args, smem, s);
 }
@@ -731,6 +745,7 @@ __global__ void ztranspose_kernel(int m, int n, const cplx* src, cplx* dst, int 
 
 cudaError_t ztranspose(int m, int n, const cplx* src, cplx* dst, int conj, cudaStream_t s) {
   dim3 grid((n + 31) / 32, (m + 31) / 32);
+  count_launch();
   ztranspose_kernel<<<grid, dim3(32, 8), 0, s>>>(m, n, src, dst, conj);
   return cudaGetLastError();
 }
@@ -747,6 +762,7 @@ cudaError_t zfill_identity_mps(cplx* A, int Ml, int D, int Mr, const int* entrie
                                cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(A, 0, sizeof(cplx) * (size_t)Ml * D * Mr, s);
   if (e != cudaSuccess) return e;
+  if (nent > 0) count_launch();
   if (nent > 0) fill_entries_kernel<<<(nent + 255) / 256, 256, 0, s>>>(A, D, Mr, entries, nent);
   return cudaGetLastError();
 }

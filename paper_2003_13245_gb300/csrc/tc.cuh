@@ -1,0 +1,46 @@
+// Tensor-core contraction interface (3xTF32 split complex operands, tcgen05).
+#pragma once
+#include "tdmrg_internal.cuh"
+
+namespace tdmrg {
+
+// Planar split operand: float planes [4][nb][rows][ld] = re_hi, re_lo, im_hi, im_lo.
+// K is the contraction extent (K-major rows), ld >= K a multiple of 4 floats, p 16-byte aligned.
+struct TcOperand {
+  float* p;
+  int rows, K, ld, nb;
+  long long plane() const { return (long long)nb * rows * ld; }
+  long long floats() const { return 4 * plane(); }
+};
+
+inline int pad4(int k) { return (k + 3) & ~3; }
+
+// C_b[m][n] = sum_{r < nred} sum_k opA(A[r*a_red + b*a_bat])[m][k] opB(B[r*b_red + b*b_bat])[n][k]
+// with opX = conjugation when conjX.  out_mode 0: complex FP64 interleaved at
+// C + b*sbc + m*ldc + n (double2 units); 1: FP32 planar (re at C + b*sbc + m*ldc + n, im at
+// + plane); 2: split planes (4 planes of `plane` floats).
+struct TcGemm {
+  int M, N, K;
+  int nred, nbatch;
+  int a_red, a_bat, b_red, b_bat;
+  int conjA, conjB;
+  int out_mode;
+  void* C;
+  long long ldc, sbc, plane;
+  int* status;
+};
+
+cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, const TcGemm& g, cudaStream_t s);
+// dst(b, row, k) = conj?(src[b*sb + row*rs + k*ks])
+cudaError_t split_f64(const cplx* src, long long sb, long long rs, long long ks, int conj,
+                      const TcOperand& dst, cudaStream_t s);
+// dst(b, row, k) = conj?(src[b*sb + k*kstride + row])   (tiled transpose)
+cudaError_t split_f64_t(const cplx* src, long long sb, long long kstride, int conj,
+                        const TcOperand& dst, cudaStream_t s);
+// MPO mixing of an FP32 planar X[wi][a][s][t][b] into split planes.  trans 0: rows (a,s,t),
+// K = b; trans 1: rows b, K = (a,s,t); trans 2: rows a, K = (s,t,b).
+cudaError_t mix_split(const MixTable& T, int Ma, int d, int Mb, const float* X, long long xs,
+                      long long xplane, const TcOperand& dst, int trans, cudaStream_t s);
+cudaError_t planes_to_f64(const TcOperand& P, cplx* out, cudaStream_t s);
+
+}  // namespace tdmrg

@@ -10,6 +10,10 @@ typedef double2 cplx;
 
 constexpr int KMAX = 32;            // largest Krylov dimension
 
+// number of kernels this library has launched (host-side counter)
+long long launch_count();
+void count_launch(int n = 1);
+
 // Strided view of a matrix operand: element (i, j) = p[i * rs + j * cs] (conjugated if conj),
 // batch b / reduction term r shift the pointer by b * sb + r * sr.
 struct MatRef {

@@ -1,0 +1,66 @@
+"""Tensor-core (tcgen05, 3xTF32) contractions against FP64 references on the same seeded
+inputs.  Tolerance: 3xTF32 keeps about 21 significant bits per product with FP32
+accumulation, so the error of a length-K complex dot product of O(1) entries is bounded by
+~ 1e-6 * sqrt(K) relative to the largest output; the tests use 2e-5 of max|C|."""
+import numpy as np
+import pytest
+
+from tests.inputs import random_complex, random_mpo_site
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+TOL = 2e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2003_13245_gb300.build import build_library
+    build_library()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+@pytest.mark.parametrize("M,N,K,cA,cB", [(128, 64, 32, 0, 0), (1, 1, 1, 0, 0), (130, 70, 33, 1, 0),
+                                         (300, 200, 700, 0, 1), (64, 129, 96, 1, 1),
+                                         (1000, 130, 128, 0, 0)])
+def test_zgemm_tc(M, N, K, cA, cB):
+    from paper_2003_13245_gb300 import binding
+    rng = np.random.default_rng(M + 3 * N + 7 * K)
+    A = random_complex(rng, (M, K))
+    B = random_complex(rng, (N, K))
+    ref = (A.conj() if cA else A) @ (B.conj() if cB else B).T
+    C = torch.zeros((M, N), dtype=torch.complex128, device="cuda")
+    binding.kernel_zgemm_tc(dev(A), dev(B), C, cA, cB)
+    err = np.abs(C.cpu().numpy() - ref).max() / np.abs(ref).max()
+    assert err < TOL, err
+
+
+HEFF_CASES = [(1, 4, 2, 1, 7), (4, 16, 4, 7, 7), (37, 53, 3, 7, 7), (64, 64, 2, 7, 7),
+              (96, 70, 4, 6, 6), (130, 129, 2, 7, 1), (128, 128, 8, 7, 7)]
+
+
+@pytest.mark.parametrize("Ml,Mr,d,Dl,Dr", HEFF_CASES)
+def test_heff_tc_matches_oracle(Ml, Mr, d, Dl, Dr):
+    from oracle import tdvp
+    from paper_2003_13245_gb300 import binding
+    rng = np.random.default_rng(2000 + Ml + Mr)
+    L = random_complex(rng, (Dl, Ml, Ml))
+    R = random_complex(rng, (Dr, Mr, Mr))
+    W = random_mpo_site(rng, Dl, Dr, d)
+    A = random_complex(rng, (Ml, d * d, Mr))
+    ref = tdvp.heff(L, W, R, A, d)
+    n = Ml * d * d * Mr
+    ws = torch.zeros(binding.heff_workspace_floats(Ml, Mr, d, Dl, Dr), dtype=torch.float32,
+                     device="cuda")
+    out = torch.zeros(n, dtype=torch.complex128, device="cuda")
+    binding.kernel_heff(dev(L), W, dev(R), dev(A), out, None, None, d,
+                        precision=binding.PREC_C64_3XTF32, ws32=ws)
+    got = out.cpu().numpy().reshape(ref.shape)
+    err = np.abs(got - ref).max() / np.abs(ref).max()
+    assert err < TOL, err

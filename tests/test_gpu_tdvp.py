@@ -109,3 +109,32 @@ def test_truncated_matches_oracle_golden():
     assert abs(m.logz() - g["logZ"]) < 1e-9
     assert np.abs(C - ref).max() / abs(ref[0]) < g["tol"]
     m.close()
+
+
+def test_mixed_precision_full_rank_against_ed():
+    """3xTF32 contractions with FP64 Lanczos/QR: C(t) within 1e-5 of C(0) of the exact result
+    (the contractions keep ~21 significant bits; the bound is the per-config statement for the
+    N=3 chain)."""
+    from paper_2003_13245_gb300 import PREC_C64_3XTF32
+    m = _model(3, [1.0], [1.0], [2], 1.0, precision=PREC_C64_3XTF32)
+    m.thermal_prepare(1.0, 0.05, 64)
+    ed = _ed(3, [1.0], [1.0], [2], 1.0, 1.0)
+    t = np.arange(0, 41, 8) * 0.05
+    C = m.correlation(t, 0.05)
+    ref = ed.correlation(t)
+    assert abs(m.logz() - ed.logZ) < 1e-5
+    assert np.abs(C - ref).max() / abs(ref[0]) < 1e-5
+    m.close()
+
+
+def test_mixed_precision_truncated_against_fp64():
+    """c1 chain at M=64: the mixed-precision C(t) against the FP64 GPU C(t)."""
+    from paper_2003_13245_gb300 import PREC_C64_3XTF32
+    t = np.arange(0, 21, 5) * 0.05
+    out = []
+    for prec in (0, PREC_C64_3XTF32):
+        m = _model(3, [1.0], [1.0], [4], 1.0, precision=prec)
+        m.thermal_prepare(1.0, 0.05, 64)
+        out.append(m.correlation(t, 0.05))
+        m.close()
+    assert np.abs(out[1] - out[0]).max() / abs(out[0][0]) < 1e-5

@@ -38,7 +38,8 @@ def parse():
     p.add_argument("--steps", type=int, default=2)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default="c128", choices=["c128", "c64"])
+    p.add_argument("--precision", default="c64", choices=["c128", "c64"],
+                   help="c64: 3xTF32 tensor-core contractions + FP64 Lanczos/QR; c128: all FP64")
     p.add_argument("--cpu-seconds", type=float, default=20.0,
                    help="CPU time budget of the oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -221,12 +222,14 @@ def run_ours(args):
     sampler.start()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
     ev0.record(stream)
     Cs = []
     for _ in range(args.steps):
         m.realtime_step(1, w["dt"])
         Cs.append(m.realtime_observe())
     ev1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     t_e2e1 = time.perf_counter()
     barrier()

@@ -76,6 +76,10 @@ int tdmrg_model_set_krylov(tdmrg_model* h, double tol, int kmax, int fixed_k);
 /* Work stream (a cudaStream_t passed as void*; NULL = legacy default stream). */
 int tdmrg_model_set_stream(tdmrg_model* h, void* stream);
 
+/* Phase timers: when on, the library synchronises its stream at every phase boundary and
+ * accumulates host wall time per phase into the stats (slightly slower; off by default). */
+int tdmrg_model_set_profiling(tdmrg_model* h, int on);
+
 int tdmrg_model_destroy(tdmrg_model* h);
 
 /* Imaginary-time preparation of Psi_beta (Eq. 5): |I> restricted to the one-carrier sector,
@@ -111,7 +115,10 @@ int tdmrg_get_logz(const tdmrg_model* h, double* logz);
  * [3] Krylov vectors, [4] bond matvecs, [5] gauge QRs, [6] completions, [7] environment
  * updates, [8] event-timed milliseconds of the site H_eff matvecs, [9] host-to-device and
  * [10] device-to-host bytes copied by the library, [11] kernels launched by the library
- * (process-wide counter, relative to this handle's last reset).  n = entries wanted (<= 12). */
+ * (process-wide counter, relative to this handle's last reset), and with profiling on the
+ * host wall seconds of [12] site exponentials, [13] gauge QRs (included in [14]),
+ * [14] gauge shifts with environment updates, [15] bond back-steps, [16] bond absorption,
+ * [17] C(t) overlaps.  n = entries wanted (<= 18). */
 int tdmrg_get_stats(const tdmrg_model* h, double* stats, int n);
 int tdmrg_reset_stats(tdmrg_model* h);
 

@@ -40,6 +40,7 @@ _SIGS = {
     "tdmrg_model_set_krylov": [_p, _d, _i, _i],
     "tdmrg_model_set_stream": [_p, _p],
     "tdmrg_model_destroy": [_p],
+    "tdmrg_model_set_profiling": [_p, _i],
     "tdmrg_thermal_prepare": [_p, _d, _d, _i],
     "tdmrg_correlation": [_p, _dp, _i, _d, _dp],
     "tdmrg_realtime_init": [_p],
@@ -170,11 +171,15 @@ class Model:
         return v.value
 
     def stats(self):
-        s = np.zeros(12)
-        _check(self._lib.tdmrg_get_stats(self._h, _dptr(s), 12), self._h)
+        s = np.zeros(18)
+        _check(self._lib.tdmrg_get_stats(self._h, _dptr(s), 18), self._h)
         keys = ["site_updates", "matvecs", "heff_flops", "krylov_vectors", "bond_matvecs", "qrs",
-                "completions", "env_updates", "heff_ms", "h2d_bytes", "d2h_bytes", "launches"]
+                "completions", "env_updates", "heff_ms", "h2d_bytes", "d2h_bytes", "launches",
+                "t_site", "t_qr", "t_env", "t_bond", "t_absorb", "t_observe"]
         return dict(zip(keys, s.tolist()))
+
+    def set_profiling(self, on=True):
+        _check(self._lib.tdmrg_model_set_profiling(self._h, int(bool(on))), self._h)
 
     def reset_stats(self):
         _check(self._lib.tdmrg_reset_stats(self._h), self._h)

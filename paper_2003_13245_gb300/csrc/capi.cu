@@ -137,6 +137,12 @@ int tdmrg_model_set_stream(tdmrg_model* h, void* stream) {
   return TDMRG_OK;
 }
 
+int tdmrg_model_set_profiling(tdmrg_model* h, int on) {
+  if (!h) return fail(nullptr, TDMRG_ERR_ARG, "NULL handle");
+  h->eng->set_profiling(on != 0);
+  return TDMRG_OK;
+}
+
 int tdmrg_model_destroy(tdmrg_model* h) {
   if (!h) return TDMRG_OK;
   if (h->eng) cudaStreamSynchronize(h->eng->stream());
@@ -212,11 +218,12 @@ int tdmrg_get_logz(const tdmrg_model* h, double* logz) {
 int tdmrg_get_stats(const tdmrg_model* h, double* stats, int n) {
   if (!h || !stats || n < 0) return fail(nullptr, TDMRG_ERR_ARG, "NULL argument");
   const auto& s = h->eng->stats;
-  const double v[12] = {s.site_updates, s.matvecs, s.heff_flops, s.krylov_vectors,
+  const double v[18] = {s.site_updates, s.matvecs, s.heff_flops, s.krylov_vectors,
                         s.bond_matvecs, s.qrs, s.completions, s.env_updates, s.heff_ms,
                         s.h2d_bytes, s.d2h_bytes,
-                        (double)tdmrg::launch_count() - s.launches_at_reset};
-  for (int i = 0; i < n && i < 12; ++i) stats[i] = v[i];
+                        (double)tdmrg::launch_count() - s.launches_at_reset,
+                        s.t_site, s.t_qr, s.t_env, s.t_bond, s.t_absorb, s.t_observe};
+  for (int i = 0; i < n && i < 18; ++i) stats[i] = v[i];
   return TDMRG_OK;
 }
 
@@ -343,7 +350,7 @@ int tdmrg_kernel_gauge_qr(int m, int n, const void* Y, int p, const void* E, voi
         if (own && st) cudaFree(st);
       }
     } fr{W, st, status == nullptr};
-    CK(cudaMalloc(&W.part, sizeof(tdmrg::cplx) * 2 * (size_t)sms * n));
+    CK(cudaMalloc(&W.part, sizeof(tdmrg::cplx) * 2 * (size_t)sms * (n + 1)));
     CK(cudaMalloc(&W.partn, sizeof(double) * 2 * (size_t)sms));
     CK(cudaMalloc(&W.bar, sizeof(unsigned) * 2));
     if (!st) {

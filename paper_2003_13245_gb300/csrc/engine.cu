@@ -5,6 +5,7 @@
 #include "tc.cuh"
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -348,19 +349,27 @@ void Engine::upload_mpo(const std::vector<MpoSite>& W, DevMpo& out) {
       irl_start[h.Dl] = pos;
     }
     const size_t ops_bytes = sizeof(cplx) * (size_t)nb * d * d;
+    const size_t ops32_bytes = sizeof(float2) * (size_t)nb * d * d;
     const size_t int_bytes = sizeof(int) * (size_t)(h.Dr + 1 + nb + h.Dl + 1 + nb);
-    const size_t total = 2 * ops_bytes + int_bytes + 64;
+    const size_t total = 2 * ops_bytes + 2 * ops32_bytes + int_bytes + 64;
     char* mem = nullptr;
     CK(cudaMalloc(&mem, total));
     s.mem = mem;
     cplx* d_olr = reinterpret_cast<cplx*>(mem);
     cplx* d_orl = d_olr + (size_t)nb * d * d;
-    int* ip = reinterpret_cast<int*>(d_orl + (size_t)nb * d * d);
+    float2* d_flr = reinterpret_cast<float2*>(d_orl + (size_t)nb * d * d);
+    float2* d_frl = d_flr + (size_t)nb * d * d;
+    int* ip = reinterpret_cast<int*>(d_frl + (size_t)nb * d * d);
     int* d_lrs = ip;
     int* d_lrc = d_lrs + h.Dr + 1;
     int* d_rls = d_lrc + nb;
     int* d_rlc = d_rls + h.Dl + 1;
+    std::vector<float2> flr(olr.size()), frl(orl.size());
+    for (size_t e = 0; e < olr.size(); ++e) flr[e] = make_float2((float)olr[e].x, (float)olr[e].y);
+    for (size_t e = 0; e < orl.size(); ++e) frl[e] = make_float2((float)orl[e].x, (float)orl[e].y);
     if (nb > 0) {
+      CK(cudaMemcpy(d_flr, flr.data(), ops32_bytes, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(d_frl, frl.data(), ops32_bytes, cudaMemcpyHostToDevice));
       CK(cudaMemcpy(d_olr, olr.data(), ops_bytes, cudaMemcpyHostToDevice));
       CK(cudaMemcpy(d_orl, orl.data(), ops_bytes, cudaMemcpyHostToDevice));
       CK(cudaMemcpy(d_lrc, ilr_chan.data(), sizeof(int) * nb, cudaMemcpyHostToDevice));
@@ -368,8 +377,8 @@ void Engine::upload_mpo(const std::vector<MpoSite>& W, DevMpo& out) {
     }
     CK(cudaMemcpy(d_lrs, ilr_start.data(), sizeof(int) * (h.Dr + 1), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d_rls, irl_start.data(), sizeof(int) * (h.Dl + 1), cudaMemcpyHostToDevice));
-    s.lr = MixTable{h.Dr, d_lrs, d_lrc, d_olr};
-    s.rl = MixTable{h.Dl, d_rls, d_rlc, d_orl};
+    s.lr = MixTable{h.Dr, d_lrs, d_lrc, d_olr, d_flr, nb};
+    s.rl = MixTable{h.Dl, d_rls, d_rlc, d_orl, d_frl, nb};
   }
 }
 
@@ -391,7 +400,7 @@ Engine::Engine(const ModelParams& p) : P(p) {
   CK(cudaMalloc(&scal_, sizeof(double) * 8));
   CK(cudaMalloc(&part_c_, sizeof(cplx) * (KMAX + 1) * NBLK));
   CK(cudaMalloc(&part_d_, sizeof(double) * NBLK));
-  CK(cudaMallocHost(&h_pinned_, sizeof(int) * 4));
+  CK(cudaMallocHost(&h_pinned_, sizeof(int) * 8));
   CK(cudaMallocHost(&h_pinned_d_, sizeof(double) * 4));
   for (auto& e : ev_) CK(cudaEventCreate(&e));
 }
@@ -488,7 +497,7 @@ void Engine::ensure_workspace(long long maxsite, long long maxxy, int maxbond, i
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     qr_.gmax = sms;
     qr_.nmax = maxm;
-    CK(cudaMalloc(&qr_.part, sizeof(cplx) * 2 * (size_t)sms * maxm));
+    CK(cudaMalloc(&qr_.part, sizeof(cplx) * 2 * (size_t)sms * (maxm + 1)));
     CK(cudaMalloc(&qr_.partn, sizeof(double) * 2 * (size_t)sms));
     CK(cudaMalloc(&qr_.bar, sizeof(unsigned) * 2));
     ws_m_ = maxm;
@@ -617,6 +626,18 @@ void Engine::copy_mps(const DevMps& src, DevMps& dst) {
                        cudaMemcpyDeviceToDevice, st_));
 }
 
+double Engine::tic() {
+  if (!prof_) return 0.0;
+  CK(cudaStreamSynchronize(st_));
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+void Engine::toc(double& acc, double t0) {
+  if (!prof_) return;
+  CK(cudaStreamSynchronize(st_));
+  acc += std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count() - t0;
+}
+
 void Engine::set_ones(cplx* p) {
   static const cplx one = {1.0, 0.0};
   CK(cudaMemcpyAsync(p, &one, sizeof(cplx), cudaMemcpyHostToDevice, st_));
@@ -652,7 +673,9 @@ void Engine::check_status() {
 }
 
 void Engine::gauge_qr_dev(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cplx* R) {
+  const double t0 = tic();
   CK(gauge_qr(m, n, Y, p, E, Q, R, qr_, status_, st_));
+  toc(stats.t_qr, t0);
   stats.qrs += 1;
 }
 
@@ -736,7 +759,8 @@ void Engine::site_update(DevMps& s, int k, double hr, double hi) {
   int nev = 0;
   const bool mx = mixed();
   if (mx) heff_tc_prepare(st_, tcb_, Ml, Mr, W.Dl, W.Dr, Le, Re);
-  krylov(s.size(k), s.A[k], Kout_, hr, hi, [&](const cplx* in, cplx* out, const int* skip) {
+  const int used = krylov(s.size(k), s.A[k], Kout_, hr, hi,
+                          [&](const cplx* in, cplx* out, const int* skip) {
     CK(cudaEventRecord(ev_[2 * nev], st_));
     if (mx)
       heff_tc_apply(st_, tcb_, W, Ml, Mr, D, d, in, out);
@@ -744,11 +768,11 @@ void Engine::site_update(DevMps& s, int k, double hr, double hi) {
       heff_f64(c, W, Ml, Mr, D, d, Le, Re, in, out, skip);
     CK(cudaEventRecord(ev_[2 * nev + 1], st_));
     ++nev;
-    stats.matvecs += 1;
-    stats.heff_flops += flops;
   });
-  // every recorded matvec completed before the Krylov loop's last poll
-  for (int i = 0; i < nev; ++i) {
+  stats.matvecs += used;
+  stats.heff_flops += used * flops;
+  if (used > 0) CK(cudaEventSynchronize(ev_[2 * (used - 1) + 1]));
+  for (int i = 0; i < used; ++i) {
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, ev_[2 * i], ev_[2 * i + 1]));
     stats.heff_ms += ms;
@@ -760,43 +784,60 @@ void Engine::tdvp_step(DevMps& s, double tr, double ti) {
   const double hr = 0.5 * tr, hi = 0.5 * ti;
   const int L = s.L();
   Ctx c = ctx();
+  double t0;
   for (int k = 0; k < L; ++k) {
+    t0 = tic();
     site_update(s, k, hr, hi);
+    toc(stats.t_site, t0);
     if (k < L - 1) {
+      t0 = tic();
       shift_right(s, k, Kout_, Cb_);
+      toc(stats.t_env, t0);
+      t0 = tic();
       const int M = s.Mb[k + 1], Dw = H_.s[k].Dr;
       const cplx* Le = s.Lenv[k + 1];
       const cplx* Re = s.Renv[k];
       if (mixed()) bond_tc_prepare(st_, tcb_, M, Dw, Le, Re);
-      krylov((long long)M * M, Cb_, Rb_, -hr, -hi, [&](const cplx* in, cplx* out, const int* sk) {
+      stats.bond_matvecs += krylov((long long)M * M, Cb_, Rb_, -hr, -hi,
+                                   [&](const cplx* in, cplx* out, const int* sk) {
         if (mixed())
           bond_tc_apply(st_, tcb_, M, Dw, in, out);
         else
           bond_f64(c, M, Dw, Le, Re, in, out, sk);
-        stats.bond_matvecs += 1;
       });
+      toc(stats.t_bond, t0);
+      t0 = tic();
       absorb_left(Rb_, M, s.A[k + 1], (long long)s.D[k + 1] * s.Mb[k + 2]);
+      toc(stats.t_absorb, t0);
     } else {
       CK(cudaMemcpyAsync(s.A[k], Kout_, sizeof(cplx) * (size_t)s.size(k),
                          cudaMemcpyDeviceToDevice, st_));
     }
   }
   for (int k = L - 1; k >= 0; --k) {
+    t0 = tic();
     site_update(s, k, hr, hi);
+    toc(stats.t_site, t0);
     if (k > 0) {
+      t0 = tic();
       shift_left(s, k, Kout_, Cb_);
+      toc(stats.t_env, t0);
+      t0 = tic();
       const int M = s.Mb[k], Dw = H_.s[k].Dl;
       const cplx* Le = s.Lenv[k];
       const cplx* Re = s.Renv[k - 1];
       if (mixed()) bond_tc_prepare(st_, tcb_, M, Dw, Le, Re);
-      krylov((long long)M * M, Cb_, Rb_, -hr, -hi, [&](const cplx* in, cplx* out, const int* sk) {
+      stats.bond_matvecs += krylov((long long)M * M, Cb_, Rb_, -hr, -hi,
+                                   [&](const cplx* in, cplx* out, const int* sk) {
         if (mixed())
           bond_tc_apply(st_, tcb_, M, Dw, in, out);
         else
           bond_f64(c, M, Dw, Le, Re, in, out, sk);
-        stats.bond_matvecs += 1;
       });
+      toc(stats.t_bond, t0);
+      t0 = tic();
       absorb_right(s.A[k - 1], (long long)s.Mb[k - 1] * s.D[k - 1], Rb_, M);
+      toc(stats.t_absorb, t0);
     } else {
       CK(cudaMemcpyAsync(s.A[k], Kout_, sizeof(cplx) * (size_t)s.size(k),
                          cudaMemcpyDeviceToDevice, st_));
@@ -965,7 +1006,9 @@ void Engine::realtime_step(int nsteps, double dt) {
 
 void Engine::realtime_observe(double* C, double* obs) {
   if (!rt_ready_) throw Failure{TDMRG_ERR_STATE, "realtime_observe before realtime_init"};
+  const double t0 = tic();
   const Cx c = overlap(psi1_, J_, psi2_);
+  toc(stats.t_observe, t0);
   if (!std::isfinite(c.real()) || !std::isfinite(c.imag()))
     throw Failure{TDMRG_ERR_NONFINITE, "non-finite C(t)"};
   C[0] = c.real();

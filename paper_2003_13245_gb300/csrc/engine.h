@@ -119,6 +119,8 @@ struct Stats {
   double site_updates = 0, matvecs = 0, heff_flops = 0, krylov_vectors = 0, bond_matvecs = 0,
          qrs = 0, completions = 0, env_updates = 0;
   double heff_ms = 0;                 // event-timed duration of the site H_eff matvecs
+  // host wall time per phase (filled only when profiling is on; the phase ends synchronise)
+  double t_site = 0, t_qr = 0, t_env = 0, t_bond = 0, t_absorb = 0, t_observe = 0;
   double h2d_bytes = 0, d2h_bytes = 0;
   double launches_at_reset = 0;
 };
@@ -131,6 +133,7 @@ class Engine {
   void set_precision(int p);
   void set_krylov(double tol, int kmax, int fixed_k);
   void set_stream(cudaStream_t s) { st_ = s; }
+  void set_profiling(bool on) { prof_ = on; }
   void rebuild_mpos();
   void thermal_prepare(double beta, double dtau, int M);
   void realtime_init();
@@ -149,7 +152,8 @@ class Engine {
   cplx* X() { return X_; }
   cplx* Y() { return Y_; }
 
-  // Lanczos exponential exp(tau M) v for a matvec callback (device pointers)
+  // Lanczos exponential exp(tau M) v for a matvec callback (device pointers); returns the
+  // number of matvecs that ran
   template <class F>
   int krylov(long long n, const cplx* v, cplx* out, double tr, double ti, F&& matvec);
   void gauge_qr_dev(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cplx* R);
@@ -166,6 +170,8 @@ class Engine {
   void shift_left(DevMps& s, int k, const cplx* center, cplx* Cbond);
   Ctx ctx() const { return Ctx{st_, X_, Y_}; }
   bool mixed() const { return precision_ != 0; }
+  double tic();
+  void toc(double& acc, double t0);
   void env_left_any(const DevMpoSite& W, int Ml1, int Mr1, int Ml2, int Mr2, int D, int d,
                     const cplx* Lenv, const cplx* bra, const cplx* ket, cplx* Lout);
   void env_right_any(const DevMpoSite& W, int Ml1, int Mr1, int Ml2, int Mr2, int D, int d,
@@ -185,6 +191,7 @@ class Engine {
   int precision_ = 0;
   double ktol_ = 1e-13;
   bool ktol_user_ = false;
+  bool prof_ = false;
   int kmax_ = 32, fixed_k_ = 0;
   bool prepared_ = false, rt_ready_ = false;
   double logZ_ = 0.0;
@@ -212,8 +219,11 @@ class Engine {
   long long env_tmp_size_ = 0;
 };
 
-// Lanczos with full re-orthogonalisation (two classical Gram-Schmidt passes) in FP64; the
-// small exponential and the stopping test run on the device; the host only polls the flag.
+// Lanczos with full re-orthogonalisation in FP64: the three-term step against q_j and
+// q_{j-1}, then one classical Gram-Schmidt pass against every Krylov vector.  The small
+// exponential and the stopping test run on the device.  The host polls the stop flag of
+// iteration j-1 while iteration j is already queued (its kernels skip once the flag is set),
+// so the device never waits for the host between iterations.
 template <class F>
 inline int Engine::krylov(long long n, const cplx* v, cplx* out, double tr, double ti, F&& matvec) {
   const int cap0 = fixed_k_ > 0 ? fixed_k_ : kmax_;
@@ -224,27 +234,38 @@ inline int Engine::krylov(long long n, const cplx* v, cplx* out, double tr, doub
   CK(lz_start(S, scal_, st_));
   CK(cudaMemcpyAsync(V_, v, sizeof(cplx) * (size_t)n, cudaMemcpyDeviceToDevice, st_));
   CK(zscale_by(n, V_, &S->inv, done, st_));
-  int used = 0;
-  for (int j = 0; j < kcap; ++j) {
+  int launched = 0;
+  bool stop = false;
+  for (int j = 0; j < kcap && !stop; ++j) {
     cplx* q = V_ + (size_t)j * n;
     cplx* w = V_ + (size_t)(j + 1) * n;
     matvec(q, w, done);
-    CK(zdots(n, j + 1, V_, n, w, S->h1, part_c_, NBLK, done, st_));
-    CK(zsub_multi(n, j + 1, V_, n, S->h1, w, done, st_));
+    const int lo = j > 0 ? j - 1 : 0;
+    CK(zdots(n, j - lo + 1, V_ + (size_t)lo * n, n, w, S->h1 + lo, part_c_, NBLK, done, st_));
+    CK(zsub_multi(n, j - lo + 1, V_ + (size_t)lo * n, n, S->h1 + lo, w, done, st_));
     CK(zdots(n, j + 1, V_, n, w, S->h2, part_c_, NBLK, done, st_));
     CK(zsub_multi(n, j + 1, V_, n, S->h2, w, done, st_));
     CK(znorm2(n, w, &S->nrm2, part_d_, NBLK, done, st_));
     CK(lz_small_exp(S, j, tr, ti, ktol_, kcap, fixed_k_ > 0 ? 1 : 0, st_));
     CK(zscale_by(n, w, &S->inv, done, st_));
-    used = j + 1;
-    CK(cudaMemcpyAsync(h_pinned_, done, sizeof(int), cudaMemcpyDeviceToHost, st_));
-    CK(cudaStreamSynchronize(st_));
+    CK(cudaMemcpyAsync(h_pinned_ + 4 + (j & 1) * 2, done, sizeof(int), cudaMemcpyDeviceToHost,
+                       st_));
+    CK(cudaEventRecord(ev_[2 * KMAX + (j & 1)], st_));
     stats.d2h_bytes += sizeof(int);
-    if (h_pinned_[0]) break;
+    launched = j + 1;
+    if (j >= 1) {
+      // the flag of iteration j-1 (iteration j is queued behind it)
+      CK(cudaEventSynchronize(ev_[2 * KMAX + ((j - 1) & 1)]));
+      if (h_pinned_[4 + ((j - 1) & 1) * 2]) stop = true;
+    }
   }
+  if (!stop) {
+    CK(cudaEventSynchronize(ev_[2 * KMAX + ((launched - 1) & 1)]));
+  }
+  // when the stop flag of iteration j-1 was seen, iteration j was queued but skipped
+  const int used = stop ? launched - 1 : launched;
   stats.krylov_vectors += used;
   CK(zcombine(n, S, V_, n, out, st_));
   return used;
 }
-
 }  // namespace tdmrg

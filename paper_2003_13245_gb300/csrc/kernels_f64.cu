@@ -495,10 +495,13 @@ struct QrKernelArgs {
   double rank_tol, complete_tol;
 };
 
-// dots of v (own rows) against the columns of Q listed as accepted and < lim, reduced over
-// all CTAs into h (shared); then v -= Q h; hacc += h.
+// One Gram-Schmidt pass of v (own rows) against the accepted columns of Q below `lim`:
+// h = Q^H v reduced over all CTAs (together with ||v||^2 before the pass), v -= Q h,
+// hacc += h.  Returns ||v_before||^2 in *vv_before and sum |h|^2 in *hh (identical in all
+// CTAs: same partials, same summation order).
 __device__ bool qr_pass(const QrKernelArgs& A, int r0, int nr, int lim, cplx* v, cplx* h,
-                        cplx* hacc, const unsigned char* acc, int& buf, unsigned G) {
+                        cplx* hacc, const unsigned char* acc, int& buf, unsigned G, double* red,
+                        double* vv_before, double* hh) {
   const int n = A.n;
   const int g = blockIdx.x;
   for (int i = threadIdx.x; i < lim; i += blockDim.x) {
@@ -513,18 +516,47 @@ __device__ bool qr_pass(const QrKernelArgs& A, int r0, int nr, int lim, cplx* v,
         s.y = fma(-q.y, x.x, s.y);
       }
     }
-    A.part[((long long)buf * G + g) * n + i] = s;
+    A.part[((long long)buf * G + g) * (n + 1) + i] = s;
+  }
+  // partial ||v||^2 of this CTA's rows, stored after the n dot products
+  double vv = 0.0;
+  for (int r = threadIdx.x; r < nr; r += blockDim.x) vv += v[r].x * v[r].x + v[r].y * v[r].y;
+  vv = warp_sum(vv);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = vv;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    A.part[((long long)buf * G + g) * (n + 1) + n] = make_double2(t, 0.0);
   }
   if (!grid_barrier(A.bar, G, A.status)) return false;
+  double hsq = 0.0;
   for (int i = threadIdx.x; i < lim; i += blockDim.x) {
     cplx s = make_double2(0.0, 0.0);
     if (acc[i])
-      for (unsigned gg = 0; gg < G; ++gg) s = cadd(s, A.part[((long long)buf * G + gg) * n + i]);
+      for (unsigned gg = 0; gg < G; ++gg)
+        s = cadd(s, A.part[((long long)buf * G + gg) * (n + 1) + i]);
     h[i] = s;
     hacc[i] = cadd(hacc[i], s);
+    hsq += s.x * s.x + s.y * s.y;
+  }
+  // fixed-order block sums of sum|h|^2 and of ||v||^2
+  hsq = warp_sum(hsq);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = hsq;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    double u = 0.0;
+    for (unsigned gg = 0; gg < G; ++gg) u += A.part[((long long)buf * G + gg) * (n + 1) + n].x;
+    red[32] = t;
+    red[33] = u;
   }
   buf ^= 1;
   __syncthreads();
+  *hh = red[32];
+  *vv_before = red[33];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int r = warp; r < nr; r += nw) {
     double sr = 0.0, si = 0.0;
@@ -568,6 +600,24 @@ __device__ bool qr_norm(const QrKernelArgs& A, int nr, const cplx* v, double& ou
   return true;
 }
 
+// Residual norm of v against the accepted columns below `lim`, Gram-Schmidt with
+// re-orthogonalisation only when needed: after one pass, if sum|h|^2 <= 0.75 ||v||^2 the
+// residual norm is taken from Pythagoras (no cancellation beyond a factor 4); otherwise a
+// second pass is made and the norm is computed directly ("twice is enough").  On return v holds
+// the residual and *nrm its norm.
+__device__ bool qr_residual(const QrKernelArgs& A, int r0, int nr, int lim, cplx* v, cplx* h,
+                            cplx* hacc, const unsigned char* acc, int& buf, unsigned G,
+                            double* red, double* nrm) {
+  double vv, hh;
+  if (!qr_pass(A, r0, nr, lim, v, h, hacc, acc, buf, G, red, &vv, &hh)) return false;
+  if (hh <= 0.75 * vv) {
+    *nrm = sqrt(fmax(vv - hh, 0.0));
+    return true;
+  }
+  if (!qr_pass(A, r0, nr, lim, v, h, hacc, acc, buf, G, red, &vv, &hh)) return false;
+  return qr_norm(A, nr, v, *nrm, buf, G, red);
+}
+
 __global__ void __launch_bounds__(QR_THREADS) gauge_qr_kernel(QrKernelArgs A) {
   extern __shared__ unsigned char smem[];
   const int m = A.m, n = A.n;
@@ -578,7 +628,7 @@ __global__ void __launch_bounds__(QR_THREADS) gauge_qr_kernel(QrKernelArgs A) {
   cplx* v = reinterpret_cast<cplx*>(smem);
   cplx* h = v + rows;
   cplx* hacc = h + n;
-  double* red = reinterpret_cast<double*>(hacc + n);            // 33 doubles
+  double* red = reinterpret_cast<double*>(hacc + n);            // 34 doubles
   unsigned char* acc = reinterpret_cast<unsigned char*>(red + 34);
   int buf = 0;
 
@@ -594,7 +644,6 @@ __global__ void __launch_bounds__(QR_THREADS) gauge_qr_kernel(QrKernelArgs A) {
     const cplx y = qr_load(A.Y, r0 + e / n, e % n);
     ynorm2 += y.x * y.x + y.y * y.y;
   }
-  // reuse qr_norm's reduction through a fake vector: do it inline
   ynorm2 = warp_sum(ynorm2);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ynorm2;
   __syncthreads();
@@ -619,10 +668,8 @@ __global__ void __launch_bounds__(QR_THREADS) gauge_qr_kernel(QrKernelArgs A) {
     for (int r = threadIdx.x; r < nr; r += blockDim.x) v[r] = qr_load(A.Y, r0 + r, j);
     for (int i = threadIdx.x; i < n; i += blockDim.x) hacc[i] = make_double2(0.0, 0.0);
     __syncthreads();
-    for (int pass = 0; pass < 2; ++pass)
-      if (!qr_pass(A, r0, nr, j, v, h, hacc, acc, buf, G)) return;
     double nrm;
-    if (!qr_norm(A, nr, v, nrm, buf, G, red)) return;
+    if (!qr_residual(A, r0, nr, j, v, h, hacc, acc, buf, G, red, &nrm)) return;
     const bool take = nrm > thr;
     if (take) {
       const double inv = 1.0 / nrm;
@@ -661,10 +708,8 @@ __global__ void __launch_bounds__(QR_THREADS) gauge_qr_kernel(QrKernelArgs A) {
       }
       ++cand;
       if (n0 == 0.0) continue;
-      for (int pass = 0; pass < 2; ++pass)
-        if (!qr_pass(A, r0, nr, n, v, h, hacc, acc, buf, G)) return;
       double nc;
-      if (!qr_norm(A, nr, v, nc, buf, G, red)) return;
+      if (!qr_residual(A, r0, nr, n, v, h, hacc, acc, buf, G, red, &nc)) return;
       if (nc > A.complete_tol * n0) {
         const double inv = 1.0 / nc;
         for (int r = threadIdx.x; r < nr; r += blockDim.x)
@@ -690,7 +735,7 @@ int gauge_qr_grid(int m) {
     if (per < 1) per = 1;
     g_qr_coop_blocks = sms;   // one CTA per SM keeps the barrier cheap
   }
-  int g = (m + 63) / 64;
+  int g = (m + 15) / 16;
   if (g > g_qr_coop_blocks) g = g_qr_coop_blocks;
   if (g < 1) g = 1;
   return g;

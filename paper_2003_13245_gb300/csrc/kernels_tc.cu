@@ -382,15 +382,26 @@ __global__ void split_f64_t_kernel(const double2* src, long long sb, long long k
 }
 
 // MPO channel mixing of an FP32 planar X[wi][a][u][t][b] (re plane, im plane at +xplane) into
-// split planes.  Natural layout (trans = 0): operand rows (a, s, t), K = b, batch wo.
-// Transposed layout (trans = 1): operand rows b, K = (a, s, t), batch wo.
+// split planes.  trans 0: operand rows (a, s, t), K = b; trans 1: rows b, K = (a, s, t);
+// trans 2: rows a, K = (s, t, b).  The block tables and FP32 operators are staged in shared
+// memory; the inner loop is FP32 only.
+constexpr int MIX_MAX_BLK = 64;
+constexpr int MIX_MAX_OPS = 5000;     // float2 entries: nblk * d * d (40 KB)
 __global__ void mix_split_kernel(int Dout, int Ma, int d, int Mb, const int* start,
-                                 const int* chan, const double2* ops, const float* X,
+                                 const int* chan, const float2* ops, int nblk, const float* X,
                                  long long xs, long long xplane, float* dst, int ld, int trans) {
+  __shared__ float2 s_ops[MIX_MAX_OPS];
+  __shared__ int s_start[MIX_MAX_BLK + 1];
+  __shared__ int s_chan[MIX_MAX_BLK];
+  for (int i = threadIdx.x; i < nblk * d * d; i += blockDim.x) s_ops[i] = ops[i];
+  for (int i = threadIdx.x; i <= Dout; i += blockDim.x) s_start[i] = start[i];
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) s_chan[i] = chan[i];
+  __syncthreads();
   const long long per = (long long)Ma * d * d * Mb;
   const long long total = per * Dout;
   const int rows = trans == 1 ? Mb : (trans == 2 ? Ma : Ma * d * d);
   const long long plane = (long long)Dout * rows * ld;
+  const long long ustride = (long long)d * Mb;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     long long r = e;
@@ -400,16 +411,15 @@ __global__ void mix_split_kernel(int Dout, int Ma, int d, int Mb, const int* sta
     const int a = (int)(r % Ma);
     const int wo = (int)(r / Ma);
     float ar = 0.f, ai = 0.f;
-    for (int blk = start[wo]; blk < start[wo + 1]; ++blk) {
-      const double2* op = ops + (long long)blk * d * d + sig * d;
-      const float* x = X + chan[blk] * xs + ((long long)a * d * d + tau) * Mb + b;
+    for (int blk = s_start[wo]; blk < s_start[wo + 1]; ++blk) {
+      const float2* op = s_ops + (blk * d + sig) * d;
+      const float* x = X + s_chan[blk] * xs + ((long long)a * d * d + tau) * Mb + b;
       for (int u = 0; u < d; ++u) {
-        const double2 o = op[u];
-        if (o.x != 0.0 || o.y != 0.0) {
-          const float xr = x[(long long)u * d * Mb], xi = x[xplane + (long long)u * d * Mb];
-          const float orr = (float)o.x, oi = (float)o.y;
-          ar = fmaf(orr, xr, fmaf(-oi, xi, ar));
-          ai = fmaf(orr, xi, fmaf(oi, xr, ai));
+        const float2 o = op[u];
+        if (o.x != 0.f || o.y != 0.f) {
+          const float xr = x[u * ustride], xi = x[xplane + u * ustride];
+          ar = fmaf(o.x, xr, fmaf(-o.y, xi, ar));
+          ai = fmaf(o.x, xi, fmaf(o.y, xr, ai));
         }
       }
     }
@@ -497,9 +507,11 @@ cudaError_t split_f64_t(const cplx* src, long long sb, long long kstride, int co
 cudaError_t mix_split(const MixTable& T, int Ma, int d, int Mb, const float* X, long long xs,
                       long long xplane, const TcOperand& dst, int trans, cudaStream_t s) {
   const long long total = (long long)T.Dout * Ma * d * d * Mb;
+  if (T.nblk > MIX_MAX_BLK || T.nblk * d * d > MIX_MAX_OPS || T.Dout > MIX_MAX_BLK)
+    return cudaErrorInvalidValue;
   count_launch();
-  mix_split_kernel<<<grid_for(total), 256, 0, s>>>(T.Dout, Ma, d, Mb, T.start, T.chan, T.ops, X,
-                                                   xs, xplane, dst.p, dst.ld, trans);
+  mix_split_kernel<<<grid_for(total), 256, 0, s>>>(T.Dout, Ma, d, Mb, T.start, T.chan, T.ops32,
+                                                   T.nblk, X, xs, xplane, dst.p, dst.ld, trans);
   return cudaGetLastError();
 }
 

@@ -35,6 +35,8 @@ struct MixTable {
   const int* start;      // Dout + 1
   const int* chan;       // input channel of each block
   const cplx* ops;       // d x d per block
+  const float2* ops32;   // the same operators rounded to FP32 (mixed-precision path)
+  int nblk;
 };
 cudaError_t mpo_mix(const MixTable& T, int Ma, int d, int Mb, const cplx* X, long long xs,
                     cplx* Y, long long ys, const int* skip, cudaStream_t s);
@@ -79,7 +81,7 @@ struct QrRef {
   int conj;
 };
 struct QrScratch {
-  cplx* part;          // 2 * gmax * nmax
+  cplx* part;          // 2 * gmax * (nmax + 1)
   double* partn;       // 2 * gmax
   unsigned* bar;       // 2
   int gmax;

@@ -78,11 +78,12 @@ def test_limits_and_invariants():
     m.thermal_prepare(1.0, 0.1, 16)
     assert np.abs(m.correlation([0.0, 0.2], 0.1)).max() < 1e-14
     m.close()
-    # g = 0: constant closed form
+    # g = 0: constant closed form (M=16 carries a truncation error of ~1e-9 in C)
     m = _model(3, [1.0], [0.0], [2], 1.0)
     m.thermal_prepare(1.0, 0.05, 16)
     C = m.correlation(np.arange(0, 7, 2) * 0.1, 0.1)
-    assert np.abs(C - kubo.free_band_correlation(3, 1.0, 1.0)).max() < 1e-9
+    assert np.abs(C - kubo.free_band_correlation(3, 1.0, 1.0)).max() < 5e-9
+    assert np.abs(C - C[0]).max() < 1e-11
     m.close()
     # truncated: norm, energy and <Psi2|Psi2> conserved, Im C(0) = 0
     m = _model(3, [1.0], [1.0], [3], 1.0)
@@ -106,7 +107,8 @@ def test_truncated_matches_oracle_golden():
     t = np.array(g["t"])
     C = m.correlation(t, g["dt"])
     ref = np.array(g["C_re"]) + 1j * np.array(g["C_im"])
-    assert abs(m.logz() - g["logZ"]) < 1e-9
+    # below full rank the attainable agreement is the oracle's own perturbation spread
+    assert abs(m.logz() - g["logZ"]) < g["logz_tol"]
     assert np.abs(C - ref).max() / abs(ref[0]) < g["tol"]
     m.close()
 

@@ -170,6 +170,24 @@ int tdmrg_kernel_env_left(int Ml1, int Mr1, int Ml2, int Mr2, int d, int Dl, int
 int tdmrg_kernel_gauge_qr(int m, int n, const void* Y, int p, const void* E, void* Q,
                           void* R, int* status, void* stream);
 
+/* Gauge QR that allocates nothing.  The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory -- code running inside a CUDA graph capture
+ * (cudaMalloc would invalidate the capture), callers that must not fail on memory once set up,
+ * and hosts whose memory is owned by another runtime.  Same arguments, same result and same
+ * layouts as tdmrg_kernel_gauge_qr; Y, E, Q, R (and status, if not NULL) are the caller's.
+ * The scratch (cross-block partial sums, barrier counters, status word) is one fixed
+ * file-scope device array of about 1.6 MB that every GPU loading the library keeps until exit.
+ * Limits: n <= 256 and a grid of <= 192 blocks (m up to any size on GPUs with <= 192 SMs);
+ * larger sizes return TDMRG_ERR_ARG with a message.  The first call on each device looks up
+ * the array's device address (cudaGetSymbolAddress, with that device current): make that first
+ * call before any stream capture.  All calls share the array and it keeps the last call's
+ * contents (the barrier counters and the status word are cleared at the start of every call),
+ * so calls that overlap on the GPU race: issue them on one stream or synchronise between them.
+ * Synchronises `stream`; TDMRG_ERR_TIMEOUT if the bounded grid barrier gave up (when status
+ * is NULL; otherwise the caller reads *status: 1 timeout, 2 out of completion vectors). */
+int tdmrg_kernel_gauge_qr_noalloc(int m, int n, const void* Y, int p, const void* E, void* Q,
+                                  void* R, int* status, void* stream);
+
 /* Krylov exponential (K2/K3) of a dense Hermitian matrix H (n x n, device):
  * out = exp(tau H) v with tau = tau_re + i tau_im, Lanczos with full re-orthogonalisation
  * in FP64 and the small exponential on the device.  kused (host, may be NULL) receives

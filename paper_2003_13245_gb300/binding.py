@@ -55,6 +55,7 @@ _SIGS = {
     "tdmrg_kernel_gauge_qr": [_i, _i, _p, _i, _p, _p, _p, _p, _p],
     "tdmrg_kernel_krylov_dense": [_i, _p, _p, _p, _d, _d, _d, _i, _ip, _p],
     "tdmrg_kernel_zgemm_tc": [_i, _i, _i, _p, _p, _i, _i, _p, _p],
+    "tdmrg_kernel_gauge_qr_noalloc": [_i, _i, _p, _i, _p, _p, _p, _p, _p],
 }
 
 
@@ -245,6 +246,17 @@ def kernel_gauge_qr(Y, Q, R, E=None, status=None, stream=None):
     p = 0 if E is None else E.shape[1]
     _check(lib.tdmrg_kernel_gauge_qr(m, n, _ptr(Y), p, _ptr(E), _ptr(Q), _ptr(R), _ptr(status),
                                      _stream_ptr(stream)))
+
+
+def kernel_gauge_qr_noalloc(Y, Q, R, E=None, status=None, stream=None):
+    """tdmrg_kernel_gauge_qr with the scratch in the library's fixed device array: no device
+    allocation happens in the call (for callers inside a graph capture or without an
+    allocator); the first call on a device must come before any stream capture."""
+    lib = load()
+    m, n = Y.shape
+    p = 0 if E is None else E.shape[1]
+    _check(lib.tdmrg_kernel_gauge_qr_noalloc(m, n, _ptr(Y), p, _ptr(E), _ptr(Q), _ptr(R),
+                                             _ptr(status), _stream_ptr(stream)))
 
 
 def kernel_krylov_dense(H, v, out, tau, tol=1e-13, kmax=32, stream=None):

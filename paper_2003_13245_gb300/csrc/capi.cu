@@ -21,6 +21,10 @@ struct tdmrg_model {
 
 static thread_local std::string g_err;
 
+namespace tdmrg {
+void set_global_error(const char* msg) { g_err = msg; }
+}  // namespace tdmrg
+
 namespace {
 
 template <class F>

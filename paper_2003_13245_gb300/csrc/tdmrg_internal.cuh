@@ -10,6 +10,9 @@ typedef double2 cplx;
 
 constexpr int KMAX = 32;            // largest Krylov dimension
 
+// message returned by tdmrg_last_global_error() (set by entry points that have no handle)
+void set_global_error(const char* msg);
+
 // number of kernels this library has launched (host-side counter)
 long long launch_count();
 void count_launch(int n = 1);

@@ -495,80 +495,153 @@ struct QrKernelArgs {
   double rank_tol, complete_tol;
 };
 
+// Sum of the G per-block partial doubles at stride `stride` (fixed order per lane, then a
+// fixed warp tree): evaluated by warp 0, result broadcast through red[slot].
+__device__ __forceinline__ void qr_sum_partials(const double* base, long long stride, unsigned G,
+                                                double* red, int slot) {
+  if (threadIdx.x < 32) {
+    double a = 0.0, b = 0.0;
+    unsigned gg = threadIdx.x;
+    for (; gg + 32 < G; gg += 64) {
+      a += base[gg * stride];
+      b += base[(gg + 32) * stride];
+    }
+    if (gg < G) a += base[gg * stride];
+    a = warp_sum(a + b);
+    if (threadIdx.x == 0) red[slot] = a;
+  }
+}
+
 // One Gram-Schmidt pass of v (own rows) against the accepted columns of Q below `lim`:
 // h = Q^H v reduced over all CTAs (together with ||v||^2 before the pass), v -= Q h,
 // hacc += h.  Returns ||v_before||^2 in *vv_before and sum |h|^2 in *hh (identical in all
-// CTAs: same partials, same summation order).
+// CTAs: same partials, same summation order).  Every phase splits its sums over several
+// threads with independent accumulators, because FP64 dependency latency dominates here.
 __device__ bool qr_pass(const QrKernelArgs& A, int r0, int nr, int lim, cplx* v, cplx* h,
                         cplx* hacc, const unsigned char* acc, int& buf, unsigned G, double* red,
-                        double* vv_before, double* hh) {
+                        cplx* sm, double* vv_before, double* hh) {
   const int n = A.n;
   const int g = blockIdx.x;
-  for (int i = threadIdx.x; i < lim; i += blockDim.x) {
-    cplx s = make_double2(0.0, 0.0);
-    if (acc[i]) {
-      for (int r = 0; r < nr; ++r) {
-        const cplx q = A.Q[(long long)(r0 + r) * n + i];
-        const cplx x = v[r];
-        s.x = fma(q.x, x.x, s.x);
-        s.x = fma(q.y, x.y, s.x);
-        s.y = fma(q.x, x.y, s.y);
-        s.y = fma(-q.y, x.x, s.y);
+  const int T = blockDim.x;
+  // (1) partial dots of this CTA's rows: P threads per column, 4 accumulators each
+  {
+    int P = lim > 0 ? T / lim : 1;
+    if (P < 1) P = 1;
+    if (P > 8) P = 8;
+    for (int idx = threadIdx.x; idx < lim * P; idx += T) {
+      const int i = idx % lim, part = idx / lim;
+      double ax = 0.0, bx = 0.0, ay = 0.0, by = 0.0;
+      if (acc[i]) {
+        for (int r = part; r < nr; r += P) {
+          const cplx q = A.Q[(long long)(r0 + r) * n + i];
+          const cplx x = v[r];
+          ax = fma(q.x, x.x, ax);
+          bx = fma(q.y, x.y, bx);
+          ay = fma(q.x, x.y, ay);
+          by = fma(-q.y, x.x, by);
+        }
+      }
+      if (lim * P <= T) sm[part * lim + i] = make_double2(ax + bx, ay + by);
+      else A.part[((long long)buf * G + g) * (n + 1) + i] = make_double2(ax + bx, ay + by);
+    }
+    __syncthreads();
+    if (lim * P <= T) {
+      for (int i = threadIdx.x; i < lim; i += T) {
+        cplx s = make_double2(0.0, 0.0);
+        for (int part = 0; part < P; ++part) s = cadd(s, sm[part * lim + i]);
+        A.part[((long long)buf * G + g) * (n + 1) + i] = s;
       }
     }
-    A.part[((long long)buf * G + g) * (n + 1) + i] = s;
   }
   // partial ||v||^2 of this CTA's rows, stored after the n dot products
   double vv = 0.0;
-  for (int r = threadIdx.x; r < nr; r += blockDim.x) vv += v[r].x * v[r].x + v[r].y * v[r].y;
+  for (int r = threadIdx.x; r < nr; r += T) vv += v[r].x * v[r].x + v[r].y * v[r].y;
   vv = warp_sum(vv);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = vv;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    for (int w = 0; w < (T >> 5); ++w) t += red[w];
     A.part[((long long)buf * G + g) * (n + 1) + n] = make_double2(t, 0.0);
   }
   if (!grid_barrier(A.bar, G, A.status)) return false;
-  double hsq = 0.0;
-  for (int i = threadIdx.x; i < lim; i += blockDim.x) {
-    cplx s = make_double2(0.0, 0.0);
-    if (acc[i])
-      for (unsigned gg = 0; gg < G; ++gg)
-        s = cadd(s, A.part[((long long)buf * G + gg) * (n + 1) + i]);
-    h[i] = s;
-    hacc[i] = cadd(hacc[i], s);
-    hsq += s.x * s.x + s.y * s.y;
-  }
-  // fixed-order block sums of sum|h|^2 and of ||v||^2
-  hsq = warp_sum(hsq);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = hsq;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-    double u = 0.0;
-    for (unsigned gg = 0; gg < G; ++gg) u += A.part[((long long)buf * G + gg) * (n + 1) + n].x;
-    red[32] = t;
-    red[33] = u;
+  // (2) reduce the G partials of every column: P threads per column, 2 accumulators each
+  {
+    const cplx* base = A.part + (long long)buf * G * (n + 1);
+    int P = lim > 0 ? T / lim : 1;
+    if (P < 1) P = 1;
+    if (P > 8) P = 8;
+    for (int idx = threadIdx.x; idx < lim * P; idx += T) {
+      const int i = idx % lim, part = idx / lim;
+      cplx s0 = make_double2(0.0, 0.0), s1 = make_double2(0.0, 0.0);
+      if (acc[i]) {
+        unsigned gg = part;
+        for (; gg + P < G; gg += 2 * P) {
+          s0 = cadd(s0, base[(long long)gg * (n + 1) + i]);
+          s1 = cadd(s1, base[(long long)(gg + P) * (n + 1) + i]);
+        }
+        if (gg < G) s0 = cadd(s0, base[(long long)gg * (n + 1) + i]);
+      }
+      const cplx s = cadd(s0, s1);
+      if (lim * P <= T) sm[part * lim + i] = s;
+      else h[i] = s;
+    }
+    __syncthreads();
+    double hsq = 0.0;
+    for (int i = threadIdx.x; i < lim; i += T) {
+      cplx s;
+      if (lim * P <= T) {
+        s = make_double2(0.0, 0.0);
+        for (int part = 0; part < P; ++part) s = cadd(s, sm[part * lim + i]);
+        h[i] = s;
+      } else {
+        s = h[i];
+      }
+      hacc[i] = cadd(hacc[i], s);
+      hsq += s.x * s.x + s.y * s.y;
+    }
+    hsq = warp_sum(hsq);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = hsq;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (T >> 5); ++w) t += red[w];
+      red[32] = t;
+    }
+    qr_sum_partials(&base[n].x, 2LL * (n + 1), G, red, 33);
   }
   buf ^= 1;
   __syncthreads();
   *hh = red[32];
   *vv_before = red[33];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int r = warp; r < nr; r += nw) {
-    double sr = 0.0, si = 0.0;
-    for (int i = lane; i < lim; i += 32) {
-      const cplx q = A.Q[(long long)(r0 + r) * n + i];
-      const cplx c = h[i];
-      sr += q.x * c.x - q.y * c.y;
-      si += q.x * c.y + q.y * c.x;
+  // (3) v -= Q h: P3 (a power of two <= 32) threads per row, 2 accumulators each
+  {
+    int P3 = 1;
+    while (P3 < 32 && 2 * P3 * nr <= T) P3 *= 2;
+    const int total = nr * P3;
+    for (int base_i = 0; base_i < total; base_i += T) {
+      const int idx = base_i + threadIdx.x;
+      const bool on = idx < total;
+      const int r = on ? idx / P3 : 0, part = idx % P3;
+      double ar = 0.0, br = 0.0, ai = 0.0, bi = 0.0;
+      if (on) {
+        for (int i = part; i < lim; i += P3) {
+          const cplx q = A.Q[(long long)(r0 + r) * n + i];
+          const cplx c = h[i];
+          ar = fma(q.x, c.x, ar);
+          br = fma(-q.y, c.y, br);
+          ai = fma(q.x, c.y, ai);
+          bi = fma(q.y, c.x, bi);
+        }
+      }
+      double sr = ar + br, si = ai + bi;
+      for (int o = P3 >> 1; o > 0; o >>= 1) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, o);
+        si += __shfl_xor_sync(0xffffffffu, si, o);
+      }
+      if (on && part == 0) v[r] = make_double2(v[r].x - sr, v[r].y - si);
     }
-    sr = warp_sum(sr);
-    si = warp_sum(si);
-    if (lane == 0) v[r] = make_double2(v[r].x - sr, v[r].y - si);
   }
   __syncthreads();
   return true;
@@ -588,11 +661,7 @@ __device__ bool qr_norm(const QrKernelArgs& A, int nr, const cplx* v, double& ou
     A.partn[buf * G + blockIdx.x] = t;
   }
   if (!grid_barrier(A.bar, G, A.status)) return false;
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (unsigned gg = 0; gg < G; ++gg) t += A.partn[buf * G + gg];
-    red[32] = t;
-  }
+  qr_sum_partials(A.partn + buf * G, 1, G, red, 32);
   __syncthreads();
   out = sqrt(red[32]);
   buf ^= 1;
@@ -607,14 +676,14 @@ __device__ bool qr_norm(const QrKernelArgs& A, int nr, const cplx* v, double& ou
 // the residual and *nrm its norm.
 __device__ bool qr_residual(const QrKernelArgs& A, int r0, int nr, int lim, cplx* v, cplx* h,
                             cplx* hacc, const unsigned char* acc, int& buf, unsigned G,
-                            double* red, double* nrm) {
+                            double* red, cplx* sm, double* nrm) {
   double vv, hh;
-  if (!qr_pass(A, r0, nr, lim, v, h, hacc, acc, buf, G, red, &vv, &hh)) return false;
+  if (!qr_pass(A, r0, nr, lim, v, h, hacc, acc, buf, G, red, sm, &vv, &hh)) return false;
   if (hh <= 0.75 * vv) {
     *nrm = sqrt(fmax(vv - hh, 0.0));
     return true;
   }
-  if (!qr_pass(A, r0, nr, lim, v, h, hacc, acc, buf, G, red, &vv, &hh)) return false;
+  if (!qr_pass(A, r0, nr, lim, v, h, hacc, acc, buf, G, red, sm, &vv, &hh)) return false;
   return qr_norm(A, nr, v, *nrm, buf, G, red);
 }
 
@@ -629,7 +698,8 @@ __global__ void __launch_bounds__(QR_THREADS) gauge_qr_kernel(QrKernelArgs A) {
   cplx* h = v + rows;
   cplx* hacc = h + n;
   double* red = reinterpret_cast<double*>(hacc + n);            // 34 doubles
-  unsigned char* acc = reinterpret_cast<unsigned char*>(red + 34);
+  cplx* sm = reinterpret_cast<cplx*>(red + 34);                  // QR_THREADS entries
+  unsigned char* acc = reinterpret_cast<unsigned char*>(sm + QR_THREADS);
   int buf = 0;
 
   for (long long e = threadIdx.x; e < (long long)nr * n; e += blockDim.x)
@@ -653,11 +723,7 @@ __global__ void __launch_bounds__(QR_THREADS) gauge_qr_kernel(QrKernelArgs A) {
     A.partn[buf * G + blockIdx.x] = t;
   }
   if (!grid_barrier(A.bar, G, A.status)) return;
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (unsigned gg = 0; gg < G; ++gg) t += A.partn[buf * G + gg];
-    red[33] = t;
-  }
+  qr_sum_partials(A.partn + buf * G, 1, G, red, 33);
   __syncthreads();
   const double thr = A.rank_tol * sqrt(red[33]);
   buf ^= 1;
@@ -669,7 +735,7 @@ __global__ void __launch_bounds__(QR_THREADS) gauge_qr_kernel(QrKernelArgs A) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) hacc[i] = make_double2(0.0, 0.0);
     __syncthreads();
     double nrm;
-    if (!qr_residual(A, r0, nr, j, v, h, hacc, acc, buf, G, red, &nrm)) return;
+    if (!qr_residual(A, r0, nr, j, v, h, hacc, acc, buf, G, red, sm, &nrm)) return;
     const bool take = nrm > thr;
     if (take) {
       const double inv = 1.0 / nrm;
@@ -709,7 +775,7 @@ __global__ void __launch_bounds__(QR_THREADS) gauge_qr_kernel(QrKernelArgs A) {
       ++cand;
       if (n0 == 0.0) continue;
       double nc;
-      if (!qr_residual(A, r0, nr, n, v, h, hacc, acc, buf, G, red, &nc)) return;
+      if (!qr_residual(A, r0, nr, n, v, h, hacc, acc, buf, G, red, sm, &nc)) return;
       if (nc > A.complete_tol * n0) {
         const double inv = 1.0 / nc;
         for (int r = threadIdx.x; r < nr; r += blockDim.x)
@@ -747,7 +813,7 @@ cudaError_t gauge_qr(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cplx* R,
   if (G > W.gmax || n > W.nmax) return cudaErrorInvalidValue;
   const int rows = (m + G - 1) / G;
   const size_t smem = (size_t)rows * sizeof(cplx) + 2 * (size_t)n * sizeof(cplx) +
-                      34 * sizeof(double) + (size_t)n + 16;
+                      34 * sizeof(double) + QR_THREADS * sizeof(cplx) + (size_t)n + 16;
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   static bool attr_set = false;
   if (!attr_set) {

@@ -73,8 +73,31 @@ int tdmrg_model_set_precision(tdmrg_model* h, int precision);
  * many vectors (smooth map for finite differences). */
 int tdmrg_model_set_krylov(tdmrg_model* h, double tol, int kmax, int fixed_k);
 
+/* Rank threshold of the gauge QR: a column whose Gram-Schmidt residual is <= rank_tol ||Y||_F
+ * is skipped and its position completed deterministically (default 1e-12 for both
+ * precisions). */
+int tdmrg_model_set_rank_tol(tdmrg_model* h, double rank_tol);
+
 /* Work stream (a cudaStream_t passed as void*; NULL = legacy default stream). */
 int tdmrg_model_set_stream(tdmrg_model* h, void* stream);
+
+/* Graph mode (needs a fixed Krylov dimension, tdmrg_model_set_krylov(h, tol, kmax, k)): each
+ * state's full second-order step is captured once into a CUDA graph and replayed, so a step
+ * is one graph launch (the thermal preparation and both real-time states each keep one graph).
+ * If no stream was set, the handle creates its own non-blocking stream. */
+int tdmrg_model_set_graphs(tdmrg_model* h, int on);
+
+/* Batched real-time stepping of several independent instances (the (V, T, N) parameter sweep):
+ * every model must have been prepared and passed tdmrg_realtime_init.  tdmrg_batch_create puts
+ * each model in graph mode on its own stream (with a QR grid capped to a quarter of the SMs
+ * so that instances run side by side; the models keep their own data), and
+ * tdmrg_batch_realtime_step launches one step of every instance before waiting for any of
+ * them.  Results are those of the individual models (tdmrg_realtime_observe on each).  The
+ * batch does not own the models; destroy it before them. */
+typedef struct tdmrg_batch tdmrg_batch;
+int tdmrg_batch_create(tdmrg_model* const* models, int n, tdmrg_batch** out);
+int tdmrg_batch_realtime_step(tdmrg_batch* b, int nsteps, double dt);
+int tdmrg_batch_destroy(tdmrg_batch* b);
 
 /* Phase timers: when on, the library synchronises its stream at every phase boundary and
  * accumulates host wall time per phase into the stats (slightly slower; off by default). */
@@ -149,7 +172,8 @@ long long tdmrg_heff_workspace_floats(int Ml, int Mr, int d, int Dl, int Dr);
 
 /* One tensor-core complex contraction C[m][n] = sum_k opA(A[m][k]) opB(B[n][k]) with opX =
  * conjugation when conjX, A: M x K, B: N x K, C: M x N (complex FP64, row-major, device).
- * The operands are split into 3xTF32 planes (allocated and freed inside); synchronises. */
+ * The operands are split into 3xTF32 planes (allocated and freed inside, with the split-K
+ * scratch used when the output has few tiles and K is long); synchronises. */
 int tdmrg_kernel_zgemm_tc(int M, int N, int K, const void* A, const void* B, int conjA, int conjB,
                           void* C, void* stream);
 
@@ -169,6 +193,14 @@ int tdmrg_kernel_env_left(int Ml1, int Mr1, int Ml2, int Mr2, int d, int Dl, int
  * status (device int, may be NULL): set to 1 if the bounded grid barrier timed out. */
 int tdmrg_kernel_gauge_qr(int m, int n, const void* Y, int p, const void* E, void* Q,
                           void* R, int* status, void* stream);
+
+/* Blocked gauge QR (the factorisation the engine uses): same definition, arguments and
+ * outputs as tdmrg_kernel_gauge_qr, computed 16 columns at a time (block Gram-Schmidt
+ * projections, Gram-form factorisation inside the block with a cancellation guard that
+ * restarts the block at any column whose residual lost more than half its norm).
+ * Allocates and frees its scratch; synchronises `stream`. */
+int tdmrg_kernel_gauge_qr_blocked(int m, int n, const void* Y, int p, const void* E, void* Q,
+                                  void* R, int* status, void* stream);
 
 /* Gauge QR that allocates nothing.  The paper has no counterpart: this entry point exists for
  * callers that cannot allocate device memory -- code running inside a CUDA graph capture

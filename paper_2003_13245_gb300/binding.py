@@ -41,6 +41,11 @@ _SIGS = {
     "tdmrg_model_set_stream": [_p, _p],
     "tdmrg_model_destroy": [_p],
     "tdmrg_model_set_profiling": [_p, _i],
+    "tdmrg_model_set_graphs": [_p, _i],
+    "tdmrg_model_set_rank_tol": [_p, _d],
+    "tdmrg_batch_create": [ctypes.POINTER(_p), _i, ctypes.POINTER(_p)],
+    "tdmrg_batch_realtime_step": [_p, _i, _d],
+    "tdmrg_batch_destroy": [_p],
     "tdmrg_thermal_prepare": [_p, _d, _d, _i],
     "tdmrg_correlation": [_p, _dp, _i, _d, _dp],
     "tdmrg_realtime_init": [_p],
@@ -56,6 +61,7 @@ _SIGS = {
     "tdmrg_kernel_krylov_dense": [_i, _p, _p, _p, _d, _d, _d, _i, _ip, _p],
     "tdmrg_kernel_zgemm_tc": [_i, _i, _i, _p, _p, _i, _i, _p, _p],
     "tdmrg_kernel_gauge_qr_noalloc": [_i, _i, _p, _i, _p, _p, _p, _p, _p],
+    "tdmrg_kernel_gauge_qr_blocked": [_i, _i, _p, _i, _p, _p, _p, _p, _p],
 }
 
 
@@ -179,11 +185,45 @@ class Model:
                 "t_site", "t_qr", "t_env", "t_bond", "t_absorb", "t_observe"]
         return dict(zip(keys, s.tolist()))
 
+    def set_rank_tol(self, tol):
+        _check(self._lib.tdmrg_model_set_rank_tol(self._h, float(tol)), self._h)
+
+    def set_graphs(self, on=True):
+        _check(self._lib.tdmrg_model_set_graphs(self._h, int(bool(on))), self._h)
+
     def set_profiling(self, on=True):
         _check(self._lib.tdmrg_model_set_profiling(self._h, int(bool(on))), self._h)
 
     def reset_stats(self):
         _check(self._lib.tdmrg_reset_stats(self._h), self._h)
+
+
+class Batch:
+    """Several prepared models (after realtime_init) stepped together (graph mode, one stream
+    each, all instances launched before any is waited for)."""
+
+    def __init__(self, models):
+        lib = load()
+        arr = (_p * len(models))(*[m._h.value for m in models])
+        h = ctypes.c_void_p()
+        _check(lib.tdmrg_batch_create(arr, len(models), ctypes.byref(h)))
+        self._h = h
+        self._lib = lib
+        self.models = list(models)
+
+    def realtime_step(self, nsteps, dt):
+        _check(self._lib.tdmrg_batch_realtime_step(self._h, int(nsteps), float(dt)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.tdmrg_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def mobility(t_grid, C, kT):
@@ -246,6 +286,14 @@ def kernel_gauge_qr(Y, Q, R, E=None, status=None, stream=None):
     p = 0 if E is None else E.shape[1]
     _check(lib.tdmrg_kernel_gauge_qr(m, n, _ptr(Y), p, _ptr(E), _ptr(Q), _ptr(R), _ptr(status),
                                      _stream_ptr(stream)))
+
+
+def kernel_gauge_qr_blocked(Y, Q, R, E=None, status=None, stream=None):
+    lib = load()
+    m, n = Y.shape
+    p = 0 if E is None else E.shape[1]
+    _check(lib.tdmrg_kernel_gauge_qr_blocked(m, n, _ptr(Y), p, _ptr(E), _ptr(Q), _ptr(R),
+                                             _ptr(status), _stream_ptr(stream)))
 
 
 def kernel_gauge_qr_noalloc(Y, Q, R, E=None, status=None, stream=None):

@@ -13,7 +13,8 @@ CSRC = os.path.join(PKG, "csrc")
 OBJ = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libtdmrg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["kernels_f64.cu", "kernels_tc.cu", "engine.cu", "capi.cu", "noalloc.cu"]
+CU_SOURCES = ["kernels_f64.cu", "qr_blocked.cu", "kernels_tc.cu", "engine.cu", "capi.cu",
+              "noalloc.cu"]
 CXX_SOURCES = ["model.cpp"]
 
 
@@ -61,7 +62,8 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
     with ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 1))) as ex:
         list(ex.map(run, jobs))
     if force or jobs or _newer(LIB, objs):
-        run([nvcc, "-shared"] + ARCH + ["-o", LIB] + objs + ["-lcudart"])
+        run([nvcc, "-shared"] + ARCH + ["-o", LIB] + objs +
+            ["-lcudart", "-Xlinker", "--no-undefined"])
     return LIB
 
 

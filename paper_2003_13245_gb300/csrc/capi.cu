@@ -19,6 +19,10 @@ struct tdmrg_model {
   std::string err;
 };
 
+struct tdmrg_batch {
+  std::vector<tdmrg_model*> models;
+};
+
 static thread_local std::string g_err;
 
 namespace tdmrg {
@@ -147,6 +151,77 @@ int tdmrg_model_set_profiling(tdmrg_model* h, int on) {
   return TDMRG_OK;
 }
 
+int tdmrg_model_set_rank_tol(tdmrg_model* h, double rank_tol) {
+  if (!h) return fail(nullptr, TDMRG_ERR_ARG, "NULL handle");
+  if (!(rank_tol > 0.0) || rank_tol > 1e-2) return fail(h, TDMRG_ERR_ARG, "rank_tol in (0, 1e-2]");
+  h->eng->set_rank_tol(rank_tol);
+  return TDMRG_OK;
+}
+
+int tdmrg_model_set_graphs(tdmrg_model* h, int on) {
+  if (!h) return fail(nullptr, TDMRG_ERR_ARG, "NULL handle");
+  return guarded(h, [&] { h->eng->set_graphs(on != 0, 0); });
+}
+
+int tdmrg_batch_create(tdmrg_model* const* models, int n, tdmrg_batch** out) {
+  if (!models || n < 1 || !out) return fail(nullptr, TDMRG_ERR_ARG, "batch: need n >= 1 models");
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!models[i]) return fail(nullptr, TDMRG_ERR_ARG, "batch: NULL model");
+    for (int j = 0; j < i; ++j)
+      if (models[j] == models[i]) return fail(nullptr, TDMRG_ERR_ARG, "batch: model listed twice");
+    if (!models[i]->eng->rt_ready())
+      return fail(nullptr, TDMRG_ERR_STATE, "batch: every model needs tdmrg_realtime_init first");
+  }
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return fail(nullptr, TDMRG_ERR_CUDA, "batch: no device");
+  // concurrent instances share the SMs: cap each QR grid so that four fit side by side
+  const int cap = sms / 4 > 8 ? sms / 4 : 8;
+  for (int i = 0; i < n; ++i) {
+    tdmrg_model* h = models[i];
+    const int rc = guarded(h, [&] {
+      h->eng->set_graphs(true, cap);
+    });
+    if (rc != TDMRG_OK) {
+      g_err = h->err;
+      return rc;
+    }
+  }
+  auto* b = new (std::nothrow) tdmrg_batch;
+  if (!b) return fail(nullptr, TDMRG_ERR_OOM, "host allocation failed");
+  b->models.assign(models, models + n);
+  *out = b;
+  return TDMRG_OK;
+}
+
+int tdmrg_batch_realtime_step(tdmrg_batch* b, int nsteps, double dt) {
+  if (!b || nsteps < 0 || !(dt > 0.0)) return fail(nullptr, TDMRG_ERR_ARG, "batch step: bad arguments");
+  for (int st = 0; st < nsteps; ++st) {
+    for (tdmrg_model* h : b->models) {
+      const int rc = guarded(h, [&] { h->eng->realtime_step_launch(dt); });
+      if (rc != TDMRG_OK) {
+        g_err = h->err;
+        return rc;
+      }
+    }
+    for (tdmrg_model* h : b->models) {
+      const int rc = guarded(h, [&] { h->eng->sync_and_check(); });
+      if (rc != TDMRG_OK) {
+        g_err = h->err;
+        return rc;
+      }
+    }
+  }
+  return TDMRG_OK;
+}
+
+int tdmrg_batch_destroy(tdmrg_batch* b) {
+  delete b;
+  return TDMRG_OK;
+}
+
 int tdmrg_model_destroy(tdmrg_model* h) {
   if (!h) return TDMRG_OK;
   if (h->eng) cudaStreamSynchronize(h->eng->stream());
@@ -225,7 +300,7 @@ int tdmrg_get_stats(const tdmrg_model* h, double* stats, int n) {
   const double v[18] = {s.site_updates, s.matvecs, s.heff_flops, s.krylov_vectors,
                         s.bond_matvecs, s.qrs, s.completions, s.env_updates, s.heff_ms,
                         s.h2d_bytes, s.d2h_bytes,
-                        (double)tdmrg::launch_count() - s.launches_at_reset,
+                        (double)tdmrg::launch_count() - s.launches_at_reset + s.replayed_launches,
                         s.t_site, s.t_qr, s.t_env, s.t_bond, s.t_absorb, s.t_observe};
   for (int i = 0; i < n && i < 18; ++i) stats[i] = v[i];
   return TDMRG_OK;
@@ -291,22 +366,26 @@ int tdmrg_kernel_zgemm_tc(int M, int N, int K, const void* A, const void* B, int
     cudaStream_t s = (cudaStream_t)stream;
     tdmrg::TcOperand a{nullptr, M, K, tdmrg::pad4(K), 1}, b{nullptr, N, K, tdmrg::pad4(K), 1};
     int* st = nullptr;
+    float* part = nullptr;
+    const long long part_len = 2LL * M * N * 64;      // room for a split-K of up to 64
     CK(cudaMalloc(&a.p, sizeof(float) * a.floats()));
     CK(cudaMalloc(&b.p, sizeof(float) * b.floats()));
     CK(cudaMalloc(&st, sizeof(int)));
+    CK(cudaMalloc(&part, sizeof(float) * part_len));
     struct F {
-      void* x[3];
+      void* x[4];
       ~F() {
         for (void* p : x)
           if (p) cudaFree(p);
       }
-    } f{{a.p, b.p, st}};
+    } f{{a.p, b.p, st, part}};
     CK(cudaMemsetAsync(st, 0, sizeof(int), s));
     CK(tdmrg::split_f64((const tdmrg::cplx*)A, 0, K, 1, 0, a, s));
     CK(tdmrg::split_f64((const tdmrg::cplx*)B, 0, K, 1, 0, b, s));
     tdmrg::TcGemm g{};
     g.M = M; g.N = N; g.K = K; g.nred = 1; g.nbatch = 1; g.conjA = conjA; g.conjB = conjB;
     g.out_mode = 0; g.C = C; g.ldc = N; g.status = st;
+    g.part = part; g.part_len = part_len;
     CK(tdmrg::tc_gemm(a, b, g, s));
     int hs = 0;
     CK(cudaMemcpyAsync(&hs, st, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -365,6 +444,58 @@ int tdmrg_kernel_gauge_qr(int m, int n, const void* Y, int p, const void* E, voi
     tdmrg::QrRef e{(const tdmrg::cplx*)(p > 0 ? E : Y), p > 0 ? p : n, 1, 1LL << 60, 0, 0};
     CK(tdmrg::gauge_qr(m, n, y, p, e, (tdmrg::cplx*)Q, (tdmrg::cplx*)R, W, st, s));
     CK(cudaStreamSynchronize(s));
+  });
+}
+
+int tdmrg_kernel_gauge_qr_blocked(int m, int n, const void* Y, int p, const void* E, void* Q,
+                                  void* R, int* status, void* stream) {
+  if (m < 1 || n < 1 || m < n || !Y || !Q || !R || p < 0 || (p > 0 && !E))
+    return fail(nullptr, TDMRG_ERR_ARG, "gauge_qr_blocked: need m >= n >= 1 and non-NULL buffers");
+  return guarded(nullptr, [&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    tdmrg::QrScratch W{};
+    W.gmax = sms;
+    W.nmax = n;
+    tdmrg::cplx* qb = nullptr;
+    unsigned char* acc = nullptr;
+    int* st = status;
+    const long long qlen = tdmrg::gauge_qr_blocked_scratch(n, sms);
+    struct Free {
+      tdmrg::QrScratch& w;
+      tdmrg::cplx*& qb;
+      unsigned char*& acc;
+      int*& st;
+      bool own;
+      ~Free() {
+        if (w.part) cudaFree(w.part);
+        if (w.partn) cudaFree(w.partn);
+        if (w.bar) cudaFree(w.bar);
+        if (qb) cudaFree(qb);
+        if (acc) cudaFree(acc);
+        if (own && st) cudaFree(st);
+      }
+    } fr{W, qb, acc, st, status == nullptr};
+    CK(cudaMalloc(&W.part, sizeof(tdmrg::cplx) * 2 * (size_t)sms * (n + 1)));
+    CK(cudaMalloc(&W.partn, sizeof(double) * 2 * (size_t)sms));
+    CK(cudaMalloc(&W.bar, sizeof(unsigned) * 2));
+    CK(cudaMalloc(&qb, sizeof(tdmrg::cplx) * (size_t)qlen));
+    CK(cudaMalloc(&acc, (size_t)n + 16));
+    if (!st) {
+      CK(cudaMalloc(&st, sizeof(int)));
+      CK(cudaMemsetAsync(st, 0, sizeof(int), s));
+    }
+    tdmrg::QrRef y{(const tdmrg::cplx*)Y, n, 1, 1LL << 60, 0, 0};
+    tdmrg::QrRef e{(const tdmrg::cplx*)(p > 0 ? E : Y), p > 0 ? p : n, 1, 1LL << 60, 0, 0};
+    CK(tdmrg::gauge_qr_blocked(m, n, y, p, e, (tdmrg::cplx*)Q, (tdmrg::cplx*)R, qb, qlen, acc, W,
+                               st, s));
+    int hs = 0;
+    CK(cudaMemcpyAsync(&hs, st, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hs == 1) throw Failure{TDMRG_ERR_TIMEOUT, "gauge QR grid barrier timed out"};
+    if (hs == 2) throw Failure{TDMRG_ERR_CUDA, "gauge QR ran out of completion vectors"};
   });
 }
 

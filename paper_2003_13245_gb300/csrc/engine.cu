@@ -16,6 +16,9 @@ namespace tdmrg {
 
 namespace {
 constexpr long long NOSPLIT = 1LL << 60;
+// gauge-QR rank threshold of the mixed path (a larger threshold, at the 3xTF32 noise level,
+// changes neither C(t) nor log Z measurably but sends many columns through completion)
+constexpr double kMixedRankTol = 1e-12;
 const cplx ONE = {1.0, 0.0};
 const cplx ZERO = {0.0, 0.0};
 
@@ -190,7 +193,7 @@ void left_x_tc(cudaStream_t st, const TcBufs& b, int Dl, int Ml1, int Ml2, int D
   TcGemm g{};
   g.M = Dl * Ml1; g.N = D * Mr2; g.K = Ml2; g.nred = 1; g.nbatch = 1;
   g.out_mode = 1; g.C = b.x32; g.ldc = (long long)D * Mr2; g.sbc = 0;
-  g.plane = (long long)Dl * Ml1 * D * Mr2; g.status = b.status;
+  g.plane = (long long)Dl * Ml1 * D * Mr2; g.status = b.status; g.part = b.kpart; g.part_len = b.kpart_len;
   CK(tc_gemm(Lp, Bt, g, st));
 }
 
@@ -203,7 +206,7 @@ void right_x_tc(cudaStream_t st, const TcBufs& b, int Dr, int Ml2, int D, int Mr
   TcGemm g{};
   g.M = Ml2 * D; g.N = Mr1; g.K = Mr2; g.nred = 1; g.nbatch = Dr; g.b_bat = 1;
   g.out_mode = 1; g.C = b.x32; g.ldc = Mr1; g.sbc = (long long)Ml2 * D * Mr1;
-  g.plane = (long long)Dr * Ml2 * D * Mr1; g.status = b.status;
+  g.plane = (long long)Dr * Ml2 * D * Mr1; g.status = b.status; g.part = b.kpart; g.part_len = b.kpart_len;
   CK(tc_gemm(Kp, Rp, g, st));
 }
 }  // namespace
@@ -217,7 +220,7 @@ void heff_tc_apply(cudaStream_t st, const TcBufs& b, const DevMpoSite& W, int Ml
   TcOperand Rp{b.envB, Mr, Mr, pad4(Mr), W.Dr};
   TcGemm g{};
   g.M = Ml * D; g.N = Mr; g.K = Mr; g.nred = W.Dr; g.nbatch = 1; g.a_red = 1; g.b_red = 1;
-  g.out_mode = 0; g.C = out; g.ldc = Mr; g.status = b.status;
+  g.out_mode = 0; g.C = out; g.ldc = Mr; g.status = b.status; g.part = b.kpart; g.part_len = b.kpart_len;
   CK(tc_gemm(Yp, Rp, g, st));
 }
 
@@ -258,7 +261,7 @@ void env_left_tc(cudaStream_t st, const TcBufs& b, const DevMpoSite& W, int Ml1,
   CK(split_f64_t(bra, 0, Mr1, 0, Bt, st));
   TcGemm g{};
   g.M = Mr1; g.N = Mr2; g.K = Ml1 * D; g.nred = 1; g.nbatch = W.Dr; g.b_bat = 1; g.conjA = 1;
-  g.out_mode = 0; g.C = Lout; g.ldc = Mr2; g.sbc = (long long)Mr1 * Mr2; g.status = b.status;
+  g.out_mode = 0; g.C = Lout; g.ldc = Mr2; g.sbc = (long long)Mr1 * Mr2; g.status = b.status; g.part = b.kpart; g.part_len = b.kpart_len;
   CK(tc_gemm(Bt, Yt, g, st));
 }
 
@@ -276,7 +279,7 @@ void env_right_tc(cudaStream_t st, const TcBufs& b, const DevMpoSite& W, int Ml1
   CK(split_f64(bra, 0, (long long)D * Mr1, 1, 0, Bp, st));
   TcGemm g{};
   g.M = Ml1; g.N = Ml2; g.K = D * Mr1; g.nred = 1; g.nbatch = W.Dl; g.b_bat = 1; g.conjA = 1;
-  g.out_mode = 0; g.C = Rout; g.ldc = Ml2; g.sbc = (long long)Ml1 * Ml2; g.status = b.status;
+  g.out_mode = 0; g.C = Rout; g.ldc = Ml2; g.sbc = (long long)Ml1 * Ml2; g.status = b.status; g.part = b.kpart; g.part_len = b.kpart_len;
   CK(tc_gemm(Bp, Yp, g, st));
 }
 
@@ -296,11 +299,11 @@ void bond_tc_apply(cudaStream_t st, const TcBufs& b, int M, int Dw, const cplx* 
   TcOperand Xp{b.mix, M, M, pad4(M), Dw};
   TcGemm g1{};
   g1.M = Dw * M; g1.N = M; g1.K = M; g1.nred = 1; g1.nbatch = 1;
-  g1.out_mode = 2; g1.C = b.mix; g1.ldc = pad4(M); g1.plane = Xp.plane(); g1.status = b.status;
+  g1.out_mode = 2; g1.C = b.mix; g1.ldc = pad4(M); g1.plane = Xp.plane(); g1.status = b.status; g1.part = b.kpart; g1.part_len = b.kpart_len;
   CK(tc_gemm(Lp, Ct, g1, st));
   TcGemm g2{};
   g2.M = M; g2.N = M; g2.K = M; g2.nred = Dw; g2.nbatch = 1; g2.a_red = 1; g2.b_red = 1;
-  g2.out_mode = 0; g2.C = out; g2.ldc = M; g2.status = b.status;
+  g2.out_mode = 0; g2.C = out; g2.ldc = M; g2.status = b.status; g2.part = b.kpart; g2.part_len = b.kpart_len;
   CK(tc_gemm(Xp, Rp, g2, st));
 }
 
@@ -406,6 +409,11 @@ Engine::Engine(const ModelParams& p) : P(p) {
 }
 
 Engine::~Engine() {
+  clear_graphs();
+  if (own_stream_) {
+    cudaStreamSynchronize(own_stream_);
+    cudaStreamDestroy(own_stream_);
+  }
   free_mps(psi_b_);
   free_mps(psi1_);
   free_mps(psi2_);
@@ -422,11 +430,13 @@ Engine::~Engine() {
   if (qr_.part) cudaFree(qr_.part);
   if (qr_.partn) cudaFree(qr_.partn);
   if (qr_.bar) cudaFree(qr_.bar);
+  if (qb_scratch_) cudaFree(qb_scratch_);
+  if (qb_acc_) cudaFree(qb_acc_);
   if (h_pinned_) cudaFreeHost(h_pinned_);
   if (h_pinned_d_) cudaFreeHost(h_pinned_d_);
   for (auto& e : ev_)
     if (e) cudaEventDestroy(e);
-  for (float* p : {tcb_.envA, tcb_.envB, tcb_.siteA, tcb_.siteB, tcb_.x32, tcb_.mix})
+  for (float* p : {tcb_.envA, tcb_.envB, tcb_.siteA, tcb_.siteB, tcb_.x32, tcb_.mix, tcb_.kpart})
     if (p) cudaFree(p);
 }
 
@@ -443,8 +453,10 @@ void Engine::set_precision(int p) {
   if (p != TDMRG_PREC_C128 && p != TDMRG_PREC_C64_3XTF32)
     throw Failure{TDMRG_ERR_ARG, "unknown precision"};
   if (p != precision_) {
+    clear_graphs();
     precision_ = p;
     if (!ktol_user_) ktol_ = (p == TDMRG_PREC_C128) ? 1e-13 : 1e-7;
+    if (!rank_tol_user_) rank_tol_ = (p == TDMRG_PREC_C128) ? 1e-12 : kMixedRankTol;
     prepared_ = false;
     rt_ready_ = false;
   }
@@ -453,6 +465,9 @@ void Engine::set_precision(int p) {
 void Engine::set_krylov(double tol, int kmax, int fixed_k) {
   if (!(tol > 0.0) || kmax < 1 || kmax > KMAX || fixed_k < 0 || fixed_k > KMAX)
     throw Failure{TDMRG_ERR_ARG, "krylov: need tol > 0, 1 <= kmax <= 32, 0 <= fixed_k <= 32"};
+  if (graphs_ && fixed_k <= 0)
+    throw Failure{TDMRG_ERR_ARG, "graph mode needs a fixed Krylov dimension"};
+  clear_graphs();
   ktol_ = tol;
   ktol_user_ = true;
   kmax_ = kmax;
@@ -500,6 +515,11 @@ void Engine::ensure_workspace(long long maxsite, long long maxxy, int maxbond, i
     CK(cudaMalloc(&qr_.part, sizeof(cplx) * 2 * (size_t)sms * (maxm + 1)));
     CK(cudaMalloc(&qr_.partn, sizeof(double) * 2 * (size_t)sms));
     CK(cudaMalloc(&qr_.bar, sizeof(unsigned) * 2));
+    if (qb_scratch_) cudaFree(qb_scratch_);
+    if (qb_acc_) cudaFree(qb_acc_);
+    qb_len_ = gauge_qr_blocked_scratch(maxm, sms);
+    CK(cudaMalloc(&qb_scratch_, sizeof(cplx) * (size_t)qb_len_));
+    CK(cudaMalloc(&qb_acc_, (size_t)maxm + 16));
     ws_m_ = maxm;
   }
 }
@@ -510,6 +530,7 @@ long long Engine::env_size(const DevMps& s, int k, int Dw, bool left) const {
 }
 
 void Engine::alloc_mps(DevMps& s, int M) {
+  clear_graphs();
   free_mps(s);
   const int L = (int)sites_.size();
   s.Mb = bond_dimensions(sites_, M);
@@ -570,6 +591,10 @@ void Engine::alloc_tc(const DevMps& s) {
     CK(cudaMalloc(&tcb_.siteB, sizeof(float) * 4 * site));
     CK(cudaMalloc(&tcb_.x32, sizeof(float) * 2 * x));
     CK(cudaMalloc(&tcb_.mix, sizeof(float) * 4 * (long long)Dmax * site));
+    if (!tcb_.kpart) {
+      tcb_.kpart_len = 4LL << 20;
+      CK(cudaMalloc(&tcb_.kpart, sizeof(float) * tcb_.kpart_len));
+    }
     tc_site_ = site;
     tc_env_ = env;
     tc_x_ = x;
@@ -607,6 +632,7 @@ void Engine::free_mps(DevMps& s) {
 
 void Engine::copy_mps(const DevMps& src, DevMps& dst) {
   if (dst.A.size() != src.A.size() || dst.Mb != src.Mb) {
+    clear_graphs();
     free_mps(dst);
     dst.Mb = src.Mb;
     dst.D = src.D;
@@ -627,13 +653,13 @@ void Engine::copy_mps(const DevMps& src, DevMps& dst) {
 }
 
 double Engine::tic() {
-  if (!prof_) return 0.0;
+  if (!prof_ || capturing_) return 0.0;
   CK(cudaStreamSynchronize(st_));
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
 void Engine::toc(double& acc, double t0) {
-  if (!prof_) return;
+  if (!prof_ || capturing_) return;
   CK(cudaStreamSynchronize(st_));
   acc += std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count() - t0;
 }
@@ -674,20 +700,45 @@ void Engine::check_status() {
 
 void Engine::gauge_qr_dev(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cplx* R) {
   const double t0 = tic();
-  CK(gauge_qr(m, n, Y, p, E, Q, R, qr_, status_, st_));
+  CK(gauge_qr_blocked(m, n, Y, p, E, Q, R, qb_scratch_, qb_len_, qb_acc_, qr_, status_, st_,
+                      qr_gcap_, rank_tol_));
   toc(stats.t_qr, t0);
   stats.qrs += 1;
 }
 
 void Engine::absorb_left(const cplx* C, int M, cplx* A, long long ncols) {
-  CK(zgemm(M, (int)ncols, M, 1, 1, ONE, mref(C, M, 1), mref(A, ncols, 1), ZERO, T1_, ncols, 0,
-           nullptr, st_));
+  if (mixed()) {
+    // T1[b][c] = sum_b' C[b][b'] A[b'][c] on the tensor cores
+    TcOperand Cp{tcb_.envA, M, M, pad4(M), 1};
+    TcOperand At{tcb_.siteA, (int)ncols, M, pad4(M), 1};
+    CK(split_f64(C, 0, M, 1, 0, Cp, st_));
+    CK(split_f64_t(A, 0, ncols, 0, At, st_));
+    TcGemm g{};
+    g.M = M; g.N = (int)ncols; g.K = M; g.nred = 1; g.nbatch = 1;
+    g.out_mode = 0; g.C = T1_; g.ldc = ncols; g.status = tcb_.status; g.part = tcb_.kpart; g.part_len = tcb_.kpart_len;
+    CK(tc_gemm(Cp, At, g, st_));
+  } else {
+    CK(zgemm(M, (int)ncols, M, 1, 1, ONE, mref(C, M, 1), mref(A, ncols, 1), ZERO, T1_, ncols, 0,
+             nullptr, st_));
+  }
   CK(cudaMemcpyAsync(A, T1_, sizeof(cplx) * (size_t)M * ncols, cudaMemcpyDeviceToDevice, st_));
 }
 
 void Engine::absorb_right(cplx* A, long long nrows, const cplx* C, int M) {
-  CK(zgemm((int)nrows, M, M, 1, 1, ONE, mref(A, M, 1), mref(C, M, 1), ZERO, T1_, M, 0, nullptr,
-           st_));
+  if (mixed()) {
+    // T1[r][b] = sum_b' A[r][b'] C[b'][b] on the tensor cores
+    TcOperand Ap{tcb_.siteA, (int)nrows, M, pad4(M), 1};
+    TcOperand Ct{tcb_.envA, M, M, pad4(M), 1};
+    CK(split_f64(A, 0, M, 1, 0, Ap, st_));
+    CK(split_f64_t(C, 0, M, 0, Ct, st_));
+    TcGemm g{};
+    g.M = (int)nrows; g.N = M; g.K = M; g.nred = 1; g.nbatch = 1;
+    g.out_mode = 0; g.C = T1_; g.ldc = M; g.status = tcb_.status; g.part = tcb_.kpart; g.part_len = tcb_.kpart_len;
+    CK(tc_gemm(Ap, Ct, g, st_));
+  } else {
+    CK(zgemm((int)nrows, M, M, 1, 1, ONE, mref(A, M, 1), mref(C, M, 1), ZERO, T1_, M, 0, nullptr,
+             st_));
+  }
   CK(cudaMemcpyAsync(A, T1_, sizeof(cplx) * (size_t)M * nrows, cudaMemcpyDeviceToDevice, st_));
 }
 
@@ -759,20 +810,21 @@ void Engine::site_update(DevMps& s, int k, double hr, double hi) {
   int nev = 0;
   const bool mx = mixed();
   if (mx) heff_tc_prepare(st_, tcb_, Ml, Mr, W.Dl, W.Dr, Le, Re);
+  const bool timed = !capturing_;
   const int used = krylov(s.size(k), s.A[k], Kout_, hr, hi,
                           [&](const cplx* in, cplx* out, const int* skip) {
-    CK(cudaEventRecord(ev_[2 * nev], st_));
+    if (timed) CK(cudaEventRecord(ev_[2 * nev], st_));
     if (mx)
       heff_tc_apply(st_, tcb_, W, Ml, Mr, D, d, in, out);
     else
       heff_f64(c, W, Ml, Mr, D, d, Le, Re, in, out, skip);
-    CK(cudaEventRecord(ev_[2 * nev + 1], st_));
+    if (timed) CK(cudaEventRecord(ev_[2 * nev + 1], st_));
     ++nev;
   });
   stats.matvecs += used;
   stats.heff_flops += used * flops;
-  if (used > 0) CK(cudaEventSynchronize(ev_[2 * (used - 1) + 1]));
-  for (int i = 0; i < used; ++i) {
+  if (timed && used > 0) CK(cudaEventSynchronize(ev_[2 * (used - 1) + 1]));
+  for (int i = 0; timed && i < used; ++i) {
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, ev_[2 * i], ev_[2 * i + 1]));
     stats.heff_ms += ms;
@@ -780,7 +832,112 @@ void Engine::site_update(DevMps& s, int k, double hr, double hi) {
   stats.site_updates += 1;
 }
 
+namespace {
+Stats stats_diff(const Stats& a, const Stats& b) {
+  Stats d;
+  d.site_updates = a.site_updates - b.site_updates;
+  d.matvecs = a.matvecs - b.matvecs;
+  d.heff_flops = a.heff_flops - b.heff_flops;
+  d.krylov_vectors = a.krylov_vectors - b.krylov_vectors;
+  d.bond_matvecs = a.bond_matvecs - b.bond_matvecs;
+  d.qrs = a.qrs - b.qrs;
+  d.completions = a.completions - b.completions;
+  d.env_updates = a.env_updates - b.env_updates;
+  d.h2d_bytes = a.h2d_bytes - b.h2d_bytes;
+  d.d2h_bytes = a.d2h_bytes - b.d2h_bytes;
+  d.replayed_launches = a.replayed_launches - b.replayed_launches;
+  return d;
+}
+void stats_add(Stats& a, const Stats& d) {
+  a.site_updates += d.site_updates;
+  a.matvecs += d.matvecs;
+  a.heff_flops += d.heff_flops;
+  a.krylov_vectors += d.krylov_vectors;
+  a.bond_matvecs += d.bond_matvecs;
+  a.qrs += d.qrs;
+  a.completions += d.completions;
+  a.env_updates += d.env_updates;
+  a.h2d_bytes += d.h2d_bytes;
+  a.d2h_bytes += d.d2h_bytes;
+  a.replayed_launches += d.replayed_launches;
+}
+}  // namespace
+
+void Engine::set_graphs(bool on, int qr_cap) {
+  if (on && fixed_k_ <= 0)
+    throw Failure{TDMRG_ERR_ARG, "graph mode needs a fixed Krylov dimension (set_krylov fixed_k)"};
+  clear_graphs();
+  graphs_ = on;
+  qr_gcap_ = qr_cap;
+  if (on && st_ == 0) {
+    if (!own_stream_) CK(cudaStreamCreateWithFlags(&own_stream_, cudaStreamNonBlocking));
+    st_ = own_stream_;
+  }
+}
+
+void Engine::clear_graphs() {
+  for (auto& g : step_graphs_)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  step_graphs_.clear();
+}
+
+const Engine::StepGraph& Engine::step_graph(DevMps& s, double tr, double ti) {
+  for (const auto& g : step_graphs_)
+    if (g.state == &s && g.tr == tr && g.ti == ti) return g;
+  const Stats before = stats;
+  const long long launches0 = launch_count();
+  capturing_ = true;
+  CK(cudaStreamBeginCapture(st_, cudaStreamCaptureModeThreadLocal));
+  cudaGraph_t graph = nullptr;
+  try {
+    tdvp_step_body(s, tr, ti);
+  } catch (...) {
+    cudaStreamEndCapture(st_, &graph);
+    if (graph) cudaGraphDestroy(graph);
+    capturing_ = false;
+    stats = before;
+    throw;
+  }
+  capturing_ = false;
+  CK(cudaStreamEndCapture(st_, &graph));
+  StepGraph g{&s, tr, ti, nullptr, stats_diff(stats, before)};
+  g.delta.replayed_launches = (double)(launch_count() - launches0);
+  // the captured launches did not run: the counter keeps counting real launches only
+  count_launch(-(int)(launch_count() - launches0));
+  stats = before;
+  const cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  CK(e);
+  step_graphs_.push_back(g);
+  return step_graphs_.back();
+}
+
 void Engine::tdvp_step(DevMps& s, double tr, double ti) {
+  if (graphs_) {
+    const StepGraph& g = step_graph(s, tr, ti);
+    CK(cudaGraphLaunch(g.exec, st_));
+    stats_add(stats, g.delta);
+    check_status();
+    return;
+  }
+  tdvp_step_body(s, tr, ti);
+  check_status();
+}
+
+void Engine::realtime_step_launch(double dt) {
+  if (!rt_ready_) throw Failure{TDMRG_ERR_STATE, "realtime_step before realtime_init"};
+  if (!graphs_) throw Failure{TDMRG_ERR_STATE, "batched stepping needs graph mode"};
+  const StepGraph& g1 = step_graph(psi1_, 0.0, -dt);
+  CK(cudaGraphLaunch(g1.exec, st_));
+  stats_add(stats, g1.delta);
+  const StepGraph& g2 = step_graph(psi2_, 0.0, -dt);
+  CK(cudaGraphLaunch(g2.exec, st_));
+  stats_add(stats, g2.delta);
+}
+
+void Engine::sync_and_check() { check_status(); }
+
+void Engine::tdvp_step_body(DevMps& s, double tr, double ti) {
   const double hr = 0.5 * tr, hi = 0.5 * ti;
   const int L = s.L();
   Ctx c = ctx();
@@ -843,7 +1000,6 @@ void Engine::tdvp_step(DevMps& s, double tr, double ti) {
                          cudaMemcpyDeviceToDevice, st_));
     }
   }
-  check_status();
 }
 
 // ------------------------------------------------------------------------------------

@@ -81,6 +81,8 @@ struct TcBufs {
   float* siteB = nullptr;
   float* x32 = nullptr;    // FP32 planar intermediate (MPO channel x site)
   float* mix = nullptr;    // split planes of an MPO-channel x site operand
+  float* kpart = nullptr;  // split-K partial sums
+  long long kpart_len = 0;
   int* status = nullptr;
 };
 void heff_tc_prepare(cudaStream_t st, const TcBufs& b, int Ml, int Mr, int Dl, int Dr,
@@ -123,6 +125,7 @@ struct Stats {
   double t_site = 0, t_qr = 0, t_env = 0, t_bond = 0, t_absorb = 0, t_observe = 0;
   double h2d_bytes = 0, d2h_bytes = 0;
   double launches_at_reset = 0;
+  double replayed_launches = 0;       // kernels launched through graph replays
 };
 
 class Engine {
@@ -133,6 +136,18 @@ class Engine {
   void set_precision(int p);
   void set_krylov(double tol, int kmax, int fixed_k);
   void set_stream(cudaStream_t s) { st_ = s; }
+  void set_rank_tol(double t) {
+    rank_tol_ = t;
+    rank_tol_user_ = true;
+    clear_graphs();
+  }
+  // Graph mode: with a fixed Krylov dimension every half-sweep pair of a state is captured
+  // once into a CUDA graph and replayed.  qr_cap > 0 caps the QR grid (batched instances).
+  void set_graphs(bool on, int qr_cap = 0);
+  bool graphs() const { return graphs_; }
+  // launch both real-time graphs of one step without waiting (batched use)
+  void realtime_step_launch(double dt);
+  void sync_and_check();
   void set_profiling(bool on) { prof_ = on; }
   void rebuild_mpos();
   void thermal_prepare(double beta, double dtau, int M);
@@ -191,7 +206,22 @@ class Engine {
   int precision_ = 0;
   double ktol_ = 1e-13;
   bool ktol_user_ = false;
+  double rank_tol_ = 1e-12;
+  bool rank_tol_user_ = false;
   bool prof_ = false;
+  bool graphs_ = false, capturing_ = false;
+  int qr_gcap_ = 0;
+  cudaStream_t own_stream_ = nullptr;
+  struct StepGraph {
+    const DevMps* state;
+    double tr, ti;
+    cudaGraphExec_t exec;
+    Stats delta;
+  };
+  std::vector<StepGraph> step_graphs_;
+  void clear_graphs();
+  void tdvp_step_body(DevMps& s, double tr, double ti);
+  const StepGraph& step_graph(DevMps& s, double tr, double ti);
   int kmax_ = 32, fixed_k_ = 0;
   bool prepared_ = false, rt_ready_ = false;
   double logZ_ = 0.0;
@@ -209,6 +239,9 @@ class Engine {
   double* scal_ = nullptr;          // device scalars
   LzState* lz_ = nullptr;
   QrScratch qr_{};
+  cplx* qb_scratch_ = nullptr;
+  long long qb_len_ = 0;
+  unsigned char* qb_acc_ = nullptr;
   int* status_ = nullptr;
   int* h_pinned_ = nullptr;
   double* h_pinned_d_ = nullptr;
@@ -253,13 +286,14 @@ inline int Engine::krylov(long long n, const cplx* v, cplx* out, double tr, doub
     CK(cudaEventRecord(ev_[2 * KMAX + (j & 1)], st_));
     stats.d2h_bytes += sizeof(int);
     launched = j + 1;
+    if (capturing_) continue;   // a captured Krylov loop runs its fixed number of vectors
     if (j >= 1) {
       // the flag of iteration j-1 (iteration j is queued behind it)
       CK(cudaEventSynchronize(ev_[2 * KMAX + ((j - 1) & 1)]));
       if (h_pinned_[4 + ((j - 1) & 1) * 2]) stop = true;
     }
   }
-  if (!stop) {
+  if (!stop && !capturing_) {
     CK(cudaEventSynchronize(ev_[2 * KMAX + ((launched - 1) & 1)]));
   }
   // when the stop flag of iteration j-1 was seen, iteration j was queued but skipped

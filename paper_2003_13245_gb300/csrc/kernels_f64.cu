@@ -468,7 +468,6 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, in
           ok = 0;
           break;
         }
-        __nanosleep(64);
       }
     }
     __threadfence();
@@ -493,6 +492,8 @@ struct QrKernelArgs {
   unsigned* bar;
   int* status;
   double rank_tol, complete_tol;
+  const unsigned char* acc_in;   // completion only: accepted flags of a factorisation done
+                                 // elsewhere (Q, R already written; only skipped columns filled)
 };
 
 // Sum of the G per-block partial doubles at stride `stride` (fixed order per lane, then a
@@ -702,6 +703,19 @@ __global__ void __launch_bounds__(QR_THREADS) gauge_qr_kernel(QrKernelArgs A) {
   unsigned char* acc = reinterpret_cast<unsigned char*>(sm + QR_THREADS);
   int buf = 0;
 
+  if (A.acc_in) {
+    // completion only: nothing to do unless a column was skipped (same decision in all CTAs)
+    __shared__ int s_missing;
+    if (threadIdx.x == 0) s_missing = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      acc[i] = A.acc_in[i];
+      if (!acc[i]) atomicOr(&s_missing, 1);
+    }
+    __syncthreads();
+    if (!s_missing) return;
+  }
+  if (!A.acc_in) {
   for (long long e = threadIdx.x; e < (long long)nr * n; e += blockDim.x)
     A.Q[(long long)r0 * n + e] = make_double2(0.0, 0.0);
   if (blockIdx.x == 0)
@@ -749,6 +763,7 @@ __global__ void __launch_bounds__(QR_THREADS) gauge_qr_kernel(QrKernelArgs A) {
     __syncthreads();
     if (threadIdx.x == 0 && take) acc[j] = 1;
     __syncthreads();
+  }
   }
   // completion of skipped positions
   long long cand = 0;
@@ -808,8 +823,9 @@ int gauge_qr_grid(int m) {
 }
 
 cudaError_t gauge_qr(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cplx* R,
-                     const QrScratch& W, int* status, cudaStream_t s) {
-  const int G = gauge_qr_grid(m);
+                     const QrScratch& W, int* status, cudaStream_t s, int gcap) {
+  int G = gauge_qr_grid(m);
+  if (gcap > 0 && G > gcap) G = gcap;
   if (G > W.gmax || n > W.nmax) return cudaErrorInvalidValue;
   const int rows = (m + G - 1) / G;
   const size_t smem = (size_t)rows * sizeof(cplx) + 2 * (size_t)n * sizeof(cplx) +
@@ -831,10 +847,56 @@ cudaError_t gauge_qr(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cplx* R,
   a.part = W.part; a.partn = W.partn; a.bar = W.bar; a.status = status;
   a.rank_tol = 1e-12;
   a.complete_tol = 1e-2;
-  void* args[] = {&a};
+  a.acc_in = nullptr;
+  // cooperative launch through cudaLaunchKernelEx (also valid inside a stream capture)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(G);
+  cfg.blockDim = dim3(QR_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   count_launch();
-  return cudaLaunchCooperativeKernel((const void*)gauge_qr_kernel, dim3(G), dim3(QR_THREADS),
-                                     args, smem, s);
+  return cudaLaunchKernelEx(&cfg, gauge_qr_kernel, a);
+}
+
+cudaError_t gauge_qr_complete(int m, int n, int p, QrRef E, cplx* Q, const unsigned char* acc,
+                              const QrScratch& W, int* status, cudaStream_t s, int gcap) {
+  int G = gauge_qr_grid(m);
+  if (gcap > 0 && G > gcap) G = gcap;
+  if (G > W.gmax || n > W.nmax) return cudaErrorInvalidValue;
+  const int rows = (m + G - 1) / G;
+  const size_t smem = (size_t)rows * sizeof(cplx) + 2 * (size_t)n * sizeof(cplx) +
+                      34 * sizeof(double) + QR_THREADS * sizeof(cplx) + (size_t)n + 16;
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(gauge_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       200 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(W.bar, 0, 2 * sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  QrKernelArgs a;
+  a.m = m; a.n = n; a.p = p;
+  a.Y = E; a.E = E;
+  a.Q = Q; a.R = nullptr;
+  a.part = W.part; a.partn = W.partn; a.bar = W.bar; a.status = status;
+  a.rank_tol = 1e-12;
+  a.complete_tol = 1e-2;
+  a.acc_in = acc;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(G);
+  cfg.blockDim = dim3(QR_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  count_launch();
+  return cudaLaunchKernelEx(&cfg, gauge_qr_kernel, a);
 }
 
 // ------------------------------------------------------------------------------------

@@ -147,9 +147,15 @@ __global__ void __launch_bounds__(128, 1)
   volatile int* s_issued = s_fail + 1;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN, bz = blockIdx.z;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int ks = g.ksplit > 1 ? g.ksplit : 1;
+  const int bz = blockIdx.z / ks, sp = blockIdx.z % ks;
   const int ktiles = (g.K + BK - 1) / BK;
-  const int total = ktiles * g.nred;
+  const int all = ktiles * g.nred;
+  const int chunk = (all + ks - 1) / ks;
+  const int tbeg = sp * chunk;
+  const int tend = min(all, tbeg + chunk);
+  const int total = tend > tbeg ? tend - tbeg : 0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NST; ++s) {
@@ -180,7 +186,8 @@ __global__ void __launch_bounds__(128, 1)
         *s_fail = 1;
         break;
       }
-      const int r = t / ktiles, k0 = (t % ktiles) * BK;
+      const int tt = tbeg + t;
+      const int r = tt / ktiles, k0 = (tt % ktiles) * BK;
       unsigned char* st = smem + s * STAGE;
       mbar_expect_tx(&full[s], STAGE);
       tma_load_4d(st, &tmA, k0, m0, r * g.a_red + bz * g.a_bat, 0, &full[s]);
@@ -245,8 +252,23 @@ __global__ void __launch_bounds__(128, 1)
       float re[16], im[16];
       tmem_ld16(lane_addr + c, re);
       tmem_ld16(lane_addr + BN + c, im);
+      if (total == 0) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) re[i] = im[i] = 0.f;
+      }
       if (row < g.M) {
-        if (g.out_mode == 0) {
+        if (ks > 1) {
+          const long long pl = (long long)g.nbatch * ks * g.M * g.N;
+          float* P = g.part + (((long long)bz * ks + sp) * g.M + row) * g.N;
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int n = n0 + c + i;
+            if (n < g.N) {
+              P[n] = re[i];
+              P[pl + n] = im[i];
+            }
+          }
+        } else if (g.out_mode == 0) {
           double2* C = reinterpret_cast<double2*>(g.C) + (long long)bz * g.sbc + (long long)row * g.ldc;
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
@@ -295,6 +317,41 @@ __global__ void __launch_bounds__(128, 1)
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(TMEM_COLS));
+  }
+}
+
+// sum of the split-K partials into the requested output form
+__global__ void split_reduce_kernel(TcGemm g) {
+  const int ks = g.ksplit;
+  const long long MN = (long long)g.M * g.N;
+  const long long total = (long long)g.nbatch * MN;
+  const long long pl = (long long)g.nbatch * ks * MN;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(e / MN);
+    const long long mn = e % MN;
+    const int row = (int)(mn / g.N), n = (int)(mn % g.N);
+    float re = 0.f, im = 0.f;
+    const float* P = g.part + (long long)b * ks * MN + mn;
+    for (int s = 0; s < ks; ++s) {
+      re += P[s * MN];
+      im += P[pl + s * MN];
+    }
+    if (g.out_mode == 0) {
+      double2* C = reinterpret_cast<double2*>(g.C) + (long long)b * g.sbc + (long long)row * g.ldc;
+      C[n] = make_double2((double)re, (double)im);
+    } else if (g.out_mode == 1) {
+      float* Cr = reinterpret_cast<float*>(g.C) + (long long)b * g.sbc + (long long)row * g.ldc;
+      Cr[n] = re;
+      Cr[g.plane + n] = im;
+    } else {
+      float* Q = reinterpret_cast<float*>(g.C) + (long long)b * g.sbc + (long long)row * g.ldc;
+      const float rh = tf32_round(re), ih = tf32_round(im);
+      Q[n] = rh;
+      Q[g.plane + n] = tf32_round(re - rh);
+      Q[2 * g.plane + n] = ih;
+      Q[3 * g.plane + n] = tf32_round(im - ih);
+    }
   }
 }
 
@@ -480,10 +537,27 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, const TcGemm& g, cud
   CUtensorMap ma, mb;
   if ((e = make_map(&ma, A, BM)) != cudaSuccess) return e;
   if ((e = make_map(&mb, B, BN)) != cudaSuccess) return e;
-  dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, g.nbatch);
+  // split-K when the output tiles cannot fill the GPU and the K loop is long
+  TcGemm gg = g;
+  gg.ksplit = 1;
+  const long long tiles = (long long)((g.N + BN - 1) / BN) * ((g.M + BM - 1) / BM) * g.nbatch;
+  const int all = ((g.K + BK - 1) / BK) * g.nred;
+  if (g.part && tiles < 76 && all >= 8) {
+    int ks = (int)((152 + tiles - 1) / tiles);
+    if (ks > all / 4) ks = all / 4;
+    while (ks > 1 && 2LL * g.nbatch * ks * g.M * g.N > g.part_len) --ks;
+    if (ks > 1) gg.ksplit = ks;
+  }
+  dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, g.nbatch * gg.ksplit);
   count_launch();
-  tc_zgemm_kernel<<<grid, 128, SMEM_BYTES, s>>>(ma, mb, g);
-  return cudaGetLastError();
+  tc_zgemm_kernel<<<grid, 128, SMEM_BYTES, s>>>(ma, mb, gg);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (gg.ksplit > 1) {
+    count_launch();
+    split_reduce_kernel<<<grid_for((long long)g.nbatch * g.M * g.N), 256, 0, s>>>(gg);
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
 cudaError_t split_f64(const cplx* src, long long sb, long long rs, long long ks, int conj,

@@ -28,6 +28,11 @@ struct TcGemm {
   void* C;
   long long ldc, sbc, plane;
   int* status;
+  // optional split-K scratch (FP32): when the output has few tiles, the (reduction x K) loop
+  // is split over CTAs into partial sums that a second kernel adds up
+  float* part;
+  long long part_len;
+  int ksplit;          // set by tc_gemm
 };
 
 cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, const TcGemm& g, cudaStream_t s);

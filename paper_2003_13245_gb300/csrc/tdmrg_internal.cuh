@@ -90,9 +90,20 @@ struct QrScratch {
   int gmax;
   int nmax;
 };
+// gcap > 0 caps the cooperative grid (several QRs of concurrent instances can then co-reside)
 cudaError_t gauge_qr(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cplx* R,
-                     const QrScratch& W, int* status, cudaStream_t s);
+                     const QrScratch& W, int* status, cudaStream_t s, int gcap = 0);
 int gauge_qr_grid(int m);
+// completion pass only (skipped positions of a factorisation whose accepted flags are `acc`)
+cudaError_t gauge_qr_complete(int m, int n, int p, QrRef E, cplx* Q, const unsigned char* acc,
+                              const QrScratch& W, int* status, cudaStream_t s, int gcap = 0);
+// blocked variant (16 columns per block); scratch: gauge_qr_blocked_scratch(n, gmax) complex
+// entries and n accepted flags; W supplies the barrier and the completion pass' scratch
+long long gauge_qr_blocked_scratch(int n, int gmax);
+cudaError_t gauge_qr_blocked(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cplx* R,
+                             cplx* scratch, long long scratch_len, unsigned char* acc,
+                             const QrScratch& W, int* status, cudaStream_t s, int gcap = 0,
+                             double rank_tol = 1e-12);
 
 // dst[j][i] = conj?(src[i][j]) for an m x n source.
 cudaError_t ztranspose(int m, int n, const cplx* src, cplx* dst, int conj, cudaStream_t s);

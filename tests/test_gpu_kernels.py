@@ -71,9 +71,11 @@ def test_env_left_matches_oracle(Ml1, Mr1, Ml2, Mr2, d, Dl, Dr):
     assert np.abs(out.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("blocked", [False, True])
 @pytest.mark.parametrize("m,n,rank,p", [(12, 5, 5, 0), (300, 64, 64, 0), (1000, 130, 97, 40),
-                                        (64, 64, 30, 0), (4096, 128, 128, 0), (256, 70, 3, 300)])
-def test_gauge_qr_matches_oracle(m, n, rank, p):
+                                        (64, 64, 30, 0), (4096, 128, 128, 0), (256, 70, 3, 300),
+                                        (8192, 128, 128, 0), (2048, 128, 60, 200)])
+def test_gauge_qr_matches_oracle(m, n, rank, p, blocked):
     """Full-rank and rank-deficient (with and without completion candidates) gauge QR."""
     from oracle import tdvp
     from paper_2003_13245_gb300 import binding
@@ -86,7 +88,8 @@ def test_gauge_qr_matches_oracle(m, n, rank, p):
     # the C ABI zeroes R rows of completed positions (the oracle returns Q^H Y there)
     Q = torch.zeros((m, n), dtype=torch.complex128, device="cuda")
     R = torch.zeros((n, n), dtype=torch.complex128, device="cuda")
-    binding.kernel_gauge_qr(dev(Y), Q, R, dev(E) if E is not None else None)
+    qr = binding.kernel_gauge_qr_blocked if blocked else binding.kernel_gauge_qr
+    qr(dev(Y), Q, R, dev(E) if E is not None else None)
     Qg, Rg = Q.cpu().numpy(), R.cpu().numpy()
     assert np.abs(Qg.conj().T @ Qg - np.eye(n)).max() < 1e-12
     assert np.abs(Qg @ Rg - Y).max() <= 1e-10 * np.abs(Y).max()

@@ -28,7 +28,8 @@ def dev(a):
 
 @pytest.mark.parametrize("M,N,K,cA,cB", [(128, 64, 32, 0, 0), (1, 1, 1, 0, 0), (130, 70, 33, 1, 0),
                                          (300, 200, 700, 0, 1), (64, 129, 96, 1, 1),
-                                         (1000, 130, 128, 0, 0)])
+                                         (1000, 130, 128, 0, 0), (128, 128, 4096, 1, 0),
+                                         (40, 70, 900, 0, 1)])
 def test_zgemm_tc(M, N, K, cA, cB):
     from paper_2003_13245_gb300 import binding
     rng = np.random.default_rng(M + 3 * N + 7 * K)

@@ -43,6 +43,9 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=20.0,
                    help="CPU time budget of the oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--profile-phases", action="store_true",
+                   help="after the timed region, run one more step with the library's phase "
+                        "timers on (stream synchronised at phase ends) and report the split")
     return p.parse_args()
 
 
@@ -236,6 +239,28 @@ def run_ours(args):
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1)
     st = m.stats()
+    phases = None
+    if args.profile_phases:
+        m.set_profiling(True)
+        m.reset_stats()
+        t0 = time.perf_counter()
+        m.realtime_step(1, w["dt"])
+        m.realtime_observe()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        ps = m.stats()
+        m.set_profiling(False)
+        phases = {"step_wall_s": wall,
+                  "site_exponentials_s": ps["t_site"],
+                  "of_which_heff_s": ps["heff_ms"] / 1e3,
+                  "of_which_lanczos_fp64_s": ps["t_site"] - ps["heff_ms"] / 1e3,
+                  "gauge_shifts_s": ps["t_env"],
+                  "of_which_gauge_qr_s": ps["t_qr"],
+                  "bond_backsteps_s": ps["t_bond"],
+                  "bond_absorb_s": ps["t_absorb"],
+                  "overlap_s": ps["t_observe"],
+                  "matvecs": ps["matvecs"], "bond_matvecs": ps["bond_matvecs"],
+                  "qrs": ps["qrs"]}
     m.close()
 
     site_updates = st["site_updates"]
@@ -267,10 +292,19 @@ def run_ours(args):
                 "per_launch": "algorithmic H_eff flops 8*(Dl*Ml^2*d^2*Mr + Dr*Ml*d^2*Mr^2) "
                               "per matvec / event-timed matvec duration"}
     else:
+        # the H_eff matvec runs inside a long step: sustained bf16 peak of measured, TF32 at half
+        # the bf16 rate (nominal ratio 1.1 : 2.25 PFLOP/s dense)
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        tf32 = peaks["bf16_tflops"] / 2.0
+        tf32 = peaks["bf16_tflops_sustained"] / 2.0
         roof = {"bound": "tensor", "achieved": heff_tflops, "peak": tf32, "unit": "TFLOP/s",
-                "frac": heff_tflops / tf32 if heff_tflops else None, "traffic": None}
+                "frac": heff_tflops / tf32 if heff_tflops else None, "traffic": None,
+                "kernel": "H_eff matvec: split + tc_zgemm_kernel (tcgen05 kind::tf32) + "
+                          "mix_split_kernel + tc_zgemm_kernel, 3xTF32 complex",
+                "peak_source": "MEASURED_PEAKS bf16_tflops_sustained / 2 (TF32 dense), of measured",
+                "per_launch": "algorithmic flops 8*(Dl*Ml^2*d^2*Mr + Dr*Ml*d^2*Mr^2) per matvec "
+                              "(1.50e10 at the d^2=64, M=128 site) / event-timed matvec duration; "
+                              "3xTF32 issues 3 TF32 MMAs per real product",
+                "traffic_note": "per-kernel DRAM bytes from ncu in profiles/heff_tc_zgemm_c2_bulk_site.md"}
     steps_total = args.steps + args.warmup
     line = {
         "metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": world,
@@ -295,6 +329,8 @@ def run_ours(args):
         "clocks": clocks,
         "C_last": [Cs[-1].real, Cs[-1].imag] if Cs else None,
     }
+    if phases is not None:
+        line["phases"] = phases
     if world == 1 and not args.no_cpu_baseline:
         u, s = oracle_sample(args.cpu_seconds)
         line["cpu_baseline"] = {"value": u / s, "unit": "site-updates/s", "cores": cpu_threads(),

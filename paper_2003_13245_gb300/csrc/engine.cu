@@ -403,6 +403,8 @@ Engine::Engine(const ModelParams& p) : P(p) {
   CK(cudaMalloc(&scal_, sizeof(double) * 8));
   CK(cudaMalloc(&part_c_, sizeof(cplx) * (KMAX + 1) * NBLK));
   CK(cudaMalloc(&part_d_, sizeof(double) * NBLK));
+  CK(cudaMalloc(&red_cnt_, sizeof(unsigned) * (KMAX + 2)));
+  CK(cudaMemset(red_cnt_, 0, sizeof(unsigned) * (KMAX + 2)));
   CK(cudaMallocHost(&h_pinned_, sizeof(int) * 8));
   CK(cudaMallocHost(&h_pinned_d_, sizeof(double) * 4));
   for (auto& e : ev_) CK(cudaEventCreate(&e));
@@ -424,6 +426,7 @@ Engine::~Engine() {
   for (cplx* b : bufs)
     if (b) cudaFree(b);
   if (part_d_) cudaFree(part_d_);
+  if (red_cnt_) cudaFree(red_cnt_);
   if (scal_) cudaFree(scal_);
   if (lz_) cudaFree(lz_);
   if (status_) cudaFree(status_);
@@ -674,7 +677,7 @@ void Engine::set_ones(cplx* p) {
 // numerics helpers
 // ------------------------------------------------------------------------------------
 double Engine::norm2_dev(const cplx* x, long long n) {
-  CK(znorm2(n, x, scal_, part_d_, NBLK, nullptr, st_));
+  CK(znorm2(n, x, scal_, part_d_, red_cnt_ + KMAX + 1, nullptr, st_));
   CK(cudaMemcpyAsync(h_pinned_d_, scal_, sizeof(double), cudaMemcpyDeviceToHost, st_));
   CK(cudaStreamSynchronize(st_));
   stats.d2h_bytes += sizeof(double);

@@ -236,6 +236,7 @@ class Engine {
   cplx *Cb_ = nullptr, *Rb_ = nullptr, *Ex_ = nullptr;
   cplx* part_c_ = nullptr;
   double* part_d_ = nullptr;
+  unsigned* red_cnt_ = nullptr;     // reduction tickets (KMAX + 2), zero between launches
   double* scal_ = nullptr;          // device scalars
   LzState* lz_ = nullptr;
   QrScratch qr_{};
@@ -263,7 +264,7 @@ inline int Engine::krylov(long long n, const cplx* v, cplx* out, double tr, doub
   const int kcap = (int)std::min<long long>(cap0, n);
   LzState* S = lz_;
   const int* done = &S->done;
-  CK(znorm2(n, v, scal_, part_d_, NBLK, nullptr, st_));
+  CK(znorm2(n, v, scal_, part_d_, red_cnt_ + KMAX + 1, nullptr, st_));
   CK(lz_start(S, scal_, st_));
   CK(cudaMemcpyAsync(V_, v, sizeof(cplx) * (size_t)n, cudaMemcpyDeviceToDevice, st_));
   CK(zscale_by(n, V_, &S->inv, done, st_));
@@ -274,11 +275,11 @@ inline int Engine::krylov(long long n, const cplx* v, cplx* out, double tr, doub
     cplx* w = V_ + (size_t)(j + 1) * n;
     matvec(q, w, done);
     const int lo = j > 0 ? j - 1 : 0;
-    CK(zdots(n, j - lo + 1, V_ + (size_t)lo * n, n, w, S->h1 + lo, part_c_, NBLK, done, st_));
+    CK(zdots(n, j - lo + 1, V_ + (size_t)lo * n, n, w, S->h1 + lo, part_c_, red_cnt_, done, st_));
     CK(zsub_multi(n, j - lo + 1, V_ + (size_t)lo * n, n, S->h1 + lo, w, done, st_));
-    CK(zdots(n, j + 1, V_, n, w, S->h2, part_c_, NBLK, done, st_));
+    CK(zdots(n, j + 1, V_, n, w, S->h2, part_c_, red_cnt_, done, st_));
     CK(zsub_multi(n, j + 1, V_, n, S->h2, w, done, st_));
-    CK(znorm2(n, w, &S->nrm2, part_d_, NBLK, done, st_));
+    CK(znorm2(n, w, &S->nrm2, part_d_, red_cnt_ + KMAX + 1, done, st_));
     CK(lz_small_exp(S, j, tr, ti, ktol_, kcap, fixed_k_ > 0 ? 1 : 0, st_));
     CK(zscale_by(n, w, &S->inv, done, st_));
     CK(cudaMemcpyAsync(h_pinned_ + 4 + (j & 1) * 2, done, sizeof(int), cudaMemcpyDeviceToHost,

@@ -189,60 +189,81 @@ __device__ __forceinline__ cplx block_sum_c(cplx v, cplx* sh) {
   return out;
 }
 
-__global__ void zdots_partial_kernel(long long n, const cplx* V, long long ldv, const cplx* w,
-                                     cplx* partial, const int* skip) {
+// Dot products h[vec] = sum_e conj(V[vec][e]) w[e] in one launch: block (x, vec) reduces a
+// grid-stride chunk, writes its partial, and the last block of each vector (ticket counter)
+// sums the partials in index order -- deterministic, no second launch.
+constexpr int RED_BLOCKS = 304;      // partial blocks per vector (2 per SM)
+
+__device__ __forceinline__ bool last_block(unsigned* counter, unsigned nblocks) {
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned t = atomicAdd(counter, 1u);
+    s_last = (t == nblocks - 1);
+  }
+  __syncthreads();
+  return s_last != 0;
+}
+
+__global__ void zdots_kernel(long long n, const cplx* V, long long ldv, const cplx* w, cplx* out,
+                             cplx* partial, unsigned* counters, const int* skip) {
   if (skip && *skip) return;
   __shared__ cplx sh[32];
   const int vec = blockIdx.y;
   const cplx* v = V + vec * ldv;
-  cplx acc = make_double2(0.0, 0.0);
+  double ax = 0.0, ay = 0.0, bx = 0.0, by = 0.0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
     const cplx a = v[e], b = w[e];
-    acc.x = fma(a.x, b.x, acc.x);
-    acc.x = fma(a.y, b.y, acc.x);
-    acc.y = fma(a.x, b.y, acc.y);
-    acc.y = fma(-a.y, b.x, acc.y);
+    ax = fma(a.x, b.x, ax);
+    bx = fma(a.y, b.y, bx);
+    ay = fma(a.x, b.y, ay);
+    by = fma(-a.y, b.x, by);
   }
-  cplx s = block_sum_c(acc, sh);
+  cplx s = block_sum_c(make_double2(ax + bx, ay + by), sh);
   if (threadIdx.x == 0) partial[vec * gridDim.x + blockIdx.x] = s;
-}
-
-__global__ void reduce_partial_c_kernel(int nvec, int nblk, const cplx* partial, cplx* out,
-                                        const int* skip) {
-  if (skip && *skip) return;
-  __shared__ cplx sh[32];
-  for (int vec = 0; vec < nvec; ++vec) {
-    cplx acc = make_double2(0.0, 0.0);
-    for (int i = threadIdx.x; i < nblk; i += blockDim.x) acc = cadd(acc, partial[vec * nblk + i]);
-    cplx s = block_sum_c(acc, sh);
-    if (threadIdx.x == 0) out[vec] = s;
+  if (!last_block(&counters[vec], gridDim.x)) return;
+  double rx = 0.0, ry = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+    const cplx p = __ldcg(&partial[vec * gridDim.x + i]);     // written by other SMs
+    rx += p.x;
+    ry += p.y;
+  }
+  cplx r = block_sum_c(make_double2(rx, ry), sh);
+  if (threadIdx.x == 0) {
+    out[vec] = r;
+    counters[vec] = 0;          // ready for the next call
   }
 }
 
 cudaError_t zdots(long long n, int nvec, const cplx* V, long long ldv, const cplx* w, cplx* out,
-                  cplx* partial, int nblk, const int* skip, cudaStream_t s) {
+                  cplx* partial, unsigned* counters, const int* skip, cudaStream_t s) {
   int g = (int)((n + 255) / 256);
-  if (g > nblk) g = nblk;
+  if (g > RED_BLOCKS) g = RED_BLOCKS;
   if (g < 1) g = 1;
-  count_launch(2);
-  zdots_partial_kernel<<<dim3(g, nvec), 256, 0, s>>>(n, V, ldv, w, partial, skip);
-  reduce_partial_c_kernel<<<1, 256, 0, s>>>(nvec, g, partial, out, skip);
+  count_launch();
+  zdots_kernel<<<dim3(g, nvec), 256, 0, s>>>(n, V, ldv, w, out, partial, counters, skip);
   return cudaGetLastError();
 }
 
 __global__ void zsub_multi_kernel(long long n, int nvec, const cplx* V, long long ldv,
                                   const cplx* h, cplx* w, const int* skip) {
   if (skip && *skip) return;
+  __shared__ cplx hs[KMAX + 1];
+  if (threadIdx.x < nvec) hs[threadIdx.x] = h[threadIdx.x];
+  __syncthreads();
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
-    cplx acc = w[e];
+    double ax = w[e].x, ay = w[e].y, bx = 0.0, by = 0.0;
     for (int i = 0; i < nvec; ++i) {
-      const cplx q = V[i * ldv + e], c = h[i];
-      acc.x -= q.x * c.x - q.y * c.y;
-      acc.y -= q.x * c.y + q.y * c.x;
+      const cplx q = V[i * ldv + e], c = hs[i];
+      ax = fma(-q.x, c.x, ax);
+      bx = fma(q.y, c.y, bx);
+      ay = fma(-q.x, c.y, ay);
+      by = fma(-q.y, c.x, by);
     }
-    w[e] = acc;
+    w[e] = make_double2(ax + bx, ay + by);
   }
 }
 
@@ -256,39 +277,36 @@ cudaError_t zsub_multi(long long n, int nvec, const cplx* V, long long ldv, cons
   return cudaGetLastError();
 }
 
-__global__ void znorm2_partial_kernel(long long n, const cplx* x, double* partial,
-                                      const int* skip) {
+__global__ void znorm2_kernel(long long n, const cplx* x, double* out, double* partial,
+                              unsigned* counter, const int* skip) {
   if (skip && *skip) return;
   __shared__ cplx sh[32];
-  double acc = 0.0;
+  double a = 0.0, b = 0.0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
-    const cplx a = x[e];
-    acc = fma(a.x, a.x, acc);
-    acc = fma(a.y, a.y, acc);
+    const cplx v = x[e];
+    a = fma(v.x, v.x, a);
+    b = fma(v.y, v.y, b);
   }
-  cplx s = block_sum_c(make_double2(acc, 0.0), sh);
+  cplx s = block_sum_c(make_double2(a + b, 0.0), sh);
   if (threadIdx.x == 0) partial[blockIdx.x] = s.x;
+  if (!last_block(counter, gridDim.x)) return;
+  double r = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) r += __ldcg(&partial[i]);
+  cplx t = block_sum_c(make_double2(r, 0.0), sh);
+  if (threadIdx.x == 0) {
+    *out = t.x;
+    *counter = 0;
+  }
 }
 
-__global__ void reduce_partial_d_kernel(int nblk, const double* partial, double* out,
-                                        const int* skip) {
-  if (skip && *skip) return;
-  __shared__ cplx sh[32];
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < nblk; i += blockDim.x) acc += partial[i];
-  cplx s = block_sum_c(make_double2(acc, 0.0), sh);
-  if (threadIdx.x == 0) *out = s.x;
-}
-
-cudaError_t znorm2(long long n, const cplx* x, double* out, double* partial, int nblk,
+cudaError_t znorm2(long long n, const cplx* x, double* out, double* partial, unsigned* counter,
                    const int* skip, cudaStream_t s) {
   int g = (int)((n + 255) / 256);
-  if (g > nblk) g = nblk;
+  if (g > RED_BLOCKS) g = RED_BLOCKS;
   if (g < 1) g = 1;
-  count_launch(2);
-  znorm2_partial_kernel<<<g, 256, 0, s>>>(n, x, partial, skip);
-  reduce_partial_d_kernel<<<1, 256, 0, s>>>(g, partial, out, skip);
+  count_launch();
+  znorm2_kernel<<<g, 256, 0, s>>>(n, x, out, partial, counter, skip);
   return cudaGetLastError();
 }
 
@@ -504,10 +522,10 @@ __device__ __forceinline__ void qr_sum_partials(const double* base, long long st
     double a = 0.0, b = 0.0;
     unsigned gg = threadIdx.x;
     for (; gg + 32 < G; gg += 64) {
-      a += base[gg * stride];
-      b += base[(gg + 32) * stride];
+      a += __ldcg(&base[gg * stride]);
+      b += __ldcg(&base[(gg + 32) * stride]);
     }
-    if (gg < G) a += base[gg * stride];
+    if (gg < G) a += __ldcg(&base[gg * stride]);
     a = warp_sum(a + b);
     if (threadIdx.x == 0) red[slot] = a;
   }
@@ -578,10 +596,10 @@ __device__ bool qr_pass(const QrKernelArgs& A, int r0, int nr, int lim, cplx* v,
       if (acc[i]) {
         unsigned gg = part;
         for (; gg + P < G; gg += 2 * P) {
-          s0 = cadd(s0, base[(long long)gg * (n + 1) + i]);
-          s1 = cadd(s1, base[(long long)(gg + P) * (n + 1) + i]);
+          s0 = cadd(s0, __ldcg(&base[(long long)gg * (n + 1) + i]));
+          s1 = cadd(s1, __ldcg(&base[(long long)(gg + P) * (n + 1) + i]));
         }
-        if (gg < G) s0 = cadd(s0, base[(long long)gg * (n + 1) + i]);
+        if (gg < G) s0 = cadd(s0, __ldcg(&base[(long long)gg * (n + 1) + i]));
       }
       const cplx s = cadd(s0, s1);
       if (lim * P <= T) sm[part * lim + i] = s;
@@ -662,7 +680,7 @@ __device__ bool qr_norm(const QrKernelArgs& A, int nr, const cplx* v, double& ou
     A.partn[buf * G + blockIdx.x] = t;
   }
   if (!grid_barrier(A.bar, G, A.status)) return false;
-  qr_sum_partials(A.partn + buf * G, 1, G, red, 32);
+  qr_sum_partials(A.partn + buf * G, 1, G, red, 32);   // reads through L2 (other CTAs)
   __syncthreads();
   out = sqrt(red[32]);
   buf ^= 1;

@@ -245,61 +245,49 @@ __global__ void __launch_bounds__(128, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const bool ok = __syncthreads_and(waited ? 1 : 0) && !*s_fail;
   if (ok) {
-    const int row = m0 + warp * 32 + lane;
+    // TMEM -> registers -> shared tile (the pipeline stages are free now), then row-coalesced
+    // global stores.  Tile rows are padded to 65 floats: conflict-free column writes.
+    constexpr int TP = BN + 1;
+    float* tre = reinterpret_cast<float*>(smem);
+    float* tim = tre + BM * TP;
+    const int lrow = warp * 32 + lane;
     const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
     for (int c = 0; c < BN; c += 16) {
       float re[16], im[16];
       tmem_ld16(lane_addr + c, re);
       tmem_ld16(lane_addr + BN + c, im);
-      if (total == 0) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) re[i] = im[i] = 0.f;
+      for (int i = 0; i < 16; ++i) {
+        tre[lrow * TP + c + i] = total == 0 ? 0.f : re[i];
+        tim[lrow * TP + c + i] = total == 0 ? 0.f : im[i];
       }
-      if (row < g.M) {
-        if (ks > 1) {
-          const long long pl = (long long)g.nbatch * ks * g.M * g.N;
-          float* P = g.part + (((long long)bz * ks + sp) * g.M + row) * g.N;
-#pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int n = n0 + c + i;
-            if (n < g.N) {
-              P[n] = re[i];
-              P[pl + n] = im[i];
-            }
-          }
-        } else if (g.out_mode == 0) {
-          double2* C = reinterpret_cast<double2*>(g.C) + (long long)bz * g.sbc + (long long)row * g.ldc;
-#pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int n = n0 + c + i;
-            if (n < g.N) C[n] = make_double2((double)re[i], (double)im[i]);
-          }
-        } else if (g.out_mode == 1) {
-          float* Cr = reinterpret_cast<float*>(g.C) + (long long)bz * g.sbc + (long long)row * g.ldc;
-          float* Ci = Cr + g.plane;
-#pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int n = n0 + c + i;
-            if (n < g.N) {
-              Cr[n] = re[i];
-              Ci[n] = im[i];
-            }
-          }
-        } else {
-          float* P = reinterpret_cast<float*>(g.C) + (long long)bz * g.sbc + (long long)row * g.ldc;
-#pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int n = n0 + c + i;
-            if (n < g.N) {
-              const float rh = tf32_round(re[i]), ih = tf32_round(im[i]);
-              P[n] = rh;
-              P[g.plane + n] = tf32_round(re[i] - rh);
-              P[2 * g.plane + n] = ih;
-              P[3 * g.plane + n] = tf32_round(im[i] - ih);
-            }
-          }
-        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < BM * BN; e += blockDim.x) {
+      const int rl = e / BN, cl = e % BN;
+      const int row = m0 + rl, n = n0 + cl;
+      if (row >= g.M || n >= g.N) continue;
+      const float vr = tre[rl * TP + cl], vi = tim[rl * TP + cl];
+      if (ks > 1) {
+        const long long pl = (long long)g.nbatch * ks * g.M * g.N;
+        float* P = g.part + (((long long)bz * ks + sp) * g.M + row) * g.N;
+        P[n] = vr;
+        P[pl + n] = vi;
+      } else if (g.out_mode == 0) {
+        double2* C = reinterpret_cast<double2*>(g.C) + (long long)bz * g.sbc + (long long)row * g.ldc;
+        C[n] = make_double2((double)vr, (double)vi);
+      } else if (g.out_mode == 1) {
+        float* Cr = reinterpret_cast<float*>(g.C) + (long long)bz * g.sbc + (long long)row * g.ldc;
+        Cr[n] = vr;
+        Cr[g.plane + n] = vi;
+      } else {
+        float* P = reinterpret_cast<float*>(g.C) + (long long)bz * g.sbc + (long long)row * g.ldc;
+        const float rh = tf32_round(vr), ih = tf32_round(vi);
+        P[n] = rh;
+        P[g.plane + n] = tf32_round(vr - rh);
+        P[2 * g.plane + n] = ih;
+        P[3 * g.plane + n] = tf32_round(vi - ih);
       }
     }
   } else if (threadIdx.x == 0) {

@@ -93,7 +93,7 @@ __device__ bool qb_reduce(const QbArgs& A, int off, int cnt, unsigned G) {
   for (int e = lo + warp; e < hi; e += nw) {
     double ax = 0.0, ay = 0.0;
     for (unsigned g = lane; g < G; g += 32) {
-      const cplx u = A.part[(long long)g * A.PS + off + e];
+      const cplx u = __ldcg(&A.part[(long long)g * A.PS + off + e]);   // other CTAs' data
       ax += u.x;
       ay += u.y;
     }
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(QB_THREADS) gauge_qr_blocked_kernel(QbArgs A) 
     }
   }
   if (!qb_reduce(A, 0, 1, G)) return;
-  const double thr = A.rank_tol * sqrt(A.fin[0].x);
+  const double thr = A.rank_tol * sqrt(__ldcg(&A.fin[0]).x);
 
   int j0 = 0;
   while (j0 < n) {
@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(QB_THREADS) gauge_qr_blocked_kernel(QbArgs A) 
       if (!qb_reduce(A, 0, j0 * QB + QB, G)) return;
       for (int e = threadIdx.x; e < j0 * bsz; e += T) {
         const int i = e / bsz, t = e % bsz;
-        const cplx h = acc[i] ? A.fin[i * QB + t] : make_double2(0.0, 0.0);
+        const cplx h = acc[i] ? __ldcg(&A.fin[i * QB + t]) : make_double2(0.0, 0.0);
         H[i * QB + t] = h;
         Hacc[i * QB + t] = make_double2(Hacc[i * QB + t].x + h.x, Hacc[i * QB + t].y + h.y);
       }
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(QB_THREADS) gauge_qr_blocked_kernel(QbArgs A) 
         s = wsum(s);
         if ((threadIdx.x & 31) == 0) {
           dvec[QB + t] = s;
-          dvec[t] = A.fin[j0 * QB + t].x;
+          dvec[t] = __ldcg(&A.fin[j0 * QB + t]).x;
         }
       }
       // v_t[r] -= sum_i Q[r][i] h_it   (thread per (r, t))
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(QB_THREADS) gauge_qr_blocked_kernel(QbArgs A) 
       mypart[e] = make_double2(ax + bx, ay + by);
     }
     if (!qb_reduce(A, 0, QB * QB, G)) return;
-    for (int e = threadIdx.x; e < QB * QB; e += T) Gb[e] = A.fin[e];
+    for (int e = threadIdx.x; e < QB * QB; e += T) Gb[e] = __ldcg(&A.fin[e]);
     __syncthreads();
     // ---- Gram-Schmidt with skips inside the block (right-looking, warp 0)
     if (threadIdx.x < 32) {

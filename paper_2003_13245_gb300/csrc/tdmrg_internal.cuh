@@ -61,12 +61,14 @@ struct LzState {
   int pad;
 };
 
-// partial[vec][blk] = sum_{e in chunk blk} conj(V[vec][e]) * w[e]
+// out[vec] = sum_e conj(V[vec][e]) * w[e], vec < nvec (one launch; partial: nvec * 304
+// entries, counters: nvec zero-initialised tickets, left at zero on return)
 cudaError_t zdots(long long n, int nvec, const cplx* V, long long ldv, const cplx* w,
-                  cplx* out, cplx* partial, int nblk, const int* skip, cudaStream_t s);
+                  cplx* out, cplx* partial, unsigned* counters, const int* skip, cudaStream_t s);
 cudaError_t zsub_multi(long long n, int nvec, const cplx* V, long long ldv, const cplx* h,
                        cplx* w, const int* skip, cudaStream_t s);
-cudaError_t znorm2(long long n, const cplx* x, double* out, double* partial, int nblk,
+// *out = sum |x|^2 (one launch; partial: 304 entries, counter: one zero-initialised ticket)
+cudaError_t znorm2(long long n, const cplx* x, double* out, double* partial, unsigned* counter,
                    const int* skip, cudaStream_t s);
 cudaError_t zscale_by(long long n, cplx* x, const double* factor, const int* skip,
                       cudaStream_t s);

@@ -43,6 +43,9 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=20.0,
                    help="CPU time budget of the oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--workload", default="c2", choices=["c2", "c3-batch", "c5"],
+                   help="c2: the headline chain; c3-batch: 36 independent instances stepped "
+                        "together; c5: Holstein-Peierls N=32, 4 modes, M=256")
     p.add_argument("--profile-phases", action="store_true",
                    help="after the timed region, run one more step with the library's phase "
                         "timers on (stream synchronised at phase ends) and report the split")
@@ -344,12 +347,112 @@ def run_ours(args):
     return 0
 
 
+# ----------------------------------------------------------------------------------------
+# secondary workloads (separate JSON lines; the default run is the c2 chain above)
+# ----------------------------------------------------------------------------------------
+C3_M = {0.25: 32, 0.5: 48, 1.0: 64, 2.0: 96, 4.0: 128, 8.0: 128}
+
+
+def run_c3_batch(args):
+    """36 instances (V in {0.25..8} x kBT in {0.5,1,2} x N in {8,24}), one mode per molecule
+    (w = g = 1, nmax = 6), M tied to V, 3xTF32, fixed Krylov dimension 8, stepped together."""
+    import torch
+    from paper_2003_13245_gb300 import Batch, Model, PREC_C64_3XTF32
+    from paper_2003_13245_gb300.build import build_library
+    build_library()
+    torch.cuda.set_device(0)
+    models, sites = [], 0
+    t0 = time.perf_counter()
+    for N in (8, 24):
+        for V, M in C3_M.items():
+            for kT in (0.5, 1.0, 2.0):
+                m = Model(N, [1.0], [1.0], [6], V, precision=PREC_C64_3XTF32,
+                          krylov=(1e-7, 32, 8))
+                m.set_graphs(True)
+                m.thermal_prepare(1.0 / kT, 0.05, M)
+                m.realtime_init()
+                models.append(m)
+                sites += 2 * N
+    prep_s = time.perf_counter() - t0
+    b = Batch(models)
+    for _ in range(args.warmup):
+        b.realtime_step(1, 0.05)
+    for m in models:
+        m.reset_stats()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    b.realtime_step(args.steps, 0.05)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t1
+    su = sum(m.stats()["site_updates"] for m in models)
+    # the same step run instance after instance (graph replay, synchronised), for comparison
+    t2 = time.perf_counter()
+    for m in models:
+        m.realtime_step(1, 0.05)
+    torch.cuda.synchronize()
+    seq = time.perf_counter() - t2
+    C = [m.realtime_observe() for m in models]
+    line = {"metric": "TDVP site-updates/s summed over 36 batched instances", "workload": "c3-batch",
+            "value": su / el, "unit": "site-updates/s", "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "instances": len(models), "sites_total": sites,
+            "site_updates_per_step": su / args.steps, "prep_s": prep_s,
+            "sequential_ms_per_step": 1e3 * seq,
+            "dtype": "c64-3xtf32", "krylov": "fixed k=8", "data": "synthetic",
+            "C_sample": [[c.real, c.imag] for c in C[:3]]}
+    print(json.dumps(line))
+    b.close()
+    for m in models:
+        m.close()
+    return 0
+
+
+def run_c5(args):
+    """Holstein-Peierls N=32, 4 modes drawn once from U[0.1,1.5] x U[0.2,1.2] (seed 2008),
+    nmax = clamp(round(10 - 6 (w - 0.1)/1.4), 4, 10), Peierls alpha = 0.1 (w_p = 0.2,
+    nmax_p = 8), V = kT = 1, M = 256, 3xTF32."""
+    import torch
+    from paper_2003_13245_gb300 import Model, PREC_C64_3XTF32
+    from paper_2003_13245_gb300.build import build_library
+    build_library()
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(2008)
+    w = rng.uniform(0.1, 1.5, 4)
+    g = rng.uniform(0.2, 1.2, 4)
+    nm = [int(min(10, max(4, round(10 - 6 * (x - 0.1) / 1.4)))) for x in w]
+    m = Model(32, list(w), list(g), nm, 1.0, peierls=(0.1, 0.2, 8), precision=PREC_C64_3XTF32)
+    t0 = time.perf_counter()
+    m.thermal_prepare(1.0, 0.05, 256)
+    m.realtime_init()
+    prep_s = time.perf_counter() - t0
+    m.reset_stats()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    m.realtime_step(args.steps, 0.05)
+    c = m.realtime_observe()
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t1
+    st = m.stats()
+    line = {"metric": "TDVP site-updates/s, Holstein-Peierls N=32 4 modes M=256", "workload": "c5",
+            "value": st["site_updates"] / el, "unit": "site-updates/s", "steps": args.steps,
+            "ms_per_step": 1e3 * el / args.steps, "sites": 32 * 6, "omega": list(w), "g": list(g),
+            "nmax": nm, "heff_tflops": st["heff_flops"] / (st["heff_ms"] / 1e3) / 1e12,
+            "prep_s": prep_s, "prep": "kT=1, dtau=0.05 (10 imaginary steps)",
+            "dtype": "c64-3xtf32", "data": "synthetic", "C": [c.real, c.imag]}
+    print(json.dumps(line))
+    m.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.steps < 1 or args.warmup < 0:
         raise SystemExit("need --steps >= 1")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "c3-batch":
+        return run_c3_batch(args)
+    if args.workload == "c5":
+        return run_c5(args)
     return run_ours(args)
 
 

@@ -779,12 +779,17 @@ void Engine::shift_left(DevMps& s, int k, const cplx* center, cplx* Cbond) {
   stats.env_updates += 1;
 }
 
+// The bond factors carry the norm of |I> on the one-carrier sector, which grows like the
+// square root of the sector's dimension (e^138 for 32 molecules with four modes): each one is
+// normalised in FP64 before it is absorbed (the tensor-core absorb holds FP32 exponents) and
+// log ||.||^2 is accumulated on the device.
 void Engine::right_canonicalize(DevMps& s) {
   const int L = s.L();
   set_ones(s.Lenv[0]);
   set_ones(s.Renv[L - 1]);
   for (int k = L - 1; k > 0; --k) {
     shift_left(s, k, s.A[k], Cb_);
+    renormalize(Cb_, (long long)s.Mb[k] * s.Mb[k]);
     absorb_right(s.A[k - 1], (long long)s.Mb[k - 1] * s.D[k - 1], Cb_, s.Mb[k]);
   }
 }
@@ -940,8 +945,19 @@ void Engine::realtime_step_launch(double dt) {
 
 void Engine::sync_and_check() { check_status(); }
 
+// Imaginary time: the center is multiplied by exp(-tau H_eff / 2) at every site and by
+// exp(+tau K / 2) at every bond, so its norm drifts by about exp(-tau <H> / 2) per half step
+// and by e^(-beta <H>) over the whole preparation.  It is renormalised after each bond
+// absorption, which keeps the tensor-core operands near unit scale, and log ||.||^2
+// accumulates on the device into log Z (a scalar: the direction of the state is unchanged).
+void Engine::renormalize(cplx* A, long long n) {
+  CK(znorm2(n, A, scal_ + 2, part_d_, red_cnt_ + KMAX + 1, nullptr, st_));
+  CK(znormalize_log(n, A, scal_ + 2, scal_ + 3, st_));
+}
+
 void Engine::tdvp_step_body(DevMps& s, double tr, double ti) {
   const double hr = 0.5 * tr, hi = 0.5 * ti;
+  const bool imag = (ti == 0.0);
   const int L = s.L();
   Ctx c = ctx();
   double t0;
@@ -968,6 +984,7 @@ void Engine::tdvp_step_body(DevMps& s, double tr, double ti) {
       toc(stats.t_bond, t0);
       t0 = tic();
       absorb_left(Rb_, M, s.A[k + 1], (long long)s.D[k + 1] * s.Mb[k + 2]);
+      if (imag) renormalize(s.A[k + 1], s.size(k + 1));
       toc(stats.t_absorb, t0);
     } else {
       CK(cudaMemcpyAsync(s.A[k], Kout_, sizeof(cplx) * (size_t)s.size(k),
@@ -997,6 +1014,7 @@ void Engine::tdvp_step_body(DevMps& s, double tr, double ti) {
       toc(stats.t_bond, t0);
       t0 = tic();
       absorb_right(s.A[k - 1], (long long)s.Mb[k - 1] * s.D[k - 1], Rb_, M);
+      if (imag) renormalize(s.A[k - 1], s.size(k - 1));
       toc(stats.t_absorb, t0);
     } else {
       CK(cudaMemcpyAsync(s.A[k], Kout_, sizeof(cplx) * (size_t)s.size(k),
@@ -1128,6 +1146,7 @@ void Engine::thermal_prepare(double beta, double dtau, int M) {
     CK(cudaStreamSynchronize(st_));
   }
   cudaFree(d_ent);
+  CK(cudaMemsetAsync(scal_ + 3, 0, sizeof(double), st_));
   right_canonicalize(psi_b_);
   check_status();
   double n2 = norm2_dev(psi_b_.A[0], psi_b_.size(0));
@@ -1141,6 +1160,10 @@ void Engine::thermal_prepare(double beta, double dtau, int M) {
     logZ_ += std::log(n2);
     scale_dev(psi_b_.A[0], psi_b_.size(0), 1.0 / std::sqrt(n2));
   }
+  // the renormalisations inside the sweeps
+  CK(cudaMemcpyAsync(h_pinned_d_ + 2, scal_ + 3, sizeof(double), cudaMemcpyDeviceToHost, st_));
+  CK(cudaStreamSynchronize(st_));
+  logZ_ += h_pinned_d_[2];
   prepared_ = true;
 }
 

@@ -195,6 +195,7 @@ class Engine {
   void absorb_left(const cplx* C, int M, cplx* A, long long ncols);
   void absorb_right(cplx* A, long long nrows, const cplx* C, int M);
   void set_ones(cplx* p);
+  void renormalize(cplx* A, long long n);
   double norm2_dev(const cplx* x, long long n);
   void scale_dev(cplx* x, long long n, double f);
   Cx overlap(const DevMps& bra, const DevMpo& W, const DevMps& ket);

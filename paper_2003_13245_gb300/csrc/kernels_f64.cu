@@ -310,6 +310,29 @@ cudaError_t znorm2(long long n, const cplx* x, double* out, double* partial, uns
   return cudaGetLastError();
 }
 
+// x *= 1/sqrt(*nrm2); *logacc += log(*nrm2)  (imaginary-time renormalisation of the center)
+__global__ void znormalize_log_kernel(long long n, cplx* x, const double* nrm2, double* logacc) {
+  const double s = *nrm2;
+  if (!(s > 0.0)) return;
+  const double f = 1.0 / sqrt(s);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *logacc += log(s);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    x[e].x *= f;
+    x[e].y *= f;
+  }
+}
+
+cudaError_t znormalize_log(long long n, cplx* x, const double* nrm2, double* logacc,
+                           cudaStream_t s) {
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  count_launch();
+  znormalize_log_kernel<<<(int)blocks, 256, 0, s>>>(n, x, nrm2, logacc);
+  return cudaGetLastError();
+}
+
 __global__ void zscale_by_kernel(long long n, cplx* x, const double* factor, const int* skip) {
   if (skip && *skip) return;
   const double f = *factor;

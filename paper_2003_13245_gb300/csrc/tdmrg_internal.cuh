@@ -72,6 +72,9 @@ cudaError_t znorm2(long long n, const cplx* x, double* out, double* partial, uns
                    const int* skip, cudaStream_t s);
 cudaError_t zscale_by(long long n, cplx* x, const double* factor, const int* skip,
                       cudaStream_t s);
+// x /= sqrt(*nrm2) and *logacc += log(*nrm2) (no host round trip)
+cudaError_t znormalize_log(long long n, cplx* x, const double* nrm2, double* logacc,
+                           cudaStream_t s);
 cudaError_t lz_start(LzState* S, const double* nrm2, cudaStream_t s);
 cudaError_t lz_small_exp(LzState* S, int j, double tau_re, double tau_im, double tol,
                          int kcap, int fixed, cudaStream_t s);

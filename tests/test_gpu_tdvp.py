@@ -140,3 +140,24 @@ def test_mixed_precision_truncated_against_fp64():
         out.append(m.correlation(t, 0.05))
         m.close()
     assert np.abs(out[1] - out[0]).max() / abs(out[0][0]) < 2e-4
+
+
+def test_mixed_precision_sector_norm_beyond_fp32():
+    """32 molecules with four modes (nmax 4..10): ||I>||^2 on the one-carrier sector is about
+    e^300, far outside the FP32 exponent range that the tensor-core operands keep.  The
+    mixed-precision preparation must still give the FP64 log Z and C(0)."""
+    from paper_2003_13245_gb300 import PREC_C64_3XTF32
+    rng = np.random.default_rng(2008)
+    w = rng.uniform(0.1, 1.5, 4)
+    g = rng.uniform(0.2, 1.2, 4)
+    nm = [int(min(10, max(4, round(10 - 6 * (x - 0.1) / 1.4)))) for x in w]
+    res = []
+    for prec in (0, PREC_C64_3XTF32):
+        m = _model(32, list(w), list(g), nm, 1.0, precision=prec)
+        m.thermal_prepare(0.1, 0.05, 8)
+        res.append((m.logz(), m.correlation(np.array([0.0]), 0.05)[0]))
+        m.close()
+    (lz0, c0), (lz1, c1) = res
+    assert np.isfinite(lz1) and lz0 > 200.0
+    assert abs(lz1 - lz0) < 1e-6 * abs(lz0)
+    assert abs(c1 - c0) < 2e-4 * abs(c0)

@@ -220,6 +220,21 @@ int tdmrg_kernel_gauge_qr_blocked(int m, int n, const void* Y, int p, const void
 int tdmrg_kernel_gauge_qr_noalloc(int m, int n, const void* Y, int p, const void* E, void* Q,
                                   void* R, int* status, void* stream);
 
+/* Bond exponential of the projector-splitting step (Eq. S1, the zero-site term):
+ * out = exp(tau K) C with (K C)[a][b] = sum_w sum_{a',b'} L[w][a][a'] C[a'][b'] R[w][b][b'],
+ * tau = tau_re + i tau_im.  L and R are Dw x M x M left/right environments (device, complex
+ * FP64 interleaved, row-major), C and out M x M (device; out may not alias C).  K must be
+ * Hermitian (as it is for environments of a Hermitian MPO).  The whole Lanczos run is one
+ * cooperative launch: contractions in complex FP32 (the mixed-precision path's bond step),
+ * orthogonalisation (two classical Gram-Schmidt passes), small exponential and norms in FP64;
+ * stop when beta_{k+1} |c_k| < tol or at kmax (<= 32) vectors.  kused (host, may be NULL)
+ * receives the number of Krylov vectors.  Allocates its scratch (freed before return);
+ * synchronises `stream`; TDMRG_ERR_TIMEOUT if the bounded grid barrier gave up;
+ * TDMRG_ERR_ARG if M is too large for one co-resident grid (M <= 1200 with 152 SMs). */
+int tdmrg_kernel_bond_exp(int M, int Dw, const void* L, const void* R, const void* C, void* out,
+                          double tau_re, double tau_im, double tol, int kmax, int* kused,
+                          void* stream);
+
 /* Krylov exponential (K2/K3) of a dense Hermitian matrix H (n x n, device):
  * out = exp(tau H) v with tau = tau_re + i tau_im, Lanczos with full re-orthogonalisation
  * in FP64 and the small exponential on the device.  kused (host, may be NULL) receives

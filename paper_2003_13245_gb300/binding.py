@@ -59,6 +59,7 @@ _SIGS = {
     "tdmrg_kernel_env_left": [_i, _i, _i, _i, _i, _i, _i, _dp, _p, _p, _p, _p, _p, _p, _p],
     "tdmrg_kernel_gauge_qr": [_i, _i, _p, _i, _p, _p, _p, _p, _p],
     "tdmrg_kernel_krylov_dense": [_i, _p, _p, _p, _d, _d, _d, _i, _ip, _p],
+    "tdmrg_kernel_bond_exp": [_i, _i, _p, _p, _p, _p, _d, _d, _d, _i, _ip, _p],
     "tdmrg_kernel_zgemm_tc": [_i, _i, _i, _p, _p, _i, _i, _p, _p],
     "tdmrg_kernel_gauge_qr_noalloc": [_i, _i, _p, _i, _p, _p, _p, _p, _p],
     "tdmrg_kernel_gauge_qr_blocked": [_i, _i, _p, _i, _p, _p, _p, _p, _p],
@@ -305,6 +306,17 @@ def kernel_gauge_qr_noalloc(Y, Q, R, E=None, status=None, stream=None):
     p = 0 if E is None else E.shape[1]
     _check(lib.tdmrg_kernel_gauge_qr_noalloc(m, n, _ptr(Y), p, _ptr(E), _ptr(Q), _ptr(R),
                                              _ptr(status), _stream_ptr(stream)))
+
+
+def kernel_bond_exp(L, R, C, out, tau, tol=1e-7, kmax=32, stream=None):
+    """out = exp(tau K) C, (K C)[a,b] = sum L[w,a,a'] C[a',b'] R[w,b,b'] (one launch)."""
+    lib = load()
+    k = ctypes.c_int()
+    Dw, M = L.shape[0], L.shape[1]
+    _check(lib.tdmrg_kernel_bond_exp(int(M), int(Dw), _ptr(L), _ptr(R), _ptr(C), _ptr(out),
+                                     float(np.real(tau)), float(np.imag(tau)), float(tol),
+                                     int(kmax), ctypes.byref(k), _stream_ptr(stream)))
+    return k.value
 
 
 def kernel_krylov_dense(H, v, out, tau, tol=1e-13, kmax=32, stream=None):

@@ -1,0 +1,468 @@
+// Fused bond exponential of the mixed-precision path: out = exp(tau K) C for the bond
+// operator K C = sum_w L_w C R_w^T (the zero-site term of the projector-splitting step,
+// Eq. S1), the whole Lanczos run in one cooperative launch.
+//
+// Why one launch: a bond matrix holds M^2 elements (16384 at M = 128), so each step of the
+// host-driven Lanczos -- two contractions, four Gram-Schmidt kernels, a norm, the small
+// exponential and the host's poll of the stop flag -- lasts a few microseconds and the
+// chain of launches sets the pace.  Here the grid synchronises through a bounded barrier
+// five times per Krylov vector and never returns to the host.
+//
+// Per Krylov vector j (CTA g owns the contiguous slice [g*S, g*S + S) of every vector):
+//  A.  T_w = L_w q_j for every channel w: complex FP32 FMA on 32 x 32 output tiles (the
+//      contraction is 2 Dw M^3 complex MACs, too small to keep a tensor-core pipeline busy);
+//  B.  P_w = T_w R_w^T, one partial per channel (the channel sum is taken in C1, in order);
+//  C1. w = sum_w P_w in FP64 on the own slice; partial dots against q_{j-1}, q_j;
+//  C2. first projection; partial dots against q_0 .. q_j (second, full pass);
+//  C3. second projection; partial ||w||^2;
+//  C4. every CTA sums the same partials in the same order and runs the same small
+//      exponential on one warp, so all reach the same result and the same stop decision
+//      without a broadcast; otherwise q_{j+1} = w / beta_{j+1} on the own slice.
+// Precision follows the mixed path: the contractions in complex FP32 (FMA, 24-bit
+// significands: no coarser than the 3xTF32 tensor-core products), every Lanczos quantity,
+// the small exponential and all norms in FP64.  All reductions have a fixed order: the
+// result does not depend on timing.
+#include "tdmrg_internal.cuh"
+#include "lanczos_exp.cuh"
+
+namespace tdmrg {
+
+namespace {
+
+constexpr int BT = 256;                 // threads per CTA
+constexpr int TL = 32;                  // output tile edge and k chunk
+constexpr int TP = TL + 2;              // padded row (16-byte aligned float2 pairs)
+constexpr int NV = KMAX + 1;            // partial-dot slots per CTA
+constexpr long long BK_TIMEOUT = 4000000000LL;   // about 2 s at 2 GHz
+
+struct BondArgs {
+  int M, Dw, G, S, kcap, fixed;
+  long long n;
+  const cplx* L;       // [Dw][M][M]
+  const cplx* R;       // [Dw][M][M]
+  const cplx* v;       // [M][M]
+  cplx* out;           // [M][M]
+  cplx* V;             // kcap vectors of n
+  cplx* W;             // n: the projected, unnormalised new vector
+  float2* T;           // [Dw][n]
+  float2* P;           // [Dw][n]
+  cplx* part;          // 2 * G * NV
+  double* partn;       // G
+  unsigned* bar;
+  int* status;
+  unsigned long long* mv;
+  double tr, ti, tol;
+};
+
+__device__ __forceinline__ double bk_wsum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ bool bk_barrier(unsigned* bar, unsigned nblocks, int* status) {
+  __syncthreads();
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = bar + 1;
+    volatile int* vstat = status;
+    const unsigned gen = *vgen;
+    __threadfence();
+    const unsigned prev = atomicAdd(bar, 1u);
+    int ok = 1;
+    if (prev == nblocks - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == gen) {
+        if (*vstat) { ok = 0; break; }
+        if (clock64() - t0 > BK_TIMEOUT) {
+          atomicExch(status, 1);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__device__ __forceinline__ void cfma32(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(a.y, b.x, acc.y);
+}
+
+struct TileSmem {
+  float2 at[TL][TP];   // A transposed: at[k][row]
+  float2 b[TL][TP];    // b[k][col]
+};
+
+// acc[i][j] += sum_{k < K} A(r0 + i, k) B(k, c0 + j) for the thread's 2 x 2 outputs
+// (r0 = 2 (tid / 16), c0 = 2 (tid % 16)) of a 32 x 32 tile, through shared memory in
+// 32-deep chunks.  ldA(r, k) / ldB(k, c) return the operand (zero outside the matrices);
+// kfastB selects the load order of B that is contiguous in global memory.
+template <bool kfastB, class FA, class FB>
+__device__ __forceinline__ void tile_cgemm(int K, FA ldA, FB ldB, TileSmem& sm,
+                                           float2 acc[2][2]) {
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  for (int k0 = 0; k0 < K; k0 += TL) {
+#pragma unroll
+    for (int u = 0; u < (TL * TL) / BT; ++u) {
+      const int e = tid + u * BT;
+      const int r = e >> 5, kk = e & 31;
+      sm.at[kk][r] = ldA(r, k0 + kk);
+      if (kfastB) {
+        sm.b[kk][r] = ldB(k0 + kk, r);          // (k fast, c = e / 32)
+      } else {
+        sm.b[r][kk] = ldB(k0 + r, kk);          // (c fast, k = e / 32)
+      }
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < TL; ++kk) {
+      const float4 a = *reinterpret_cast<const float4*>(&sm.at[kk][2 * ty]);
+      const float4 b = *reinterpret_cast<const float4*>(&sm.b[kk][2 * tx]);
+      const float2 a0 = make_float2(a.x, a.y), a1 = make_float2(a.z, a.w);
+      const float2 b0 = make_float2(b.x, b.y), b1 = make_float2(b.z, b.w);
+      cfma32(acc[0][0], a0, b0);
+      cfma32(acc[0][1], a0, b1);
+      cfma32(acc[1][0], a1, b0);
+      cfma32(acc[1][1], a1, b1);
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ float2 to_f2(cplx z) {
+  return make_float2(__double2float_rn(z.x), __double2float_rn(z.y));
+}
+
+// Warp `wv` computes the partial dots of vectors i = i0 + wv, i0 + wv + 8, ... < i1 over the
+// own slice (lanes stride the slice, fixed warp tree) and stores them at part[g * NV + i].
+__device__ __forceinline__ void slice_dots(const BondArgs& A, const cplx* ws, long long e0,
+                                           int len, int i0, int i1, cplx* part) {
+  const int lane = threadIdx.x & 31, wv = threadIdx.x >> 5;
+  for (int i = i0 + wv; i < i1; i += BT / 32) {
+    const cplx* q = A.V + (size_t)i * A.n + e0;
+    double sr = 0.0, si = 0.0;
+    for (int e = lane; e < len; e += 32) {
+      const cplx a = q[e], b = ws[e];
+      sr = fma(a.x, b.x, sr);
+      sr = fma(a.y, b.y, sr);
+      si = fma(a.x, b.y, si);
+      si = fma(-a.y, b.x, si);
+    }
+    sr = bk_wsum(sr);
+    si = bk_wsum(si);
+    if (lane == 0) part[(size_t)blockIdx.x * NV + i] = make_double2(sr, si);
+  }
+}
+
+// h[i] = sum_g part[g * NV + i] for i in [i0, i1), every CTA in the same order.
+__device__ __forceinline__ void reduce_dots(const BondArgs& A, const cplx* part, int i0, int i1,
+                                            cplx* h) {
+  const int lane = threadIdx.x & 31, wv = threadIdx.x >> 5;
+  for (int i = i0 + wv; i < i1; i += BT / 32) {
+    double sr = 0.0, si = 0.0;
+    for (int g = lane; g < A.G; g += 32) {
+      const cplx p = __ldcg(&part[(size_t)g * NV + i]);
+      sr += p.x;
+      si += p.y;
+    }
+    sr = bk_wsum(sr);
+    si = bk_wsum(si);
+    if (lane == 0) h[i] = make_double2(sr, si);
+  }
+  __syncthreads();
+}
+
+// ws[e] -= sum_{i in [i0, i1)} h[i] q_i[e] on the own slice
+__device__ __forceinline__ void slice_project(const BondArgs& A, cplx* ws, long long e0, int len,
+                                              int i0, int i1, const cplx* h) {
+  for (int e = threadIdx.x; e < len; e += BT) {
+    double ax = ws[e].x, ay = ws[e].y;
+    for (int i = i0; i < i1; ++i) {
+      const cplx q = A.V[(size_t)i * A.n + e0 + e], c = h[i];
+      ax = fma(-q.x, c.x, ax);
+      ax = fma(q.y, c.y, ax);
+      ay = fma(-q.x, c.y, ay);
+      ay = fma(-q.y, c.x, ay);
+    }
+    ws[e] = make_double2(ax, ay);
+  }
+  __syncthreads();
+}
+
+// sum over CTAs of partn (warp 0, fixed order), broadcast through *dst
+__device__ __forceinline__ void reduce_norm(const BondArgs& A, double* dst) {
+  if (threadIdx.x < 32) {
+    double s = 0.0;
+    for (int g = threadIdx.x; g < A.G; g += 32) s += __ldcg(&A.partn[g]);
+    s = bk_wsum(s);
+    if (threadIdx.x == 0) *dst = s;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void slice_norm(const BondArgs& A, const cplx* ws, int len,
+                                           double* red) {
+  double s = 0.0;
+  for (int e = threadIdx.x; e < len; e += BT) s = fma(ws[e].x, ws[e].x, fma(ws[e].y, ws[e].y, s));
+  s = bk_wsum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < BT / 32; ++w) t += red[w];
+    A.partn[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(BT, 1) bond_exp_kernel(BondArgs A) {
+  extern __shared__ __align__(16) unsigned char dyn[];
+  cplx* ws = reinterpret_cast<cplx*>(dyn);            // own slice of w, S entries
+  __shared__ __align__(16) TileSmem sm;
+  __shared__ cplx h1[NV], h2[NV], cc[KMAX];
+  __shared__ double alpha[KMAX], beta[KMAX + 1], red[BT / 32];
+  __shared__ double s_nrm, s_b0, s_scale;
+  __shared__ int s_done, s_k;
+
+  const int M = A.M, Dw = A.Dw;
+  const long long n = A.n;
+  const long long e0 = (long long)blockIdx.x * A.S;
+  const int len = (int)(e0 < n ? (n - e0 < A.S ? n - e0 : A.S) : 0);
+  const int nt = (M + TL - 1) / TL;
+  const int items = Dw * nt * nt;
+  cplx* part1 = A.part;
+  cplx* part2 = A.part + (size_t)A.G * NV;
+
+  // ||v||: q_0 = v / ||v||
+  for (int e = threadIdx.x; e < len; e += BT) ws[e] = A.v[e0 + e];
+  __syncthreads();
+  slice_norm(A, ws, len, red);
+  if (!bk_barrier(A.bar, A.G, A.status)) return;
+  reduce_norm(A, &s_nrm);
+  const double b0 = sqrt(s_nrm);
+  if (threadIdx.x == 0) {
+    s_b0 = b0;
+    s_done = 0;
+    s_k = 0;
+  }
+  if (b0 == 0.0) {
+    for (int e = threadIdx.x; e < len; e += BT) A.out[e0 + e] = make_double2(0.0, 0.0);
+    return;
+  }
+  double inv = 1.0 / b0;
+  for (int e = threadIdx.x; e < len; e += BT)
+    A.V[e0 + e] = make_double2(ws[e].x * inv, ws[e].y * inv);
+  const cplx* src = A.v;        // q_j = src * inv (src is read by every CTA)
+
+  int k = 0;
+  for (int j = 0; j < A.kcap; ++j) {
+    // ---- A: T_w = L_w q_j
+    for (int it = blockIdx.x; it < items; it += A.G) {
+      const int w = it / (nt * nt), rem = it - w * nt * nt;
+      const int ra = (rem / nt) * TL, cb = (rem % nt) * TL;
+      const cplx* Lw = A.L + (size_t)w * M * M;
+      const double sc = inv;
+      float2 acc[2][2] = {};
+      tile_cgemm<false>(
+          M,
+          [&](int r, int kk) {
+            const int a = ra + r;
+            return (a < M && kk < M) ? to_f2(__ldg(&Lw[(size_t)a * M + kk]))
+                                     : make_float2(0.f, 0.f);
+          },
+          [&](int kk, int c) {
+            const int b = cb + c;
+            if (kk >= M || b >= M) return make_float2(0.f, 0.f);
+            const cplx z = __ldcg(&src[(size_t)kk * M + b]);
+            return make_float2(__double2float_rn(z.x * sc), __double2float_rn(z.y * sc));
+          },
+          sm, acc);
+      const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+      float2* Tw = A.T + (size_t)w * n;
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj) {
+          const int a = ra + 2 * ty + i, b = cb + 2 * tx + jj;
+          if (a < M && b < M) Tw[(size_t)a * M + b] = acc[i][jj];
+        }
+    }
+    if (!bk_barrier(A.bar, A.G, A.status)) return;
+    // ---- B: P_w = T_w R_w^T
+    for (int it = blockIdx.x; it < items; it += A.G) {
+      const int w = it / (nt * nt), rem = it - w * nt * nt;
+      const int ra = (rem / nt) * TL, cb = (rem % nt) * TL;
+      const float2* Tw = A.T + (size_t)w * n;
+      const cplx* Rw = A.R + (size_t)w * M * M;
+      float2 acc[2][2] = {};
+      tile_cgemm<true>(
+          M,
+          [&](int r, int kk) {
+            const int a = ra + r;
+            return (a < M && kk < M) ? __ldcg(&Tw[(size_t)a * M + kk]) : make_float2(0.f, 0.f);
+          },
+          [&](int kk, int c) {
+            const int b = cb + c;
+            return (kk < M && b < M) ? to_f2(__ldg(&Rw[(size_t)b * M + kk]))
+                                     : make_float2(0.f, 0.f);
+          },
+          sm, acc);
+      const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+      float2* Pw = A.P + (size_t)w * n;
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj) {
+          const int a = ra + 2 * ty + i, b = cb + 2 * tx + jj;
+          if (a < M && b < M) Pw[(size_t)a * M + b] = acc[i][jj];
+        }
+    }
+    if (!bk_barrier(A.bar, A.G, A.status)) return;
+    // ---- C1: w = sum_w P_w (FP64, channel order); dots against q_lo .. q_j
+    for (int e = threadIdx.x; e < len; e += BT) {
+      double x = 0.0, y = 0.0;
+      for (int w = 0; w < Dw; ++w) {
+        const float2 p = __ldcg(&A.P[(size_t)w * n + e0 + e]);
+        x += (double)p.x;
+        y += (double)p.y;
+      }
+      ws[e] = make_double2(x, y);
+    }
+    __syncthreads();
+    const int lo = j > 0 ? j - 1 : 0;
+    slice_dots(A, ws, e0, len, lo, j + 1, part1);
+    if (!bk_barrier(A.bar, A.G, A.status)) return;
+    // ---- C2: first projection; dots against q_0 .. q_j
+    reduce_dots(A, part1, lo, j + 1, h1);
+    slice_project(A, ws, e0, len, lo, j + 1, h1);
+    slice_dots(A, ws, e0, len, 0, j + 1, part2);
+    if (!bk_barrier(A.bar, A.G, A.status)) return;
+    // ---- C3: second projection; ||w||^2
+    reduce_dots(A, part2, 0, j + 1, h2);
+    slice_project(A, ws, e0, len, 0, j + 1, h2);
+    for (int e = threadIdx.x; e < len; e += BT) A.W[e0 + e] = ws[e];
+    slice_norm(A, ws, len, red);
+    if (!bk_barrier(A.bar, A.G, A.status)) return;
+    // ---- C4: tridiagonal bookkeeping and the small exponential (warp 0 of every CTA)
+    reduce_norm(A, &s_nrm);
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      const int kk = j + 1;
+      const double aj = h1[j].x + h2[j].x;       // alpha_j = Re <q_j, K q_j>
+      const double nb = sqrt(s_nrm);              // beta_{j+1}
+      const double a = lane < j ? alpha[lane] : (lane == j ? aj : 0.0);
+      const double bl = (lane >= 1 && lane < kk) ? beta[lane] : 0.0;
+      const double br = (lane + 1 < kk) ? beta[lane + 1] : 0.0;
+      __syncwarp();
+      if (lane == 0) {
+        alpha[j] = aj;
+        beta[j + 1] = nb;
+      }
+      const double rowsum = fabs(a) + fabs(bl) + fabs(br);
+      const double tnorm = lz_warp_max(rowsum);
+      const double scale = lz_warp_max(fmax(fabs(a), fabs(bl)));
+      double yr, yi;
+      lz_taylor_exp(a, bl, br, tnorm, A.tr, A.ti, yr, yi);
+      const double ylr = __shfl_sync(0xffffffffu, yr, kk - 1);
+      const double yli = __shfl_sync(0xffffffffu, yi, kk - 1);
+      const double err = nb * sqrt(ylr * ylr + yli * yli);
+      const bool breakdown = nb <= 1e-12 * fmax(scale, 1e-300);
+      const bool done = breakdown || kk >= A.kcap || (!A.fixed && err < A.tol);
+      if (done && lane < kk) cc[lane] = make_double2(s_b0 * yr, s_b0 * yi);
+      if (lane == 0) {
+        s_done = done ? 1 : 0;
+        s_k = kk;
+        s_scale = nb;
+      }
+    }
+    __syncthreads();
+    k = s_k;
+    if (s_done) break;
+    inv = 1.0 / s_scale;
+    for (int e = threadIdx.x; e < len; e += BT)
+      A.V[(size_t)(j + 1) * n + e0 + e] = make_double2(ws[e].x * inv, ws[e].y * inv);
+    src = A.W;
+  }
+  // out = sum_{i < k} c_i q_i on the own slice
+  for (int e = threadIdx.x; e < len; e += BT) {
+    double x = 0.0, y = 0.0;
+    for (int i = 0; i < k; ++i) {
+      const cplx q = A.V[(size_t)i * n + e0 + e], c = cc[i];
+      x = fma(c.x, q.x, x);
+      x = fma(-c.y, q.y, x);
+      y = fma(c.x, q.y, y);
+      y = fma(c.y, q.x, y);
+    }
+    A.out[e0 + e] = make_double2(x, y);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && A.mv) atomicAdd(A.mv, (unsigned long long)k);
+}
+
+}  // namespace
+
+int bond_exp_grid(int M, int Dw, int gcap, int sms) {
+  const int nt = (M + TL - 1) / TL;
+  const long long n = (long long)M * M;
+  long long g = (long long)Dw * nt * nt;
+  const long long gn = (n + BT - 1) / BT;
+  if (gn > g) g = gn;
+  int cap = sms;
+  if (gcap > 0 && gcap < cap) cap = gcap;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+size_t bond_exp_smem(int M, int G) {
+  const long long n = (long long)M * M;
+  const long long S = (n + G - 1) / G;
+  return (size_t)S * sizeof(cplx);
+}
+
+cudaError_t bond_exp_fused(int M, int Dw, const cplx* L, const cplx* R, const cplx* C, cplx* out,
+                           cplx* V, const BondScratch& W, int* status, double tr, double ti,
+                           double tol, int kcap, int fixed, int gcap, cudaStream_t s) {
+  if (M < 1 || Dw < 1 || Dw > W.maxDw || (long long)M * M > W.maxn || kcap < 1 || kcap > KMAX)
+    return cudaErrorInvalidValue;
+  const int G = bond_exp_grid(M, Dw, gcap, W.gmax);
+  const size_t smem = bond_exp_smem(M, G);
+  if (smem > BOND_EXP_MAX_SMEM) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(bond_exp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)BOND_EXP_MAX_SMEM);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(W.bar, 0, 2 * sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  BondArgs a;
+  a.M = M; a.Dw = Dw; a.G = G;
+  a.n = (long long)M * M;
+  a.S = (int)((a.n + G - 1) / G);
+  a.kcap = kcap; a.fixed = fixed;
+  a.L = L; a.R = R; a.v = C; a.out = out; a.V = V;
+  a.W = W.W; a.T = W.T; a.P = W.P; a.part = W.part; a.partn = W.partn; a.bar = W.bar;
+  a.status = status; a.mv = W.mv;
+  a.tr = tr; a.ti = ti; a.tol = tol;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(G);
+  cfg.blockDim = dim3(BT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  count_launch();
+  return cudaLaunchKernelEx(&cfg, bond_exp_kernel, a);
+}
+
+}  // namespace tdmrg

@@ -499,6 +499,61 @@ int tdmrg_kernel_gauge_qr_blocked(int m, int n, const void* Y, int p, const void
   });
 }
 
+int tdmrg_kernel_bond_exp(int M, int Dw, const void* L, const void* R, const void* C, void* out,
+                          double tau_re, double tau_im, double tol, int kmax, int* kused,
+                          void* stream) {
+  if (M < 1 || Dw < 1 || !L || !R || !C || !out || kmax < 1 || kmax > tdmrg::KMAX ||
+      !(tol > 0.0))
+    return fail(nullptr, TDMRG_ERR_ARG, "bond_exp: need M, Dw >= 1, 1 <= kmax <= 32, tol > 0");
+  return guarded(nullptr, [&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const long long n = (long long)M * M;
+    if (tdmrg::bond_exp_smem(M, tdmrg::bond_exp_grid(M, Dw, 0, sms)) > tdmrg::BOND_EXP_MAX_SMEM)
+      throw Failure{TDMRG_ERR_ARG, "bond_exp: bond dimension too large for one cooperative grid"};
+    const int kcap = (int)std::min<long long>(kmax, n);
+    tdmrg::BondScratch W{};
+    W.maxn = n;
+    W.maxDw = Dw;
+    W.gmax = sms;
+    tdmrg::cplx* V = nullptr;
+    int* st = nullptr;
+    struct Free {
+      tdmrg::BondScratch& w;
+      tdmrg::cplx*& V;
+      int*& st;
+      ~Free() {
+        for (void* p : {(void*)w.W, (void*)w.T, (void*)w.P, (void*)w.part, (void*)w.partn,
+                        (void*)w.bar, (void*)w.mv, (void*)V, (void*)st})
+          if (p) cudaFree(p);
+      }
+    } fr{W, V, st};
+    CK(cudaMalloc(&W.W, sizeof(tdmrg::cplx) * (size_t)n));
+    CK(cudaMalloc(&W.T, sizeof(float2) * (size_t)Dw * n));
+    CK(cudaMalloc(&W.P, sizeof(float2) * (size_t)Dw * n));
+    CK(cudaMalloc(&W.part, sizeof(tdmrg::cplx) * 2 * (size_t)sms * (tdmrg::KMAX + 1)));
+    CK(cudaMalloc(&W.partn, sizeof(double) * (size_t)sms));
+    CK(cudaMalloc(&W.bar, sizeof(unsigned) * 2));
+    CK(cudaMalloc(&W.mv, sizeof(unsigned long long)));
+    CK(cudaMalloc(&V, sizeof(tdmrg::cplx) * (size_t)kcap * n));
+    CK(cudaMalloc(&st, sizeof(int)));
+    CK(cudaMemsetAsync(W.mv, 0, sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(st, 0, sizeof(int), s));
+    CK(tdmrg::bond_exp_fused(M, Dw, (const tdmrg::cplx*)L, (const tdmrg::cplx*)R,
+                             (const tdmrg::cplx*)C, (tdmrg::cplx*)out, V, W, st, tau_re, tau_im,
+                             tol, kcap, 0, 0, s));
+    int hs = 0;
+    unsigned long long used = 0;
+    CK(cudaMemcpyAsync(&hs, st, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&used, W.mv, sizeof(used), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hs == 1) throw Failure{TDMRG_ERR_TIMEOUT, "bond exponential grid barrier timed out"};
+    if (kused) *kused = (int)used;
+  });
+}
+
 int tdmrg_kernel_krylov_dense(int n, const void* H, const void* v, void* out, double tau_re,
                               double tau_im, double tol, int kmax, int* kused, void* stream) {
   if (n < 1 || !H || !v || !out || kmax < 1 || kmax > tdmrg::KMAX || !(tol > 0.0))

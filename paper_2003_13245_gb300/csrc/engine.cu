@@ -441,6 +441,10 @@ Engine::~Engine() {
     if (e) cudaEventDestroy(e);
   for (float* p : {tcb_.envA, tcb_.envB, tcb_.siteA, tcb_.siteB, tcb_.x32, tcb_.mix, tcb_.kpart})
     if (p) cudaFree(p);
+  for (void* p : {(void*)bs_.W, (void*)bs_.T, (void*)bs_.P, (void*)bs_.part, (void*)bs_.partn,
+                  (void*)bs_.bar, (void*)bs_.mv})
+    if (p) cudaFree(p);
+  if (h_mv_) cudaFreeHost(h_mv_);
 }
 
 void Engine::rebuild_mpos() {
@@ -506,6 +510,7 @@ void Engine::ensure_workspace(long long maxsite, long long maxxy, int maxbond, i
     CK(cudaMalloc(&Rb_, sizeof(cplx) * (size_t)maxbond * maxbond));
     ws_bond_ = maxbond;
   }
+  ensure_bond_scratch(maxbond);
   if (maxm > ws_m_) {
     if (qr_.part) cudaFree(qr_.part);
     if (qr_.partn) cudaFree(qr_.partn);
@@ -692,11 +697,59 @@ void Engine::scale_dev(cplx* x, long long n, double f) {
   CK(cudaStreamSynchronize(st_));
 }
 
+void Engine::ensure_bond_scratch(int maxbond) {
+  const long long maxn = (long long)maxbond * maxbond;
+  const int maxDw = std::max(H_.maxD, J_.maxD);
+  if (maxn <= bs_.maxn && maxDw <= bs_.maxDw) return;
+  for (void* p : {(void*)bs_.W, (void*)bs_.T, (void*)bs_.P})
+    if (p) cudaFree(p);
+  bs_.W = nullptr;
+  bs_.T = bs_.P = nullptr;
+  CK(cudaMalloc(&bs_.W, sizeof(cplx) * (size_t)maxn));
+  CK(cudaMalloc(&bs_.T, sizeof(float2) * (size_t)maxDw * maxn));
+  CK(cudaMalloc(&bs_.P, sizeof(float2) * (size_t)maxDw * maxn));
+  if (!bs_.part) {
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    bs_.gmax = sms;
+    CK(cudaMalloc(&bs_.part, sizeof(cplx) * 2 * (size_t)sms * (KMAX + 1)));
+    CK(cudaMalloc(&bs_.partn, sizeof(double) * (size_t)sms));
+    CK(cudaMalloc(&bs_.bar, sizeof(unsigned) * 2));
+    CK(cudaMalloc(&bs_.mv, sizeof(unsigned long long)));
+    CK(cudaMemset(bs_.mv, 0, sizeof(unsigned long long)));
+    CK(cudaMallocHost(&h_mv_, sizeof(unsigned long long)));
+    mv_seen_ = 0;
+  }
+  bs_.maxn = maxn;
+  bs_.maxDw = maxDw;
+}
+
+// exp(tau K) Cb_ -> Rb_ in one cooperative launch (mixed path); the number of Krylov vectors
+// it used is accumulated on the device and collected by check_status().
+void Engine::bond_exp(int M, int Dw, const cplx* Le, const cplx* Re, double tr, double ti) {
+  const int cap0 = fixed_k_ > 0 ? fixed_k_ : kmax_;
+  const int kcap = (int)std::min<long long>(cap0, (long long)M * M);
+  CK(bond_exp_fused(M, Dw, Le, Re, Cb_, Rb_, V_, bs_, status_ + 1, tr, ti, ktol_, kcap,
+                    fixed_k_ > 0 ? 1 : 0, qr_gcap_, st_));
+}
+
 void Engine::check_status() {
   CK(cudaMemcpyAsync(h_pinned_ + 1, status_, 3 * sizeof(int), cudaMemcpyDeviceToHost, st_));
-  CK(cudaStreamSynchronize(st_));
   stats.d2h_bytes += 3 * sizeof(int);
+  if (bs_.mv) {
+    CK(cudaMemcpyAsync(h_mv_, bs_.mv, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st_));
+    stats.d2h_bytes += sizeof(unsigned long long);
+  }
+  CK(cudaStreamSynchronize(st_));
+  if (bs_.mv) {
+    const double used = (double)(*h_mv_ - mv_seen_);
+    mv_seen_ = *h_mv_;
+    stats.bond_matvecs += used;
+    stats.krylov_vectors += used;
+  }
   if (h_pinned_[1] == 1) throw Failure{TDMRG_ERR_TIMEOUT, "gauge QR grid barrier timed out"};
+  if (h_pinned_[2] == 1) throw Failure{TDMRG_ERR_TIMEOUT, "bond exponential grid barrier timed out"};
   if (h_pinned_[1] == 2) throw Failure{TDMRG_ERR_CUDA, "gauge QR ran out of completion vectors"};
   if (h_pinned_[3] != 0) throw Failure{TDMRG_ERR_TIMEOUT, "tensor-core pipeline wait timed out"};
 }
@@ -973,14 +1026,18 @@ void Engine::tdvp_step_body(DevMps& s, double tr, double ti) {
       const int M = s.Mb[k + 1], Dw = H_.s[k].Dr;
       const cplx* Le = s.Lenv[k + 1];
       const cplx* Re = s.Renv[k];
-      if (mixed()) bond_tc_prepare(st_, tcb_, M, Dw, Le, Re);
-      stats.bond_matvecs += krylov((long long)M * M, Cb_, Rb_, -hr, -hi,
-                                   [&](const cplx* in, cplx* out, const int* sk) {
-        if (mixed())
-          bond_tc_apply(st_, tcb_, M, Dw, in, out);
-        else
-          bond_f64(c, M, Dw, Le, Re, in, out, sk);
-      });
+      if (mixed() && M <= kFusedBondMaxM) {
+        bond_exp(M, Dw, Le, Re, -hr, -hi);
+      } else {
+        if (mixed()) bond_tc_prepare(st_, tcb_, M, Dw, Le, Re);
+        stats.bond_matvecs += krylov((long long)M * M, Cb_, Rb_, -hr, -hi,
+                                     [&](const cplx* in, cplx* out, const int* sk) {
+          if (mixed())
+            bond_tc_apply(st_, tcb_, M, Dw, in, out);
+          else
+            bond_f64(c, M, Dw, Le, Re, in, out, sk);
+        });
+      }
       toc(stats.t_bond, t0);
       t0 = tic();
       absorb_left(Rb_, M, s.A[k + 1], (long long)s.D[k + 1] * s.Mb[k + 2]);
@@ -1003,14 +1060,18 @@ void Engine::tdvp_step_body(DevMps& s, double tr, double ti) {
       const int M = s.Mb[k], Dw = H_.s[k].Dl;
       const cplx* Le = s.Lenv[k];
       const cplx* Re = s.Renv[k - 1];
-      if (mixed()) bond_tc_prepare(st_, tcb_, M, Dw, Le, Re);
-      stats.bond_matvecs += krylov((long long)M * M, Cb_, Rb_, -hr, -hi,
-                                   [&](const cplx* in, cplx* out, const int* sk) {
-        if (mixed())
-          bond_tc_apply(st_, tcb_, M, Dw, in, out);
-        else
-          bond_f64(c, M, Dw, Le, Re, in, out, sk);
-      });
+      if (mixed() && M <= kFusedBondMaxM) {
+        bond_exp(M, Dw, Le, Re, -hr, -hi);
+      } else {
+        if (mixed()) bond_tc_prepare(st_, tcb_, M, Dw, Le, Re);
+        stats.bond_matvecs += krylov((long long)M * M, Cb_, Rb_, -hr, -hi,
+                                     [&](const cplx* in, cplx* out, const int* sk) {
+          if (mixed())
+            bond_tc_apply(st_, tcb_, M, Dw, in, out);
+          else
+            bond_f64(c, M, Dw, Le, Re, in, out, sk);
+        });
+      }
       toc(stats.t_bond, t0);
       t0 = tic();
       absorb_right(s.A[k - 1], (long long)s.Mb[k - 1] * s.D[k - 1], Rb_, M);

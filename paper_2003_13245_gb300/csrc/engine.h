@@ -128,6 +128,11 @@ struct Stats {
   double replayed_launches = 0;       // kernels launched through graph replays
 };
 
+// Mixed path: bond exponentials up to this bond dimension run as one fused cooperative launch
+// (FP32 FMA contractions, 2 Dw M^3 complex MACs per Krylov vector); larger bonds use the
+// host-driven Lanczos with the tensor-core contraction.
+constexpr int kFusedBondMaxM = 256;
+
 class Engine {
  public:
   explicit Engine(const ModelParams& P);
@@ -201,6 +206,8 @@ class Engine {
   Cx overlap(const DevMps& bra, const DevMpo& W, const DevMps& ket);
   void fit_apply(const DevMpo& W, const DevMps& psi, DevMps& phi, int sweeps);
   void check_status();
+  void ensure_bond_scratch(int maxbond);
+  void bond_exp(int M, int Dw, const cplx* Le, const cplx* Re, double tr, double ti);
   long long env_size(const DevMps& s, int k, int Dw, bool left) const;
 
   cudaStream_t st_ = 0;
@@ -250,6 +257,9 @@ class Engine {
   cplx* env_tmp_[2] = {nullptr, nullptr};
   cudaEvent_t ev_[2 * KMAX + 2] = {};
   TcBufs tcb_{};
+  BondScratch bs_{};
+  unsigned long long* h_mv_ = nullptr;   // pinned copy of the device Krylov-vector counter
+  unsigned long long mv_seen_ = 0;
   long long tc_site_ = 0, tc_env_ = 0, tc_x_ = 0;
   long long env_tmp_size_ = 0;
 };

@@ -2,6 +2,7 @@
 // the environment updates and the bond step), sparse MPO channel mixing, Lanczos
 // reductions, the small Krylov exponential and the cooperative gauge QR.
 #include "tdmrg_internal.cuh"
+#include "lanczos_exp.cuh"
 
 #include <cooperative_groups.h>
 #include <cmath>
@@ -354,11 +355,8 @@ cudaError_t zscale_by(long long n, cplx* x, const double* factor, const int* ski
 }
 
 // ------------------------------------------------------------------------------------
-// Lanczos bookkeeping and the small exponential exp(tau T_k) e_1 (one warp, FP64).
-// T_k is real symmetric tridiagonal; the exponential is evaluated by its Taylor series
-// with scaling: s = ceil(|tau| ||T||_inf / 0.5) sub-steps, each summed until the term
-// falls below 1e-18 of the partial sum (Moler & Van Loan, "Nineteen dubious ways", method
-// 1 with scaling).  Lane i holds row i.
+// Lanczos bookkeeping and the small exponential exp(tau T_k) e_1 (one warp, FP64, the
+// Taylor-with-sub-steps routine of lanczos_exp.cuh).  Lane i holds row i of T_k.
 // ------------------------------------------------------------------------------------
 __global__ void lz_start_kernel(LzState* S, const double* nrm2) {
   if (threadIdx.x == 0) {
@@ -401,32 +399,8 @@ __global__ void lz_small_exp_kernel(LzState* S, int j, double tr, double ti, dou
   const double tnorm = warp_max(rowsum);
   // scale used for the breakdown test: entries of T_k only
   const double scale = warp_max(fmax(fabs(a), fabs(bl)));
-  const double tabs = sqrt(tr * tr + ti * ti);
-  int nsub = (int)ceil(tabs * tnorm / 0.5);
-  if (nsub < 1) nsub = 1;
-  const double sr = tr / nsub, si = ti / nsub;
-  double yr = (lane == 0) ? 1.0 : 0.0, yi = 0.0;
-  for (int st = 0; st < nsub; ++st) {
-    double tr_ = yr, ti_ = yi, ar = yr, ai = yi;
-    for (int q = 1; q <= 60; ++q) {
-      const double ur = __shfl_up_sync(0xffffffffu, tr_, 1);
-      const double ui = __shfl_up_sync(0xffffffffu, ti_, 1);
-      const double dr = __shfl_down_sync(0xffffffffu, tr_, 1);
-      const double di = __shfl_down_sync(0xffffffffu, ti_, 1);
-      const double xr = a * tr_ + (lane >= 1 ? bl * ur : 0.0) + (lane < 31 ? br * dr : 0.0);
-      const double xi = a * ti_ + (lane >= 1 ? bl * ui : 0.0) + (lane < 31 ? br * di : 0.0);
-      // term <- (tau / nsub) * (T term) / q
-      tr_ = (sr * xr - si * xi) / q;
-      ti_ = (sr * xi + si * xr) / q;
-      ar += tr_;
-      ai += ti_;
-      const double tm = warp_max(fabs(tr_) + fabs(ti_));
-      const double am = warp_max(fabs(ar) + fabs(ai));
-      if (tm <= 1e-18 * am) break;
-    }
-    yr = ar;
-    yi = ai;
-  }
+  double yr, yi;
+  lz_taylor_exp(a, bl, br, tnorm, tr, ti, yr, yi);
   const double ylr = __shfl_sync(0xffffffffu, yr, k - 1);
   const double yli = __shfl_sync(0xffffffffu, yi, k - 1);
   const double err = nb * sqrt(ylr * ylr + yli * yli);

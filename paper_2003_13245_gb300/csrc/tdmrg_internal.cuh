@@ -88,6 +88,26 @@ struct QrRef {
   long long rs, cs, cb, cbs;
   int conj;
 };
+// Fused bond exponential (bond_krylov.cu): out = exp(tau K) C, K C = sum_w L_w C R_w^T, the
+// whole Lanczos run in one cooperative launch (complex FP32 contractions, FP64 Lanczos).
+struct BondScratch {
+  cplx* W = nullptr;                 // maxn
+  float2* T = nullptr;               // maxDw * maxn
+  float2* P = nullptr;               // maxDw * maxn
+  cplx* part = nullptr;              // 2 * gmax * (KMAX + 1)
+  double* partn = nullptr;           // gmax
+  unsigned* bar = nullptr;           // 2 (barrier counter, generation)
+  unsigned long long* mv = nullptr;  // Krylov vectors used, accumulated over launches
+  long long maxn = 0;
+  int maxDw = 0, gmax = 0;
+};
+constexpr size_t BOND_EXP_MAX_SMEM = 160 * 1024;
+int bond_exp_grid(int M, int Dw, int gcap, int sms);
+size_t bond_exp_smem(int M, int G);
+cudaError_t bond_exp_fused(int M, int Dw, const cplx* L, const cplx* R, const cplx* C, cplx* out,
+                           cplx* V, const BondScratch& W, int* status, double tr, double ti,
+                           double tol, int kcap, int fixed, int gcap, cudaStream_t s);
+
 struct QrScratch {
   cplx* part;          // 2 * gmax * (nmax + 1)
   double* partn;       // 2 * gmax

@@ -43,3 +43,8 @@ def test_argument_errors_are_reported(lib):
     with pytest.raises(binding.TdmrgError) as e:
         binding.Model(2, [1.0], [1.0], [4], 1.0)     # N < 3 is rejected before any CUDA call
     assert e.value.code == -1
+    # kernel-level entry points check their arguments before touching the device
+    rc = lib.tdmrg_kernel_bond_exp(0, 7, None, None, None, None, 0.0, -0.05, 1e-7, 32, None, None)
+    assert rc == -1
+    rc = lib.tdmrg_kernel_bond_exp(16, 7, 1, 1, 1, 1, 0.0, -0.05, 1e-7, 33, None, None)
+    assert rc == -1

@@ -230,7 +230,8 @@ int tdmrg_kernel_gauge_qr_noalloc(int m, int n, const void* Y, int p, const void
  * stop when beta_{k+1} |c_k| < tol or at kmax (<= 32) vectors.  kused (host, may be NULL)
  * receives the number of Krylov vectors.  Allocates its scratch (freed before return);
  * synchronises `stream`; TDMRG_ERR_TIMEOUT if the bounded grid barrier gave up;
- * TDMRG_ERR_ARG if M is too large for one co-resident grid (M <= 1200 with 152 SMs). */
+ * TDMRG_ERR_ARG unless 1 <= M <= 256 (the whole contraction depth is staged in shared
+ * memory). */
 int tdmrg_kernel_bond_exp(int M, int Dw, const void* L, const void* R, const void* C, void* out,
                           double tau_re, double tau_im, double tol, int kmax, int* kused,
                           void* stream);

@@ -9,8 +9,9 @@
 // five times per Krylov vector and never returns to the host.
 //
 // Per Krylov vector j (CTA g owns the contiguous slice [g*S, g*S + S) of every vector):
-//  A.  T_w = L_w q_j for every channel w: complex FP32 FMA on 32 x 32 output tiles (the
-//      contraction is 2 Dw M^3 complex MACs, too small to keep a tensor-core pipeline busy);
+//  A.  T_w = L_w q_j for every channel w: complex FP32 FMA on 32 x 32 output tiles with the
+//      whole K = M extent staged in shared memory (M <= 256; the contraction is 2 Dw M^3
+//      complex MACs, too small to keep a tensor-core pipeline busy);
 //  B.  P_w = T_w R_w^T, one partial per channel (the channel sum is taken in C1, in order);
 //  C1. w = sum_w P_w in FP64 on the own slice; partial dots against q_{j-1}, q_j;
 //  C2. first projection; partial dots against q_0 .. q_j (second, full pass);
@@ -59,29 +60,27 @@ __device__ __forceinline__ double bk_wsum(double v) {
   return v;
 }
 
-__device__ bool bk_barrier(unsigned* bar, unsigned nblocks, int* status) {
+// Grid barrier on one monotonic counter: barrier number e is passed once the counter
+// reaches e * nblocks (one atomic per CTA; the counter is cleared before every launch).
+// Bounded: gives up after ~2 s, sets *status = 1, and every CTA then leaves.
+__device__ bool bk_barrier(unsigned* bar, unsigned nblocks, unsigned& epoch, int* status) {
   __syncthreads();
   __shared__ int s_ok;
+  ++epoch;
   if (threadIdx.x == 0) {
-    volatile unsigned* vgen = bar + 1;
+    volatile unsigned* vbar = bar;
     volatile int* vstat = status;
-    const unsigned gen = *vgen;
+    const unsigned target = epoch * nblocks;
     __threadfence();
-    const unsigned prev = atomicAdd(bar, 1u);
+    atomicAdd(bar, 1u);
     int ok = 1;
-    if (prev == nblocks - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      const long long t0 = clock64();
-      while (*vgen == gen) {
-        if (*vstat) { ok = 0; break; }
-        if (clock64() - t0 > BK_TIMEOUT) {
-          atomicExch(status, 1);
-          ok = 0;
-          break;
-        }
+    const long long t0 = clock64();
+    while (*vbar < target) {
+      if (*vstat) { ok = 0; break; }
+      if (clock64() - t0 > BK_TIMEOUT) {
+        atomicExch(status, 1);
+        ok = 0;
+        break;
       }
     }
     __threadfence();
@@ -98,46 +97,62 @@ __device__ __forceinline__ void cfma32(float2& acc, float2 a, float2 b) {
   acc.y = fmaf(a.y, b.x, acc.y);
 }
 
-struct TileSmem {
-  float2 at[TL][TP];   // A transposed: at[k][row]
-  float2 b[TL][TP];    // b[k][col]
-};
+constexpr int KT = BOND_EXP_MAX_M;      // largest K staged at once (bond dimension)
+constexpr size_t TILE_SMEM = 2 * (size_t)KT * TP * sizeof(float2);
 
 // acc[i][j] += sum_{k < K} A(r0 + i, k) B(k, c0 + j) for the thread's 2 x 2 outputs
-// (r0 = 2 (tid / 16), c0 = 2 (tid % 16)) of a 32 x 32 tile, through shared memory in
-// 32-deep chunks.  ldA(r, k) / ldB(k, c) return the operand (zero outside the matrices);
-// kfastB selects the load order of B that is contiguous in global memory.
+// (r0 = 2 (tid / 16), c0 = 2 (tid % 16)) of a 32 x 32 tile.  The whole K extent (<= KT,
+// zero-padded to a multiple of 32) is staged in shared memory at once -- at[k][row] (A
+// transposed) and b[k][col] -- so that one round of loads is in flight per tile.  ldA(r, k)
+// / ldB(k, c) return the operand (zero outside the matrices); kfastB selects the load order
+// of B that is contiguous in global memory.
 template <bool kfastB, class FA, class FB>
-__device__ __forceinline__ void tile_cgemm(int K, FA ldA, FB ldB, TileSmem& sm,
+__device__ __forceinline__ void tile_cgemm(int K, FA ldA, FB ldB, float2* at, float2* bt,
                                            float2 acc[2][2]) {
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  for (int k0 = 0; k0 < K; k0 += TL) {
+  const int nk = (K + TL - 1) / TL;
+  for (int c0 = 0; c0 < nk; c0 += 2) {
+    float2 ra[2][4], rb[2][4];
 #pragma unroll
-    for (int u = 0; u < (TL * TL) / BT; ++u) {
-      const int e = tid + u * BT;
-      const int r = e >> 5, kk = e & 31;
-      sm.at[kk][r] = ldA(r, k0 + kk);
-      if (kfastB) {
-        sm.b[kk][r] = ldB(k0 + kk, r);          // (k fast, c = e / 32)
-      } else {
-        sm.b[r][kk] = ldB(k0 + r, kk);          // (c fast, k = e / 32)
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = tid + u * BT;
+        const int r = e >> 5, kk = e & 31, k0 = (c0 + c) * TL;
+        const bool live = c0 + c < nk;
+        ra[c][u] = live ? ldA(r, k0 + kk) : make_float2(0.f, 0.f);
+        rb[c][u] = live ? (kfastB ? ldB(k0 + kk, r) : ldB(k0 + r, kk)) : make_float2(0.f, 0.f);
       }
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int kk = 0; kk < TL; ++kk) {
-      const float4 a = *reinterpret_cast<const float4*>(&sm.at[kk][2 * ty]);
-      const float4 b = *reinterpret_cast<const float4*>(&sm.b[kk][2 * tx]);
-      const float2 a0 = make_float2(a.x, a.y), a1 = make_float2(a.z, a.w);
-      const float2 b0 = make_float2(b.x, b.y), b1 = make_float2(b.z, b.w);
-      cfma32(acc[0][0], a0, b0);
-      cfma32(acc[0][1], a0, b1);
-      cfma32(acc[1][0], a1, b0);
-      cfma32(acc[1][1], a1, b1);
-    }
-    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = tid + u * BT;
+        const int r = e >> 5, kk = e & 31, k0 = (c0 + c) * TL;
+        if (c0 + c < nk) {
+          at[(k0 + kk) * TP + r] = ra[c][u];
+          if (kfastB)
+            bt[(k0 + kk) * TP + r] = rb[c][u];      // (k fast, c = e / 32)
+          else
+            bt[(k0 + r) * TP + kk] = rb[c][u];      // (c fast, k = e / 32)
+        }
+      }
   }
+  __syncthreads();
+  const int kend = nk * TL;
+#pragma unroll 8
+  for (int kk = 0; kk < kend; ++kk) {
+    const float4 a = *reinterpret_cast<const float4*>(&at[kk * TP + 2 * ty]);
+    const float4 b = *reinterpret_cast<const float4*>(&bt[kk * TP + 2 * tx]);
+    const float2 a0 = make_float2(a.x, a.y), a1 = make_float2(a.z, a.w);
+    const float2 b0 = make_float2(b.x, b.y), b1 = make_float2(b.z, b.w);
+    cfma32(acc[0][0], a0, b0);
+    cfma32(acc[0][1], a0, b1);
+    cfma32(acc[1][0], a1, b0);
+    cfma32(acc[1][1], a1, b1);
+  }
+  __syncthreads();
 }
 
 __device__ __forceinline__ float2 to_f2(cplx z) {
@@ -227,8 +242,10 @@ __device__ __forceinline__ void slice_norm(const BondArgs& A, const cplx* ws, in
 
 __global__ void __launch_bounds__(BT, 1) bond_exp_kernel(BondArgs A) {
   extern __shared__ __align__(16) unsigned char dyn[];
-  cplx* ws = reinterpret_cast<cplx*>(dyn);            // own slice of w, S entries
-  __shared__ __align__(16) TileSmem sm;
+  float2* at = reinterpret_cast<float2*>(dyn);        // [KT][TP]
+  float2* bt = at + (size_t)KT * TP;                  // [KT][TP]
+  cplx* ws = reinterpret_cast<cplx*>(dyn + TILE_SMEM);   // own slice of w, S entries
+  unsigned epoch = 0;
   __shared__ cplx h1[NV], h2[NV], cc[KMAX];
   __shared__ double alpha[KMAX], beta[KMAX + 1], red[BT / 32];
   __shared__ double s_nrm, s_b0, s_scale;
@@ -247,7 +264,7 @@ __global__ void __launch_bounds__(BT, 1) bond_exp_kernel(BondArgs A) {
   for (int e = threadIdx.x; e < len; e += BT) ws[e] = A.v[e0 + e];
   __syncthreads();
   slice_norm(A, ws, len, red);
-  if (!bk_barrier(A.bar, A.G, A.status)) return;
+  if (!bk_barrier(A.bar, A.G, epoch, A.status)) return;
   reduce_norm(A, &s_nrm);
   const double b0 = sqrt(s_nrm);
   if (threadIdx.x == 0) {
@@ -286,7 +303,7 @@ __global__ void __launch_bounds__(BT, 1) bond_exp_kernel(BondArgs A) {
             const cplx z = __ldcg(&src[(size_t)kk * M + b]);
             return make_float2(__double2float_rn(z.x * sc), __double2float_rn(z.y * sc));
           },
-          sm, acc);
+          at, bt, acc);
       const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
       float2* Tw = A.T + (size_t)w * n;
 #pragma unroll
@@ -297,7 +314,7 @@ __global__ void __launch_bounds__(BT, 1) bond_exp_kernel(BondArgs A) {
           if (a < M && b < M) Tw[(size_t)a * M + b] = acc[i][jj];
         }
     }
-    if (!bk_barrier(A.bar, A.G, A.status)) return;
+    if (!bk_barrier(A.bar, A.G, epoch, A.status)) return;
     // ---- B: P_w = T_w R_w^T
     for (int it = blockIdx.x; it < items; it += A.G) {
       const int w = it / (nt * nt), rem = it - w * nt * nt;
@@ -316,7 +333,7 @@ __global__ void __launch_bounds__(BT, 1) bond_exp_kernel(BondArgs A) {
             return (kk < M && b < M) ? to_f2(__ldg(&Rw[(size_t)b * M + kk]))
                                      : make_float2(0.f, 0.f);
           },
-          sm, acc);
+          at, bt, acc);
       const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
       float2* Pw = A.P + (size_t)w * n;
 #pragma unroll
@@ -327,7 +344,7 @@ __global__ void __launch_bounds__(BT, 1) bond_exp_kernel(BondArgs A) {
           if (a < M && b < M) Pw[(size_t)a * M + b] = acc[i][jj];
         }
     }
-    if (!bk_barrier(A.bar, A.G, A.status)) return;
+    if (!bk_barrier(A.bar, A.G, epoch, A.status)) return;
     // ---- C1: w = sum_w P_w (FP64, channel order); dots against q_lo .. q_j
     for (int e = threadIdx.x; e < len; e += BT) {
       double x = 0.0, y = 0.0;
@@ -341,18 +358,18 @@ __global__ void __launch_bounds__(BT, 1) bond_exp_kernel(BondArgs A) {
     __syncthreads();
     const int lo = j > 0 ? j - 1 : 0;
     slice_dots(A, ws, e0, len, lo, j + 1, part1);
-    if (!bk_barrier(A.bar, A.G, A.status)) return;
+    if (!bk_barrier(A.bar, A.G, epoch, A.status)) return;
     // ---- C2: first projection; dots against q_0 .. q_j
     reduce_dots(A, part1, lo, j + 1, h1);
     slice_project(A, ws, e0, len, lo, j + 1, h1);
     slice_dots(A, ws, e0, len, 0, j + 1, part2);
-    if (!bk_barrier(A.bar, A.G, A.status)) return;
+    if (!bk_barrier(A.bar, A.G, epoch, A.status)) return;
     // ---- C3: second projection; ||w||^2
     reduce_dots(A, part2, 0, j + 1, h2);
     slice_project(A, ws, e0, len, 0, j + 1, h2);
     for (int e = threadIdx.x; e < len; e += BT) A.W[e0 + e] = ws[e];
     slice_norm(A, ws, len, red);
-    if (!bk_barrier(A.bar, A.G, A.status)) return;
+    if (!bk_barrier(A.bar, A.G, epoch, A.status)) return;
     // ---- C4: tridiagonal bookkeeping and the small exponential (warp 0 of every CTA)
     reduce_norm(A, &s_nrm);
     if (threadIdx.x < 32) {
@@ -368,11 +385,9 @@ __global__ void __launch_bounds__(BT, 1) bond_exp_kernel(BondArgs A) {
         alpha[j] = aj;
         beta[j + 1] = nb;
       }
-      const double rowsum = fabs(a) + fabs(bl) + fabs(br);
-      const double tnorm = lz_warp_max(rowsum);
       const double scale = lz_warp_max(fmax(fabs(a), fabs(bl)));
       double yr, yi;
-      lz_taylor_exp(a, bl, br, tnorm, A.tr, A.ti, yr, yi);
+      lz_exp_tridiag(a, bl, br, kk, A.tr, A.ti, yr, yi);
       const double ylr = __shfl_sync(0xffffffffu, yr, kk - 1);
       const double yli = __shfl_sync(0xffffffffu, yi, kk - 1);
       const double err = nb * sqrt(ylr * ylr + yli * yli);
@@ -426,13 +441,14 @@ int bond_exp_grid(int M, int Dw, int gcap, int sms) {
 size_t bond_exp_smem(int M, int G) {
   const long long n = (long long)M * M;
   const long long S = (n + G - 1) / G;
-  return (size_t)S * sizeof(cplx);
+  return TILE_SMEM + (size_t)S * sizeof(cplx);
 }
 
 cudaError_t bond_exp_fused(int M, int Dw, const cplx* L, const cplx* R, const cplx* C, cplx* out,
                            cplx* V, const BondScratch& W, int* status, double tr, double ti,
                            double tol, int kcap, int fixed, int gcap, cudaStream_t s) {
-  if (M < 1 || Dw < 1 || Dw > W.maxDw || (long long)M * M > W.maxn || kcap < 1 || kcap > KMAX)
+  if (M < 1 || M > KT || Dw < 1 || Dw > W.maxDw || (long long)M * M > W.maxn || kcap < 1 ||
+      kcap > KMAX)
     return cudaErrorInvalidValue;
   const int G = bond_exp_grid(M, Dw, gcap, W.gmax);
   const size_t smem = bond_exp_smem(M, G);

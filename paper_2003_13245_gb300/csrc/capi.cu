@@ -502,9 +502,10 @@ int tdmrg_kernel_gauge_qr_blocked(int m, int n, const void* Y, int p, const void
 int tdmrg_kernel_bond_exp(int M, int Dw, const void* L, const void* R, const void* C, void* out,
                           double tau_re, double tau_im, double tol, int kmax, int* kused,
                           void* stream) {
-  if (M < 1 || Dw < 1 || !L || !R || !C || !out || kmax < 1 || kmax > tdmrg::KMAX ||
-      !(tol > 0.0))
-    return fail(nullptr, TDMRG_ERR_ARG, "bond_exp: need M, Dw >= 1, 1 <= kmax <= 32, tol > 0");
+  if (M < 1 || M > tdmrg::BOND_EXP_MAX_M || Dw < 1 || !L || !R || !C || !out || kmax < 1 ||
+      kmax > tdmrg::KMAX || !(tol > 0.0))
+    return fail(nullptr, TDMRG_ERR_ARG,
+                "bond_exp: need 1 <= M <= 256, Dw >= 1, 1 <= kmax <= 32, tol > 0");
   return guarded(nullptr, [&] {
     cudaStream_t s = (cudaStream_t)stream;
     int dev = 0, sms = 0;

@@ -131,7 +131,7 @@ struct Stats {
 // Mixed path: bond exponentials up to this bond dimension run as one fused cooperative launch
 // (FP32 FMA contractions, 2 Dw M^3 complex MACs per Krylov vector); larger bonds use the
 // host-driven Lanczos with the tensor-core contraction.
-constexpr int kFusedBondMaxM = 256;
+constexpr int kFusedBondMaxM = BOND_EXP_MAX_M;
 
 class Engine {
  public:

@@ -395,12 +395,10 @@ __global__ void lz_small_exp_kernel(LzState* S, int j, double tr, double ti, dou
     S->alpha[j] = aj;
     S->beta[j + 1] = nb;
   }
-  const double rowsum = fabs(a) + fabs(bl) + fabs(br);
-  const double tnorm = warp_max(rowsum);
   // scale used for the breakdown test: entries of T_k only
   const double scale = warp_max(fmax(fabs(a), fabs(bl)));
   double yr, yi;
-  lz_taylor_exp(a, bl, br, tnorm, tr, ti, yr, yi);
+  lz_exp_tridiag(a, bl, br, k, tr, ti, yr, yi);
   const double ylr = __shfl_sync(0xffffffffu, yr, k - 1);
   const double yli = __shfl_sync(0xffffffffu, yi, k - 1);
   const double err = nb * sqrt(ylr * ylr + yli * yli);

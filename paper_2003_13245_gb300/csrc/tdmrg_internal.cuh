@@ -101,7 +101,8 @@ struct BondScratch {
   long long maxn = 0;
   int maxDw = 0, gmax = 0;
 };
-constexpr size_t BOND_EXP_MAX_SMEM = 160 * 1024;
+constexpr int BOND_EXP_MAX_M = 256;
+constexpr size_t BOND_EXP_MAX_SMEM = 200 * 1024;
 int bond_exp_grid(int M, int Dw, int gcap, int sms);
 size_t bond_exp_smem(int M, int G);
 cudaError_t bond_exp_fused(int M, int Dw, const cplx* L, const cplx* R, const cplx* C, cplx* out,

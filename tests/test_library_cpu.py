@@ -48,3 +48,5 @@ def test_argument_errors_are_reported(lib):
     assert rc == -1
     rc = lib.tdmrg_kernel_bond_exp(16, 7, 1, 1, 1, 1, 0.0, -0.05, 1e-7, 33, None, None)
     assert rc == -1
+    rc = lib.tdmrg_kernel_bond_exp(257, 7, 1, 1, 1, 1, 0.0, -0.05, 1e-7, 32, None, None)
+    assert rc == -1

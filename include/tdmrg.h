@@ -141,7 +141,9 @@ int tdmrg_get_logz(const tdmrg_model* h, double* logz);
  * (process-wide counter, relative to this handle's last reset), and with profiling on the
  * host wall seconds of [12] site exponentials, [13] gauge QRs (included in [14]),
  * [14] gauge shifts with environment updates, [15] bond back-steps, [16] bond absorption,
- * [17] C(t) overlaps.  n = entries wanted (<= 18). */
+ * [17] C(t) overlaps; [18] event-timed milliseconds of the gauge QRs run outside graph
+ * captures and [19] their algorithmic FP64 flops (one Gram-Schmidt pass, 8 m n^2 per QR of an
+ * m x n matrix).  n = entries wanted (<= 20). */
 int tdmrg_get_stats(const tdmrg_model* h, double* stats, int n);
 int tdmrg_reset_stats(tdmrg_model* h);
 

@@ -297,20 +297,19 @@ int tdmrg_get_logz(const tdmrg_model* h, double* logz) {
 int tdmrg_get_stats(const tdmrg_model* h, double* stats, int n) {
   if (!h || !stats || n < 0) return fail(nullptr, TDMRG_ERR_ARG, "NULL argument");
   const auto& s = h->eng->stats;
-  const double v[18] = {s.site_updates, s.matvecs, s.heff_flops, s.krylov_vectors,
+  const double v[20] = {s.site_updates, s.matvecs, s.heff_flops, s.krylov_vectors,
                         s.bond_matvecs, s.qrs, s.completions, s.env_updates, s.heff_ms,
                         s.h2d_bytes, s.d2h_bytes,
                         (double)tdmrg::launch_count() - s.launches_at_reset + s.replayed_launches,
-                        s.t_site, s.t_qr, s.t_env, s.t_bond, s.t_absorb, s.t_observe};
-  for (int i = 0; i < n && i < 18; ++i) stats[i] = v[i];
+                        s.t_site, s.t_qr, s.t_env, s.t_bond, s.t_absorb, s.t_observe,
+                        s.qr_ms, s.qr_flops};
+  for (int i = 0; i < n && i < 20; ++i) stats[i] = v[i];
   return TDMRG_OK;
 }
 
 int tdmrg_reset_stats(tdmrg_model* h) {
   if (!h) return fail(nullptr, TDMRG_ERR_ARG, "NULL handle");
-  h->eng->stats = tdmrg::Stats();
-  h->eng->stats.launches_at_reset = (double)tdmrg::launch_count();
-  return TDMRG_OK;
+  return guarded(h, [&] { h->eng->reset_stats(); });
 }
 
 const char* tdmrg_last_error(const tdmrg_model* h) { return h ? h->err.c_str() : g_err.c_str(); }

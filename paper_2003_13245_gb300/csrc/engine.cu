@@ -408,6 +408,7 @@ Engine::Engine(const ModelParams& p) : P(p) {
   CK(cudaMallocHost(&h_pinned_, sizeof(int) * 8));
   CK(cudaMallocHost(&h_pinned_d_, sizeof(double) * 4));
   for (auto& e : ev_) CK(cudaEventCreate(&e));
+  for (auto& e : qr_ev_) CK(cudaEventCreate(&e));
 }
 
 Engine::~Engine() {
@@ -438,6 +439,8 @@ Engine::~Engine() {
   if (h_pinned_) cudaFreeHost(h_pinned_);
   if (h_pinned_d_) cudaFreeHost(h_pinned_d_);
   for (auto& e : ev_)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : qr_ev_)
     if (e) cudaEventDestroy(e);
   for (float* p : {tcb_.envA, tcb_.envB, tcb_.siteA, tcb_.siteB, tcb_.x32, tcb_.mix, tcb_.kpart})
     if (p) cudaFree(p);
@@ -742,6 +745,7 @@ void Engine::check_status() {
     stats.d2h_bytes += sizeof(unsigned long long);
   }
   CK(cudaStreamSynchronize(st_));
+  harvest_qr_events();
   if (bs_.mv) {
     const double used = (double)(*h_mv_ - mv_seen_);
     mv_seen_ = *h_mv_;
@@ -754,12 +758,35 @@ void Engine::check_status() {
   if (h_pinned_[3] != 0) throw Failure{TDMRG_ERR_TIMEOUT, "tensor-core pipeline wait timed out"};
 }
 
+// Every gauge QR outside a graph capture is bracketed by a pair of events; the pairs are read
+// at the next status check (the stream is synchronised there) or when the ring is full.
 void Engine::gauge_qr_dev(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cplx* R) {
   const double t0 = tic();
+  const bool timed = !capturing_;
+  if (timed) {
+    if (qr_ev_n_ == QR_EV) harvest_qr_events();
+    CK(cudaEventRecord(qr_ev_[2 * qr_ev_n_], st_));
+  }
   CK(gauge_qr_blocked(m, n, Y, p, E, Q, R, qb_scratch_, qb_len_, qb_acc_, qr_, status_, st_,
                       qr_gcap_, rank_tol_));
+  if (timed) {
+    CK(cudaEventRecord(qr_ev_[2 * qr_ev_n_ + 1], st_));
+    ++qr_ev_n_;
+    stats.qr_flops += 8.0 * m * (double)n * n;   // one Gram-Schmidt pass
+  }
   toc(stats.t_qr, t0);
   stats.qrs += 1;
+}
+
+void Engine::harvest_qr_events() {
+  if (qr_ev_n_ == 0) return;
+  CK(cudaEventSynchronize(qr_ev_[2 * qr_ev_n_ - 1]));
+  for (int i = 0; i < qr_ev_n_; ++i) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, qr_ev_[2 * i], qr_ev_[2 * i + 1]));
+    stats.qr_ms += ms;
+  }
+  qr_ev_n_ = 0;
 }
 
 void Engine::absorb_left(const cplx* C, int M, cplx* A, long long ncols) {
@@ -997,6 +1024,12 @@ void Engine::realtime_step_launch(double dt) {
 }
 
 void Engine::sync_and_check() { check_status(); }
+
+void Engine::reset_stats() {
+  harvest_qr_events();
+  stats = Stats();
+  stats.launches_at_reset = (double)launch_count();
+}
 
 // Imaginary time: the center is multiplied by exp(-tau H_eff / 2) at every site and by
 // exp(+tau K / 2) at every bond, so its norm drifts by about exp(-tau <H> / 2) per half step

@@ -121,6 +121,7 @@ struct Stats {
   double site_updates = 0, matvecs = 0, heff_flops = 0, krylov_vectors = 0, bond_matvecs = 0,
          qrs = 0, completions = 0, env_updates = 0;
   double heff_ms = 0;                 // event-timed duration of the site H_eff matvecs
+  double qr_ms = 0, qr_flops = 0;     // event-timed gauge QRs and their algorithmic flops
   // host wall time per phase (filled only when profiling is on; the phase ends synchronise)
   double t_site = 0, t_qr = 0, t_env = 0, t_bond = 0, t_absorb = 0, t_observe = 0;
   double h2d_bytes = 0, d2h_bytes = 0;
@@ -153,6 +154,7 @@ class Engine {
   // launch both real-time graphs of one step without waiting (batched use)
   void realtime_step_launch(double dt);
   void sync_and_check();
+  void reset_stats();   // reads pending QR timings first, then zeroes the counters
   void set_profiling(bool on) { prof_ = on; }
   void rebuild_mpos();
   void thermal_prepare(double beta, double dtau, int M);
@@ -206,6 +208,7 @@ class Engine {
   Cx overlap(const DevMps& bra, const DevMpo& W, const DevMps& ket);
   void fit_apply(const DevMpo& W, const DevMps& psi, DevMps& phi, int sweeps);
   void check_status();
+  void harvest_qr_events();
   void ensure_bond_scratch(int maxbond);
   void bond_exp(int M, int Dw, const cplx* Le, const cplx* Re, double tr, double ti);
   long long env_size(const DevMps& s, int k, int Dw, bool left) const;
@@ -256,6 +259,9 @@ class Engine {
   double* h_pinned_d_ = nullptr;
   cplx* env_tmp_[2] = {nullptr, nullptr};
   cudaEvent_t ev_[2 * KMAX + 2] = {};
+  static constexpr int QR_EV = 256;   // gauge-QR event pairs held before they are read
+  cudaEvent_t qr_ev_[2 * QR_EV] = {};
+  int qr_ev_n_ = 0;
   TcBufs tcb_{};
   BondScratch bs_{};
   unsigned long long* h_mv_ = nullptr;   // pinned copy of the device Krylov-vector counter

@@ -23,6 +23,7 @@ namespace {
 
 constexpr int QB = 16;                 // columns per block
 constexpr int QB_THREADS = 256;
+static_assert(QB * QB == QB_THREADS, "the in-block update gives one Gram entry to each thread");
 constexpr long long QB_TIMEOUT = 4000000000LL;
 
 __device__ __forceinline__ double wsum(double v) {
@@ -30,29 +31,27 @@ __device__ __forceinline__ double wsum(double v) {
   return v;
 }
 
-__device__ bool qb_barrier(unsigned* bar, unsigned nblocks, int* status) {
+// Grid barrier on one monotonic counter: barrier number e is passed once the counter reaches
+// e * nblocks (one atomic per CTA; the launcher clears the counter).  Bounded: gives up after
+// ~2 s, sets *status = 1, and every CTA then leaves.
+__device__ bool qb_barrier(unsigned* bar, unsigned nblocks, int* status, unsigned& epoch) {
   __syncthreads();
   __shared__ int s_ok;
+  ++epoch;
   if (threadIdx.x == 0) {
-    volatile unsigned* vgen = bar + 1;
+    volatile unsigned* vbar = bar;
     volatile int* vstat = status;
-    const unsigned gen = *vgen;
+    const unsigned target = epoch * nblocks;
     __threadfence();
-    const unsigned prev = atomicAdd(bar, 1u);
+    atomicAdd(bar, 1u);
     int ok = 1;
-    if (prev == nblocks - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      const long long t0 = clock64();
-      while (*vgen == gen) {
-        if (*vstat) { ok = 0; break; }
-        if (clock64() - t0 > QB_TIMEOUT) {
-          atomicExch(status, 1);
-          ok = 0;
-          break;
-        }
+    const long long t0 = clock64();
+    while (*vbar < target) {
+      if (*vstat) { ok = 0; break; }
+      if (clock64() - t0 > QB_TIMEOUT) {
+        atomicExch(status, 1);
+        ok = 0;
+        break;
       }
     }
     __threadfence();
@@ -85,8 +84,8 @@ __device__ __forceinline__ cplx qb_load(const QrRef& Y, long long r, long long c
 // Reduce `cnt` partial entries (offset `off` in each CTA's partial block) over all CTAs into
 // fin[off..off+cnt): CTA g sums the slice it owns -- one warp per entry, every lane loading its
 // share of the G partials at once -- then a barrier, then everyone may read fin.
-__device__ bool qb_reduce(const QbArgs& A, int off, int cnt, unsigned G) {
-  if (!qb_barrier(A.bar, G, A.status)) return false;
+__device__ bool qb_reduce(const QbArgs& A, int off, int cnt, unsigned G, unsigned& ep) {
+  if (!qb_barrier(A.bar, G, A.status, ep)) return false;
   const int per = (cnt + (int)G - 1) / (int)G;
   const int lo = blockIdx.x * per, hi = min(cnt, lo + per);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -101,7 +100,7 @@ __device__ bool qb_reduce(const QbArgs& A, int off, int cnt, unsigned G) {
     ay = wsum(ay);
     if (lane == 0) A.fin[off + e] = make_double2(ax, ay);
   }
-  return qb_barrier(A.bar, G, A.status);
+  return qb_barrier(A.bar, G, A.status, ep);
 }
 
 }  // namespace
@@ -123,6 +122,7 @@ __global__ void __launch_bounds__(QB_THREADS) gauge_qr_blocked_kernel(QbArgs A) 
   unsigned char* accb = acc + n;                              // [QB]
   int* sint = reinterpret_cast<int*>(((reinterpret_cast<uintptr_t>(accb + QB) + 15) & ~(uintptr_t)15));
   cplx* mypart = A.part + (long long)blockIdx.x * A.PS;
+  unsigned ep = 0;                                            // grid barriers passed
 
   for (long long e = threadIdx.x; e < (long long)nr * n; e += T)
     A.Q[(long long)r0 * n + e] = make_double2(0.0, 0.0);
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(QB_THREADS) gauge_qr_blocked_kernel(QbArgs A) 
       mypart[0] = make_double2(t, 0.0);
     }
   }
-  if (!qb_reduce(A, 0, 1, G)) return;
+  if (!qb_reduce(A, 0, 1, G, ep)) return;
   const double thr = A.rank_tol * sqrt(__ldcg(&A.fin[0]).x);
 
   int j0 = 0;
@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(QB_THREADS) gauge_qr_blocked_kernel(QbArgs A) 
         if ((threadIdx.x & 31) == 0) mypart[j0 * QB + t] = make_double2(s, 0.0);
       }
       // reduce the j0*QB coefficients and, right after them, the QB norms
-      if (!qb_reduce(A, 0, j0 * QB + QB, G)) return;
+      if (!qb_reduce(A, 0, j0 * QB + QB, G, ep)) return;
       for (int e = threadIdx.x; e < j0 * bsz; e += T) {
         const int i = e / bsz, t = e % bsz;
         const cplx h = acc[i] ? __ldcg(&A.fin[i * QB + t]) : make_double2(0.0, 0.0);
@@ -208,20 +208,51 @@ __global__ void __launch_bounds__(QB_THREADS) gauge_qr_blocked_kernel(QbArgs A) 
           dvec[t] = __ldcg(&A.fin[j0 * QB + t]).x;
         }
       }
-      // v_t[r] -= sum_i Q[r][i] h_it   (thread per (r, t))
-      for (int e = threadIdx.x; e < nr * bsz; e += T) {
-        const int r = e / bsz, t = e % bsz;
-        double ax = 0.0, bx = 0.0, ay = 0.0, by = 0.0;
-        for (int i = 0; i < j0; ++i) {
-          const cplx q = A.Q[(long long)(r0 + r) * n + i];
-          const cplx h = H[i * QB + t];
-          ax = fma(q.x, h.x, ax);
-          bx = fma(-q.y, h.y, bx);
-          ay = fma(q.x, h.y, ay);
-          by = fma(q.y, h.x, by);
+      // v_t[r] -= sum_i Q[r][i] h_it: thread per (r, t, part of the i range).  With few
+      // (r, t) pairs the i range is split over up to 8 threads (partials summed in order through
+      // shared memory): FP64 instructions cost the same whatever the number of active lanes, so
+      // the work is spread over every warp.
+      {
+        const int pairs = nr * bsz;
+        int split = 1;
+        while (split < 8 && pairs * split * 2 <= T) split *= 2;
+        cplx* hpart = Gb;      // QB*QB = T entries, free until the block Gram matrix
+        for (int e0 = 0; e0 < pairs; e0 += T / split) {
+          const int e = e0 + threadIdx.x / split, part = threadIdx.x % split;
+          double ax = 0.0, bx = 0.0, ay = 0.0, by = 0.0;
+          if (e < pairs) {
+            const int r = e / bsz, t = e % bsz;
+            for (int i = part; i < j0; i += split) {
+              const cplx q = A.Q[(long long)(r0 + r) * n + i];
+              const cplx h = H[i * QB + t];
+              ax = fma(q.x, h.x, ax);
+              bx = fma(-q.y, h.y, bx);
+              ay = fma(q.x, h.y, ay);
+              by = fma(q.y, h.x, by);
+            }
+          }
+          if (split == 1) {
+            if (e < pairs) {
+              const int r = e / bsz, t = e % bsz;
+              cplx& v = vb[t * rows + r];
+              v = make_double2(v.x - (ax + bx), v.y - (ay + by));
+            }
+          } else {
+            hpart[threadIdx.x] = make_double2(ax + bx, ay + by);
+            __syncthreads();
+            if (part == 0 && e < pairs) {
+              const int r = e / bsz, t = e % bsz;
+              double sx = 0.0, sy = 0.0;
+              for (int k = 0; k < split; ++k) {
+                sx += hpart[threadIdx.x + k].x;
+                sy += hpart[threadIdx.x + k].y;
+              }
+              cplx& v = vb[t * rows + r];
+              v = make_double2(v.x - sx, v.y - sy);
+            }
+            __syncthreads();
+          }
         }
-        cplx& v = vb[t * rows + r];
-        v = make_double2(v.x - (ax + bx), v.y - (ay + by));
       }
       __syncthreads();
       bool again = false;
@@ -245,50 +276,54 @@ __global__ void __launch_bounds__(QB_THREADS) gauge_qr_blocked_kernel(QbArgs A) 
       }
       mypart[e] = make_double2(ax + bx, ay + by);
     }
-    if (!qb_reduce(A, 0, QB * QB, G)) return;
+    if (!qb_reduce(A, 0, QB * QB, G, ep)) return;
     for (int e = threadIdx.x; e < QB * QB; e += T) Gb[e] = __ldcg(&A.fin[e]);
     __syncthreads();
-    // ---- Gram-Schmidt with skips inside the block (right-looking, warp 0)
-    if (threadIdx.x < 32) {
-      const int lane = threadIdx.x;
-      if (lane < QB) dvec[2 * QB + lane] = lane < bsz ? Gb[lane * QB + lane].x : 0.0;
-      __syncwarp();
-      int stop = bsz;
-      for (int s = 0; s < bsz; ++s) {
-        const double rho = Gb[s * QB + s].x;
-        if (s > 0 && rho < 0.25 * dvec[2 * QB + s]) {
-          stop = s;
-          break;
-        }
-        const double nrm = sqrt(fmax(rho, 0.0));
-        const bool take = nrm > thr;
-        __syncwarp();
-        if (lane == 0) {
-          accb[s] = take ? 1 : 0;
-          Gb[s * QB + s] = make_double2(take ? nrm : 0.0, 0.0);
-        }
-        // row s of R: R_st = G'_st / R_ss (t > s); rows of skipped columns are zero
-        if (lane > s && lane < bsz) {
-          const cplx g = Gb[s * QB + lane];
-          Gb[s * QB + lane] = take ? make_double2(g.x / nrm, g.y / nrm) : make_double2(0.0, 0.0);
-        }
-        __syncwarp();
-        // trailing update G'_tu -= conj(R_st) R_su for s < t <= u
-        if (take) {
-          for (int e = lane; e < QB * QB; e += 32) {
-            const int t = e / QB, u = e % QB;
-            if (t > s && u >= t && u < bsz) {
-              const cplx a = Gb[s * QB + t], b = Gb[s * QB + u];
-              Gb[t * QB + u] = make_double2(Gb[t * QB + u].x - (a.x * b.x + a.y * b.y),
-                                            Gb[t * QB + u].y - (a.x * b.y - a.y * b.x));
-            }
-          }
-        }
-        __syncwarp();
-      }
-      if (lane == 0) sint[0] = stop;
+    // ---- Gram-Schmidt with skips inside the block (Gram form, right-looking).  Thread 0 takes
+    // the pivot (cancellation guard, acceptance, one reciprocal); the row scaling and the
+    // trailing update use every thread, one entry each (QB * QB = T).
+    if (threadIdx.x < QB)
+      dvec[2 * QB + threadIdx.x] = threadIdx.x < bsz ? Gb[threadIdx.x * QB + threadIdx.x].x : 0.0;
+    if (threadIdx.x == 0) {
+      sint[0] = bsz;
+      sint[1] = 0;
     }
     __syncthreads();
+    for (int s = 0; s < bsz; ++s) {
+      if (threadIdx.x == 0) {
+        const double rho = Gb[s * QB + s].x;
+        if (s > 0 && rho < 0.25 * dvec[2 * QB + s]) {
+          sint[0] = s;          // the next block starts at this column
+          sint[1] = 1;
+        } else {
+          const double nrm = sqrt(fmax(rho, 0.0));
+          const bool take = nrm > thr;
+          accb[s] = take ? 1 : 0;
+          Gb[s * QB + s] = make_double2(take ? nrm : 0.0, 0.0);
+          dvec[3 * QB + s] = take ? 1.0 / nrm : 0.0;
+        }
+      }
+      __syncthreads();
+      if (sint[1]) break;
+      const bool take = accb[s] != 0;
+      const double inv = dvec[3 * QB + s];
+      // row s of R: R_st = G'_st / R_ss (t > s); rows of skipped columns are zero
+      if ((int)threadIdx.x > s && (int)threadIdx.x < bsz) {
+        const cplx g = Gb[s * QB + threadIdx.x];
+        Gb[s * QB + threadIdx.x] = take ? make_double2(g.x * inv, g.y * inv) : make_double2(0.0, 0.0);
+      }
+      __syncthreads();
+      // trailing update G'_tu -= conj(R_st) R_su for s < t <= u
+      if (take) {
+        const int t = threadIdx.x / QB, u = threadIdx.x % QB;
+        if (t > s && u >= t && u < bsz) {
+          const cplx a = Gb[s * QB + t], b = Gb[s * QB + u];
+          Gb[t * QB + u] = make_double2(Gb[t * QB + u].x - (a.x * b.x + a.y * b.y),
+                                        Gb[t * QB + u].y - (a.x * b.y - a.y * b.x));
+        }
+      }
+      __syncthreads();
+    }
     const int done = sint[0];
     // ---- form the accepted columns locally: q_t = (v_t - sum_{s<t} q_s R_st) / R_tt
     for (int r = threadIdx.x; r < nr; r += T) {
@@ -301,7 +336,7 @@ __global__ void __launch_bounds__(QB_THREADS) gauge_qr_blocked_kernel(QbArgs A) 
           x -= q.x * c.x - q.y * c.y;
           y -= q.x * c.y + q.y * c.x;
         }
-        const double inv = 1.0 / Gb[t * QB + t].x;
+        const double inv = dvec[3 * QB + t];
         const cplx qt = make_double2(x * inv, y * inv);
         vb[t * rows + r] = qt;
         A.Q[(long long)(r0 + r) * n + j0 + t] = qt;

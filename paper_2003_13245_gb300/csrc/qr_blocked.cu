@@ -296,11 +296,14 @@ __global__ void __launch_bounds__(QB_THREADS) gauge_qr_blocked_kernel(QbArgs A) 
           sint[0] = s;          // the next block starts at this column
           sint[1] = 1;
         } else {
-          const double nrm = sqrt(fmax(rho, 0.0));
+          // one reciprocal square root gives both R_ss and 1 / R_ss
+          const double rp = fmax(rho, 0.0);
+          const double rin = rp > 0.0 ? rsqrt(rp) : 0.0;
+          const double nrm = rp * rin;
           const bool take = nrm > thr;
           accb[s] = take ? 1 : 0;
           Gb[s * QB + s] = make_double2(take ? nrm : 0.0, 0.0);
-          dvec[3 * QB + s] = take ? 1.0 / nrm : 0.0;
+          dvec[3 * QB + s] = take ? rin : 0.0;
         }
       }
       __syncthreads();

@@ -258,7 +258,8 @@ def run_ours(args):
         phases = {"step_wall_s": wall,
                   "site_exponentials_s": ps["t_site"],
                   "of_which_heff_s": ps["heff_ms"] / 1e3,
-                  "of_which_lanczos_fp64_s": ps["t_site"] - ps["heff_ms"] / 1e3,
+                  "of_which_not_heff_s": ps["t_site"] - ps["heff_ms"] / 1e3,
+                  "of_which_lanczos_steps_gpu_s": ps["lz_ms"] / 1e3,
                   "gauge_shifts_s": ps["t_env"],
                   "of_which_gauge_qr_s": ps["t_qr"],
                   "bond_backsteps_s": ps["t_bond"],

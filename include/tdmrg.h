@@ -143,7 +143,9 @@ int tdmrg_get_logz(const tdmrg_model* h, double* logz);
  * [14] gauge shifts with environment updates, [15] bond back-steps, [16] bond absorption,
  * [17] C(t) overlaps; [18] event-timed milliseconds of the gauge QRs run outside graph
  * captures and [19] their algorithmic FP64 flops (one Gram-Schmidt pass, 8 m n^2 per QR of an
- * m x n matrix).  n = entries wanted (<= 20). */
+ * m x n matrix), [20] event-timed milliseconds of the Lanczos orthogonalisation steps of the
+ * host-driven Krylov exponentials (site updates; also bond steps of the FP64 path).
+ * n = entries wanted (<= 21). */
 int tdmrg_get_stats(const tdmrg_model* h, double* stats, int n);
 int tdmrg_reset_stats(tdmrg_model* h);
 

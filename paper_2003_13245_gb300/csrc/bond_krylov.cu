@@ -23,8 +23,7 @@
 // significands: no coarser than the 3xTF32 tensor-core products), every Lanczos quantity,
 // the small exponential and all norms in FP64.  All reductions have a fixed order: the
 // result does not depend on timing.
-#include "tdmrg_internal.cuh"
-#include "lanczos_exp.cuh"
+#include "lanczos_coop.cuh"
 
 namespace tdmrg {
 
@@ -33,8 +32,7 @@ namespace {
 constexpr int BT = 256;                 // threads per CTA
 constexpr int TL = 32;                  // output tile edge and k chunk
 constexpr int TP = TL + 2;              // padded row (16-byte aligned float2 pairs)
-constexpr int NV = KMAX + 1;            // partial-dot slots per CTA
-constexpr long long BK_TIMEOUT = 4000000000LL;   // about 2 s at 2 GHz
+using lzc::NV;
 
 struct BondArgs {
   int M, Dw, G, S, kcap, fixed;
@@ -54,41 +52,6 @@ struct BondArgs {
   unsigned long long* mv;
   double tr, ti, tol;
 };
-
-__device__ __forceinline__ double bk_wsum(double v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Grid barrier on one monotonic counter: barrier number e is passed once the counter
-// reaches e * nblocks (one atomic per CTA; the counter is cleared before every launch).
-// Bounded: gives up after ~2 s, sets *status = 1, and every CTA then leaves.
-__device__ bool bk_barrier(unsigned* bar, unsigned nblocks, unsigned& epoch, int* status) {
-  __syncthreads();
-  __shared__ int s_ok;
-  ++epoch;
-  if (threadIdx.x == 0) {
-    volatile unsigned* vbar = bar;
-    volatile int* vstat = status;
-    const unsigned target = epoch * nblocks;
-    __threadfence();
-    atomicAdd(bar, 1u);
-    int ok = 1;
-    const long long t0 = clock64();
-    while (*vbar < target) {
-      if (*vstat) { ok = 0; break; }
-      if (clock64() - t0 > BK_TIMEOUT) {
-        atomicExch(status, 1);
-        ok = 0;
-        break;
-      }
-    }
-    __threadfence();
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
 
 __device__ __forceinline__ void cfma32(float2& acc, float2 a, float2 b) {
   acc.x = fmaf(a.x, b.x, acc.x);
@@ -159,87 +122,6 @@ __device__ __forceinline__ float2 to_f2(cplx z) {
   return make_float2(__double2float_rn(z.x), __double2float_rn(z.y));
 }
 
-// Warp `wv` computes the partial dots of vectors i = i0 + wv, i0 + wv + 8, ... < i1 over the
-// own slice (lanes stride the slice, fixed warp tree) and stores them at part[g * NV + i].
-__device__ __forceinline__ void slice_dots(const BondArgs& A, const cplx* ws, long long e0,
-                                           int len, int i0, int i1, cplx* part) {
-  const int lane = threadIdx.x & 31, wv = threadIdx.x >> 5;
-  for (int i = i0 + wv; i < i1; i += BT / 32) {
-    const cplx* q = A.V + (size_t)i * A.n + e0;
-    double sr = 0.0, si = 0.0;
-    for (int e = lane; e < len; e += 32) {
-      const cplx a = q[e], b = ws[e];
-      sr = fma(a.x, b.x, sr);
-      sr = fma(a.y, b.y, sr);
-      si = fma(a.x, b.y, si);
-      si = fma(-a.y, b.x, si);
-    }
-    sr = bk_wsum(sr);
-    si = bk_wsum(si);
-    if (lane == 0) part[(size_t)blockIdx.x * NV + i] = make_double2(sr, si);
-  }
-}
-
-// h[i] = sum_g part[g * NV + i] for i in [i0, i1), every CTA in the same order.
-__device__ __forceinline__ void reduce_dots(const BondArgs& A, const cplx* part, int i0, int i1,
-                                            cplx* h) {
-  const int lane = threadIdx.x & 31, wv = threadIdx.x >> 5;
-  for (int i = i0 + wv; i < i1; i += BT / 32) {
-    double sr = 0.0, si = 0.0;
-    for (int g = lane; g < A.G; g += 32) {
-      const cplx p = __ldcg(&part[(size_t)g * NV + i]);
-      sr += p.x;
-      si += p.y;
-    }
-    sr = bk_wsum(sr);
-    si = bk_wsum(si);
-    if (lane == 0) h[i] = make_double2(sr, si);
-  }
-  __syncthreads();
-}
-
-// ws[e] -= sum_{i in [i0, i1)} h[i] q_i[e] on the own slice
-__device__ __forceinline__ void slice_project(const BondArgs& A, cplx* ws, long long e0, int len,
-                                              int i0, int i1, const cplx* h) {
-  for (int e = threadIdx.x; e < len; e += BT) {
-    double ax = ws[e].x, ay = ws[e].y;
-    for (int i = i0; i < i1; ++i) {
-      const cplx q = A.V[(size_t)i * A.n + e0 + e], c = h[i];
-      ax = fma(-q.x, c.x, ax);
-      ax = fma(q.y, c.y, ax);
-      ay = fma(-q.x, c.y, ay);
-      ay = fma(-q.y, c.x, ay);
-    }
-    ws[e] = make_double2(ax, ay);
-  }
-  __syncthreads();
-}
-
-// sum over CTAs of partn (warp 0, fixed order), broadcast through *dst
-__device__ __forceinline__ void reduce_norm(const BondArgs& A, double* dst) {
-  if (threadIdx.x < 32) {
-    double s = 0.0;
-    for (int g = threadIdx.x; g < A.G; g += 32) s += __ldcg(&A.partn[g]);
-    s = bk_wsum(s);
-    if (threadIdx.x == 0) *dst = s;
-  }
-  __syncthreads();
-}
-
-__device__ __forceinline__ void slice_norm(const BondArgs& A, const cplx* ws, int len,
-                                           double* red) {
-  double s = 0.0;
-  for (int e = threadIdx.x; e < len; e += BT) s = fma(ws[e].x, ws[e].x, fma(ws[e].y, ws[e].y, s));
-  s = bk_wsum(s);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < BT / 32; ++w) t += red[w];
-    A.partn[blockIdx.x] = t;
-  }
-}
-
 __global__ void __launch_bounds__(BT, 1) bond_exp_kernel(BondArgs A) {
   extern __shared__ __align__(16) unsigned char dyn[];
   float2* at = reinterpret_cast<float2*>(dyn);        // [KT][TP]
@@ -263,9 +145,9 @@ __global__ void __launch_bounds__(BT, 1) bond_exp_kernel(BondArgs A) {
   // ||v||: q_0 = v / ||v||
   for (int e = threadIdx.x; e < len; e += BT) ws[e] = A.v[e0 + e];
   __syncthreads();
-  slice_norm(A, ws, len, red);
-  if (!bk_barrier(A.bar, A.G, epoch, A.status)) return;
-  reduce_norm(A, &s_nrm);
+  lzc::slice_norm(ws, len, red, A.partn);
+  if (!lzc::barrier(A.bar, A.G, epoch, A.status)) return;
+  lzc::reduce_norm(A.partn, A.G, &s_nrm);
   const double b0 = sqrt(s_nrm);
   if (threadIdx.x == 0) {
     s_b0 = b0;
@@ -314,7 +196,7 @@ __global__ void __launch_bounds__(BT, 1) bond_exp_kernel(BondArgs A) {
           if (a < M && b < M) Tw[(size_t)a * M + b] = acc[i][jj];
         }
     }
-    if (!bk_barrier(A.bar, A.G, epoch, A.status)) return;
+    if (!lzc::barrier(A.bar, A.G, epoch, A.status)) return;
     // ---- B: P_w = T_w R_w^T
     for (int it = blockIdx.x; it < items; it += A.G) {
       const int w = it / (nt * nt), rem = it - w * nt * nt;
@@ -344,7 +226,7 @@ __global__ void __launch_bounds__(BT, 1) bond_exp_kernel(BondArgs A) {
           if (a < M && b < M) Pw[(size_t)a * M + b] = acc[i][jj];
         }
     }
-    if (!bk_barrier(A.bar, A.G, epoch, A.status)) return;
+    if (!lzc::barrier(A.bar, A.G, epoch, A.status)) return;
     // ---- C1: w = sum_w P_w (FP64, channel order); dots against q_lo .. q_j
     for (int e = threadIdx.x; e < len; e += BT) {
       double x = 0.0, y = 0.0;
@@ -357,47 +239,32 @@ __global__ void __launch_bounds__(BT, 1) bond_exp_kernel(BondArgs A) {
     }
     __syncthreads();
     const int lo = j > 0 ? j - 1 : 0;
-    slice_dots(A, ws, e0, len, lo, j + 1, part1);
-    if (!bk_barrier(A.bar, A.G, epoch, A.status)) return;
+    lzc::slice_dots(A.V, n, ws, e0, len, lo, j + 1, part1);
+    if (!lzc::barrier(A.bar, A.G, epoch, A.status)) return;
     // ---- C2: first projection; dots against q_0 .. q_j
-    reduce_dots(A, part1, lo, j + 1, h1);
-    slice_project(A, ws, e0, len, lo, j + 1, h1);
-    slice_dots(A, ws, e0, len, 0, j + 1, part2);
-    if (!bk_barrier(A.bar, A.G, epoch, A.status)) return;
+    lzc::reduce_dots(part1, A.G, lo, j + 1, h1);
+    lzc::slice_project(A.V, n, ws, e0, len, lo, j + 1, h1);
+    lzc::slice_dots(A.V, n, ws, e0, len, 0, j + 1, part2);
+    if (!lzc::barrier(A.bar, A.G, epoch, A.status)) return;
     // ---- C3: second projection; ||w||^2
-    reduce_dots(A, part2, 0, j + 1, h2);
-    slice_project(A, ws, e0, len, 0, j + 1, h2);
+    lzc::reduce_dots(part2, A.G, 0, j + 1, h2);
+    lzc::slice_project(A.V, n, ws, e0, len, 0, j + 1, h2);
     for (int e = threadIdx.x; e < len; e += BT) A.W[e0 + e] = ws[e];
-    slice_norm(A, ws, len, red);
-    if (!bk_barrier(A.bar, A.G, epoch, A.status)) return;
+    lzc::slice_norm(ws, len, red, A.partn);
+    if (!lzc::barrier(A.bar, A.G, epoch, A.status)) return;
     // ---- C4: tridiagonal bookkeeping and the small exponential (warp 0 of every CTA)
-    reduce_norm(A, &s_nrm);
+    lzc::reduce_norm(A.partn, A.G, &s_nrm);
     if (threadIdx.x < 32) {
       const int lane = threadIdx.x;
-      const int kk = j + 1;
-      const double aj = h1[j].x + h2[j].x;       // alpha_j = Re <q_j, K q_j>
-      const double nb = sqrt(s_nrm);              // beta_{j+1}
-      const double a = lane < j ? alpha[lane] : (lane == j ? aj : 0.0);
-      const double bl = (lane >= 1 && lane < kk) ? beta[lane] : 0.0;
-      const double br = (lane + 1 < kk) ? beta[lane + 1] : 0.0;
-      __syncwarp();
-      if (lane == 0) {
-        alpha[j] = aj;
-        beta[j + 1] = nb;
-      }
-      const double scale = lz_warp_max(fmax(fabs(a), fabs(bl)));
-      double yr, yi;
-      lz_exp_tridiag(a, bl, br, kk, A.tr, A.ti, yr, yi);
-      const double ylr = __shfl_sync(0xffffffffu, yr, kk - 1);
-      const double yli = __shfl_sync(0xffffffffu, yi, kk - 1);
-      const double err = nb * sqrt(ylr * ylr + yli * yli);
-      const bool breakdown = nb <= 1e-12 * fmax(scale, 1e-300);
-      const bool done = breakdown || kk >= A.kcap || (!A.fixed && err < A.tol);
-      if (done && lane < kk) cc[lane] = make_double2(s_b0 * yr, s_b0 * yi);
+      double yr, yi, err;
+      bool done, bd;
+      lzc::tridiag_step(j, h1[j].x + h2[j].x, s_nrm, A.tr, A.ti, A.tol, A.kcap, A.fixed, alpha,
+                        beta, true, yr, yi, done, err, bd);
+      if (done && lane <= j) cc[lane] = make_double2(s_b0 * yr, s_b0 * yi);
       if (lane == 0) {
         s_done = done ? 1 : 0;
-        s_k = kk;
-        s_scale = nb;
+        s_k = j + 1;
+        s_scale = sqrt(s_nrm);
       }
     }
     __syncthreads();

@@ -409,6 +409,7 @@ Engine::Engine(const ModelParams& p) : P(p) {
   CK(cudaMallocHost(&h_pinned_d_, sizeof(double) * 4));
   for (auto& e : ev_) CK(cudaEventCreate(&e));
   for (auto& e : qr_ev_) CK(cudaEventCreate(&e));
+  for (auto& e : lz_ev_) CK(cudaEventCreate(&e));
 }
 
 Engine::~Engine() {
@@ -441,6 +442,8 @@ Engine::~Engine() {
   for (auto& e : ev_)
     if (e) cudaEventDestroy(e);
   for (auto& e : qr_ev_)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : lz_ev_)
     if (e) cudaEventDestroy(e);
   for (float* p : {tcb_.envA, tcb_.envB, tcb_.siteA, tcb_.siteB, tcb_.x32, tcb_.mix, tcb_.kpart})
     if (p) cudaFree(p);
@@ -753,7 +756,7 @@ void Engine::check_status() {
     stats.krylov_vectors += used;
   }
   if (h_pinned_[1] == 1) throw Failure{TDMRG_ERR_TIMEOUT, "gauge QR grid barrier timed out"};
-  if (h_pinned_[2] == 1) throw Failure{TDMRG_ERR_TIMEOUT, "bond exponential grid barrier timed out"};
+  if (h_pinned_[2] == 1) throw Failure{TDMRG_ERR_TIMEOUT, "Lanczos grid barrier timed out"};
   if (h_pinned_[1] == 2) throw Failure{TDMRG_ERR_CUDA, "gauge QR ran out of completion vectors"};
   if (h_pinned_[3] != 0) throw Failure{TDMRG_ERR_TIMEOUT, "tensor-core pipeline wait timed out"};
 }
@@ -778,15 +781,26 @@ void Engine::gauge_qr_dev(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cplx* 
   stats.qrs += 1;
 }
 
+// reads the event pairs of the gauge QRs and of the Lanczos steps recorded so far
 void Engine::harvest_qr_events() {
-  if (qr_ev_n_ == 0) return;
-  CK(cudaEventSynchronize(qr_ev_[2 * qr_ev_n_ - 1]));
-  for (int i = 0; i < qr_ev_n_; ++i) {
-    float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, qr_ev_[2 * i], qr_ev_[2 * i + 1]));
-    stats.qr_ms += ms;
+  if (qr_ev_n_ > 0) {
+    CK(cudaEventSynchronize(qr_ev_[2 * qr_ev_n_ - 1]));
+    for (int i = 0; i < qr_ev_n_; ++i) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, qr_ev_[2 * i], qr_ev_[2 * i + 1]));
+      stats.qr_ms += ms;
+    }
+    qr_ev_n_ = 0;
   }
-  qr_ev_n_ = 0;
+  if (lz_ev_n_ > 0) {
+    CK(cudaEventSynchronize(lz_ev_[2 * lz_ev_n_ - 1]));
+    for (int i = 0; i < lz_ev_n_; ++i) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, lz_ev_[2 * i], lz_ev_[2 * i + 1]));
+      stats.lz_ms += ms;
+    }
+    lz_ev_n_ = 0;
+  }
 }
 
 void Engine::absorb_left(const cplx* C, int M, cplx* A, long long ncols) {

@@ -122,6 +122,7 @@ struct Stats {
          qrs = 0, completions = 0, env_updates = 0;
   double heff_ms = 0;                 // event-timed duration of the site H_eff matvecs
   double qr_ms = 0, qr_flops = 0;     // event-timed gauge QRs and their algorithmic flops
+  double lz_ms = 0;                   // event-timed Lanczos orthogonalisation steps
   // host wall time per phase (filled only when profiling is on; the phase ends synchronise)
   double t_site = 0, t_qr = 0, t_env = 0, t_bond = 0, t_absorb = 0, t_observe = 0;
   double h2d_bytes = 0, d2h_bytes = 0;
@@ -262,6 +263,8 @@ class Engine {
   static constexpr int QR_EV = 256;   // gauge-QR event pairs held before they are read
   cudaEvent_t qr_ev_[2 * QR_EV] = {};
   int qr_ev_n_ = 0;
+  cudaEvent_t lz_ev_[2 * QR_EV] = {};
+  int lz_ev_n_ = 0;
   TcBufs tcb_{};
   BondScratch bs_{};
   unsigned long long* h_mv_ = nullptr;   // pinned copy of the device Krylov-vector counter
@@ -271,8 +274,8 @@ class Engine {
 };
 
 // Lanczos with full re-orthogonalisation in FP64: the three-term step against q_j and
-// q_{j-1}, then one classical Gram-Schmidt pass against every Krylov vector.  The small
-// exponential and the stopping test run on the device.  The host polls the stop flag of
+// q_{j-1}, then one classical Gram-Schmidt pass against every Krylov vector, the norm, the
+// small exponential and the stopping test -- one cooperative launch per Krylov vector.  The host polls the stop flag of
 // iteration j-1 while iteration j is already queued (its kernels skip once the flag is set),
 // so the device never waits for the host between iterations.
 template <class F>
@@ -291,14 +294,15 @@ inline int Engine::krylov(long long n, const cplx* v, cplx* out, double tr, doub
     cplx* q = V_ + (size_t)j * n;
     cplx* w = V_ + (size_t)(j + 1) * n;
     matvec(q, w, done);
-    const int lo = j > 0 ? j - 1 : 0;
-    CK(zdots(n, j - lo + 1, V_ + (size_t)lo * n, n, w, S->h1 + lo, part_c_, red_cnt_, done, st_));
-    CK(zsub_multi(n, j - lo + 1, V_ + (size_t)lo * n, n, S->h1 + lo, w, done, st_));
-    CK(zdots(n, j + 1, V_, n, w, S->h2, part_c_, red_cnt_, done, st_));
-    CK(zsub_multi(n, j + 1, V_, n, S->h2, w, done, st_));
-    CK(znorm2(n, w, &S->nrm2, part_d_, red_cnt_ + KMAX + 1, done, st_));
-    CK(lz_small_exp(S, j, tr, ti, ktol_, kcap, fixed_k_ > 0 ? 1 : 0, st_));
-    CK(zscale_by(n, w, &S->inv, done, st_));
+    // both Gram-Schmidt passes, norm, small exponential, stop test and scaling: one launch
+    const bool timed = !capturing_;
+    if (timed) {
+      if (lz_ev_n_ == QR_EV) harvest_qr_events();
+      CK(cudaEventRecord(lz_ev_[2 * lz_ev_n_], st_));
+    }
+    CK(lz_step(n, j, V_, S, bs_, status_ + 1, tr, ti, ktol_, kcap, fixed_k_ > 0 ? 1 : 0,
+               qr_gcap_, st_));
+    if (timed) CK(cudaEventRecord(lz_ev_[2 * lz_ev_n_++ + 1], st_));
     CK(cudaMemcpyAsync(h_pinned_ + 4 + (j & 1) * 2, done, sizeof(int), cudaMemcpyDeviceToHost,
                        st_));
     CK(cudaEventRecord(ev_[2 * KMAX + (j & 1)], st_));

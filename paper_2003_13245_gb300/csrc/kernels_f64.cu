@@ -2,7 +2,6 @@
 // the environment updates and the bond step), sparse MPO channel mixing, Lanczos
 // reductions, the small Krylov exponential and the cooperative gauge QR.
 #include "tdmrg_internal.cuh"
-#include "lanczos_exp.cuh"
 
 #include <cooperative_groups.h>
 #include <cmath>
@@ -190,8 +189,7 @@ __device__ __forceinline__ cplx block_sum_c(cplx v, cplx* sh) {
   return out;
 }
 
-// Dot products h[vec] = sum_e conj(V[vec][e]) w[e] in one launch: block (x, vec) reduces a
-// grid-stride chunk, writes its partial, and the last block of each vector (ticket counter)
+// Cross-block sums (znorm2): block x writes its partial, the last block (ticket counter)
 // sums the partials in index order -- deterministic, no second launch.
 constexpr int RED_BLOCKS = 304;      // partial blocks per vector (2 per SM)
 
@@ -205,77 +203,6 @@ __device__ __forceinline__ bool last_block(unsigned* counter, unsigned nblocks) 
   }
   __syncthreads();
   return s_last != 0;
-}
-
-__global__ void zdots_kernel(long long n, const cplx* V, long long ldv, const cplx* w, cplx* out,
-                             cplx* partial, unsigned* counters, const int* skip) {
-  if (skip && *skip) return;
-  __shared__ cplx sh[32];
-  const int vec = blockIdx.y;
-  const cplx* v = V + vec * ldv;
-  double ax = 0.0, ay = 0.0, bx = 0.0, by = 0.0;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
-       e += (long long)gridDim.x * blockDim.x) {
-    const cplx a = v[e], b = w[e];
-    ax = fma(a.x, b.x, ax);
-    bx = fma(a.y, b.y, bx);
-    ay = fma(a.x, b.y, ay);
-    by = fma(-a.y, b.x, by);
-  }
-  cplx s = block_sum_c(make_double2(ax + bx, ay + by), sh);
-  if (threadIdx.x == 0) partial[vec * gridDim.x + blockIdx.x] = s;
-  if (!last_block(&counters[vec], gridDim.x)) return;
-  double rx = 0.0, ry = 0.0;
-  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
-    const cplx p = __ldcg(&partial[vec * gridDim.x + i]);     // written by other SMs
-    rx += p.x;
-    ry += p.y;
-  }
-  cplx r = block_sum_c(make_double2(rx, ry), sh);
-  if (threadIdx.x == 0) {
-    out[vec] = r;
-    counters[vec] = 0;          // ready for the next call
-  }
-}
-
-cudaError_t zdots(long long n, int nvec, const cplx* V, long long ldv, const cplx* w, cplx* out,
-                  cplx* partial, unsigned* counters, const int* skip, cudaStream_t s) {
-  int g = (int)((n + 255) / 256);
-  if (g > RED_BLOCKS) g = RED_BLOCKS;
-  if (g < 1) g = 1;
-  count_launch();
-  zdots_kernel<<<dim3(g, nvec), 256, 0, s>>>(n, V, ldv, w, out, partial, counters, skip);
-  return cudaGetLastError();
-}
-
-__global__ void zsub_multi_kernel(long long n, int nvec, const cplx* V, long long ldv,
-                                  const cplx* h, cplx* w, const int* skip) {
-  if (skip && *skip) return;
-  __shared__ cplx hs[KMAX + 1];
-  if (threadIdx.x < nvec) hs[threadIdx.x] = h[threadIdx.x];
-  __syncthreads();
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
-       e += (long long)gridDim.x * blockDim.x) {
-    double ax = w[e].x, ay = w[e].y, bx = 0.0, by = 0.0;
-    for (int i = 0; i < nvec; ++i) {
-      const cplx q = V[i * ldv + e], c = hs[i];
-      ax = fma(-q.x, c.x, ax);
-      bx = fma(q.y, c.y, bx);
-      ay = fma(-q.x, c.y, ay);
-      by = fma(-q.y, c.x, by);
-    }
-    w[e] = make_double2(ax + bx, ay + by);
-  }
-}
-
-cudaError_t zsub_multi(long long n, int nvec, const cplx* V, long long ldv, const cplx* h,
-                       cplx* w, const int* skip, cudaStream_t s) {
-  long long blocks = (n + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  if (blocks < 1) blocks = 1;
-  count_launch();
-  zsub_multi_kernel<<<(int)blocks, 256, 0, s>>>(n, nvec, V, ldv, h, w, skip);
-  return cudaGetLastError();
 }
 
 __global__ void znorm2_kernel(long long n, const cplx* x, double* out, double* partial,
@@ -355,8 +282,8 @@ cudaError_t zscale_by(long long n, cplx* x, const double* factor, const int* ski
 }
 
 // ------------------------------------------------------------------------------------
-// Lanczos bookkeeping and the small exponential exp(tau T_k) e_1 (one warp, FP64, the
-// Taylor-with-sub-steps routine of lanczos_exp.cuh).  Lane i holds row i of T_k.
+// Lanczos bookkeeping: the start of a run and the final combination (the orthogonalisation
+// steps themselves are one cooperative launch each, lanczos_step.cu).
 // ------------------------------------------------------------------------------------
 __global__ void lz_start_kernel(LzState* S, const double* nrm2) {
   if (threadIdx.x == 0) {
@@ -376,52 +303,6 @@ __global__ void lz_start_kernel(LzState* S, const double* nrm2) {
 cudaError_t lz_start(LzState* S, const double* nrm2, cudaStream_t s) {
   count_launch();
   lz_start_kernel<<<1, 32, 0, s>>>(S, nrm2);
-  return cudaGetLastError();
-}
-
-__global__ void lz_small_exp_kernel(LzState* S, int j, double tr, double ti, double tol,
-                                    int kcap, int fixed) {
-  if (S->done) return;
-  const int lane = threadIdx.x;
-  const int k = j + 1;
-  const double aj = S->h1[j].x + S->h2[j].x;       // alpha_j = Re <q_j, H q_j>
-  const double nb = sqrt(S->nrm2);                  // beta_{j+1}
-  // row `lane` of T_k: diagonal alpha_lane, off-diagonals beta_lane (left), beta_{lane+1}
-  const double a = lane < j ? S->alpha[lane] : (lane == j ? aj : 0.0);
-  const double bl = (lane >= 1 && lane < k) ? S->beta[lane] : 0.0;
-  const double br = (lane + 1 < k) ? S->beta[lane + 1] : 0.0;
-  __syncwarp();
-  if (lane == 0) {
-    S->alpha[j] = aj;
-    S->beta[j + 1] = nb;
-  }
-  // scale used for the breakdown test: entries of T_k only
-  const double scale = warp_max(fmax(fabs(a), fabs(bl)));
-  double yr, yi;
-  lz_exp_tridiag(a, bl, br, k, tr, ti, yr, yi);
-  const double ylr = __shfl_sync(0xffffffffu, yr, k - 1);
-  const double yli = __shfl_sync(0xffffffffu, yi, k - 1);
-  const double err = nb * sqrt(ylr * ylr + yli * yli);
-  const bool breakdown = nb <= 1e-12 * fmax(scale, 1e-300);
-  const bool done = breakdown || k >= kcap || (!fixed && err < tol);
-  if (done) {
-    if (lane < k) S->c[lane] = make_double2(S->b0 * yr, S->b0 * yi);
-    if (lane == 0) {
-      S->k = k;
-      S->err = err;
-      S->noconv = (!breakdown && !fixed && err > 1e3 * tol) ? 1 : 0;
-      __threadfence();
-      S->done = 1;
-    }
-  } else if (lane == 0) {
-    S->inv = 1.0 / nb;
-  }
-}
-
-cudaError_t lz_small_exp(LzState* S, int j, double tau_re, double tau_im, double tol, int kcap,
-                         int fixed, cudaStream_t s) {
-  count_launch();
-  lz_small_exp_kernel<<<1, 32, 0, s>>>(S, j, tau_re, tau_im, tol, kcap, fixed);
   return cudaGetLastError();
 }
 

@@ -2,10 +2,9 @@
 // warp: lane i holds row i (diagonal a, off-diagonals bl on its left and br on its right;
 // rows >= k are zero).  Taylor series with scaling (Moler & Van Loan, "Nineteen dubious
 // ways to compute the exponential of a matrix", method 1, with the squaring replaced by
-// repeated sub-steps): s = ceil(|tau| ||T - sigma||_inf / 0.5) sub-steps after a shift by
-// the Gershgorin centre sigma, each summed until the term falls below 1e-19 of the
-// sub-step's starting maximum.  Shared by the host-driven Lanczos and the fused bond
-// exponential so that both take the same small exponential.
+// repeated sub-steps): s = ceil(|tau| ||T - sigma||_inf) sub-steps after a shift by the
+// Gershgorin centre sigma, each a Taylor sum with a term count fixed by the sub-step's norm.
+// Shared by the Lanczos drivers so that all take the same small exponential.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -29,49 +28,101 @@ static __constant__ double kLzInvQ[64] = {
     LZ_R4(53.0), LZ_R4(57.0), 1.0 / 61.0, 1.0 / 62.0, 1.0 / 63.0};
 #undef LZ_R4
 
+// Product of the tridiagonal rows with a lane-distributed vector: (T u)_lane.
+__device__ __forceinline__ double lz_tri(double a, double bl, double br, double u) {
+  const int lane = threadIdx.x & 31;
+  const double up = __shfl_up_sync(0xffffffffu, u, 1);
+  const double dn = __shfl_down_sync(0xffffffffu, u, 1);
+  return a * u + (lane >= 1 ? bl * up : 0.0) + (lane < 31 ? br * dn : 0.0);
+}
+
 // exp(tau T) e_1 for a T whose rows are given per lane (a: diagonal, bl/br: off-diagonals);
 // tnorm = ||T||_inf.  All 32 lanes call it; returns the lane's entry in (yr, yi).
+// Sub-steps of norm x = |tau| tnorm / s <= 1; the number of Taylor terms q is fixed in advance
+// from x so that the first neglected term x^(q+1)/(q+1)! stays below 1e-18 (no per-term
+// reduction across the warp).  T is real, so a real tau keeps the series real, and an
+// imaginary tau = i theta needs only real tridiagonal products: in the first sub-step (start
+// vector e_1, real) the terms alternate between real and imaginary (one product per term),
+// afterwards the real and imaginary parts each take one product.
 __device__ __forceinline__ void lz_taylor_exp(double a, double bl, double br, double tnorm,
                                               double tr, double ti, double& yr, double& yi) {
   const int lane = threadIdx.x & 31;
   const double tabs = sqrt(tr * tr + ti * ti);
-  int nsub = (int)ceil(tabs * tnorm / 0.5);
+  int nsub = (int)ceil(tabs * tnorm);
   if (nsub < 1) nsub = 1;
+  const double x = tabs * tnorm / nsub;
+  const int nq = x > 0.5 ? 20 : x > 0.25 ? 16 : x > 0.1 ? 14 : x > 0.01 ? 11 : x > 1e-3 ? 8 : 6;
   const double sr = tr / nsub, si = ti / nsub;
   yr = (lane == 0) ? 1.0 : 0.0;
   yi = 0.0;
+  if (ti == 0.0) {
+    // real tau: real series
+    for (int st = 0; st < nsub; ++st) {
+      double t = yr, acc = yr;
+      for (int q = 1; q <= nq; ++q) {
+        t = (sr * kLzInvQ[q]) * lz_tri(a, bl, br, t);
+        acc += t;
+      }
+      yr = acc;
+    }
+    return;
+  }
+  if (tr == 0.0) {
+    // imaginary tau = i theta.  First sub-step: term q = (i theta/s)^q T^q e_1 / q!, kept as
+    // the real r_q = (theta/s)^q T^q e_1 / q! and added with the phase i^q.
+    {
+      double r = yr, ar = yr, ai = 0.0;
+      for (int q = 1; q <= nq; ++q) {
+        r = (si * kLzInvQ[q]) * lz_tri(a, bl, br, r);
+        switch (q & 3) {
+          case 1: ai += r; break;
+          case 2: ar -= r; break;
+          case 3: ai -= r; break;
+          default: ar += r; break;
+        }
+      }
+      yr = ar;
+      yi = ai;
+    }
+    for (int st = 1; st < nsub; ++st) {
+      double ur = yr, ui = yi, ar = yr, ai = yi;
+      for (int q = 1; q <= nq; ++q) {
+        const double c = si * kLzInvQ[q];
+        const double xr = lz_tri(a, bl, br, ur), xi = lz_tri(a, bl, br, ui);
+        ur = -c * xi;                 // (i c)(xr + i xi)
+        ui = c * xr;
+        ar += ur;
+        ai += ui;
+      }
+      yr = ar;
+      yi = ai;
+    }
+    return;
+  }
   for (int st = 0; st < nsub; ++st) {
-    // over one sub-step ||exp(tau T / s)|| >= e^-0.5, so the result keeps at least
-    // e^-0.5 / sqrt(32) of the starting maximum: terms are compared against that maximum
-    const double am = lz_warp_max(fabs(yr) + fabs(yi));
     double tr_ = yr, ti_ = yi, ar = yr, ai = yi;
-    for (int q = 1; q <= 60; ++q) {
-      const double ur = __shfl_up_sync(0xffffffffu, tr_, 1);
-      const double ui = __shfl_up_sync(0xffffffffu, ti_, 1);
-      const double dr = __shfl_down_sync(0xffffffffu, tr_, 1);
-      const double di = __shfl_down_sync(0xffffffffu, ti_, 1);
-      const double xr = a * tr_ + (lane >= 1 ? bl * ur : 0.0) + (lane < 31 ? br * dr : 0.0);
-      const double xi = a * ti_ + (lane >= 1 ? bl * ui : 0.0) + (lane < 31 ? br * di : 0.0);
+    for (int q = 1; q <= nq; ++q) {
+      const double xr = lz_tri(a, bl, br, tr_), xi = lz_tri(a, bl, br, ti_);
       // term <- (tau / nsub) (T term) / q
       const double cr = sr * kLzInvQ[q], ci = si * kLzInvQ[q];
       tr_ = cr * xr - ci * xi;
       ti_ = cr * xi + ci * xr;
       ar += tr_;
       ai += ti_;
-      const double tm = lz_warp_max(fabs(tr_) + fabs(ti_));
-      if (tm <= 1e-19 * am) break;
     }
     yr = ar;
     yi = ai;
   }
 }
 
-// exp(tau T_k) e_1 for the Lanczos tridiagonal T_k (rows >= k zero).  T_k is shifted by the
-// centre sigma of its Gershgorin interval, exp(tau T) = e^(tau sigma) exp(tau (T - sigma)),
-// so that the number of sub-steps follows the spread of the spectrum rather than its offset
-// (the energy of the state, often much larger than the spread).
-__device__ __forceinline__ void lz_exp_tridiag(double a, double bl, double br, int k, double tr,
-                                               double ti, double& yr, double& yi) {
+// exp(tau (T_k - sigma)) e_1 for the Lanczos tridiagonal T_k (rows >= k zero), sigma the
+// centre of its Gershgorin interval; exp(tau T) = e^(tau sigma) exp(tau (T - sigma)), so the
+// number of sub-steps follows the spread of the spectrum rather than its offset (the energy
+// of the state, often much larger than the spread).  The factor e^(tau sigma) is applied by
+// lz_shift_factor: its modulus e^(Re(tau) sigma) whenever Re(tau) != 0, its phase only where
+// the caller needs the vector itself (the phase does not change |y|).
+__device__ __forceinline__ double lz_exp_shifted(double a, double bl, double br, int k,
+                                                 double tr, double ti, double& yr, double& yi) {
   const int lane = threadIdx.x & 31;
   const bool in = lane < k;
   const double rad = fabs(bl) + fabs(br);
@@ -80,14 +131,25 @@ __device__ __forceinline__ void lz_exp_tridiag(double a, double bl, double br, i
   const double sigma = 0.5 * (lo + hi);
   const double as = in ? a - sigma : 0.0;
   const double tnorm = lz_warp_max(fabs(as) + rad);
-  double zr, zi;
-  lz_taylor_exp(as, bl, br, tnorm, tr, ti, zr, zi);
-  const double er = exp(tr * sigma);
-  double sn, cs;
-  sincos(ti * sigma, &sn, &cs);
-  const double fr = er * cs, fi = er * sn;
-  yr = zr * fr - zi * fi;
-  yi = zr * fi + zi * fr;
+  lz_taylor_exp(as, bl, br, tnorm, tr, ti, yr, yi);
+  return sigma;
+}
+
+// y *= e^(Re(tau) sigma) (modulus) and, when `phase`, y *= e^(i Im(tau) sigma)
+__device__ __forceinline__ void lz_shift_factor(double sigma, double tr, double ti, bool phase,
+                                                double& yr, double& yi) {
+  if (tr != 0.0) {
+    const double m = exp(tr * sigma);
+    yr *= m;
+    yi *= m;
+  }
+  if (phase && ti != 0.0) {
+    double sn, cs;
+    sincos(ti * sigma, &sn, &cs);
+    const double r = yr * cs - yi * sn;
+    yi = yr * sn + yi * cs;
+    yr = r;
+  }
 }
 
 }  // namespace tdmrg

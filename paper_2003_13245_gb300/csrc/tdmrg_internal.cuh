@@ -61,12 +61,6 @@ struct LzState {
   int pad;
 };
 
-// out[vec] = sum_e conj(V[vec][e]) * w[e], vec < nvec (one launch; partial: nvec * 304
-// entries, counters: nvec zero-initialised tickets, left at zero on return)
-cudaError_t zdots(long long n, int nvec, const cplx* V, long long ldv, const cplx* w,
-                  cplx* out, cplx* partial, unsigned* counters, const int* skip, cudaStream_t s);
-cudaError_t zsub_multi(long long n, int nvec, const cplx* V, long long ldv, const cplx* h,
-                       cplx* w, const int* skip, cudaStream_t s);
 // *out = sum |x|^2 (one launch; partial: 304 entries, counter: one zero-initialised ticket)
 cudaError_t znorm2(long long n, const cplx* x, double* out, double* partial, unsigned* counter,
                    const int* skip, cudaStream_t s);
@@ -76,8 +70,6 @@ cudaError_t zscale_by(long long n, cplx* x, const double* factor, const int* ski
 cudaError_t znormalize_log(long long n, cplx* x, const double* nrm2, double* logacc,
                            cudaStream_t s);
 cudaError_t lz_start(LzState* S, const double* nrm2, cudaStream_t s);
-cudaError_t lz_small_exp(LzState* S, int j, double tau_re, double tau_im, double tol,
-                         int kcap, int fixed, cudaStream_t s);
 cudaError_t zcombine(long long n, const LzState* S, const cplx* V, long long ldv, cplx* out,
                      cudaStream_t s);
 
@@ -101,6 +93,12 @@ struct BondScratch {
   long long maxn = 0;
   int maxDw = 0, gmax = 0;
 };
+// One orthogonalisation step of the host-driven Lanczos (lanczos_step.cu): w = V[j+1] holds
+// H q_j; both Gram-Schmidt passes, the norm, the small exponential, the stop test and the
+// scaling into q_{j+1} in one cooperative launch (part, partn, bar of W are used).
+cudaError_t lz_step(long long n, int j, cplx* V, LzState* S, const BondScratch& W, int* status,
+                    double tr, double ti, double tol, int kcap, int fixed, int gcap,
+                    cudaStream_t s);
 constexpr int BOND_EXP_MAX_M = 256;
 constexpr size_t BOND_EXP_MAX_SMEM = 200 * 1024;
 int bond_exp_grid(int M, int Dw, int gcap, int sms);

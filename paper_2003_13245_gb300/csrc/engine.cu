@@ -401,7 +401,6 @@ Engine::Engine(const ModelParams& p) : P(p) {
   CK(cudaMemset(status_, 0, sizeof(int) * 4));
   CK(cudaMalloc(&lz_, sizeof(LzState)));
   CK(cudaMalloc(&scal_, sizeof(double) * 8));
-  CK(cudaMalloc(&part_c_, sizeof(cplx) * (KMAX + 1) * NBLK));
   CK(cudaMalloc(&part_d_, sizeof(double) * NBLK));
   CK(cudaMalloc(&red_cnt_, sizeof(unsigned) * (KMAX + 2)));
   CK(cudaMemset(red_cnt_, 0, sizeof(unsigned) * (KMAX + 2)));
@@ -424,7 +423,7 @@ Engine::~Engine() {
   free_mpo(H_);
   free_mpo(J_);
   free_mpo(I_);
-  cplx* bufs[] = {X_, Y_, V_, Kout_, T1_, Cb_, Rb_, Ex_, env_tmp_[0], env_tmp_[1], part_c_};
+  cplx* bufs[] = {X_, Y_, V_, Kout_, T1_, Cb_, Rb_, Ex_, env_tmp_[0], env_tmp_[1]};
   for (cplx* b : bufs)
     if (b) cudaFree(b);
   if (part_d_) cudaFree(part_d_);

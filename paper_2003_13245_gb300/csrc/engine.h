@@ -8,7 +8,7 @@
 
 namespace tdmrg {
 
-constexpr int NBLK = 1024;   // partial-sum blocks of the two-stage reductions
+constexpr int NBLK = 1024;   // partial sums of the one-launch FP64 norm (>= its 304 blocks)
 
 struct Failure {
   int code;
@@ -246,7 +246,6 @@ class Engine {
   int ws_bond_ = 0, ws_m_ = 0;
   cplx *X_ = nullptr, *Y_ = nullptr, *V_ = nullptr, *Kout_ = nullptr, *T1_ = nullptr;
   cplx *Cb_ = nullptr, *Rb_ = nullptr, *Ex_ = nullptr;
-  cplx* part_c_ = nullptr;
   double* part_d_ = nullptr;
   unsigned* red_cnt_ = nullptr;     // reduction tickets (KMAX + 2), zero between launches
   double* scal_ = nullptr;          // device scalars

@@ -103,7 +103,7 @@ def test_gauge_qr_matches_oracle(m, n, rank, p, blocked):
         assert np.abs(np.abs(np.einsum("ij,ij->j", Qg.conj(), Qr)) - 1).max() < 1e-6
 
 
-@pytest.mark.parametrize("tau", [-0.3j, -0.05, 0.05, -2.0j])
+@pytest.mark.parametrize("tau", [-0.3j, -0.05, 0.05, -2.0j, 0.4 - 1.5j])
 def test_krylov_dense_matches_expm(tau):
     import scipy.linalg
     from paper_2003_13245_gb300 import binding

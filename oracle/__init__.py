@@ -16,6 +16,9 @@ TD-DMRG for the carrier mobility of organic semiconductors"):
   one-site projector-splitting integrator the paper uses for both imaginary
   and real time.
 * ``kubo``   -- quadrature of Eq. 2 and the hopping-limit closed form of Eq. 7.
+* ``gradient`` -- exact dC(t)/dtheta and dmu/dtheta (theta = omega_m, g_m, V) and the
+  isotope derivative, by Frechet derivatives of the matrix exponential in the
+  one-carrier sector: the reference for an adjoint of the TDVP step.
 
 Every function is slow and literal on purpose.  It shares no code, tables or
 helpers with the CUDA path.

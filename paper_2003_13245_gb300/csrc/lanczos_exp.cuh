@@ -20,6 +20,8 @@ __device__ __forceinline__ double lz_warp_min(double v) {
   return v;
 }
 
+constexpr int LZ_MAX_SUBSTEPS = 4096;
+
 // 1/q for the Taylor terms (q <= 60), rounded once by the compiler
 #define LZ_R4(q) 1.0 / (q), 1.0 / ((q) + 1), 1.0 / ((q) + 2), 1.0 / ((q) + 3)
 static __constant__ double kLzInvQ[64] = {
@@ -48,9 +50,13 @@ __device__ __forceinline__ void lz_taylor_exp(double a, double bl, double br, do
                                               double tr, double ti, double& yr, double& yi) {
   const int lane = threadIdx.x & 31;
   const double tabs = sqrt(tr * tr + ti * ti);
-  int nsub = (int)ceil(tabs * tnorm);
-  if (nsub < 1) nsub = 1;
-  const double x = tabs * tnorm / nsub;
+  // sub-steps bounded: |tau| ||T|| is ~1..100 for a healthy Lanczos run; a non-finite or
+  // absurd norm (a state that already overflowed) gets a bounded, meaningless result instead
+  // of a loop of billions of sub-steps, and the non-finite norm check reports the state
+  const double want = ceil(tabs * tnorm);
+  int nsub = (want >= 1.0 && want <= (double)LZ_MAX_SUBSTEPS) ? (int)want
+             : (want > (double)LZ_MAX_SUBSTEPS ? LZ_MAX_SUBSTEPS : 1);
+  const double x = fmin(tabs * tnorm / nsub, 1.0);
   const int nq = x > 0.5 ? 20 : x > 0.25 ? 16 : x > 0.1 ? 14 : x > 0.01 ? 11 : x > 1e-3 ? 8 : 6;
   const double sr = tr / nsub, si = ti / nsub;
   yr = (lane == 0) ? 1.0 : 0.0;

@@ -1,6 +1,7 @@
 // FP64 kernels of the TDVP sweep: strided batched complex GEMM (the contractions of H_eff,
-// the environment updates and the bond step), sparse MPO channel mixing, Lanczos
-// reductions, the small Krylov exponential and the cooperative gauge QR.
+// the environment updates and the bond step), sparse MPO channel mixing, the one-launch
+// norm, the start and final combination of a Lanczos run, and the column-wise cooperative
+// gauge QR (completion pass and kernel-level entry points).
 #include "tdmrg_internal.cuh"
 
 #include <cooperative_groups.h>

@@ -19,9 +19,11 @@ TD-DMRG for the carrier mobility of organic semiconductors"):
 * ``gradient`` -- exact dC(t)/dtheta and dmu/dtheta (theta = omega_m, g_m, V) and the
   isotope derivative, by Frechet derivatives of the matrix exponential in the
   one-carrier sector: the reference for an adjoint of the TDVP step.
-* ``adjoint`` -- vector-Jacobian products of the TDVP building blocks: the H_eff and
-  bond products, the environment updates and the Krylov exponential (Frechet
-  integral by Gauss-Legendre quadrature).
+* ``adjoint`` -- vector-Jacobian products of the TDVP building blocks (the H_eff and
+  bond products, the environment updates, the Krylov exponential with its Frechet
+  integral by Gauss-Legendre quadrature, the full-rank gauge QR) and the discrete
+  adjoint of one projector-splitting step recorded on a tape, with the parameter
+  gradient through the MPO.
 
 Every function is slow and literal on purpose.  It shares no code, tables or
 helpers with the CUDA path.

@@ -26,7 +26,8 @@ from typing import Callable, List, Tuple
 
 import numpy as np
 
-from .tdvp import _split, krylov_expm
+from .tdvp import (_split, bond_heff, gauge_qr, heff, krylov_expm, update_left,
+                   update_right)
 
 
 def heff_vjp(Lenv, W, Renv, A, d, ybar):
@@ -137,3 +138,215 @@ def expm_krylov_vjp(matvec: Callable[[np.ndarray], np.ndarray], v: np.ndarray, t
         a, _ = krylov_expm(matvec, ybar, (1.0 - s) * np.conj(tau), tol=tol)
         pairs.append((ws * np.conj(tau) * a, b))
     return vbar, pairs
+
+
+def qr_vjp(Q, R, Qbar, Rbar):
+    """VJP of the thin QR Y = Q R (m >= n, full column rank, diag(R) real positive: the gauge
+    QR when no column is skipped).
+
+    With M = R Rbar^H - Qbar^H Q, Ybar = (Qbar + Q copyltu(M)) R^{-H}, where copyltu(M) is the
+    Hermitian matrix that keeps the strictly lower triangle of M, mirrors it (conjugated) into
+    the upper triangle and keeps the real part of the diagonal (the imaginary part of a
+    diagonal entry pairs with a phase of a column of Q, which the real-diagonal gauge fixes).
+    From Q^H dQ anti-Hermitian, Q^H dY R^{-1} = Q^H dQ + dR R^{-1} with dR R^{-1} upper
+    triangular with a real diagonal."""
+    Rbar = np.triu(Rbar)               # entries below the diagonal of R are structural zeros
+    M = R @ Rbar.conj().T - Qbar.conj().T @ Q
+    low = np.tril(M, -1)
+    sym = low + low.conj().T + np.diag(np.diag(M).real)
+    rhs = Qbar + Q @ sym
+    # Ybar = rhs R^{-H}: solve Ybar R^H = rhs, i.e. R Ybar^H = rhs^H (R upper triangular)
+    return sl_solve_triangular(R, rhs.conj().T).conj().T
+
+
+def sl_solve_triangular(R, B):
+    """x with R x = B for upper-triangular R (back substitution, column by column of B)."""
+    n = R.shape[0]
+    X = np.zeros(B.shape, dtype=complex)
+    for i in range(n - 1, -1, -1):
+        X[i] = (B[i] - R[i, i + 1:] @ X[i + 1:]) / R[i, i]
+    return X
+
+
+# ---------------------------------------------------------------------------------
+# discrete adjoint of one projector-splitting step
+# ---------------------------------------------------------------------------------
+
+class Tape:
+    """Values and the operations that produced them, for reverse accumulation."""
+
+    def __init__(self):
+        self.vals = {}
+        self.ops = []            # (input ids, output ids, vjp(out_bars) -> in_bars)
+
+    def var(self, x):
+        i = len(self.vals)
+        self.vals[i] = x
+        return i
+
+    def op(self, outs, ins, vjp):
+        ids = [self.var(v) for v in outs]
+        self.ops.append((ins, ids, vjp))
+        return ids
+
+    def backward(self, seeds):
+        """Cotangents of every value from the cotangents `seeds` {id: bar} of some outputs."""
+        bars = dict(seeds)
+        for ins, outs, vjp in reversed(self.ops):
+            obars = [bars.get(o) for o in outs]
+            if all(b is None for b in obars):
+                continue
+            obars = [np.zeros_like(self.vals[o]) if b is None else b for o, b in zip(outs, obars)]
+            for i, b in zip(ins, vjp(obars)):
+                if b is not None:
+                    bars[i] = b if i not in bars else bars[i] + b
+        return bars
+
+
+def _op_exp_heff(T, l, w, r, a, d, h, tol):
+    Lk, Wk, Rk, A = T.vals[l], T.vals[w], T.vals[r], T.vals[a]
+    mv = lambda x: heff(Lk, Wk, Rk, x, d)                      # noqa: E731
+    y, _ = krylov_expm(mv, A, h, tol=tol)
+
+    def vjp(bars):
+        vbar, pairs = expm_krylov_vjp(mv, A, h, bars[0], tol=tol)
+        Lb, Wb, Rb = np.zeros_like(Lk), np.zeros_like(Wk, dtype=complex), np.zeros_like(Rk)
+        for c, b in pairs:
+            _, l_, w_, r_ = heff_vjp(Lk, Wk, Rk, b, d, c)
+            Lb, Wb, Rb = Lb + l_, Wb + w_, Rb + r_
+        return [Lb, Wb, Rb, vbar]
+    return T.op([y], [l, w, r, a], vjp)[0]
+
+
+def _op_exp_bond(T, l, r, c, h, tol):
+    Lk, Rk, C = T.vals[l], T.vals[r], T.vals[c]
+    mv = lambda x: bond_heff(Lk, Rk, x)                        # noqa: E731
+    y, _ = krylov_expm(mv, C, h, tol=tol)
+
+    def vjp(bars):
+        vbar, pairs = expm_krylov_vjp(mv, C, h, bars[0], tol=tol)
+        Lb, Rb = np.zeros_like(Lk), np.zeros_like(Rk)
+        for cs, b in pairs:
+            _, l_, r_ = bond_heff_vjp(Lk, Rk, b, cs)
+            Lb, Rb = Lb + l_, Rb + r_
+        return [Lb, Rb, vbar]
+    return T.op([y], [l, r, c], vjp)[0]
+
+
+def _op_qr_right(T, a):
+    """A_k (Ml, Ds, Mr) = Q R with Q left-orthonormal; outputs (Q as a site tensor, R)."""
+    A = T.vals[a]
+    Ml, Ds, Mr = A.shape
+    Q, R = gauge_qr(A.reshape(Ml * Ds, Mr))
+    _assert_full_rank(R)
+
+    def vjp(bars):
+        Yb = qr_vjp(Q, R, bars[0].reshape(Ml * Ds, Mr), bars[1])
+        return [Yb.reshape(Ml, Ds, Mr)]
+    return T.op([Q.reshape(Ml, Ds, Mr), R], [a], vjp)
+
+
+def _op_qr_left(T, a):
+    """A_k = C Q with Q right-orthonormal (QR of A^H); outputs (Q as a site tensor, C)."""
+    A = T.vals[a]
+    Ml, Ds, Mr = A.shape
+    Q2, R2 = gauge_qr(A.reshape(Ml, Ds * Mr).conj().T)
+    _assert_full_rank(R2)
+
+    def vjp(bars):
+        Qb = bars[0].reshape(Ml, Ds * Mr).conj().T             # output Q2^H
+        Rb = bars[1].conj().T                                   # output C = R2^H
+        Yb = qr_vjp(Q2, R2, Qb, Rb)
+        return [Yb.conj().T.reshape(Ml, Ds, Mr)]
+    return T.op([Q2.conj().T.reshape(Ml, Ds, Mr), R2.conj().T], [a], vjp)
+
+
+def _assert_full_rank(R):
+    if np.min(np.abs(np.diag(R))) == 0.0:
+        raise ValueError("the adjoint step needs full-rank gauge shifts (no completed columns)")
+
+
+def _op_env_left(T, l, q, w, d):
+    Lk, Q, Wk = T.vals[l], T.vals[q], T.vals[w]
+
+    def vjp(bars):
+        Lb, bb, Wb, kb = update_left_vjp(Lk, Q, Wk, Q, d, bars[0])
+        return [Lb, bb + kb, Wb]
+    return T.op([update_left(Lk, Q, Wk, Q, d)], [l, q, w], vjp)[0]
+
+
+def _op_env_right(T, r, q, w, d):
+    Rk, Q, Wk = T.vals[r], T.vals[q], T.vals[w]
+
+    def vjp(bars):
+        Rb, bb, Wb, kb = update_right_vjp(Rk, Q, Wk, Q, d, bars[0])
+        return [Rb, bb + kb, Wb]
+    return T.op([update_right(Rk, Q, Wk, Q, d)], [r, q, w], vjp)[0]
+
+
+def _op_absorb_left(T, c, a):
+    """A' = C A (bond matrix into the left index of the next site)."""
+    C, A = T.vals[c], T.vals[a]
+
+    def vjp(bars):
+        Ab = bars[0]
+        return [np.einsum("asc,bsc->ab", Ab, np.conj(A)), np.einsum("ab,asc->bsc", np.conj(C), Ab)]
+    return T.op([np.einsum("ab,bsc->asc", C, A)], [c, a], vjp)[0]
+
+
+def _op_absorb_right(T, a, c):
+    """A' = A C (bond matrix into the right index of the previous site)."""
+    A, C = T.vals[a], T.vals[c]
+
+    def vjp(bars):
+        Ab = bars[0]
+        return [np.einsum("asc,bc->asb", Ab, np.conj(C)), np.einsum("asb,asc->bc", np.conj(A), Ab)]
+    return T.op([np.einsum("asb,bc->asc", A, C)], [a, c], vjp)[0]
+
+
+def step_with_tape(Ws, d, A_in, tau, tol=1e-14):
+    """The second-order projector-splitting step exp(tau H) of ``tdvp.PurifiedMPS.step`` written
+    on a tape: right environments of the input (sites 1.. right-orthonormal, center at 0),
+    left-to-right and right-to-left half-sweeps with dt/2 site exponentials, gauge shifts,
+    environment updates, backward bond exponentials and absorption.  Full-rank gauge shifts
+    only (no completion).  Returns (tape, ids of the output sites, ids of the input sites,
+    ids of the MPO sites)."""
+    T = Tape()
+    L = len(A_in)
+    a_in = [T.var(np.asarray(x, dtype=complex)) for x in A_in]
+    w_ids = [T.var(np.asarray(W)) for W in Ws]
+    a = list(a_in)
+    one = np.ones((1, 1, 1), dtype=complex)
+    Lenv, Renv = [None] * L, [None] * L
+    Lenv[0] = T.var(one)
+    Renv[L - 1] = T.var(one)
+    for k in range(L - 1, 0, -1):
+        Renv[k - 1] = _op_env_right(T, Renv[k], a[k], w_ids[k], d[k])
+    h = 0.5 * tau
+    for k in range(L):
+        a[k] = _op_exp_heff(T, Lenv[k], w_ids[k], Renv[k], a[k], d[k], h, tol)
+        if k < L - 1:
+            a[k], r = _op_qr_right(T, a[k])
+            Lenv[k + 1] = _op_env_left(T, Lenv[k], a[k], w_ids[k], d[k])
+            c = _op_exp_bond(T, Lenv[k + 1], Renv[k], r, -h, tol)
+            a[k + 1] = _op_absorb_left(T, c, a[k + 1])
+    for k in range(L - 1, -1, -1):
+        a[k] = _op_exp_heff(T, Lenv[k], w_ids[k], Renv[k], a[k], d[k], h, tol)
+        if k > 0:
+            a[k], c = _op_qr_left(T, a[k])
+            Renv[k - 1] = _op_env_right(T, Renv[k], a[k], w_ids[k], d[k])
+            c = _op_exp_bond(T, Lenv[k], Renv[k - 1], c, -h, tol)
+            a[k - 1] = _op_absorb_right(T, a[k - 1], c)
+    return T, a, a_in, w_ids
+
+
+def step_parameter_gradient(model, Wbars, mpo_builder) -> dict:
+    """dl/dtheta for theta = omega_m, g_m, V from the MPO cotangents of a step: the MPO of
+    Eq. 1 / Eq. 10 is affine in each parameter, so dW/dtheta = W(theta + 1) - W(theta)."""
+    from .gradient import parameters, shifted
+    W0 = mpo_builder(model)
+    out = {}
+    for p in parameters(model):
+        W1 = mpo_builder(shifted(model, p, 1.0))
+        out[p] = sum(float(np.vdot(b, w1 - w0).real) for b, w0, w1 in zip(Wbars, W0, W1))
+    return out

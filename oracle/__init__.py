@@ -23,7 +23,8 @@ TD-DMRG for the carrier mobility of organic semiconductors"):
   bond products, the environment updates, the Krylov exponential with its Frechet
   integral by Gauss-Legendre quadrature, the full-rank gauge QR) and the discrete
   adjoint of one projector-splitting step recorded on a tape, with the parameter
-  gradient through the MPO.
+  gradient through the MPO; the reverse pass of the real-time correlation (steps of
+  both states and the j overlaps, recomputed from stored states).
 
 Every function is slow and literal on purpose.  It shares no code, tables or
 helpers with the CUDA path.

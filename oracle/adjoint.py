@@ -350,3 +350,92 @@ def step_parameter_gradient(model, Wbars, mpo_builder) -> dict:
         W1 = mpo_builder(shifted(model, p, 1.0))
         out[p] = sum(float(np.vdot(b, w1 - w0).real) for b, w0, w1 in zip(Wbars, W0, W1))
     return out
+
+
+# ---------------------------------------------------------------------------------
+# real-time correlation: steps of both states and the overlaps, reversed with checkpoints
+# ---------------------------------------------------------------------------------
+
+def _overlap_with_tape(T, bra, w, ket, d):
+    """<bra| W |ket> as a chain of left environment updates (Eq. 6 overlap, traced over P and
+    Q by the fused sites); returns the id of the final 1 x 1 x 1 environment."""
+    e = T.var(np.ones((1, 1, 1), dtype=complex))
+    for k in range(len(bra)):
+        Lk, B, Wk, K = T.vals[e], T.vals[bra[k]], T.vals[w[k]], T.vals[ket[k]]
+
+        def vjp(bars, Lk=Lk, B=B, Wk=Wk, K=K, dk=d[k]):
+            Lb, bb, Wb, kb = update_left_vjp(Lk, B, Wk, K, dk, bars[0])
+            return [Lb, bb, Wb, kb]
+        e = T.op([update_left(Lk, B, Wk, K, d[k])], [e, bra[k], w[k], ket[k]], vjp)[0]
+    return e
+
+
+def overlap_vjp(bra, Wj, ket, d, cbar):
+    """(C, brabar, Wjbar, ketbar) of C = <bra| Wj |ket> for the cotangent cbar of C."""
+    T = Tape()
+    b = [T.var(x) for x in bra]
+    w = [T.var(x) for x in Wj]
+    k = [T.var(x) for x in ket]
+    e = _overlap_with_tape(T, b, w, k, d)
+    C = complex(T.vals[e][0, 0, 0])
+    seed = np.zeros((1, 1, 1), dtype=complex)
+    seed[0, 0, 0] = cbar
+    bars = T.backward({e: seed})
+    z = lambda i: bars.get(i, np.zeros_like(T.vals[i]))      # noqa: E731
+    return C, [z(i) for i in b], [z(i) for i in w], [z(i) for i in k]
+
+
+def correlation_vjp(Ws, Wj, d, psi1, psi2, dt, nsteps, cbar, every=2, tol=1e-14):
+    """C_n = <psi1(n dt)| j |psi2(n dt)>, n = 0 .. nsteps, both states evolved by the
+    projector-splitting step exp(-i dt H); and the cotangents of psi1(0), psi2(0), of the
+    H-MPO sites and of the j-MPO sites for the real loss Re sum_n conj(cbar_n) C_n.
+
+    The states are stored every `every` steps on the forward pass; the backward pass
+    recomputes each stretch of steps from its stored state, records it on a tape and
+    reverses it (memory: nsteps / every stored states plus one stretch of tapes)."""
+    tau = -1j * dt
+    ckpt = {0: ([x.copy() for x in psi1], [x.copy() for x in psi2])}
+    C = np.zeros(nsteps + 1, dtype=complex)
+    s1, s2 = ckpt[0]
+    for n in range(nsteps + 1):
+        if n > 0:
+            T1, o1, _, _ = step_with_tape(Ws, d, s1, tau, tol)
+            T2, o2, _, _ = step_with_tape(Ws, d, s2, tau, tol)
+            s1 = [T1.vals[i] for i in o1]
+            s2 = [T2.vals[i] for i in o2]
+            if n % every == 0:
+                ckpt[n] = (s1, s2)
+        C[n] = overlap_vjp(s1, Wj, s2, d, 0.0)[0]
+    # reverse pass over the stretches between stored states, latest first
+    Wbar = [np.zeros_like(np.asarray(W), dtype=complex) for W in Ws]
+    Wjbar = [np.zeros_like(np.asarray(W), dtype=complex) for W in Wj]
+    g1 = [np.zeros_like(x, dtype=complex) for x in psi1]
+    g2 = [np.zeros_like(x, dtype=complex) for x in psi2]
+
+    def add_overlap(n, a1, a2):
+        nonlocal g1, g2, Wjbar
+        _, b1, wjb, b2 = overlap_vjp(a1, Wj, a2, d, cbar[n])
+        g1 = [x + y for x, y in zip(g1, b1)]
+        g2 = [x + y for x, y in zip(g2, b2)]
+        Wjbar = [x + y for x, y in zip(Wjbar, wjb)]
+
+    cps = sorted(ckpt)
+    segs = [(c, cps[i + 1] if i + 1 < len(cps) else nsteps) for i, c in enumerate(cps)]
+    for s0, e0 in reversed([sg for sg in segs if sg[1] > sg[0]]):
+        states = [ckpt[s0]]
+        tapes = []
+        for n in range(s0 + 1, e0 + 1):
+            T1, o1, i1, w1 = step_with_tape(Ws, d, states[-1][0], tau, tol)
+            T2, o2, i2, w2 = step_with_tape(Ws, d, states[-1][1], tau, tol)
+            tapes.append((T1, o1, i1, w1, T2, o2, i2, w2))
+            states.append(([T1.vals[i] for i in o1], [T2.vals[i] for i in o2]))
+        for n in range(e0, s0, -1):
+            add_overlap(n, *states[n - s0])
+            T1, o1, i1, w1, T2, o2, i2, w2 = tapes[n - s0 - 1]
+            bars1 = T1.backward(dict(zip(o1, g1)))
+            bars2 = T2.backward(dict(zip(o2, g2)))
+            g1 = [bars1.get(i, np.zeros_like(T1.vals[i])) for i in i1]
+            g2 = [bars2.get(i, np.zeros_like(T2.vals[i])) for i in i2]
+            Wbar = [x + bars1.get(a, 0) + bars2.get(b, 0) for x, a, b in zip(Wbar, w1, w2)]
+    add_overlap(0, *ckpt[0])
+    return C, g1, g2, Wbar, Wjbar

@@ -129,3 +129,25 @@ def test_krylov_vjp_through_bond_environments():
     h = 1e-4
     fd = (loss(h) - loss(-h)) / (2 * h)
     _close(fd, ip(Lbar, dL), 1e-7)
+
+
+def test_heff_vjp_is_forward_contractions_with_transformed_operands():
+    """The cotangents of an H_eff product are forward contractions of the sweep:
+    Abar = heff(L^dagger per channel, W^T conj, R^dagger per channel, ybar),
+    Lbar = conj(update_right(R, ybar, W, A)),  Rbar = conj(update_left(L, ybar, W, A))
+    (the cotangent takes the place of the bra), so an adjoint step can reuse the H_eff and
+    environment kernels."""
+    rng = np.random.default_rng(45)
+    Ml, Mr, d, Dl, Dr = 5, 6, 3, 4, 3
+    L = random_complex(rng, (Dl, Ml, Ml))
+    R = random_complex(rng, (Dr, Mr, Mr))
+    W = random_mpo_site(rng, Dl, Dr, d) + 0j
+    A = random_complex(rng, (Ml, d * d, Mr))
+    yb = random_complex(rng, (Ml, d * d, Mr))
+    Abar, Lbar, Wbar, Rbar = adjoint.heff_vjp(L, W, R, A, d, yb)
+    Lh = np.conj(np.swapaxes(L, 1, 2))
+    Rh = np.conj(np.swapaxes(R, 1, 2))
+    Wt = np.conj(np.swapaxes(W, 2, 3))
+    assert np.abs(tdvp.heff(Lh, Wt, Rh, yb, d) - Abar).max() < 1e-12 * np.abs(Abar).max()
+    assert np.abs(np.conj(tdvp.update_right(R, yb, W, A, d)) - Lbar).max() < 1e-12 * np.abs(Lbar).max()
+    assert np.abs(np.conj(tdvp.update_left(L, yb, W, A, d)) - Rbar).max() < 1e-12 * np.abs(Rbar).max()

@@ -171,6 +171,23 @@ int tdmrg_kernel_heff(int Ml, int Mr, int d, int Dl, int Dr, const double* W_hos
                       const void* L, const void* R, const void* A, void* out,
                       void* X, void* Y, void* ws32, int precision, void* stream);
 
+/* Vector-Jacobian product of the H_eff product of the one-site step (Eq. S1) -- the building
+ * block an adjoint of the step needs (the adjoint itself has no counterpart in the paper).
+ * For y = H_eff(L, W, R) A and a cotangent ybar (real loss l with dl = Re<ybar, dy>):
+ *   Abar = H_eff(L^dagger, W^T conj, R^dagger) ybar      (per-channel Hermitian conjugates),
+ *   Lbar[w,x,y] = sum ybar[x,s,t,b] conj(W[w,v,s,u] A[y,u,t,c] R[v,b,c])
+ *               = conj(right environment update with bra = ybar, ket = A),
+ *   Rbar[v,b,c] = sum ybar[x,s,t,b] conj(L[w,x,y] W[w,v,s,u] A[y,u,t,c])
+ *               = conj(left environment update with bra = ybar, ket = A),
+ * so that dl = Re<Abar, dA> + Re<Lbar, dL> + Re<Rbar, dR>.  Layouts as tdmrg_kernel_heff
+ * (FP64 complex, device): A, ybar, Abar Ml x d*d x Mr; L, Lbar Dl x Ml x Ml; R, Rbar
+ * Dr x Mr x Mr; W_host on the host.  X, Y: workspaces of max(Dl,Dr) * Ml * d*d * Mr complex
+ * entries.  Allocates two environment-sized temporaries (freed before return); synchronises
+ * `stream`. */
+int tdmrg_kernel_heff_vjp(int Ml, int Mr, int d, int Dl, int Dr, const double* W_host,
+                          const void* L, const void* R, const void* A, const void* ybar,
+                          void* Abar, void* Lbar, void* Rbar, void* X, void* Y, void* stream);
+
 /* Size in floats of the 3xTF32 workspace of tdmrg_kernel_heff (-1 for invalid sizes). */
 long long tdmrg_heff_workspace_floats(int Ml, int Mr, int d, int Dl, int Dr);
 

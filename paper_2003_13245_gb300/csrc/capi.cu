@@ -358,6 +358,61 @@ int tdmrg_kernel_heff(int Ml, int Mr, int d, int Dl, int Dr, const double* W_hos
   });
 }
 
+int tdmrg_kernel_heff_vjp(int Ml, int Mr, int d, int Dl, int Dr, const double* W_host,
+                          const void* L, const void* R, const void* A, const void* ybar,
+                          void* Abar, void* Lbar, void* Rbar, void* X, void* Y, void* stream) {
+  if (Ml < 1 || Mr < 1 || d < 1 || Dl < 1 || Dr < 1 || !W_host || !L || !R || !A || !ybar ||
+      !Abar || !Lbar || !Rbar || !X || !Y)
+    return fail(nullptr, TDMRG_ERR_ARG, "heff_vjp: bad arguments");
+  return guarded(nullptr, [&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    using tdmrg::cplx;
+    const int D = d * d;
+    // W^T conj: op'[s][u] = conj(op[u][s]) for every channel pair
+    std::vector<double> Wt((size_t)2 * Dl * Dr * D);
+    for (int b = 0; b < Dl * Dr; ++b)
+      for (int si = 0; si < d; ++si)
+        for (int ui = 0; ui < d; ++ui) {
+          const size_t dst = 2 * ((size_t)b * D + si * d + ui);
+          const size_t src = 2 * ((size_t)b * D + ui * d + si);
+          Wt[dst] = W_host[src];
+          Wt[dst + 1] = -W_host[src + 1];
+        }
+    TempMpo W(Dl, Dr, d, W_host);
+    TempMpo Wc(Dl, Dr, d, Wt.data());
+    cplx* Lh = nullptr;
+    cplx* Rh = nullptr;
+    struct Free {
+      cplx*& a;
+      cplx*& b;
+      ~Free() {
+        if (a) cudaFree(a);
+        if (b) cudaFree(b);
+      }
+    } fr{Lh, Rh};
+    CK(cudaMalloc(&Lh, sizeof(cplx) * (size_t)Dl * Ml * Ml));
+    CK(cudaMalloc(&Rh, sizeof(cplx) * (size_t)Dr * Mr * Mr));
+    // per-channel Hermitian conjugates of the environments
+    for (int w = 0; w < Dl; ++w)
+      CK(tdmrg::ztranspose(Ml, Ml, (const cplx*)L + (size_t)w * Ml * Ml, Lh + (size_t)w * Ml * Ml,
+                           1, s));
+    for (int w = 0; w < Dr; ++w)
+      CK(tdmrg::ztranspose(Mr, Mr, (const cplx*)R + (size_t)w * Mr * Mr, Rh + (size_t)w * Mr * Mr,
+                           1, s));
+    tdmrg::Ctx c{s, (cplx*)X, (cplx*)Y};
+    // Abar = H_eff(L^dagger, W^T conj, R^dagger) ybar
+    tdmrg::heff_f64(c, Wc.m.s[0], Ml, Mr, D, d, Lh, Rh, (const cplx*)ybar, (cplx*)Abar, nullptr);
+    // Lbar = conj(env_right(R, bra = ybar, W, ket = A)); Rbar = conj(env_left(L, ybar, W, A))
+    tdmrg::env_right_f64(c, W.m.s[0], Ml, Mr, Ml, Mr, D, d, (const cplx*)R, (const cplx*)ybar,
+                         (const cplx*)A, (cplx*)Lbar);
+    CK(tdmrg::zconj((long long)Dl * Ml * Ml, (cplx*)Lbar, s));
+    tdmrg::env_left_f64(c, W.m.s[0], Ml, Mr, Ml, Mr, D, d, (const cplx*)L, (const cplx*)ybar,
+                        (const cplx*)A, (cplx*)Rbar);
+    CK(tdmrg::zconj((long long)Dr * Mr * Mr, (cplx*)Rbar, s));
+    CK(cudaStreamSynchronize(s));
+  });
+}
+
 int tdmrg_kernel_zgemm_tc(int M, int N, int K, const void* A, const void* B, int conjA, int conjB,
                           void* C, void* stream) {
   if (M < 1 || N < 1 || K < 1 || !A || !B || !C) return fail(nullptr, TDMRG_ERR_ARG, "zgemm_tc: bad arguments");

@@ -262,6 +262,21 @@ cudaError_t znormalize_log(long long n, cplx* x, const double* nrm2, double* log
   return cudaGetLastError();
 }
 
+__global__ void zconj_kernel(long long n, cplx* x) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    x[e].y = -x[e].y;
+}
+
+cudaError_t zconj(long long n, cplx* x, cudaStream_t s) {
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  count_launch();
+  zconj_kernel<<<(int)blocks, 256, 0, s>>>(n, x);
+  return cudaGetLastError();
+}
+
 __global__ void zscale_by_kernel(long long n, cplx* x, const double* factor, const int* skip) {
   if (skip && *skip) return;
   const double f = *factor;

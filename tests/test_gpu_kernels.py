@@ -149,3 +149,29 @@ def test_bond_exp_matches_oracle(M, Dw, tau):
     out2 = torch.zeros_like(out)
     binding.kernel_bond_exp(dev(L), dev(R), dev(C), out2, tau, tol=1e-7)
     assert torch.equal(out, out2)
+
+
+@pytest.mark.parametrize("Ml,Mr,d,Dl,Dr", HEFF_CASES)
+def test_heff_vjp_matches_oracle(Ml, Mr, d, Dl, Dr):
+    """VJP of the H_eff product (the adjoint step's building block, made of the forward
+    H_eff and environment kernels with daggered operands) against the oracle's contraction
+    VJP, FP64."""
+    from oracle import adjoint
+    from paper_2003_13245_gb300 import binding
+    rng = np.random.default_rng(2000 + Ml + Mr)
+    L = random_complex(rng, (Dl, Ml, Ml))
+    R = random_complex(rng, (Dr, Mr, Mr))
+    W = random_mpo_site(rng, Dl, Dr, d) + 0.3j * random_mpo_site(rng, Dl, Dr, d)
+    A = random_complex(rng, (Ml, d * d, Mr))
+    yb = random_complex(rng, (Ml, d * d, Mr))
+    Ar, Lr, _, Rr = adjoint.heff_vjp(L, W, R, A, d, yb)
+    n = Ml * d * d * Mr
+    X = torch.zeros(max(Dl, Dr) * n, dtype=torch.complex128, device="cuda")
+    Y = torch.zeros_like(X)
+    Ab = torch.zeros(A.shape, dtype=torch.complex128, device="cuda")
+    Lb = torch.zeros(L.shape, dtype=torch.complex128, device="cuda")
+    Rb = torch.zeros(R.shape, dtype=torch.complex128, device="cuda")
+    binding.kernel_heff_vjp(dev(L), W, dev(R), dev(A), dev(yb), Ab, Lb, Rb, X, Y, d)
+    for got, ref in ((Ab, Ar), (Lb, Lr), (Rb, Rr)):
+        g = got.cpu().numpy()
+        assert np.abs(g - ref).max() <= 1e-12 * np.abs(ref).max()

@@ -188,6 +188,23 @@ int tdmrg_kernel_heff_vjp(int Ml, int Mr, int d, int Dl, int Dr, const double* W
                           const void* L, const void* R, const void* A, const void* ybar,
                           void* Abar, void* Lbar, void* Rbar, void* X, void* Y, void* stream);
 
+/* Vector-Jacobian product of the site exponential of the one-site step (Eq. S1),
+ * y = exp(tau H_eff(L, W, R)) A with H_eff Hermitian (environments of a Hermitian MPO) -- a
+ * building block of an adjoint of the step (the adjoint has no counterpart in the paper).
+ * For a cotangent ybar (dl = Re<ybar, dy>):
+ *   Abar = exp(conj(tau) H_eff) ybar,
+ *   Lbar, Rbar from Hbar = conj(tau) int_0^1 a(s) b(s)^H ds, a(s) = exp((1-s) conj(tau) H) ybar,
+ *   b(s) = exp(s tau H) A, mapped onto L and R like tdmrg_kernel_heff_vjp's Lbar and Rbar
+ *   (conjugated environment updates with a(s) as bra and b(s) as ket),
+ * with the integral taken by Gauss-Legendre quadrature on `nodes` (1..64) points and every
+ * exponential by the FP64 Lanczos of the sweep at tolerance `tol`.  Layouts as
+ * tdmrg_kernel_heff_vjp.  Allocates its scratch (freed before return); synchronises `stream`;
+ * TDMRG_ERR_TIMEOUT if a bounded grid barrier gave up. */
+int tdmrg_kernel_site_exp_vjp(int Ml, int Mr, int d, int Dl, int Dr, const double* W_host,
+                              const void* L, const void* R, const void* A, const void* ybar,
+                              double tau_re, double tau_im, int nodes, double tol, void* Abar,
+                              void* Lbar, void* Rbar, void* stream);
+
 /* Size in floats of the 3xTF32 workspace of tdmrg_kernel_heff (-1 for invalid sizes). */
 long long tdmrg_heff_workspace_floats(int Ml, int Mr, int d, int Dl, int Dr);
 

@@ -61,6 +61,8 @@ _SIGS = {
     "tdmrg_kernel_krylov_dense": [_i, _p, _p, _p, _d, _d, _d, _i, _ip, _p],
     "tdmrg_kernel_bond_exp": [_i, _i, _p, _p, _p, _p, _d, _d, _d, _i, _ip, _p],
     "tdmrg_kernel_heff_vjp": [_i, _i, _i, _i, _i, _dp, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p],
+    "tdmrg_kernel_site_exp_vjp": [_i, _i, _i, _i, _i, _dp, _p, _p, _p, _p, _d, _d, _i, _d, _p, _p,
+                                  _p, _p],
     "tdmrg_kernel_zgemm_tc": [_i, _i, _i, _p, _p, _i, _i, _p, _p],
     "tdmrg_kernel_gauge_qr_noalloc": [_i, _i, _p, _i, _p, _p, _p, _p, _p],
     "tdmrg_kernel_gauge_qr_blocked": [_i, _i, _p, _i, _p, _p, _p, _p, _p],
@@ -268,6 +270,19 @@ def kernel_heff_vjp(L, W, R, A, ybar, Abar, Lbar, Rbar, X, Y, d, stream=None):
     _check(lib.tdmrg_kernel_heff_vjp(Ml, Mr, d, Dl, Dr, _dptr(Wc), _ptr(L), _ptr(R), _ptr(A),
                                      _ptr(ybar), _ptr(Abar), _ptr(Lbar), _ptr(Rbar), _ptr(X),
                                      _ptr(Y), _stream_ptr(stream)))
+
+
+def kernel_site_exp_vjp(L, W, R, A, ybar, tau, Abar, Lbar, Rbar, d, nodes=16, tol=1e-13,
+                        stream=None):
+    """(Abar, Lbar, Rbar) of y = exp(tau H_eff(L, W, R)) A for the cotangent ybar (FP64)."""
+    lib = load()
+    Dl, Ml, _ = L.shape
+    Dr, Mr, _ = R.shape
+    Wc = np.ascontiguousarray(W, dtype=np.complex128).view(np.float64)
+    _check(lib.tdmrg_kernel_site_exp_vjp(Ml, Mr, d, Dl, Dr, _dptr(Wc), _ptr(L), _ptr(R), _ptr(A),
+                                         _ptr(ybar), float(np.real(tau)), float(np.imag(tau)),
+                                         int(nodes), float(tol), _ptr(Abar), _ptr(Lbar),
+                                         _ptr(Rbar), _stream_ptr(stream)))
 
 
 def heff_workspace_floats(Ml, Mr, d, Dl, Dr):

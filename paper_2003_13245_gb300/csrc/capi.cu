@@ -609,6 +609,101 @@ int tdmrg_kernel_bond_exp(int M, int Dw, const void* L, const void* R, const voi
   });
 }
 
+namespace {
+// Gauss-Legendre nodes and weights on [0, 1] (n <= 64): Newton iteration on the three-term
+// recurrence of the Legendre polynomials from the usual cosine first guesses.
+void gauss_legendre01(int n, std::vector<double>& s, std::vector<double>& w) {
+  s.assign(n, 0.0);
+  w.assign(n, 0.0);
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < (n + 1) / 2; ++i) {
+    double z = std::cos(pi * (i + 0.75) / (n + 0.5)), pp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p1 = 1.0, p2 = 0.0;
+      for (int j = 1; j <= n; ++j) {
+        const double p3 = p2;
+        p2 = p1;
+        p1 = ((2.0 * j - 1.0) * z * p2 - (j - 1.0) * p3) / j;
+      }
+      pp = n * (z * p1 - p2) / (z * z - 1.0);
+      const double dz = p1 / pp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    const double wi = 2.0 / ((1.0 - z * z) * pp * pp);
+    s[i] = 0.5 * (1.0 - z);            // ascending on [0, 1]
+    s[n - 1 - i] = 0.5 * (1.0 + z);
+    w[i] = w[n - 1 - i] = 0.5 * wi;
+  }
+}
+}  // namespace
+
+int tdmrg_kernel_site_exp_vjp(int Ml, int Mr, int d, int Dl, int Dr, const double* W_host,
+                              const void* L, const void* R, const void* A, const void* ybar,
+                              double tau_re, double tau_im, int nodes, double tol, void* Abar,
+                              void* Lbar, void* Rbar, void* stream) {
+  if (Ml < 1 || Mr < 1 || d < 1 || Dl < 1 || Dr < 1 || !W_host || !L || !R || !A || !ybar ||
+      !Abar || !Lbar || !Rbar || nodes < 1 || nodes > 64 || !(tol > 0.0))
+    return fail(nullptr, TDMRG_ERR_ARG, "site_exp_vjp: bad arguments");
+  return guarded(nullptr, [&] {
+    using tdmrg::cplx;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int D = d * d;
+    const long long n = (long long)Ml * D * Mr;
+    const long long nl = (long long)Dl * Ml * Ml, nr = (long long)Dr * Mr * Mr;
+    TempMpo W(Dl, Dr, d, W_host);
+    tdmrg::ModelParams P;
+    P.N = 3;
+    Engine eng(P);
+    eng.set_stream(s);
+    eng.set_krylov(tol, tdmrg::KMAX, 0);
+    eng.ensure_workspace(n, n, 1, 1);
+    cplx *X = nullptr, *Y = nullptr, *a = nullptr, *b = nullptr, *El = nullptr, *Er = nullptr;
+    struct Free {
+      cplx** p[6];
+      ~Free() {
+        for (auto q : p)
+          if (*q) cudaFree(*q);
+      }
+    } fr{{&X, &Y, &a, &b, &El, &Er}};
+    const long long xy = (long long)std::max(Dl, Dr) * n;
+    CK(cudaMalloc(&X, sizeof(cplx) * (size_t)xy));
+    CK(cudaMalloc(&Y, sizeof(cplx) * (size_t)xy));
+    CK(cudaMalloc(&a, sizeof(cplx) * (size_t)n));
+    CK(cudaMalloc(&b, sizeof(cplx) * (size_t)n));
+    CK(cudaMalloc(&El, sizeof(cplx) * (size_t)nl));
+    CK(cudaMalloc(&Er, sizeof(cplx) * (size_t)nr));
+    tdmrg::Ctx c{s, X, Y};
+    const cplx* Ld = (const cplx*)L;
+    const cplx* Rd = (const cplx*)R;
+    auto heff = [&](const cplx* in, cplx* out, const int* skip) {
+      tdmrg::heff_f64(c, W.m.s[0], Ml, Mr, D, d, Ld, Rd, in, out, skip);
+    };
+    // Abar = exp(conj(tau) H) ybar  (H Hermitian)
+    eng.krylov(n, (const cplx*)ybar, (cplx*)Abar, tau_re, -tau_im, heff);
+    // Hbar = conj(tau) int_0^1 a(s) b(s)^H ds, a(s) = e^{(1-s) conj(tau) H} ybar,
+    // b(s) = e^{s tau H} A; its L and R parts are conjugated environment updates with a(s)
+    // as bra and b(s) as ket: Lbar = conj(sum_s conj(k_s) env_right(R, a_s, W, b_s)),
+    // k_s = w_s conj(tau), and the same for Rbar with env_left.
+    CK(cudaMemsetAsync(Lbar, 0, sizeof(cplx) * (size_t)nl, s));
+    CK(cudaMemsetAsync(Rbar, 0, sizeof(cplx) * (size_t)nr, s));
+    std::vector<double> sn, wn;
+    gauss_legendre01(nodes, sn, wn);
+    for (int q = 0; q < nodes; ++q) {
+      eng.krylov(n, (const cplx*)A, b, sn[q] * tau_re, sn[q] * tau_im, heff);
+      eng.krylov(n, (const cplx*)ybar, a, (1.0 - sn[q]) * tau_re, -(1.0 - sn[q]) * tau_im, heff);
+      const cplx kc = {wn[q] * tau_re, wn[q] * tau_im};     // conj(w_s conj(tau)) = w_s tau
+      tdmrg::env_right_f64(c, W.m.s[0], Ml, Mr, Ml, Mr, D, d, Rd, a, b, El);
+      CK(tdmrg::zaxpy(nl, kc, El, (cplx*)Lbar, s));
+      tdmrg::env_left_f64(c, W.m.s[0], Ml, Mr, Ml, Mr, D, d, Ld, a, b, Er);
+      CK(tdmrg::zaxpy(nr, kc, Er, (cplx*)Rbar, s));
+    }
+    CK(tdmrg::zconj(nl, (cplx*)Lbar, s));
+    CK(tdmrg::zconj(nr, (cplx*)Rbar, s));
+    eng.sync_and_check();
+  });
+}
+
 int tdmrg_kernel_krylov_dense(int n, const void* H, const void* v, void* out, double tau_re,
                               double tau_im, double tol, int kmax, int* kused, void* stream) {
   if (n < 1 || !H || !v || !out || kmax < 1 || kmax > tdmrg::KMAX || !(tol > 0.0))

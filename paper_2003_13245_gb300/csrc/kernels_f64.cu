@@ -268,6 +268,24 @@ __global__ void zconj_kernel(long long n, cplx* x) {
     x[e].y = -x[e].y;
 }
 
+__global__ void zaxpy_kernel(long long n, cplx alpha, const cplx* x, cplx* y) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const cplx v = x[e];
+    y[e].x = fma(alpha.x, v.x, fma(-alpha.y, v.y, y[e].x));
+    y[e].y = fma(alpha.x, v.y, fma(alpha.y, v.x, y[e].y));
+  }
+}
+
+cudaError_t zaxpy(long long n, cplx alpha, const cplx* x, cplx* y, cudaStream_t s) {
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  count_launch();
+  zaxpy_kernel<<<(int)blocks, 256, 0, s>>>(n, alpha, x, y);
+  return cudaGetLastError();
+}
+
 cudaError_t zconj(long long n, cplx* x, cudaStream_t s) {
   long long blocks = (n + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;

@@ -133,6 +133,8 @@ cudaError_t gauge_qr_blocked(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cpl
 cudaError_t ztranspose(int m, int n, const cplx* src, cplx* dst, int conj, cudaStream_t s);
 // x <- conj(x)
 cudaError_t zconj(long long n, cplx* x, cudaStream_t s);
+// y <- y + alpha x
+cudaError_t zaxpy(long long n, cplx alpha, const cplx* x, cplx* y, cudaStream_t s);
 cudaError_t zfill_identity_mps(cplx* A, int Ml, int D, int Mr, const int* entries, int nent,
                                cudaStream_t s);
 

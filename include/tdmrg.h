@@ -205,6 +205,17 @@ int tdmrg_kernel_site_exp_vjp(int Ml, int Mr, int d, int Dl, int Dr, const doubl
                               double tau_re, double tau_im, int nodes, double tol, void* Abar,
                               void* Lbar, void* Rbar, void* stream);
 
+/* Vector-Jacobian product of the gauge QR Y = Q R (K4) at full column rank, diag(R) real
+ * and positive (no completed columns) -- a building block of an adjoint of the step (no
+ * counterpart in the paper).  With M = R Rbar^H - Qbar^H Q and S the Hermitian matrix made
+ * of the strictly lower triangle of M, its conjugate mirror and Re(M_ii) on the diagonal:
+ *   Ybar = (Qbar + Q S) R^{-H},
+ * so that dl = Re<Qbar, dQ> + Re<Rbar, dR> = Re<Ybar, dY>.  Q, Qbar, Ybar m x n, R, Rbar
+ * n x n (complex FP64, row-major, device; entries of Rbar below the diagonal are ignored).
+ * Allocates its scratch (freed before return); synchronises `stream`. */
+int tdmrg_kernel_qr_vjp(int m, int n, const void* Q, const void* R, const void* Qbar,
+                        const void* Rbar, void* Ybar, void* stream);
+
 /* Size in floats of the 3xTF32 workspace of tdmrg_kernel_heff (-1 for invalid sizes). */
 long long tdmrg_heff_workspace_floats(int Ml, int Mr, int d, int Dl, int Dr);
 

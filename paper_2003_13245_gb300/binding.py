@@ -61,6 +61,7 @@ _SIGS = {
     "tdmrg_kernel_krylov_dense": [_i, _p, _p, _p, _d, _d, _d, _i, _ip, _p],
     "tdmrg_kernel_bond_exp": [_i, _i, _p, _p, _p, _p, _d, _d, _d, _i, _ip, _p],
     "tdmrg_kernel_heff_vjp": [_i, _i, _i, _i, _i, _dp, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p],
+    "tdmrg_kernel_qr_vjp": [_i, _i, _p, _p, _p, _p, _p, _p],
     "tdmrg_kernel_site_exp_vjp": [_i, _i, _i, _i, _i, _dp, _p, _p, _p, _p, _d, _d, _i, _d, _p, _p,
                                   _p, _p],
     "tdmrg_kernel_zgemm_tc": [_i, _i, _i, _p, _p, _i, _i, _p, _p],
@@ -283,6 +284,13 @@ def kernel_site_exp_vjp(L, W, R, A, ybar, tau, Abar, Lbar, Rbar, d, nodes=16, to
                                          _ptr(ybar), float(np.real(tau)), float(np.imag(tau)),
                                          int(nodes), float(tol), _ptr(Abar), _ptr(Lbar),
                                          _ptr(Rbar), _stream_ptr(stream)))
+
+
+def kernel_qr_vjp(Q, R, Qbar, Rbar, Ybar, stream=None):
+    """Ybar of the full-rank QR Y = Q R for the cotangents Qbar, Rbar (FP64 CUDA tensors)."""
+    m, n = Q.shape
+    _check(load().tdmrg_kernel_qr_vjp(int(m), int(n), _ptr(Q), _ptr(R), _ptr(Qbar), _ptr(Rbar),
+                                      _ptr(Ybar), _stream_ptr(stream)))
 
 
 def heff_workspace_floats(Ml, Mr, d, Dl, Dr):

@@ -704,6 +704,45 @@ int tdmrg_kernel_site_exp_vjp(int Ml, int Mr, int d, int Dl, int Dr, const doubl
   });
 }
 
+int tdmrg_kernel_qr_vjp(int m, int n, const void* Q, const void* R, const void* Qbar,
+                        const void* Rbar, void* Ybar, void* stream) {
+  if (m < 1 || n < 1 || m < n || !Q || !R || !Qbar || !Rbar || !Ybar)
+    return fail(nullptr, TDMRG_ERR_ARG, "qr_vjp: need m >= n >= 1 and non-NULL buffers");
+  return guarded(nullptr, [&] {
+    using tdmrg::cplx;
+    using tdmrg::MatRef;
+    cudaStream_t s = (cudaStream_t)stream;
+    cplx *Ru = nullptr, *M = nullptr, *S = nullptr, *rhs = nullptr;
+    struct Free {
+      cplx** p[4];
+      ~Free() {
+        for (auto q : p)
+          if (*q) cudaFree(*q);
+      }
+    } fr{{&Ru, &M, &S, &rhs}};
+    CK(cudaMalloc(&Ru, sizeof(cplx) * (size_t)n * n));
+    CK(cudaMalloc(&M, sizeof(cplx) * (size_t)n * n));
+    CK(cudaMalloc(&S, sizeof(cplx) * (size_t)n * n));
+    CK(cudaMalloc(&rhs, sizeof(cplx) * (size_t)m * n));
+    const cplx one = {1.0, 0.0}, mone = {-1.0, 0.0}, zero = {0.0, 0.0};
+    // entries of Rbar below the diagonal are structural zeros of R
+    CK(cudaMemcpyAsync(Ru, Rbar, sizeof(cplx) * (size_t)n * n, cudaMemcpyDeviceToDevice, s));
+    CK(tdmrg::triu_inplace(n, Ru, s));
+    // M = R Rbar^H - Qbar^H Q
+    CK(tdmrg::zgemm(n, n, n, 1, 1, one, MatRef{(const cplx*)R, n, 1, 0, 0, 0},
+                    MatRef{Ru, 1, n, 0, 0, 1}, zero, M, n, 0, nullptr, s));
+    CK(tdmrg::zgemm(n, n, m, 1, 1, mone, MatRef{(const cplx*)Qbar, 1, n, 0, 0, 1},
+                    MatRef{(const cplx*)Q, n, 1, 0, 0, 0}, one, M, n, 0, nullptr, s));
+    CK(tdmrg::herm_lower(n, M, S, s));
+    // rhs = Qbar + Q S;  Ybar R^H = rhs
+    CK(cudaMemcpyAsync(rhs, Qbar, sizeof(cplx) * (size_t)m * n, cudaMemcpyDeviceToDevice, s));
+    CK(tdmrg::zgemm(m, n, n, 1, 1, one, MatRef{(const cplx*)Q, n, 1, 0, 0, 0},
+                    MatRef{S, n, 1, 0, 0, 0}, one, rhs, n, 0, nullptr, s));
+    CK(tdmrg::solve_rh(m, n, (const cplx*)R, rhs, (cplx*)Ybar, s));
+    CK(cudaStreamSynchronize(s));
+  });
+}
+
 int tdmrg_kernel_krylov_dense(int n, const void* H, const void* v, void* out, double tau_re,
                               double tau_im, double tol, int kmax, int* kused, void* stream) {
   if (n < 1 || !H || !v || !out || kmax < 1 || kmax > tdmrg::KMAX || !(tol > 0.0))

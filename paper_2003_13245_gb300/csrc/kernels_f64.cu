@@ -286,6 +286,75 @@ cudaError_t zaxpy(long long n, cplx alpha, const cplx* x, cplx* y, cudaStream_t 
   return cudaGetLastError();
 }
 
+// S = the Hermitian matrix with the strictly lower triangle of M, its conjugate mirror above
+// the diagonal and Re(M_ii) on it (n x n, row-major)
+__global__ void herm_lower_kernel(int n, const cplx* M, cplx* S) {
+  const long long nn = (long long)n * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nn;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    cplx v;
+    if (i > j) v = M[e];
+    else if (i < j) v = make_double2(M[(long long)j * n + i].x, -M[(long long)j * n + i].y);
+    else v = make_double2(M[e].x, 0.0);
+    S[e] = v;
+  }
+}
+
+cudaError_t herm_lower(int n, const cplx* M, cplx* S, cudaStream_t s) {
+  long long blocks = ((long long)n * n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  count_launch();
+  herm_lower_kernel<<<(int)blocks, 256, 0, s>>>(n, M, S);
+  return cudaGetLastError();
+}
+
+// X[r][:] R^H = B[r][:] for every row r (R n x n upper triangular, row-major): back
+// substitution, one thread per row, x_j = (b_j - sum_{k>j} x_k conj(R_jk)) / conj(R_jj)
+__global__ void solve_rh_kernel(int m, int n, const cplx* R, const cplx* B, cplx* X) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) {
+    const cplx* b = B + (size_t)r * n;
+    cplx* x = X + (size_t)r * n;
+    for (int j = n - 1; j >= 0; --j) {
+      double ar = b[j].x, ai = b[j].y;
+      for (int k = j + 1; k < n; ++k) {
+        const cplx q = R[(size_t)j * n + k], v = x[k];
+        ar -= v.x * q.x + v.y * q.y;
+        ai -= v.y * q.x - v.x * q.y;
+      }
+      const cplx dj = R[(size_t)j * n + j];          // divide by conj(dj) = multiply by dj/|dj|^2
+      const double nd = dj.x * dj.x + dj.y * dj.y;
+      x[j] = make_double2((ar * dj.x - ai * dj.y) / nd, (ai * dj.x + ar * dj.y) / nd);
+    }
+  }
+}
+
+cudaError_t solve_rh(int m, int n, const cplx* R, const cplx* B, cplx* X, cudaStream_t s) {
+  int blocks = (m + 127) / 128;
+  if (blocks < 1) blocks = 1;
+  count_launch();
+  solve_rh_kernel<<<blocks, 128, 0, s>>>(m, n, R, B, X);
+  return cudaGetLastError();
+}
+
+// triu: zero the strictly lower triangle of an n x n matrix in place
+__global__ void triu_kernel(int n, cplx* A) {
+  const long long nn = (long long)n * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nn;
+       e += (long long)gridDim.x * blockDim.x)
+    if (e / n > e % n) A[e] = make_double2(0.0, 0.0);
+}
+
+cudaError_t triu_inplace(int n, cplx* A, cudaStream_t s) {
+  long long blocks = ((long long)n * n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  count_launch();
+  triu_kernel<<<(int)blocks, 256, 0, s>>>(n, A);
+  return cudaGetLastError();
+}
+
 cudaError_t zconj(long long n, cplx* x, cudaStream_t s) {
   long long blocks = (n + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;

@@ -135,6 +135,11 @@ cudaError_t ztranspose(int m, int n, const cplx* src, cplx* dst, int conj, cudaS
 cudaError_t zconj(long long n, cplx* x, cudaStream_t s);
 // y <- y + alpha x
 cudaError_t zaxpy(long long n, cplx alpha, const cplx* x, cplx* y, cudaStream_t s);
+// QR VJP helpers: S = Hermitian fold of the strictly lower triangle of M with Re diag;
+// X R^H = B row by row (R upper triangular); zero the strictly lower triangle in place
+cudaError_t herm_lower(int n, const cplx* M, cplx* S, cudaStream_t s);
+cudaError_t solve_rh(int m, int n, const cplx* R, const cplx* B, cplx* X, cudaStream_t s);
+cudaError_t triu_inplace(int n, cplx* A, cudaStream_t s);
 cudaError_t zfill_identity_mps(cplx* A, int Ml, int D, int Mr, const int* entries, int nent,
                                cudaStream_t s);
 

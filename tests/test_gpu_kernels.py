@@ -211,3 +211,19 @@ def test_site_exp_vjp_matches_oracle(tau):
                                 nodes=16, tol=1e-13)
     for got, ref in ((Ab, Ar), (Lb, Lr), (Rb, Rr)):
         assert np.abs(got.cpu().numpy() - ref).max() <= 1e-9 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("m,n", [(12, 5), (300, 64), (1000, 128), (64, 64)])
+def test_qr_vjp_matches_oracle(m, n):
+    """VJP of the full-rank gauge QR against the oracle's formula on the oracle's factors."""
+    from oracle import adjoint, tdvp
+    from paper_2003_13245_gb300 import binding
+    rng = np.random.default_rng(4000 + m + n)
+    Y = random_complex(rng, (m, n))
+    Q, R = tdvp.gauge_qr(Y)
+    Qb = random_complex(rng, (m, n))
+    Rb = random_complex(rng, (n, n))
+    ref = adjoint.qr_vjp(Q, R, Qb, Rb)
+    out = torch.zeros((m, n), dtype=torch.complex128, device="cuda")
+    binding.kernel_qr_vjp(dev(Q), dev(R), dev(Qb), dev(Rb), out)
+    assert np.abs(out.cpu().numpy() - ref).max() <= 1e-10 * np.abs(ref).max()

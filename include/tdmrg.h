@@ -205,6 +205,19 @@ int tdmrg_kernel_site_exp_vjp(int Ml, int Mr, int d, int Dl, int Dr, const doubl
                               double tau_re, double tau_im, int nodes, double tol, void* Abar,
                               void* Lbar, void* Rbar, void* stream);
 
+/* Vector-Jacobian product of the bond exponential of the projector-splitting step (Eq. S1,
+ * zero-site term), y = exp(tau K) C with (K C)[a][b] = sum_w sum L[w][a][a'] C[a'][b']
+ * R[w][b][b'] Hermitian -- a building block of an adjoint of the step (no counterpart in the
+ * paper).  For a cotangent ybar: Cbar = exp(conj(tau) K) ybar; with the cotangent of K,
+ * conj(tau) int_0^1 a(s) b(s)^H ds (a(s) = exp((1-s) conj(tau) K) ybar, b(s) = exp(s tau K) C,
+ * Gauss-Legendre on `nodes` points, FP64 Lanczos at tolerance `tol`):
+ *   Lbar_w = sum_s k_s a_s conj(R_w) b_s^H,   Rbar_w = sum_s k_s a_s^T conj(L_w) conj(b_s).
+ * L, R, Lbar, Rbar Dw x M x M; C, ybar, Cbar M x M (complex FP64, row-major, device).
+ * Allocates its scratch (freed before return); synchronises `stream`. */
+int tdmrg_kernel_bond_exp_vjp(int M, int Dw, const void* L, const void* R, const void* C,
+                              const void* ybar, double tau_re, double tau_im, int nodes,
+                              double tol, void* Cbar, void* Lbar, void* Rbar, void* stream);
+
 /* Vector-Jacobian product of the gauge QR Y = Q R (K4) at full column rank, diag(R) real
  * and positive (no completed columns) -- a building block of an adjoint of the step (no
  * counterpart in the paper).  With M = R Rbar^H - Qbar^H Q and S the Hermitian matrix made

@@ -62,6 +62,7 @@ _SIGS = {
     "tdmrg_kernel_bond_exp": [_i, _i, _p, _p, _p, _p, _d, _d, _d, _i, _ip, _p],
     "tdmrg_kernel_heff_vjp": [_i, _i, _i, _i, _i, _dp, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p],
     "tdmrg_kernel_qr_vjp": [_i, _i, _p, _p, _p, _p, _p, _p],
+    "tdmrg_kernel_bond_exp_vjp": [_i, _i, _p, _p, _p, _p, _d, _d, _i, _d, _p, _p, _p, _p],
     "tdmrg_kernel_site_exp_vjp": [_i, _i, _i, _i, _i, _dp, _p, _p, _p, _p, _d, _d, _i, _d, _p, _p,
                                   _p, _p],
     "tdmrg_kernel_zgemm_tc": [_i, _i, _i, _p, _p, _i, _i, _p, _p],
@@ -291,6 +292,16 @@ def kernel_qr_vjp(Q, R, Qbar, Rbar, Ybar, stream=None):
     m, n = Q.shape
     _check(load().tdmrg_kernel_qr_vjp(int(m), int(n), _ptr(Q), _ptr(R), _ptr(Qbar), _ptr(Rbar),
                                       _ptr(Ybar), _stream_ptr(stream)))
+
+
+def kernel_bond_exp_vjp(L, R, C, ybar, tau, Cbar, Lbar, Rbar, nodes=16, tol=1e-13,
+                        stream=None):
+    """(Cbar, Lbar, Rbar) of y = exp(tau K(L, R)) C for the cotangent ybar (FP64)."""
+    Dw, M = L.shape[0], L.shape[1]
+    _check(load().tdmrg_kernel_bond_exp_vjp(int(M), int(Dw), _ptr(L), _ptr(R), _ptr(C),
+                                            _ptr(ybar), float(np.real(tau)), float(np.imag(tau)),
+                                            int(nodes), float(tol), _ptr(Cbar), _ptr(Lbar),
+                                            _ptr(Rbar), _stream_ptr(stream)))
 
 
 def heff_workspace_floats(Ml, Mr, d, Dl, Dr):

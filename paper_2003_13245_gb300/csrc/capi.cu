@@ -704,6 +704,69 @@ int tdmrg_kernel_site_exp_vjp(int Ml, int Mr, int d, int Dl, int Dr, const doubl
   });
 }
 
+int tdmrg_kernel_bond_exp_vjp(int M, int Dw, const void* L, const void* R, const void* C,
+                              const void* ybar, double tau_re, double tau_im, int nodes,
+                              double tol, void* Cbar, void* Lbar, void* Rbar, void* stream) {
+  if (M < 1 || Dw < 1 || !L || !R || !C || !ybar || !Cbar || !Lbar || !Rbar || nodes < 1 ||
+      nodes > 64 || !(tol > 0.0))
+    return fail(nullptr, TDMRG_ERR_ARG, "bond_exp_vjp: bad arguments");
+  return guarded(nullptr, [&] {
+    using tdmrg::cplx;
+    using tdmrg::MatRef;
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long mm = (long long)M * M;
+    tdmrg::ModelParams P;
+    P.N = 3;
+    Engine eng(P);
+    eng.set_stream(s);
+    eng.set_krylov(tol, tdmrg::KMAX, 0);
+    eng.ensure_workspace(mm, mm, 1, 1);
+    cplx *X = nullptr, *a = nullptr, *b = nullptr, *T = nullptr;
+    struct Free {
+      cplx** p[4];
+      ~Free() {
+        for (auto q : p)
+          if (*q) cudaFree(*q);
+      }
+    } fr{{&X, &a, &b, &T}};
+    CK(cudaMalloc(&X, sizeof(cplx) * (size_t)Dw * mm));
+    CK(cudaMalloc(&a, sizeof(cplx) * (size_t)mm));
+    CK(cudaMalloc(&b, sizeof(cplx) * (size_t)mm));
+    CK(cudaMalloc(&T, sizeof(cplx) * (size_t)Dw * mm));
+    tdmrg::Ctx c{s, X, nullptr};
+    const cplx* Ld = (const cplx*)L;
+    const cplx* Rd = (const cplx*)R;
+    auto kmv = [&](const cplx* in, cplx* out, const int* skip) {
+      tdmrg::bond_f64(c, M, Dw, Ld, Rd, in, out, skip);
+    };
+    // Cbar = exp(conj(tau) K) ybar
+    eng.krylov(mm, (const cplx*)ybar, (cplx*)Cbar, tau_re, -tau_im, kmv);
+    // cotangent of K: sum_s k_s a_s b_s^H with k_s = w_s conj(tau); for K C = sum_w L_w C R_w^T
+    //   Lbar_w = sum_s k_s a_s conj(R_w) b_s^H,   Rbar_w = sum_s k_s a_s^T conj(L_w) conj(b_s)
+    CK(cudaMemsetAsync(Lbar, 0, sizeof(cplx) * (size_t)Dw * mm, s));
+    CK(cudaMemsetAsync(Rbar, 0, sizeof(cplx) * (size_t)Dw * mm, s));
+    std::vector<double> sn, wn;
+    gauss_legendre01(nodes, sn, wn);
+    const cplx one = {1.0, 0.0}, zero = {0.0, 0.0};
+    for (int q = 0; q < nodes; ++q) {
+      eng.krylov(mm, (const cplx*)C, b, sn[q] * tau_re, sn[q] * tau_im, kmv);
+      eng.krylov(mm, (const cplx*)ybar, a, (1.0 - sn[q]) * tau_re, -(1.0 - sn[q]) * tau_im, kmv);
+      const cplx k = {wn[q] * tau_re, -wn[q] * tau_im};
+      // T_w = conj(R_w) b^H;  Lbar_w += k a T_w
+      CK(tdmrg::zgemm(M, M, M, Dw, 1, one, MatRef{Rd, M, 1, mm, 0, 1}, MatRef{b, 1, M, 0, 0, 1},
+                      zero, T, M, mm, nullptr, s));
+      CK(tdmrg::zgemm(M, M, M, Dw, 1, k, MatRef{a, M, 1, 0, 0, 0}, MatRef{T, M, 1, mm, 0, 0}, one,
+                      (cplx*)Lbar, M, mm, nullptr, s));
+      // T_w = conj(L_w) conj(b);  Rbar_w += k a^T T_w
+      CK(tdmrg::zgemm(M, M, M, Dw, 1, one, MatRef{Ld, M, 1, mm, 0, 1}, MatRef{b, M, 1, 0, 0, 1},
+                      zero, T, M, mm, nullptr, s));
+      CK(tdmrg::zgemm(M, M, M, Dw, 1, k, MatRef{a, 1, M, 0, 0, 0}, MatRef{T, M, 1, mm, 0, 0}, one,
+                      (cplx*)Rbar, M, mm, nullptr, s));
+    }
+    eng.sync_and_check();
+  });
+}
+
 int tdmrg_kernel_qr_vjp(int m, int n, const void* Q, const void* R, const void* Qbar,
                         const void* Rbar, void* Ybar, void* stream) {
   if (m < 1 || n < 1 || m < n || !Q || !R || !Qbar || !Rbar || !Ybar)

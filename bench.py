@@ -183,6 +183,21 @@ def run_reference(args):
     return 0
 
 
+def combine_ranks(dist, ms, units, e2e_s, e2e_units, device):
+    """Replicas (independent instances, no collective on the data path): the job's time is
+    the maximum over ranks and its work the sum over ranks.  Returns
+    (max ms, summed units, max end-to-end seconds, summed end-to-end units)."""
+    if dist is None:
+        return ms, units, e2e_s, e2e_units
+    import torch
+    t = torch.tensor([ms, units, e2e_s, e2e_units], dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = t.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return mx[0].item(), sm[1].item(), mx[2].item(), sm[3].item()
+
+
 # ----------------------------------------------------------------------------------------
 # GPU run
 # ----------------------------------------------------------------------------------------
@@ -274,14 +289,8 @@ def run_ours(args):
     ms_max = ms
     e2e_units = site_updates + pre["site_updates"]
     e2e_s = t_e2e1 - t_e2e0
-    if dist is not None:
-        t = torch.tensor([ms, site_updates, e2e_s, e2e_units], dtype=torch.float64, device="cuda")
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = t.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        ms_max, total_units = mx[0].item(), sm[1].item()
-        e2e_s, e2e_units = mx[2].item(), sm[3].item()
+    ms_max, total_units, e2e_s, e2e_units = combine_ranks(dist, ms, site_updates, e2e_s,
+                                                          e2e_units, "cuda")
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()

@@ -45,7 +45,8 @@ extern "C" {
 
 #define TDMRG_PREC_C128        0 /* every contraction in complex FP64                    */
 #define TDMRG_PREC_C64_3XTF32  1 /* H_eff / environment contractions as complex FP32 via
-                                    3xTF32 split products on the tensor cores; Lanczos
+                                    3xTF32 split products on the tensor cores, bond
+                                    contractions (M <= 256) as complex FP32 FMA; Lanczos
                                     orthogonalisation, small exponential, QR and all norms
                                     and traces stay FP64                                   */
 
@@ -154,9 +155,9 @@ const char* tdmrg_last_global_error(void);
 
 /* ----------------------------------------------------------------------------------
  * Kernel-level entry points (device pointers, complex FP64 interleaved re/im, row-major).
- * They run one hot-path contraction in isolation, for parity tests and measurement.
+ * They run one hot-path operation in isolation, for parity tests and measurement.
  * Arguments are sizes and device pointers owned by the caller; nothing is allocated
- * except where noted; the call returns after the work is enqueued on `stream`.
+ * except where noted; each entry states whether it synchronises `stream`.
  * ---------------------------------------------------------------------------------- */
 
 /* Effective Hamiltonian of one site (K1):

@@ -160,7 +160,7 @@ const char* tdmrg_last_global_error(void);
  * except where noted; each entry states whether it synchronises `stream`.
  * ---------------------------------------------------------------------------------- */
 
-/* Effective Hamiltonian of one site (K1):
+/* Effective Hamiltonian of one site (the site step of Eq. S1):
  *   out[a,s,t,b] = sum L[w,a,y] W[w,v,s,u] A[y,u,t,c] R[v,b,c]
  * L: Dl x Ml x Ml, R: Dr x Mr x Mr, A/out: Ml x (d*d) x Mr (complex FP64), W: Dl x Dr x d x d
  * (dense, host pointer, complex interleaved).  TDMRG_PREC_C128: X, Y are device workspaces of
@@ -219,7 +219,7 @@ int tdmrg_kernel_bond_exp_vjp(int M, int Dw, const void* L, const void* R, const
                               const void* ybar, double tau_re, double tau_im, int nodes,
                               double tol, void* Cbar, void* Lbar, void* Rbar, void* stream);
 
-/* Vector-Jacobian product of the gauge QR Y = Q R (K4) at full column rank, diag(R) real
+/* Vector-Jacobian product of the gauge QR Y = Q R at full column rank, diag(R) real
  * and positive (no completed columns) -- a building block of an adjoint of the step (no
  * counterpart in the paper).  With M = R Rbar^H - Qbar^H Q and S the Hermitian matrix made
  * of the strictly lower triangle of M, its conjugate mirror and Re(M_ii) on the diagonal:
@@ -240,20 +240,21 @@ long long tdmrg_heff_workspace_floats(int Ml, int Mr, int d, int Dl, int Dr);
 int tdmrg_kernel_zgemm_tc(int M, int N, int K, const void* A, const void* B, int conjA, int conjB,
                           void* C, void* stream);
 
-/* Left environment update (K5):
+/* Left environment update (the gauge shift of Eq. S1 carries it along the sweep):
  *   Lout[v,b,c] = sum conj(bra[a,s,t,b]) L[w,a,y] W[w,v,s,u] ket[y,u,t,c]
  * bra: Ml1 x d*d x Mr1, ket: Ml2 x d*d x Mr2, L: Dl x Ml1 x Ml2, Lout: Dr x Mr1 x Mr2.
- * X, Y: workspace of max(Dl,Dr) * Ml2 * d*d * Mr2 complex entries. */
+ * X, Y: workspace of max(Dl,Dr) * Ml2 * d*d * Mr2 complex entries.  Synchronises `stream`. */
 int tdmrg_kernel_env_left(int Ml1, int Mr1, int Ml2, int Mr2, int d, int Dl, int Dr,
                           const double* W_host, const void* L, const void* bra,
                           const void* ket, void* Lout, void* X, void* Y, void* stream);
 
-/* Gauge QR (K4): Y (m x n row-major, m >= n) = Q R with the deterministic completion
- * described for the oracle: accepted columns are Gram-Schmidt residuals (twice) above
+/* Gauge QR of the shifts of Eq. S1: Y (m x n row-major, m >= n) = Q R with a deterministic
+ * completion: accepted columns are Gram-Schmidt residuals (twice) above
  * 1e-12 ||Y||_F; skipped positions are filled from the columns of E (m x p row-major, may
  * be NULL with p = 0) then unit vectors, each taken when its residual exceeds 1e-2 of its
  * norm.  Q (m x n) and R (n x n) row-major outputs; R rows of completed positions are 0.
- * status (device int, may be NULL): set to 1 if the bounded grid barrier timed out. */
+ * status (device int, may be NULL): set to 1 if the bounded grid barrier timed out.
+ * Allocates its scratch (freed before return); synchronises `stream`. */
 int tdmrg_kernel_gauge_qr(int m, int n, const void* Y, int p, const void* E, void* Q,
                           void* R, int* status, void* stream);
 
@@ -299,7 +300,8 @@ int tdmrg_kernel_bond_exp(int M, int Dw, const void* L, const void* R, const voi
                           double tau_re, double tau_im, double tol, int kmax, int* kused,
                           void* stream);
 
-/* Krylov exponential (K2/K3) of a dense Hermitian matrix H (n x n, device):
+/* Krylov exponential of a dense Hermitian matrix H (n x n, device) -- the site and bond
+ * exponentials of Eq. S1 on an explicit matrix:
  * out = exp(tau H) v with tau = tau_re + i tau_im, Lanczos with full re-orthogonalisation
  * in FP64 and the small exponential on the device.  kused (host, may be NULL) receives
  * the number of Krylov vectors.  Allocates its own workspace (freed before return);

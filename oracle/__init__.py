@@ -24,7 +24,8 @@ TD-DMRG for the carrier mobility of organic semiconductors"):
   integral by Gauss-Legendre quadrature, the full-rank gauge QR) and the discrete
   adjoint of one projector-splitting step recorded on a tape, with the parameter
   gradient through the MPO; the reverse pass of the real-time correlation (steps of
-  both states and the j overlaps, recomputed from stored states).
+  both states and the j overlaps, recomputed from stored states) and of the
+  imaginary-time preparation (d log Z / dtheta), completed gauge columns included.
 
 Every function is slow and literal on purpose.  It shares no code, tables or
 helpers with the CUDA path.

@@ -26,8 +26,8 @@ from typing import Callable, List, Tuple
 
 import numpy as np
 
-from .tdvp import (_split, bond_heff, gauge_qr, heff, krylov_expm, update_left,
-                   update_right)
+from .tdvp import (_split, bond_heff, gauge_qr, heff, krylov_expm, left_expansion,
+                   right_expansion, update_left, update_right)
 
 
 def heff_vjp(Lenv, W, Renv, A, d, ybar):
@@ -233,37 +233,33 @@ def _op_exp_bond(T, l, r, c, h, tol):
     return T.op([y], [l, r, c], vjp)[0]
 
 
-def _op_qr_right(T, a):
-    """A_k (Ml, Ds, Mr) = Q R with Q left-orthonormal; outputs (Q as a site tensor, R)."""
+def _op_qr_right(T, a, completion=lambda A: None):
+    """A_k (Ml, Ds, Mr) = Q R with Q left-orthonormal; outputs (Q as a site tensor, R).
+    Skipped columns are completed from completion(A) (then unit vectors) and, in the reverse
+    pass, taken as constants."""
     A = T.vals[a]
     Ml, Ds, Mr = A.shape
-    Q, R = gauge_qr(A.reshape(Ml * Ds, Mr))
-    _assert_full_rank(R)
+    Q, R = gauge_qr(A.reshape(Ml * Ds, Mr), completion(A))
 
     def vjp(bars):
-        Yb = qr_vjp(Q, R, bars[0].reshape(Ml * Ds, Mr), bars[1])
+        Yb = qr_vjp_selected(Q, R, bars[0].reshape(Ml * Ds, Mr), bars[1])
         return [Yb.reshape(Ml, Ds, Mr)]
     return T.op([Q.reshape(Ml, Ds, Mr), R], [a], vjp)
 
 
-def _op_qr_left(T, a):
-    """A_k = C Q with Q right-orthonormal (QR of A^H); outputs (Q as a site tensor, C)."""
+def _op_qr_left(T, a, completion=lambda A: None):
+    """A_k = C Q with Q right-orthonormal (QR of A^H); outputs (Q as a site tensor, C).
+    Skipped columns as in _op_qr_right."""
     A = T.vals[a]
     Ml, Ds, Mr = A.shape
-    Q2, R2 = gauge_qr(A.reshape(Ml, Ds * Mr).conj().T)
-    _assert_full_rank(R2)
+    Q2, R2 = gauge_qr(A.reshape(Ml, Ds * Mr).conj().T, completion(A))
 
     def vjp(bars):
         Qb = bars[0].reshape(Ml, Ds * Mr).conj().T             # output Q2^H
         Rb = bars[1].conj().T                                   # output C = R2^H
-        Yb = qr_vjp(Q2, R2, Qb, Rb)
+        Yb = qr_vjp_selected(Q2, R2, Qb, Rb)
         return [Yb.conj().T.reshape(Ml, Ds, Mr)]
     return T.op([Q2.conj().T.reshape(Ml, Ds, Mr), R2.conj().T], [a], vjp)
-
-
-def _assert_full_rank(R):
-    if np.min(np.abs(np.diag(R))) == 0.0:
-        raise ValueError("the adjoint step needs full-rank gauge shifts (no completed columns)")
 
 
 def _op_env_left(T, l, q, w, d):
@@ -308,8 +304,10 @@ def step_with_tape(Ws, d, A_in, tau, tol=1e-14):
     """The second-order projector-splitting step exp(tau H) of ``tdvp.PurifiedMPS.step`` written
     on a tape: right environments of the input (sites 1.. right-orthonormal, center at 0),
     left-to-right and right-to-left half-sweeps with dt/2 site exponentials, gauge shifts,
-    environment updates, backward bond exponentials and absorption.  Full-rank gauge shifts
-    only (no completion).  Returns (tape, ids of the output sites, ids of the input sites,
+    environment updates, backward bond exponentials and absorption.  Skipped gauge columns
+    are completed as the oracle step completes them (the H coupling of the site, then unit
+    vectors) and taken as constants in the reverse pass: at full bond dimension the outputs
+    that do not depend on the gauge (norms, overlaps) do not depend on them.  Returns (tape, ids of the output sites, ids of the input sites,
     ids of the MPO sites)."""
     T = Tape()
     L = len(A_in)
@@ -326,14 +324,16 @@ def step_with_tape(Ws, d, A_in, tau, tol=1e-14):
     for k in range(L):
         a[k] = _op_exp_heff(T, Lenv[k], w_ids[k], Renv[k], a[k], d[k], h, tol)
         if k < L - 1:
-            a[k], r = _op_qr_right(T, a[k])
+            a[k], r = _op_qr_right(T, a[k], lambda A, k=k: left_expansion(
+                T.vals[Lenv[k]], T.vals[w_ids[k]], A, d[k]))
             Lenv[k + 1] = _op_env_left(T, Lenv[k], a[k], w_ids[k], d[k])
             c = _op_exp_bond(T, Lenv[k + 1], Renv[k], r, -h, tol)
             a[k + 1] = _op_absorb_left(T, c, a[k + 1])
     for k in range(L - 1, -1, -1):
         a[k] = _op_exp_heff(T, Lenv[k], w_ids[k], Renv[k], a[k], d[k], h, tol)
         if k > 0:
-            a[k], c = _op_qr_left(T, a[k])
+            a[k], c = _op_qr_left(T, a[k], lambda A, k=k: right_expansion(
+                T.vals[w_ids[k]], A, T.vals[Renv[k]], d[k]))
             Renv[k - 1] = _op_env_right(T, Renv[k], a[k], w_ids[k], d[k])
             c = _op_exp_bond(T, Lenv[k], Renv[k - 1], c, -h, tol)
             a[k - 1] = _op_absorb_right(T, a[k - 1], c)
@@ -439,3 +439,81 @@ def correlation_vjp(Ws, Wj, d, psi1, psi2, dt, nsteps, cbar, every=2, tol=1e-14)
             Wbar = [x + bars1.get(a, 0) + bars2.get(b, 0) for x, a, b in zip(Wbar, w1, w2)]
     add_overlap(0, *ckpt[0])
     return C, g1, g2, Wbar, Wjbar
+
+
+def qr_vjp_selected(Q, R, Qbar, Rbar):
+    """VJP of the gauge QR with skipped columns (rows of R at completed positions are zero).
+
+    The completed columns are Gram-Schmidt residuals of candidate vectors against everything
+    taken before them; with the candidates held fixed, every parameter value gives a valid
+    orthonormal gauge.  Taking the current completed columns Q_K themselves as the fixed
+    candidates, the factorisation in processing order (accepted columns S first, then the
+    completed ones) is the full-rank QR of Z = [Y_S | Q_K] with R_Z = [[R_SS, 0], [0, I]], and
+    R_S = Q_S^H Y.  The loss Re<Qbar, Q> + Re<Rbar_S, R_S> then gives
+        Ybar = Q_S Rbar_S + scatter_S( first |S| columns of
+               qr_vjp([Q_S | Q_K], R_Z, [Qbar_S + Y Rbar_S^H | Qbar_K], 0) ).
+    Without skipped columns this equals ``qr_vjp``."""
+    acc = np.abs(np.diag(R)) > 0
+    S = np.flatnonzero(acc)
+    K = np.flatnonzero(~acc)
+    ns = len(S)
+    Y = Q[:, S] @ R[S, :]
+    Rb = np.triu(Rbar)
+    order = np.concatenate([S, K])
+    Qp = Q[:, order]
+    Rp = np.zeros((len(order), len(order)), dtype=complex)
+    Rp[:ns, :ns] = R[np.ix_(S, S)]
+    Rp[ns:, ns:] = np.eye(len(K))
+    Qbp = Qbar[:, order].astype(complex)
+    Qbp[:, :ns] += Y @ Rb[S, :].conj().T
+    Zbar = qr_vjp(Qp, Rp, Qbp, np.zeros_like(Rp))
+    Ybar = Q[:, S] @ Rb[S, :]
+    Ybar[:, S] += Zbar[:, :ns]
+    return Ybar
+
+
+def thermal_logz_gradient(model, beta, dtau, M, mpo_builder, tol=1e-14):
+    """log Z of ``tdvp.thermal_state`` and dlogZ/dtheta (theta = omega_m, g_m, V) by reversing
+    the imaginary-time steps on tapes.  The right-canonicalised |I> (theta enters only its
+    completed directions) is the constant start; each step is followed by the normalisation
+    of the center, log Z += log ||A_0||^2, whose VJP is 2 A_0 / ||A_0||^2 for the log and
+    (abar - <A0n, abar> A0n) / ||A_0|| (real part of the projection) for A0n = A_0 / ||A_0||."""
+    from .model import site_list
+    from .tdvp import PurifiedMPS, identity_state
+    Ws = mpo_builder(model)
+    d = [s_[3] for s_ in site_list(model)]
+    psi = PurifiedMPS(model, identity_state(model, M), Ws)
+    psi.right_canonicalize()
+    nrm = np.linalg.norm(psi.A[0])
+    psi.A[0] = psi.A[0] / nrm
+    logZ = 2.0 * np.log(nrm)
+    nsteps = int(round(beta / (2.0 * dtau)))
+    states = [[x.copy() for x in psi.A]]
+    tapes = []
+    for _ in range(nsteps):
+        T, out, inp, wids = step_with_tape(Ws, d, states[-1], -dtau, tol)
+        A = [T.vals[i] for i in out]
+        n = np.linalg.norm(A[0])
+        logZ += 2.0 * np.log(n)
+        A[0] = A[0] / n
+        tapes.append((T, out, inp, wids, n))
+        states.append(A)
+    # reverse: loss = log Z; the final normalised state does not enter it
+    Wbar = [np.zeros_like(np.asarray(W), dtype=complex) for W in Ws]
+    gbar = None                       # cotangent of the normalised state after a step
+    for T, out, inp, wids, n in reversed(tapes):
+        A0 = T.vals[out[0]]
+        A0n = A0 / n
+        # log ||A0||^2: d = 2 Re<A0, dA0> / n^2 ; normalisation A0n = A0 / n
+        bar0 = 2.0 * A0 / n ** 2
+        seeds = {}
+        if gbar is not None:
+            g0 = gbar[0]
+            bar0 = bar0 + (g0 - np.vdot(A0n, g0).real * A0n) / n
+            for i, g in zip(out[1:], gbar[1:]):
+                seeds[i] = g
+        seeds[out[0]] = bar0
+        bars = T.backward(seeds)
+        gbar = [bars.get(i, np.zeros_like(T.vals[i])) for i in inp]
+        Wbar = [x + bars.get(w, 0) for x, w in zip(Wbar, wids)]
+    return logZ, step_parameter_gradient(model, Wbar, mpo_builder)

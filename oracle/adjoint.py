@@ -12,6 +12,8 @@ conjugate pairing is taken accordingly.
                          y = sum L[w,x,y] W[w,v,s,u] A[y,u,t,c] R[v,b,c];
 * ``bond_heff_vjp``   -- the zero-site (bond) product, y = sum L[w,x,y] C[y,c] R[w,b,c];
 * ``update_left_vjp`` / ``update_right_vjp`` -- the environment updates;
+* ``left_expansion_vjp`` / ``right_expansion_vjp`` -- the gauge completion candidates (what
+  H_eff couples the site into), which move the completed directions of a gauge QR;
 * ``expm_krylov_vjp`` -- y = exp(tau H) v for a Hermitian H given as a linear map:
   vbar = exp(conj(tau) H) ybar, and the cotangent of H as the integral
   Hbar = conj(tau) int_0^1 a(s) b(s)^H ds,  a(s) = exp((1-s) conj(tau) H) ybar,
@@ -26,7 +28,7 @@ from typing import Callable, List, Tuple
 
 import numpy as np
 
-from .tdvp import (_split, bond_heff, gauge_qr, heff, krylov_expm, left_expansion,
+from .tdvp import (RANK_TOL, _split, bond_heff, gauge_qr, heff, krylov_expm, left_expansion,
                    right_expansion, update_left, update_right)
 
 
@@ -120,6 +122,30 @@ def update_right_vjp(Renv, bra, W, ket, d, Rbar_out):
     return Rbar, brabar, Wbar, ketbar
 
 
+def left_expansion_vjp(Lenv, W, A, d, Xbar):
+    """VJP of ``tdvp.left_expansion``, X[(x,s,t), (v,c)] = sum L[w,x,y] W[w,v,s,u] A[y,u,t,c]:
+    trilinear, so each cotangent is Xbar contracted with the conjugates of the other two
+    factors.  Returns (Lbar, Wbar, Abar)."""
+    As = _split(A, d)                                          # [y, u, t, c]
+    Xb = Xbar.reshape(A.shape[0], d, d, W.shape[1], A.shape[2])  # [x, s, t, v, c]
+    Lb = np.einsum("xstvc,wvsu,yutc->wxy", Xb, np.conj(W), np.conj(As))
+    Wb = np.einsum("xstvc,wxy,yutc->wvsu", Xb, np.conj(Lenv), np.conj(As))
+    Ab = np.einsum("xstvc,wxy,wvsu->yutc", Xb, np.conj(Lenv), np.conj(W))
+    return Lb, Wb, Ab.reshape(A.shape)
+
+
+def right_expansion_vjp(W, A, Renv, d, Xbar):
+    """VJP of ``tdvp.right_expansion``, X = P^H with
+    P[(w,y), (s,t,b)] = sum W[w,v,s,u] A[y,u,t,c] R[v,b,c]: Re<Xbar, P^H> = Re<Xbar^H, P>, so
+    Pbar = Xbar^H and the trilinear rule applies.  Returns (Wbar, Abar, Rbar)."""
+    As = _split(A, d)                                          # [y, u, t, c]
+    Pb = Xbar.conj().T.reshape(W.shape[0], A.shape[0], d, d, Renv.shape[1])  # [w, y, s, t, b]
+    Wb = np.einsum("wystb,yutc,vbc->wvsu", Pb, np.conj(As), np.conj(Renv))
+    Ab = np.einsum("wystb,wvsu,vbc->yutc", Pb, np.conj(W), np.conj(Renv))
+    Rb = np.einsum("wystb,wvsu,yutc->vbc", Pb, np.conj(W), np.conj(As))
+    return Wb, Ab.reshape(A.shape), Rb
+
+
 def expm_krylov_vjp(matvec: Callable[[np.ndarray], np.ndarray], v: np.ndarray, tau: complex,
                     ybar: np.ndarray, nodes: int = 16, tol: float = 1e-14
                     ) -> Tuple[np.ndarray, List[Tuple[np.ndarray, np.ndarray]]]:
@@ -173,9 +199,11 @@ def sl_solve_triangular(R, B):
 # ---------------------------------------------------------------------------------
 
 class Tape:
-    """Values and the operations that produced them, for reverse accumulation."""
+    """Values and the operations that produced them, for reverse accumulation; rank_tol is
+    the rank threshold of the gauge QRs recorded on it."""
 
-    def __init__(self):
+    def __init__(self, rank_tol=RANK_TOL):
+        self.rank_tol = rank_tol
         self.vals = {}
         self.ops = []            # (input ids, output ids, vjp(out_bars) -> in_bars)
 
@@ -233,33 +261,80 @@ def _op_exp_bond(T, l, r, c, h, tol):
     return T.op([y], [l, r, c], vjp)[0]
 
 
-def _op_qr_right(T, a, completion=lambda A: None):
+def _chosen_columns(X, chosen, m):
+    """The vectors that completed a gauge QR: column i of X for a source i < p, e_{i-p}
+    otherwise (the sources ``gauge_qr`` records)."""
+    p = 0 if X is None else X.shape[1]
+    out = np.zeros((m, len(chosen)), dtype=complex)
+    for j, src in enumerate(chosen):
+        if src < p:
+            out[:, j] = X[:, src]
+        else:
+            out[src - p, j] = 1.0
+    return out
+
+
+def _scatter_chosen(Xsbar, chosen, shape):
+    """Cotangent of the candidate matrix from that of its chosen columns (unit vectors are
+    constants and take none)."""
+    Xbar = np.zeros(shape, dtype=complex)
+    for j, src in enumerate(chosen):
+        if src < shape[1]:
+            Xbar[:, src] += Xsbar[:, j]
+    return Xbar
+
+
+def _op_qr_right(T, a, cand=None):
     """A_k (Ml, Ds, Mr) = Q R with Q left-orthonormal; outputs (Q as a site tensor, R).
-    Skipped columns are completed from completion(A) (then unit vectors) and, in the reverse
-    pass, taken as constants."""
+    Skipped columns are completed as the oracle sweep completes them: cand = (ids of L, W and
+    the site tensor A_c, d) puts the candidates left_expansion(L, W, A_c) on the tape, so the
+    reverse pass follows the completed directions as they move with L, W and A_c."""
     A = T.vals[a]
     Ml, Ds, Mr = A.shape
-    Q, R = gauge_qr(A.reshape(Ml * Ds, Mr), completion(A))
+    m = Ml * Ds
+    X = None if cand is None else left_expansion(T.vals[cand[0]], T.vals[cand[1]],
+                                                 T.vals[cand[2]], cand[3])
+    chosen = []
+    Q, R = gauge_qr(A.reshape(m, Mr), X, rank_tol=T.rank_tol, chosen=chosen)
+    Xs = _chosen_columns(X, chosen, m)
 
     def vjp(bars):
-        Yb = qr_vjp_selected(Q, R, bars[0].reshape(Ml * Ds, Mr), bars[1])
-        return [Yb.reshape(Ml, Ds, Mr)]
-    return T.op([Q.reshape(Ml, Ds, Mr), R], [a], vjp)
+        Yb, Xsb = qr_vjp_completed(Q, R, bars[0].reshape(m, Mr), bars[1], Xs)
+        out = [Yb.reshape(Ml, Ds, Mr)]
+        if cand is not None:
+            Xb = _scatter_chosen(Xsb, chosen, X.shape)
+            out += list(left_expansion_vjp(T.vals[cand[0]], T.vals[cand[1]], T.vals[cand[2]],
+                                           cand[3], Xb))
+        return out
+    ins = [a] if cand is None else [a, cand[0], cand[1], cand[2]]
+    return T.op([Q.reshape(Ml, Ds, Mr), R], ins, vjp)
 
 
-def _op_qr_left(T, a, completion=lambda A: None):
+def _op_qr_left(T, a, cand=None):
     """A_k = C Q with Q right-orthonormal (QR of A^H); outputs (Q as a site tensor, C).
-    Skipped columns as in _op_qr_right."""
+    cand = (ids of W, A_c and R, d) puts the candidates right_expansion(W, A_c, R) on the
+    tape, as in _op_qr_right."""
     A = T.vals[a]
     Ml, Ds, Mr = A.shape
-    Q2, R2 = gauge_qr(A.reshape(Ml, Ds * Mr).conj().T, completion(A))
+    m = Ds * Mr
+    X = None if cand is None else right_expansion(T.vals[cand[0]], T.vals[cand[1]],
+                                                  T.vals[cand[2]], cand[3])
+    chosen = []
+    Q2, R2 = gauge_qr(A.reshape(Ml, m).conj().T, X, rank_tol=T.rank_tol, chosen=chosen)
+    Xs = _chosen_columns(X, chosen, m)
 
     def vjp(bars):
-        Qb = bars[0].reshape(Ml, Ds * Mr).conj().T             # output Q2^H
+        Qb = bars[0].reshape(Ml, m).conj().T                    # output Q2^H
         Rb = bars[1].conj().T                                   # output C = R2^H
-        Yb = qr_vjp_selected(Q2, R2, Qb, Rb)
-        return [Yb.conj().T.reshape(Ml, Ds, Mr)]
-    return T.op([Q2.conj().T.reshape(Ml, Ds, Mr), R2.conj().T], [a], vjp)
+        Yb, Xsb = qr_vjp_completed(Q2, R2, Qb, Rb, Xs)
+        out = [Yb.conj().T.reshape(Ml, Ds, Mr)]
+        if cand is not None:
+            Xb = _scatter_chosen(Xsb, chosen, X.shape)
+            out += list(right_expansion_vjp(T.vals[cand[0]], T.vals[cand[1]],
+                                            T.vals[cand[2]], cand[3], Xb))
+        return out
+    ins = [a] if cand is None else [a, cand[0], cand[1], cand[2]]
+    return T.op([Q2.conj().T.reshape(Ml, Ds, Mr), R2.conj().T], ins, vjp)
 
 
 def _op_env_left(T, l, q, w, d):
@@ -300,16 +375,16 @@ def _op_absorb_right(T, a, c):
     return T.op([np.einsum("asb,bc->asc", A, C)], [a, c], vjp)[0]
 
 
-def step_with_tape(Ws, d, A_in, tau, tol=1e-14):
+def step_with_tape(Ws, d, A_in, tau, tol=1e-14, rank_tol=RANK_TOL):
     """The second-order projector-splitting step exp(tau H) of ``tdvp.PurifiedMPS.step`` written
     on a tape: right environments of the input (sites 1.. right-orthonormal, center at 0),
     left-to-right and right-to-left half-sweeps with dt/2 site exponentials, gauge shifts,
     environment updates, backward bond exponentials and absorption.  Skipped gauge columns
     are completed as the oracle step completes them (the H coupling of the site, then unit
-    vectors) and taken as constants in the reverse pass: at full bond dimension the outputs
-    that do not depend on the gauge (norms, overlaps) do not depend on them.  Returns (tape, ids of the output sites, ids of the input sites,
-    ids of the MPO sites)."""
-    T = Tape()
+    vectors), with the coupling candidates on the tape: below full bond dimension the span
+    of the completed columns enters the projected evolution.  Returns (tape, ids of the
+    output sites, ids of the input sites, ids of the MPO sites)."""
+    T = Tape(rank_tol)
     L = len(A_in)
     a_in = [T.var(np.asarray(x, dtype=complex)) for x in A_in]
     w_ids = [T.var(np.asarray(W)) for W in Ws]
@@ -324,16 +399,14 @@ def step_with_tape(Ws, d, A_in, tau, tol=1e-14):
     for k in range(L):
         a[k] = _op_exp_heff(T, Lenv[k], w_ids[k], Renv[k], a[k], d[k], h, tol)
         if k < L - 1:
-            a[k], r = _op_qr_right(T, a[k], lambda A, k=k: left_expansion(
-                T.vals[Lenv[k]], T.vals[w_ids[k]], A, d[k]))
+            a[k], r = _op_qr_right(T, a[k], (Lenv[k], w_ids[k], a[k], d[k]))
             Lenv[k + 1] = _op_env_left(T, Lenv[k], a[k], w_ids[k], d[k])
             c = _op_exp_bond(T, Lenv[k + 1], Renv[k], r, -h, tol)
             a[k + 1] = _op_absorb_left(T, c, a[k + 1])
     for k in range(L - 1, -1, -1):
         a[k] = _op_exp_heff(T, Lenv[k], w_ids[k], Renv[k], a[k], d[k], h, tol)
         if k > 0:
-            a[k], c = _op_qr_left(T, a[k], lambda A, k=k: right_expansion(
-                T.vals[w_ids[k]], A, T.vals[Renv[k]], d[k]))
+            a[k], c = _op_qr_left(T, a[k], (w_ids[k], a[k], Renv[k], d[k]))
             Renv[k - 1] = _op_env_right(T, Renv[k], a[k], w_ids[k], d[k])
             c = _op_exp_bond(T, Lenv[k], Renv[k - 1], c, -h, tol)
             a[k - 1] = _op_absorb_right(T, a[k - 1], c)
@@ -385,7 +458,8 @@ def overlap_vjp(bra, Wj, ket, d, cbar):
     return C, [z(i) for i in b], [z(i) for i in w], [z(i) for i in k]
 
 
-def correlation_vjp(Ws, Wj, d, psi1, psi2, dt, nsteps, cbar, every=2, tol=1e-14):
+def correlation_vjp(Ws, Wj, d, psi1, psi2, dt, nsteps, cbar, every=2, tol=1e-14,
+                    rank_tol=RANK_TOL):
     """C_n = <psi1(n dt)| j |psi2(n dt)>, n = 0 .. nsteps, both states evolved by the
     projector-splitting step exp(-i dt H); and the cotangents of psi1(0), psi2(0), of the
     H-MPO sites and of the j-MPO sites for the real loss Re sum_n conj(cbar_n) C_n.
@@ -399,8 +473,8 @@ def correlation_vjp(Ws, Wj, d, psi1, psi2, dt, nsteps, cbar, every=2, tol=1e-14)
     s1, s2 = ckpt[0]
     for n in range(nsteps + 1):
         if n > 0:
-            T1, o1, _, _ = step_with_tape(Ws, d, s1, tau, tol)
-            T2, o2, _, _ = step_with_tape(Ws, d, s2, tau, tol)
+            T1, o1, _, _ = step_with_tape(Ws, d, s1, tau, tol, rank_tol)
+            T2, o2, _, _ = step_with_tape(Ws, d, s2, tau, tol, rank_tol)
             s1 = [T1.vals[i] for i in o1]
             s2 = [T2.vals[i] for i in o2]
             if n % every == 0:
@@ -425,8 +499,8 @@ def correlation_vjp(Ws, Wj, d, psi1, psi2, dt, nsteps, cbar, every=2, tol=1e-14)
         states = [ckpt[s0]]
         tapes = []
         for n in range(s0 + 1, e0 + 1):
-            T1, o1, i1, w1 = step_with_tape(Ws, d, states[-1][0], tau, tol)
-            T2, o2, i2, w2 = step_with_tape(Ws, d, states[-1][1], tau, tol)
+            T1, o1, i1, w1 = step_with_tape(Ws, d, states[-1][0], tau, tol, rank_tol)
+            T2, o2, i2, w2 = step_with_tape(Ws, d, states[-1][1], tau, tol, rank_tol)
             tapes.append((T1, o1, i1, w1, T2, o2, i2, w2))
             states.append(([T1.vals[i] for i in o1], [T2.vals[i] for i in o2]))
         for n in range(e0, s0, -1):
@@ -441,18 +515,17 @@ def correlation_vjp(Ws, Wj, d, psi1, psi2, dt, nsteps, cbar, every=2, tol=1e-14)
     return C, g1, g2, Wbar, Wjbar
 
 
-def qr_vjp_selected(Q, R, Qbar, Rbar):
-    """VJP of the gauge QR with skipped columns (rows of R at completed positions are zero).
+def qr_vjp_completed(Q, R, Qbar, Rbar, X):
+    """VJP of the gauge QR with skipped columns (rows of R at completed positions are zero),
+    with respect to Y and to the vectors X (m x |K|) that completed it.
 
-    The completed columns are Gram-Schmidt residuals of candidate vectors against everything
-    taken before them; with the candidates held fixed, every parameter value gives a valid
-    orthonormal gauge.  Taking the current completed columns Q_K themselves as the fixed
-    candidates, the factorisation in processing order (accepted columns S first, then the
-    completed ones) is the full-rank QR of Z = [Y_S | Q_K] with R_Z = [[R_SS, 0], [0, I]], and
-    R_S = Q_S^H Y.  The loss Re<Qbar, Q> + Re<Rbar_S, R_S> then gives
-        Ybar = Q_S Rbar_S + scatter_S( first |S| columns of
-               qr_vjp([Q_S | Q_K], R_Z, [Qbar_S + Y Rbar_S^H | Qbar_K], 0) ).
-    Without skipped columns this equals ``qr_vjp``."""
+    The completed columns are Gram-Schmidt residuals of the chosen candidates X against
+    everything taken before them, so in processing order (accepted columns S first, then the
+    completed ones K) the factorisation is the full-rank QR of Z = [Y_S | X] with
+    R_Z = triu(Q_(S,K)^H Z), and R_S = Q_S^H Y.  The loss Re<Qbar, Q> + Re<Rbar_S, R_S> gives
+        Zbar = qr_vjp(Q_(S,K), R_Z, [Qbar_S + Y Rbar_S^H | Qbar_K], 0),
+        Ybar = Q_S Rbar_S + scatter_S(Zbar_S),   Xbar = Zbar_K.
+    Returns (Ybar, Xbar)."""
     acc = np.abs(np.diag(R)) > 0
     S = np.flatnonzero(acc)
     K = np.flatnonzero(~acc)
@@ -461,51 +534,78 @@ def qr_vjp_selected(Q, R, Qbar, Rbar):
     Rb = np.triu(Rbar)
     order = np.concatenate([S, K])
     Qp = Q[:, order]
-    Rp = np.zeros((len(order), len(order)), dtype=complex)
+    Z = np.concatenate([Y[:, S], X], axis=1)
+    Rp = np.triu(Qp.conj().T @ Z)
     Rp[:ns, :ns] = R[np.ix_(S, S)]
-    Rp[ns:, ns:] = np.eye(len(K))
     Qbp = Qbar[:, order].astype(complex)
     Qbp[:, :ns] += Y @ Rb[S, :].conj().T
     Zbar = qr_vjp(Qp, Rp, Qbp, np.zeros_like(Rp))
     Ybar = Q[:, S] @ Rb[S, :]
     Ybar[:, S] += Zbar[:, :ns]
-    return Ybar
+    return Ybar, Zbar[:, ns:]
 
 
-def thermal_logz_gradient(model, beta, dtau, M, mpo_builder, tol=1e-14):
-    """log Z of ``tdvp.thermal_state`` and dlogZ/dtheta (theta = omega_m, g_m, V) by reversing
-    the imaginary-time steps on tapes.  The right-canonicalised |I> (theta enters only its
-    completed directions) is the constant start; each step is followed by the normalisation
-    of the center, log Z += log ||A_0||^2, whose VJP is 2 A_0 / ||A_0||^2 for the log and
-    (abar - <A0n, abar> A0n) / ||A_0|| (real part of the projection) for A0n = A_0 / ||A_0||."""
-    from .model import site_list
-    from .tdvp import PurifiedMPS, identity_state
-    Ws = mpo_builder(model)
-    d = [s_[3] for s_ in site_list(model)]
-    psi = PurifiedMPS(model, identity_state(model, M), Ws)
-    psi.right_canonicalize()
-    nrm = np.linalg.norm(psi.A[0])
-    psi.A[0] = psi.A[0] / nrm
-    logZ = 2.0 * np.log(nrm)
-    nsteps = int(round(beta / (2.0 * dtau)))
-    states = [[x.copy() for x in psi.A]]
+def qr_vjp_selected(Q, R, Qbar, Rbar):
+    """``qr_vjp_completed`` with the current completed columns Q_K themselves as the fixed
+    candidates (every parameter value then gives a valid orthonormal gauge): R_Z has the
+    identity in its K block.  Without skipped columns this equals ``qr_vjp``."""
+    K = np.flatnonzero(~(np.abs(np.diag(R)) > 0))
+    return qr_vjp_completed(Q, R, Qbar, Rbar, Q[:, K])[0]
+
+
+def _canonicalize_with_tape(Ws, d, A_in, rank_tol=RANK_TOL):
+    """``tdvp.PurifiedMPS.right_canonicalize`` on a tape: LQ shifts from the right end with
+    the H coupling of each site as completion candidates, right environments on the way,
+    the center ends at site 0.  Returns (tape, ids of the output sites, ids of the input
+    sites, ids of the MPO sites)."""
+    T = Tape(rank_tol)
+    L = len(A_in)
+    a_in = [T.var(np.asarray(x, dtype=complex)) for x in A_in]
+    w_ids = [T.var(np.asarray(W)) for W in Ws]
+    a = list(a_in)
+    Renv = [None] * L
+    Renv[L - 1] = T.var(np.ones((1, 1, 1), dtype=complex))
+    for k in range(L - 1, 0, -1):
+        a[k], c = _op_qr_left(T, a[k], (w_ids[k], a[k], Renv[k], d[k]))
+        Renv[k - 1] = _op_env_right(T, Renv[k], a[k], w_ids[k], d[k])
+        a[k - 1] = _op_absorb_right(T, a[k - 1], c)
+    return T, a, a_in, w_ids
+
+
+def _thermal_with_tapes(Ws, d, model, beta, dtau, M, tol, rank_tol=RANK_TOL):
+    """``tdvp.thermal_state`` on tapes: the right-canonicalisation of |I> (theta enters its
+    completed directions through W), then n = round(beta / (2 dtau)) steps exp(-dtau H), each
+    followed by the normalisation of the center, log Z += log ||A_0||^2.  Returns (final
+    normalised state, log Z, [(tape, output ids, input ids, MPO ids, ||A_0||)])."""
+    from .tdvp import identity_state
     tapes = []
-    for _ in range(nsteps):
-        T, out, inp, wids = step_with_tape(Ws, d, states[-1], -dtau, tol)
+    T, out, inp, wids = _canonicalize_with_tape(Ws, d, identity_state(model, M), rank_tol)
+    A = [T.vals[i] for i in out]
+    nrm = np.linalg.norm(A[0])
+    A[0] = A[0] / nrm
+    logZ = 2.0 * np.log(nrm)
+    tapes.append((T, out, inp, wids, nrm))
+    for _ in range(int(round(beta / (2.0 * dtau)))):
+        T, out, inp, wids = step_with_tape(Ws, d, A, -dtau, tol, rank_tol)
         A = [T.vals[i] for i in out]
         n = np.linalg.norm(A[0])
         logZ += 2.0 * np.log(n)
         A[0] = A[0] / n
         tapes.append((T, out, inp, wids, n))
-        states.append(A)
-    # reverse: loss = log Z; the final normalised state does not enter it
+    return A, logZ, tapes
+
+
+def _thermal_reverse(tapes, Ws, state_bar, logz_bar):
+    """Cotangents of the H-MPO sites for a loss with cotangent state_bar (or None) of the
+    final normalised state and logz_bar of log Z.  Per tape, the normalisation
+    A0n = A_0 / ||A_0|| has the VJP (abar - Re<A0n, abar> A0n) / ||A_0|| and log ||A_0||^2 the
+    VJP 2 A_0 / ||A_0||^2; the input of the first tape (|I>) is a constant."""
     Wbar = [np.zeros_like(np.asarray(W), dtype=complex) for W in Ws]
-    gbar = None                       # cotangent of the normalised state after a step
+    gbar = state_bar
     for T, out, inp, wids, n in reversed(tapes):
         A0 = T.vals[out[0]]
         A0n = A0 / n
-        # log ||A0||^2: d = 2 Re<A0, dA0> / n^2 ; normalisation A0n = A0 / n
-        bar0 = 2.0 * A0 / n ** 2
+        bar0 = logz_bar * 2.0 * A0 / n ** 2
         seeds = {}
         if gbar is not None:
             g0 = gbar[0]
@@ -515,5 +615,113 @@ def thermal_logz_gradient(model, beta, dtau, M, mpo_builder, tol=1e-14):
         seeds[out[0]] = bar0
         bars = T.backward(seeds)
         gbar = [bars.get(i, np.zeros_like(T.vals[i])) for i in inp]
-        Wbar = [x + bars.get(w, 0) for x, w in zip(Wbar, wids)]
+        Wbar = [x + bars.get(wi, 0) for x, wi in zip(Wbar, wids)]
+    return Wbar
+
+
+def thermal_logz_gradient(model, beta, dtau, M, mpo_builder, tol=1e-14):
+    """log Z of ``tdvp.thermal_state`` and dlogZ/dtheta (theta = omega_m, g_m, V) by reversing
+    the canonicalisation and the imaginary-time steps on their tapes."""
+    from .model import site_list
+    Ws = mpo_builder(model)
+    d = [s_[3] for s_ in site_list(model)]
+    _, logZ, tapes = _thermal_with_tapes(Ws, d, model, beta, dtau, M, tol)
+    Wbar = _thermal_reverse(tapes, Ws, None, 1.0)
     return logZ, step_parameter_gradient(model, Wbar, mpo_builder)
+
+
+# ---------------------------------------------------------------------------------
+# the whole C(t) pipeline: imaginary-time preparation, j fit, real-time steps, overlaps
+# ---------------------------------------------------------------------------------
+
+def _op_heff(T, l, w, r, a, d):
+    """y = H_eff(L, W, R) A as a plain contraction (the fit's local projection)."""
+    Lk, Wk, Rk, A = T.vals[l], T.vals[w], T.vals[r], T.vals[a]
+
+    def vjp(bars):
+        Ab, Lb, Wb, Rb = heff_vjp(Lk, Wk, Rk, A, d, bars[0])
+        return [Lb, Wb, Rb, Ab]
+    return T.op([heff(Lk, Wk, Rk, A, d)], [l, w, r, a], vjp)[0]
+
+
+def _op_env_left2(T, l, bra, w, ket, d):
+    Lk, B, Wk, K = T.vals[l], T.vals[bra], T.vals[w], T.vals[ket]
+
+    def vjp(bars):
+        Lb, bb, Wb, kb = update_left_vjp(Lk, B, Wk, K, d, bars[0])
+        return [Lb, bb, Wb, kb]
+    return T.op([update_left(Lk, B, Wk, K, d)], [l, bra, w, ket], vjp)[0]
+
+
+def _op_env_right2(T, r, bra, w, ket, d):
+    Rk, B, Wk, K = T.vals[r], T.vals[bra], T.vals[w], T.vals[ket]
+
+    def vjp(bars):
+        Rb, bb, Wb, kb = update_right_vjp(Rk, B, Wk, K, d, bars[0])
+        return [Rb, bb, Wb, kb]
+    return T.op([update_right(Rk, B, Wk, K, d)], [r, bra, w, ket], vjp)[0]
+
+
+def fit_with_tape(Wop, d, psi, sweeps=2, rank_tol=RANK_TOL):
+    """``tdvp.fit_apply`` (phi ~ Wop|psi> by one-site variational fitting) on a tape.
+    Returns (tape, ids of phi, ids of psi, ids of the Wop sites)."""
+    T = Tape(rank_tol)
+    L = len(psi)
+    p = [T.var(np.asarray(x, dtype=complex)) for x in psi]
+    w = [T.var(np.asarray(x)) for x in Wop]
+    phi = list(p)                                  # phi starts as psi
+    one = np.ones((1, 1, 1), dtype=complex)
+    Lf, Rf = [None] * L, [None] * L
+    Lf[0] = T.var(one)
+    Rf[L - 1] = T.var(one)
+    for k in range(L - 1, 0, -1):
+        Rf[k - 1] = _op_env_right2(T, Rf[k], phi[k], w[k], p[k], d[k])
+    for _ in range(sweeps):
+        for k in range(L):
+            a = _op_heff(T, Lf[k], w[k], Rf[k], p[k], d[k])
+            if k < L - 1:
+                phi[k], _ = _op_qr_right(T, a, (Lf[k], w[k], p[k], d[k]))
+                Lf[k + 1] = _op_env_left2(T, Lf[k], phi[k], w[k], p[k], d[k])
+            else:
+                phi[k] = a
+        for k in range(L - 1, -1, -1):
+            a = _op_heff(T, Lf[k], w[k], Rf[k], p[k], d[k])
+            if k > 0:
+                phi[k], _ = _op_qr_left(T, a, (w[k], p[k], Rf[k], d[k]))
+                Rf[k - 1] = _op_env_right2(T, Rf[k], phi[k], w[k], p[k], d[k])
+            else:
+                phi[k] = a
+    return T, phi, p, w
+
+
+def correlation_pipeline_gradient(model, beta, dtau, M, dt, nsteps, cbar, mpo_h, mpo_j,
+                                  every=2, tol=1e-14, rank_tol=RANK_TOL):
+    """C_n (n = 0 .. nsteps) of the oracle pipeline (``tdvp.correlation`` with fit_sweeps=2)
+    and dl/dtheta for l = Re sum_n conj(cbar_n) C_n: the real-time reverse pass, then the
+    j fit, then the imaginary-time preparation, with the MPO cotangents of H and j mapped
+    to omega_m, g_m, V.
+
+    The gauge QRs use rank_tol.  Where a bond is wider than the rank of the state (the
+    one-carrier sector at full bond dimension), columns whose exact residual is zero come out
+    of Gram-Schmidt at rounding size; with the default 1e-12 some of them are accepted,
+    their direction is set by rounding, and R^{-1} in the QR VJP amplifies it.  A threshold
+    above rounding (1e-8) completes them from the candidates instead and keeps the reverse
+    pass conditioned; the forward C then moves by the dropped residuals only."""
+    from .model import site_list
+    d = [s_[3] for s_ in site_list(model)]
+    Ws, Wj = mpo_h(model), mpo_j(model)
+    psi, _, ttapes = _thermal_with_tapes(Ws, d, model, beta, dtau, M, tol, rank_tol)
+    Tf, phi_ids, psi_ids, wj_ids = fit_with_tape(Wj, d, psi, rank_tol=rank_tol)
+    phi = [Tf.vals[i] for i in phi_ids]
+    C, g1, g2, Wb, Wjb = correlation_vjp(Ws, Wj, d, psi, phi, dt, nsteps, cbar, every, tol,
+                                         rank_tol)
+    # the fit: phi = fit(Wj, psi)
+    fb = Tf.backward(dict(zip(phi_ids, g2)))
+    gpsi = [x + fb.get(i, np.zeros_like(x)) for x, i in zip(g1, psi_ids)]
+    Wjb = [x + fb.get(i, 0) for x, i in zip(Wjb, wj_ids)]
+    # the preparation
+    Wb2 = _thermal_reverse(ttapes, Ws, gpsi, 0.0)
+    Wb = [x + y for x, y in zip(Wb, Wb2)]
+    gH = step_parameter_gradient(model, Wb, mpo_h)
+    gJ = step_parameter_gradient(model, Wjb, mpo_j)
+    return C, {p: gH[p] + gJ[p] for p in gH}

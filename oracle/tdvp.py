@@ -44,7 +44,8 @@ COMPLETE_TOL = 1e-2   # unit vector e_i used for completion if its residual norm
 # ---------------------------------------------------------------------------------
 
 def gauge_qr(Y: np.ndarray, extra: Optional[np.ndarray] = None,
-             rank_tol: float = RANK_TOL, complete_tol: float = COMPLETE_TOL):
+             rank_tol: float = RANK_TOL, complete_tol: float = COMPLETE_TOL,
+             chosen: Optional[list] = None):
     """Y (m x n, m >= n) = Q R with Q^H Q = I.
 
     Column j of Q is the Gram-Schmidt residual of Y[:, j] against the accepted earlier
@@ -56,6 +57,9 @@ def gauge_qr(Y: np.ndarray, extra: Optional[np.ndarray] = None,
     own norm.  R = Q^H Y, except that the rows of completed positions are set to zero
     (their entries are residuals below rank_tol * ||Y||_F, which the Gram-Schmidt
     coefficients of the skipped columns do not carry).
+
+    If ``chosen`` is a list, the source of each completed position is appended to it, in
+    increasing position order: i < p for column i of ``extra``, p + i for e_i.
     """
     m, n = Y.shape
     assert m >= n
@@ -81,14 +85,15 @@ def gauge_qr(Y: np.ndarray, extra: Optional[np.ndarray] = None,
             nb += 1
             have.add(j)
 
+    p = 0 if extra is None else extra.shape[1]
+
     def candidates():
-        if extra is not None:
-            for i in range(extra.shape[1]):
-                yield extra[:, i].astype(complex)
+        for i in range(p):
+            yield i, extra[:, i].astype(complex)
         for i in range(m):
             e = np.zeros(m, dtype=complex)
             e[i] = 1.0
-            yield e
+            yield p + i, e
 
     gen = candidates()
     completed = []
@@ -97,7 +102,7 @@ def gauge_qr(Y: np.ndarray, extra: Optional[np.ndarray] = None,
             continue
         completed.append(j)
         while True:
-            c = next(gen, None)
+            src, c = next(gen, (None, None))
             if c is None:
                 raise RuntimeError("gauge_qr: ran out of completion vectors")
             n0 = np.linalg.norm(c)
@@ -110,6 +115,8 @@ def gauge_qr(Y: np.ndarray, extra: Optional[np.ndarray] = None,
                 B[:, nb] = Q[:, j]
                 nb += 1
                 have.add(j)
+                if chosen is not None:
+                    chosen.append(src)
                 break
     R = Q.conj().T @ Y
     R[completed, :] = 0.0

@@ -131,6 +131,24 @@ int tdmrg_realtime_observe(tdmrg_model* h, double* C_out, double* obs);
  * t_grid[nt], C[2*nt] host; pure host arithmetic, no handle needed. */
 int tdmrg_mobility(const double* t_grid, const double* C, int nt, double kT, double* mu_out);
 
+/* One site of an MPO of the chain, dense, built on the host (no handle, no GPU): the chain of
+ * tdmrg_model_create (same arguments and checks) with, when nmax_p != 0, the bond mode of
+ * tdmrg_model_set_peierls (alpha, omega_p, nmax_p in [2, 32]).  which: TDMRG_MPO_H (Eq. 1 /
+ * Eq. 10), TDMRG_MPO_J (Eq. 3) or TDMRG_MPO_IDENTITY.  param = -1 gives the site itself;
+ * param >= 0 its derivative with respect to the parameter theta_param, numbered omega_0 ..
+ * omega_{modes-1}, g_0 .. g_{modes-1}, V, then (bond mode only) alpha, omega_p.  Every block
+ * is affine in each parameter on its own, so the derivative is W(theta + 1) - W(theta) exactly;
+ * H = sum_k (site k replaced by its derivative) gives dH/dtheta, as the adjoint needs it.
+ * dims[3] (host) receives (Dl, Dr, d); W_out (host, may be NULL to query dims) receives
+ * Dl*Dr*d*d complex entries, interleaved re/im, layout [wl][wr][s][u] (row s = output level),
+ * zero outside the automaton's blocks.  TDMRG_ERR_ARG on a bad argument. */
+#define TDMRG_MPO_H        0
+#define TDMRG_MPO_J        1
+#define TDMRG_MPO_IDENTITY 2
+int tdmrg_host_mpo_site(int N, int modes, const double* omega, const double* g, double V,
+                        const int* nmax, double alpha, double omega_p, int nmax_p, int which,
+                        int param, int site, int* dims, double* W_out);
+
 /* log Z = log Tr[exp(-beta H) P_1] accumulated by tdmrg_thermal_prepare. */
 int tdmrg_get_logz(const tdmrg_model* h, double* logz);
 

@@ -68,6 +68,7 @@ _SIGS = {
     "tdmrg_kernel_zgemm_tc": [_i, _i, _i, _p, _p, _i, _i, _p, _p],
     "tdmrg_kernel_gauge_qr_noalloc": [_i, _i, _p, _i, _p, _p, _p, _p, _p],
     "tdmrg_kernel_gauge_qr_blocked": [_i, _i, _p, _i, _p, _p, _p, _p, _p],
+    "tdmrg_host_mpo_site": [_i, _i, _dp, _dp, _d, _ip, _d, _d, _i, _i, _i, _i, _ip, _dp],
 }
 
 
@@ -243,6 +244,33 @@ def mobility(t_grid, C, kT):
     mu = ctypes.c_double()
     _check(lib.tdmrg_mobility(_dptr(t), _dptr(c), int(t.size), float(kT), ctypes.byref(mu)))
     return mu.value
+
+
+MPO_H, MPO_J, MPO_IDENTITY = 0, 1, 2
+
+
+def host_mpo(N, omega, g, nmax, V, which=MPO_H, param=-1, peierls=None):
+    """Every site of an MPO of the chain (or of its derivative with respect to parameter
+    `param`: omega_m, g_m, V, then alpha, omega_p) through tdmrg_host_mpo_site, as complex
+    arrays [Dl, Dr, d, d]; host only."""
+    lib = load()
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    gg = np.ascontiguousarray(g, dtype=np.float64)
+    nm = np.ascontiguousarray(nmax, dtype=np.int32)
+    alpha, omega_p, nmax_p = peierls if peierls is not None else (0.0, 0.0, 0)
+    L = int(N) * (1 + om.size + (1 if peierls is not None else 0))
+    out = []
+    dims = np.zeros(3, dtype=np.int32)
+    for k in range(L):
+        args = [int(N), int(om.size), _dptr(om), _dptr(gg), float(V), nm.ctypes.data_as(_ip),
+                float(alpha), float(omega_p), int(nmax_p), int(which), int(param), k,
+                dims.ctypes.data_as(_ip)]
+        _check(lib.tdmrg_host_mpo_site(*args, None))
+        Dl, Dr, d = (int(x) for x in dims)
+        buf = np.zeros(2 * Dl * Dr * d * d)
+        _check(lib.tdmrg_host_mpo_site(*args, _dptr(buf)))
+        out.append((buf[0::2] + 1j * buf[1::2]).reshape(Dl, Dr, d, d))
+    return out
 
 
 # --- kernel-level entry points (device pointers from torch tensors) -------------------------

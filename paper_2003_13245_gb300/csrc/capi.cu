@@ -81,6 +81,25 @@ struct TempMpo {
   ~TempMpo() { Engine::free_mpo(m); }
 };
 
+// the chain of Eq. 1 from the arguments of tdmrg_model_create; nullptr or the failed check
+const char* fill_params(int N, int modes, const double* omega, const double* g, double V,
+                        const int* nmax, tdmrg::ModelParams& P) {
+  if (N < 3) return "N must be >= 3 (periodic chain)";
+  if (modes < 0 || modes > 64) return "modes out of range";
+  if (modes > 0 && (!omega || !g || !nmax)) return "NULL mode arrays";
+  P.N = N;
+  P.V = V;
+  for (int m = 0; m < modes; ++m) {
+    if (nmax[m] < 2 || nmax[m] > 32) return "nmax must be in [2, 32]";
+    if (!std::isfinite(omega[m]) || !std::isfinite(g[m])) return "non-finite mode parameter";
+    P.omega.push_back(omega[m]);
+    P.g.push_back(g[m]);
+    P.nmax.push_back(nmax[m]);
+  }
+  if (!std::isfinite(V)) return "non-finite V";
+  return nullptr;
+}
+
 }  // namespace
 
 extern "C" {
@@ -89,21 +108,9 @@ int tdmrg_model_create(int N, int modes, const double* omega, const double* g, d
                        const int* nmax, tdmrg_model** out) {
   if (!out) return fail(nullptr, TDMRG_ERR_ARG, "out is NULL");
   *out = nullptr;
-  if (N < 3) return fail(nullptr, TDMRG_ERR_ARG, "N must be >= 3 (periodic chain)");
-  if (modes < 0 || modes > 64) return fail(nullptr, TDMRG_ERR_ARG, "modes out of range");
-  if (modes > 0 && (!omega || !g || !nmax)) return fail(nullptr, TDMRG_ERR_ARG, "NULL mode arrays");
   tdmrg::ModelParams P;
-  P.N = N;
-  P.V = V;
-  for (int m = 0; m < modes; ++m) {
-    if (nmax[m] < 2 || nmax[m] > 32) return fail(nullptr, TDMRG_ERR_ARG, "nmax must be in [2, 32]");
-    if (!std::isfinite(omega[m]) || !std::isfinite(g[m]))
-      return fail(nullptr, TDMRG_ERR_ARG, "non-finite mode parameter");
-    P.omega.push_back(omega[m]);
-    P.g.push_back(g[m]);
-    P.nmax.push_back(nmax[m]);
-  }
-  if (!std::isfinite(V)) return fail(nullptr, TDMRG_ERR_ARG, "non-finite V");
+  if (const char* msg = fill_params(N, modes, omega, g, V, nmax, P))
+    return fail(nullptr, TDMRG_ERR_ARG, msg);
   auto* h = new (std::nothrow) tdmrg_model;
   if (!h) return fail(nullptr, TDMRG_ERR_OOM, "host allocation failed");
   const int rc = guarded(h, [&] { h->eng.reset(new Engine(P)); });
@@ -285,6 +292,45 @@ int tdmrg_mobility(const double* t_grid, const double* C, int nt, double kT, dou
   }
   *mu_out = 2.0 * integral / (2.0 * kT);
   return TDMRG_OK;
+}
+
+int tdmrg_host_mpo_site(int N, int modes, const double* omega, const double* g, double V,
+                        const int* nmax, double alpha, double omega_p, int nmax_p, int which,
+                        int param, int site, int* dims, double* W_out) {
+  if (!dims) return fail(nullptr, TDMRG_ERR_ARG, "host_mpo_site: dims is NULL");
+  tdmrg::ModelParams P;
+  if (const char* msg = fill_params(N, modes, omega, g, V, nmax, P))
+    return fail(nullptr, TDMRG_ERR_ARG, msg);
+  if (nmax_p != 0) {
+    if (nmax_p < 2 || nmax_p > 32 || !std::isfinite(alpha) || !std::isfinite(omega_p))
+      return fail(nullptr, TDMRG_ERR_ARG, "host_mpo_site: nmax_p in [2, 32], finite alpha and omega_p");
+    P.peierls = true;
+    P.alpha = alpha;
+    P.omega_p = omega_p;
+    P.nmax_p = nmax_p;
+  }
+  if (which < TDMRG_MPO_H || which > TDMRG_MPO_IDENTITY)
+    return fail(nullptr, TDMRG_ERR_ARG, "host_mpo_site: unknown operator");
+  if (param < -1 || param >= tdmrg::parameter_count(P))
+    return fail(nullptr, TDMRG_ERR_ARG, "host_mpo_site: parameter index out of range");
+  if (site < 0 || site >= (int)tdmrg::chain_sites(P).size())
+    return fail(nullptr, TDMRG_ERR_ARG, "host_mpo_site: site out of range");
+  return guarded(nullptr, [&] {
+    const tdmrg::MpoSite W = param < 0 ? tdmrg::build_mpo(P, which)[site]
+                                       : tdmrg::mpo_site_derivative(P, which, param, site);
+    dims[0] = W.Dl;
+    dims[1] = W.Dr;
+    dims[2] = W.d;
+    if (!W_out) return;
+    const size_t dd = (size_t)W.d * W.d;
+    std::memset(W_out, 0, sizeof(double) * 2 * (size_t)W.Dl * W.Dr * dd);
+    for (const auto& b : W.blocks)
+      for (size_t e = 0; e < dd; ++e) {
+        const size_t off = 2 * (((size_t)b.wl * W.Dr + b.wr) * dd + e);
+        W_out[off] += b.op[e].real();
+        W_out[off + 1] += b.op[e].imag();
+      }
+  });
 }
 
 int tdmrg_get_logz(const tdmrg_model* h, double* logz) {

@@ -248,4 +248,62 @@ std::vector<int> bond_dimensions(const std::vector<SiteInfo>& sites, int M) {
   return out;
 }
 
+std::vector<MpoSite> build_mpo(const ModelParams& P, int which) {
+  if (which == 0) return hamiltonian_mpo(P);
+  if (which == 1) return current_mpo(P);
+  if (which == 2) return identity_mpo(P);
+  throw std::invalid_argument("build_mpo: which must be 0 (H), 1 (j) or 2 (identity)");
+}
+
+int parameter_count(const ModelParams& P) {
+  return 2 * (int)P.omega.size() + 1 + (P.peierls ? 2 : 0);
+}
+
+ModelParams shifted(const ModelParams& P, int param, double delta) {
+  const int K = (int)P.omega.size();
+  if (param < 0 || param >= parameter_count(P))
+    throw std::invalid_argument("shifted: parameter index out of range");
+  ModelParams Q = P;
+  if (param < K)
+    Q.omega[param] += delta;
+  else if (param < 2 * K)
+    Q.g[param - K] += delta;
+  else if (param == 2 * K)
+    Q.V += delta;
+  else if (param == 2 * K + 1)
+    Q.alpha += delta;
+  else
+    Q.omega_p += delta;
+  return Q;
+}
+
+MpoSite mpo_site_derivative(const ModelParams& P, int which, int param, int k) {
+  const auto W0 = build_mpo(P, which);
+  const auto W1 = build_mpo(shifted(P, param, 1.0), which);
+  if (k < 0 || k >= (int)W0.size()) throw std::invalid_argument("mpo_site_derivative: bad site");
+  const MpoSite& a = W0[k];
+  const MpoSite& b = W1[k];
+  // the automata add their blocks in an order that does not depend on the parameter values
+  if (a.blocks.size() != b.blocks.size())
+    throw std::logic_error("mpo_site_derivative: block structure depends on the parameter");
+  MpoSite out;
+  out.Dl = a.Dl;
+  out.Dr = a.Dr;
+  out.d = a.d;
+  for (size_t i = 0; i < a.blocks.size(); ++i) {
+    const MpoBlock& x = a.blocks[i];
+    const MpoBlock& y = b.blocks[i];
+    if (x.wl != y.wl || x.wr != y.wr)
+      throw std::logic_error("mpo_site_derivative: block structure depends on the parameter");
+    std::vector<Cx> op(x.op.size());
+    bool nz = false;
+    for (size_t e = 0; e < op.size(); ++e) {
+      op[e] = y.op[e] - x.op[e];
+      nz = nz || op[e] != Cx(0, 0);
+    }
+    if (nz) out.blocks.push_back({x.wl, x.wr, std::move(op)});
+  }
+  return out;
+}
+
 }  // namespace tdmrg

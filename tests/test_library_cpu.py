@@ -50,3 +50,55 @@ def test_argument_errors_are_reported(lib):
     assert rc == -1
     rc = lib.tdmrg_kernel_bond_exp(257, 7, 1, 1, 1, 1, 0.0, -0.05, 1e-7, 32, None, None)
     assert rc == -1
+
+
+def _mpo_params(peierls):
+    from oracle.model import HolsteinModel
+    extra = {} if peierls is None else dict(zip(("alpha", "omega_p", "nmax_p"), peierls))
+    return HolsteinModel(N=3, omega=[0.7], g=[1.3], nmax=[2], V=0.6, **extra)
+
+
+def _host_mpo(model, which, param=-1):
+    from paper_2003_13245_gb300 import binding
+    peierls = (model.alpha, model.omega_p, model.nmax_p) if model.peierls else None
+    return binding.host_mpo(model.N, model.omega, model.g, model.nmax, model.V, which, param,
+                            peierls)
+
+
+@pytest.mark.parametrize("peierls", [None, (0.3, 0.5, 2)])
+def test_host_mpo_equals_definition(lib, peierls):
+    """The library's MPOs of H and j (built on the host, no GPU) contract to the operators of
+    Eq. 1 / Eq. 10 and Eq. 3 written term by term with Kronecker products."""
+    from oracle.model import dense_from_definition, mpo_to_dense
+    from paper_2003_13245_gb300 import binding
+    model = _mpo_params(peierls)
+    H, J = dense_from_definition(model)
+    assert np.abs(mpo_to_dense(_host_mpo(model, binding.MPO_H)) - H).max() < 1e-13
+    assert np.abs(mpo_to_dense(_host_mpo(model, binding.MPO_J)) - J).max() < 1e-13
+    Id = mpo_to_dense(_host_mpo(model, binding.MPO_IDENTITY))
+    assert np.array_equal(Id, np.eye(H.shape[0]))
+
+
+@pytest.mark.parametrize("peierls", [None, (0.3, 0.5, 2)])
+def test_host_mpo_parameter_derivatives(lib, peierls):
+    """sum_k (MPO with site k replaced by its derivative site) == dH/dtheta and dj/dtheta of
+    the term-by-term operators, for omega, g, V (and alpha, omega_p with a bond mode); both
+    operators are affine in each parameter, so the derivative is the difference at +1."""
+    import dataclasses
+    from oracle.model import dense_from_definition, mpo_to_dense
+    from paper_2003_13245_gb300 import binding
+    model = _mpo_params(peierls)
+    shifts = [dict(omega=[model.omega[0] + 1.0]), dict(g=[model.g[0] + 1.0]),
+              dict(V=model.V + 1.0)]
+    if peierls is not None:
+        shifts += [dict(alpha=model.alpha + 1.0), dict(omega_p=model.omega_p + 1.0)]
+    H0, J0 = dense_from_definition(model)
+    W0 = {w: _host_mpo(model, w) for w in (binding.MPO_H, binding.MPO_J)}
+    for p, sh in enumerate(shifts):
+        H1, J1 = dense_from_definition(dataclasses.replace(model, **sh))
+        for w, ref in ((binding.MPO_H, H1 - H0), (binding.MPO_J, J1 - J0)):
+            dW = _host_mpo(model, w, p)
+            D = sum(mpo_to_dense(W0[w][:k] + [dW[k]] + W0[w][k + 1:]) for k in range(len(dW)))
+            assert np.abs(D - ref).max() < 1e-12, (p, w)
+    with pytest.raises(binding.TdmrgError):
+        _host_mpo(model, binding.MPO_H, len(shifts))      # one past the last parameter

@@ -39,7 +39,9 @@ extern "C" {
 #define TDMRG_ERR_CUDA      -2   /* a CUDA runtime call failed                           */
 #define TDMRG_ERR_OOM       -3   /* device allocation failed                             */
 #define TDMRG_ERR_NONFINITE -4   /* NaN/Inf detected in a norm after a half-sweep        */
-#define TDMRG_ERR_NOCONV    -5   /* Krylov exponential did not converge (estimate > 1e3 tol) */
+#define TDMRG_ERR_NOCONV    -5   /* reserved: a Krylov exponential that stopped at kmax with
+                                    its error estimate above 1e3 tol; the device records this
+                                    in its Lanczos state, no entry point returns it yet   */
 #define TDMRG_ERR_TIMEOUT   -6   /* a bounded device-side wait (grid barrier) gave up    */
 #define TDMRG_ERR_STATE     -7   /* call out of order (e.g. correlation before prepare)  */
 

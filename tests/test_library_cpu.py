@@ -43,6 +43,15 @@ def test_argument_errors_are_reported(lib):
     with pytest.raises(binding.TdmrgError) as e:
         binding.Model(2, [1.0], [1.0], [4], 1.0)     # N < 3 is rejected before any CUDA call
     assert e.value.code == -1
+    # non-finite parameters (a corrupted configuration) are rejected before any CUDA call
+    for bad in (dict(omega=[float("nan")]), dict(g=[float("inf")]), dict(V=float("nan"))):
+        a = {**dict(N=3, omega=[1.0], g=[1.0], nmax=[4], V=1.0), **bad}
+        with pytest.raises(binding.TdmrgError) as e:
+            binding.Model(a["N"], a["omega"], a["g"], a["nmax"], a["V"])
+        assert e.value.code == -1 and "non-finite" in str(e.value)
+        with pytest.raises(binding.TdmrgError) as e:
+            binding.host_mpo(a["N"], a["omega"], a["g"], a["nmax"], a["V"])
+        assert e.value.code == -1
     # kernel-level entry points check their arguments before touching the device
     rc = lib.tdmrg_kernel_bond_exp(0, 7, None, None, None, None, 0.0, -0.05, 1e-7, 32, None, None)
     assert rc == -1

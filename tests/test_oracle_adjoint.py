@@ -151,3 +151,41 @@ def test_heff_vjp_is_forward_contractions_with_transformed_operands():
     assert np.abs(tdvp.heff(Lh, Wt, Rh, yb, d) - Abar).max() < 1e-12 * np.abs(Abar).max()
     assert np.abs(np.conj(tdvp.update_right(R, yb, W, A, d)) - Lbar).max() < 1e-12 * np.abs(Lbar).max()
     assert np.abs(np.conj(tdvp.update_left(L, yb, W, A, d)) - Rbar).max() < 1e-12 * np.abs(Rbar).max()
+
+
+def test_environment_vjp_is_forward_contractions_with_transformed_operands():
+    """The cotangents of an environment update are forward contractions too, with the
+    cotangent G in place of an environment (per-channel daggers and transposes):
+      left  L' = update_left(L, bra, W, ket):  ketbar = heff(L^dagger, W^T conj, G^T, bra),
+            brabar = heff(L, W, conj G, ket),  Lbar = conj(update_right(conj G, bra, W, ket));
+      right R' = update_right(R, bra, W, ket): ketbar = heff(G^T, W^T conj, R^dagger, bra),
+            brabar = heff(conj G, W, R, ket),  Rbar = conj(update_left(conj G, bra, W, ket)),
+    so a reverse sweep can run on the H_eff and environment kernels alone."""
+    rng = np.random.default_rng(46)
+    Ml, Mr, d, Dl, Dr = 5, 6, 3, 4, 3
+    W = random_mpo_site(rng, Dl, Dr, d) + 0j
+    bra = random_complex(rng, (Ml, d * d, Mr))
+    ket = random_complex(rng, (Ml, d * d, Mr))
+    Wt = np.conj(np.swapaxes(W, 2, 3))
+
+    def dag(E):
+        return np.conj(np.swapaxes(E, 1, 2))
+
+    def tr(E):
+        return np.swapaxes(E, 1, 2)
+
+    def close(a, b):
+        assert np.abs(a - b).max() < 1e-12 * np.abs(b).max()
+
+    L = random_complex(rng, (Dl, Ml, Ml))
+    G = random_complex(rng, (Dr, Mr, Mr))
+    Lb, bb, _, kb = adjoint.update_left_vjp(L, bra, W, ket, d, G)
+    close(tdvp.heff(dag(L), Wt, tr(G), bra, d), kb)
+    close(tdvp.heff(L, W, np.conj(G), ket, d), bb)
+    close(np.conj(tdvp.update_right(np.conj(G), bra, W, ket, d)), Lb)
+    R = random_complex(rng, (Dr, Mr, Mr))
+    G = random_complex(rng, (Dl, Ml, Ml))
+    Rb, bb, _, kb = adjoint.update_right_vjp(R, bra, W, ket, d, G)
+    close(tdvp.heff(tr(G), Wt, dag(R), bra, d), kb)
+    close(tdvp.heff(np.conj(G), W, R, ket, d), bb)
+    close(np.conj(tdvp.update_left(np.conj(G), bra, W, ket, d)), Rb)

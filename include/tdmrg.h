@@ -250,6 +250,57 @@ int tdmrg_kernel_bond_exp_vjp(int M, int Dw, const void* L, const void* R, const
 int tdmrg_kernel_qr_vjp(int m, int n, const void* Q, const void* R, const void* Qbar,
                         const void* Rbar, void* Ybar, void* stream);
 
+/* Vector-Jacobian product of an environment update of the sweep (Eq. S1) -- a building block of
+ * an adjoint of the step (no counterpart in the paper).  side 0 (left):
+ *   E'[v,b,c] = sum conj(bra[a,s,t,b]) E[w,a,y] W[w,v,s,u] ket[y,u,t,c],
+ * E Dl x Ml x Ml, G (the cotangent of E') Dr x Mr x Mr; side 1 (right):
+ *   E'[w,a,y] = sum conj(bra[a,s,t,b]) E[v,b,c] W[w,v,s,u] ket[y,u,t,c],
+ * E Dr x Mr x Mr, G Dl x Ml x Ml.  bra, ket, brabar, ketbar are Ml x d*d x Mr; W_host is the
+ * dense MPO site [Dl][Dr][d][d] (complex interleaved, host).  Writes Ebar (shape of E), brabar,
+ * ketbar (device) with Re<G, dE'> = Re<Ebar, dE> + Re<brabar, dbra> + Re<ketbar, dket>; they are
+ * forward contractions with transformed operands (side 0: ketbar = H_eff(E^dagger, W^T conj,
+ * G^T) bra, brabar = H_eff(E, W, conj G) ket, Ebar = conj(env_right(conj G, bra, W, ket)); side
+ * 1 mirrored).  For nparam derivative sites dW_host[nparam][Dl][Dr][d][d] (host, as
+ * tdmrg_host_mpo_site writes them) it writes theta_bar[p] = Re<G, E'(W -> dW_p)> (host).
+ * X, Y: device workspaces of max(Dl, Dr) * Ml * d*d * Mr complex entries each.  Complex FP64,
+ * row-major, device unless stated; allocates its scratch (freed before return); synchronises
+ * `stream`. */
+int tdmrg_kernel_env_vjp(int side, int Ml, int Mr, int d, int Dl, int Dr, const double* W_host,
+                         int nparam, const double* dW_host, const void* E, const void* bra,
+                         const void* ket, const void* G, void* Ebar, void* brabar, void* ketbar,
+                         double* theta_bar, void* X, void* Y, void* stream);
+
+/* Vector-Jacobian product of the completion candidates of the gauge QR (what H_eff couples a
+ * site into, Eq. S1's projector directions).  side 0 (left-to-right shift):
+ *   X[(x,s,t), (v,c)] = sum L[w,x,y] W[w,v,s,u] A[y,u,t,c],   Ml d^2 rows, Dr Mr columns,
+ * E = L (Dl x Ml x Ml); side 1 (right-to-left shift): X = P^H with
+ *   P[(w,y), (s,t,b)] = sum W[w,v,s,u] A[y,u,t,c] R[v,b,c],   d^2 Mr rows, Dl Ml columns,
+ * E = R (Dr x Mr x Mr).  Xbar (device, rows x columns, row-major) -> Ebar (shape of E) and Abar
+ * (Ml x d*d x Mr) with Re<Xbar, dX> = Re<Ebar, dE> + Re<Abar, dA>, and theta_bar[p] =
+ * Re<Xbar, X(W -> dW_p)> for nparam derivative sites as in tdmrg_kernel_env_vjp.  X, Y as
+ * there.  Complex FP64; allocates its scratch (freed before return); synchronises `stream`. */
+int tdmrg_kernel_expansion_vjp(int side, int Ml, int Mr, int d, int Dl, int Dr,
+                               const double* W_host, int nparam, const double* dW_host,
+                               const void* E, const void* A, const void* Xbar, void* Ebar,
+                               void* Abar, double* theta_bar, void* X, void* Y, void* stream);
+
+/* Vector-Jacobian product of the gauge QR with completed columns (no counterpart in the paper).
+ * accepted[n] (host): 1 for a column that Gram-Schmidt took from Y (positions S), 0 for a
+ * completed one (positions K, R's row zero there).  The completed columns are residuals of the
+ * vectors Xsel (device, m x |K|, in increasing position order) against everything taken before
+ * them, so in the order (S, K) the factorisation is the full-rank QR of Z = [Y_S | Xsel] with
+ * R_Z = triu(Q^H Z), and R_S = Q_S^H Y.  With Qbar (m x n) and Rbar (n x n, rows K and entries
+ * below the diagonal ignored) it writes
+ *   Zbar = full-rank QR VJP of Z for Qbar (Qbar_S + Y Rbar_S^H on the columns S), Rbar_Z = 0,
+ *   Ybar = Q_S Rbar_S + Zbar_S (scattered to S),   Xselbar = Zbar_K   (device),
+ * so that Re<Qbar, dQ> + Re<Rbar_S, dR_S> = Re<Ybar, dY> + Re<Xselbar, dXsel>.  Without
+ * completed columns it equals tdmrg_kernel_qr_vjp (Xsel, Xselbar may then be NULL).  Q, R as
+ * the gauge QR wrote them; complex FP64, row-major; allocates its scratch (freed before
+ * return); synchronises `stream`. */
+int tdmrg_kernel_qr_vjp_completed(int m, int n, const int* accepted, const void* Q, const void* R,
+                                  const void* Xsel, const void* Qbar, const void* Rbar,
+                                  void* Ybar, void* Xselbar, void* stream);
+
 /* Size in floats of the 3xTF32 workspace of tdmrg_kernel_heff (-1 for invalid sizes). */
 long long tdmrg_heff_workspace_floats(int Ml, int Mr, int d, int Dl, int Dr);
 

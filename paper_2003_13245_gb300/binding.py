@@ -69,6 +69,11 @@ _SIGS = {
     "tdmrg_kernel_gauge_qr_noalloc": [_i, _i, _p, _i, _p, _p, _p, _p, _p],
     "tdmrg_kernel_gauge_qr_blocked": [_i, _i, _p, _i, _p, _p, _p, _p, _p],
     "tdmrg_host_mpo_site": [_i, _i, _dp, _dp, _d, _ip, _d, _d, _i, _i, _i, _i, _ip, _dp],
+    "tdmrg_kernel_env_vjp": [_i, _i, _i, _i, _i, _i, _dp, _i, _dp, _p, _p, _p, _p, _p, _p, _p,
+                             _dp, _p, _p, _p],
+    "tdmrg_kernel_expansion_vjp": [_i, _i, _i, _i, _i, _i, _dp, _i, _dp, _p, _p, _p, _p, _p, _dp,
+                                   _p, _p, _p],
+    "tdmrg_kernel_qr_vjp_completed": [_i, _i, _ip, _p, _p, _p, _p, _p, _p, _p, _p],
 }
 
 
@@ -330,6 +335,58 @@ def kernel_bond_exp_vjp(L, R, C, ybar, tau, Cbar, Lbar, Rbar, nodes=16, tol=1e-1
                                             _ptr(ybar), float(np.real(tau)), float(np.imag(tau)),
                                             int(nodes), float(tol), _ptr(Cbar), _ptr(Lbar),
                                             _ptr(Rbar), _stream_ptr(stream)))
+
+
+def _dense_sites(dW, shape):
+    """nparam dense MPO sites as one interleaved FP64 host array (None when there are none)."""
+    if dW is None or len(dW) == 0:
+        return 0, None
+    arr = np.ascontiguousarray(np.stack([np.asarray(x).reshape(shape) for x in dW]),
+                               dtype=np.complex128)
+    return arr.shape[0], arr.view(np.float64)
+
+
+def kernel_env_vjp(side, E, bra, W, ket, G, Ebar, brabar, ketbar, X, Y, d, dW=None,
+                   stream=None):
+    """(Ebar, brabar, ketbar) of an environment update (side 0: left, 1: right) for the
+    cotangent G, written into the given CUDA tensors, and theta_bar[p] = Re<G, update with
+    W -> dW[p]> (returned, numpy); W and dW numpy complex on the host."""
+    lib = load()
+    Ml, _, Mr = bra.shape
+    Dl, Dr = W.shape[0], W.shape[1]
+    Wc = np.ascontiguousarray(W, dtype=np.complex128).view(np.float64)
+    npar, dWc = _dense_sites(dW, W.shape)
+    tb = np.zeros(max(npar, 1))
+    _check(lib.tdmrg_kernel_env_vjp(int(side), Ml, Mr, d, Dl, Dr, _dptr(Wc), npar,
+                                    _dptr(dWc) if dWc is not None else None, _ptr(E), _ptr(bra),
+                                    _ptr(ket), _ptr(G), _ptr(Ebar), _ptr(brabar), _ptr(ketbar),
+                                    _dptr(tb), _ptr(X), _ptr(Y), _stream_ptr(stream)))
+    return tb[:npar]
+
+
+def kernel_expansion_vjp(side, E, W, A, Xbar, Ebar, Abar, X, Y, d, dW=None, stream=None):
+    """(Ebar, Abar) of the gauge-completion candidates (side 0: left_expansion(L, W, A),
+    side 1: right_expansion(W, A, R)) for the cotangent Xbar, and theta_bar (returned)."""
+    lib = load()
+    Ml, _, Mr = A.shape
+    Dl, Dr = W.shape[0], W.shape[1]
+    Wc = np.ascontiguousarray(W, dtype=np.complex128).view(np.float64)
+    npar, dWc = _dense_sites(dW, W.shape)
+    tb = np.zeros(max(npar, 1))
+    _check(lib.tdmrg_kernel_expansion_vjp(int(side), Ml, Mr, d, Dl, Dr, _dptr(Wc), npar,
+                                          _dptr(dWc) if dWc is not None else None, _ptr(E),
+                                          _ptr(A), _ptr(Xbar), _ptr(Ebar), _ptr(Abar), _dptr(tb),
+                                          _ptr(X), _ptr(Y), _stream_ptr(stream)))
+    return tb[:npar]
+
+
+def kernel_qr_vjp_completed(accepted, Q, R, Xsel, Qbar, Rbar, Ybar, Xselbar, stream=None):
+    """(Ybar, Xselbar) of the gauge QR with completed columns (accepted: host flags)."""
+    m, n = Q.shape
+    acc = np.ascontiguousarray(accepted, dtype=np.int32)
+    _check(load().tdmrg_kernel_qr_vjp_completed(int(m), int(n), acc.ctypes.data_as(_ip), _ptr(Q),
+                                                _ptr(R), _ptr(Xsel), _ptr(Qbar), _ptr(Rbar),
+                                                _ptr(Ybar), _ptr(Xselbar), _stream_ptr(stream)))
 
 
 def heff_workspace_floats(Ml, Mr, d, Dl, Dr):

@@ -852,6 +852,296 @@ int tdmrg_kernel_qr_vjp(int m, int n, const void* Q, const void* R, const void* 
   });
 }
 
+}  // extern "C"
+
+namespace {
+using tdmrg::cplx;
+
+tdmrg::MatRef mat(const void* p, long long rs, long long cs, long long sb = 0, long long sr = 0,
+                  int conj = 0) {
+  return tdmrg::MatRef{(const cplx*)p, rs, cs, sb, sr, conj};
+}
+
+// device temporaries of one entry point, freed when it returns
+struct DevBufs {
+  std::vector<void*> p;
+  cplx* get(long long n) {
+    void* q = nullptr;
+    CK(cudaMalloc(&q, sizeof(cplx) * (size_t)(n > 0 ? n : 1)));
+    p.push_back(q);
+    return (cplx*)q;
+  }
+  ~DevBufs() {
+    for (void* q : p) cudaFree(q);
+  }
+};
+
+// op'[s][u] = conj(op[u][s]) for every channel pair of a dense site [Dl][Dr][d][d]
+std::vector<double> transpose_conj_ops(const double* W, int Dl, int Dr, int d) {
+  const int D = d * d;
+  std::vector<double> out((size_t)2 * Dl * Dr * D);
+  for (int b = 0; b < Dl * Dr; ++b)
+    for (int si = 0; si < d; ++si)
+      for (int ui = 0; ui < d; ++ui) {
+        const size_t dst = 2 * ((size_t)b * D + si * d + ui);
+        const size_t src = 2 * ((size_t)b * D + ui * d + si);
+        out[dst] = W[src];
+        out[dst + 1] = -W[src + 1];
+      }
+  return out;
+}
+
+bool any_nonzero(const double* x, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (x[i] != 0.0) return true;
+  return false;
+}
+
+// Re <g, x> = Re sum conj(g_i) x_i: 256 chunk sums by one batched GEMM plus the tail, added
+// on the host in a fixed order.  part: 257 device entries.  Synchronises s.
+double dot_re(const cplx* g, const cplx* x, long long n, cplx* part, cudaStream_t s) {
+  const int B = 256;
+  const long long kc = n / B, rem = n - kc * B;
+  const cplx one = {1.0, 0.0}, zero = {0.0, 0.0};
+  if (kc > 0)
+    CK(tdmrg::zgemm(1, 1, (int)kc, B, 1, one, mat(g, 0, 1, kc, 0, 1), mat(x, 1, 0, kc), zero,
+                    part, 1, 1, nullptr, s));
+  if (rem > 0)
+    CK(tdmrg::zgemm(1, 1, (int)rem, 1, 1, one, mat(g + kc * B, 0, 1, 0, 0, 1),
+                    mat(x + kc * B, 1, 0), zero, part + B, 1, 0, nullptr, s));
+  std::vector<cplx> h(B + 1);
+  CK(cudaMemcpyAsync(h.data(), part, sizeof(cplx) * (B + 1), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  double acc = 0.0;
+  if (kc > 0)
+    for (int b = 0; b < B; ++b) acc += h[b].x;
+  if (rem > 0) acc += h[B].x;
+  return acc;
+}
+}  // namespace
+
+extern "C" {
+
+int tdmrg_kernel_env_vjp(int side, int Ml, int Mr, int d, int Dl, int Dr, const double* W_host,
+                         int nparam, const double* dW_host, const void* E, const void* bra,
+                         const void* ket, const void* G, void* Ebar, void* brabar, void* ketbar,
+                         double* theta_bar, void* X, void* Y, void* stream) {
+  if ((side != 0 && side != 1) || Ml < 1 || Mr < 1 || d < 1 || Dl < 1 || Dr < 1 || !W_host ||
+      nparam < 0 || (nparam > 0 && (!dW_host || !theta_bar)) || !E || !bra || !ket || !G ||
+      !Ebar || !brabar || !ketbar || !X || !Y)
+    return fail(nullptr, TDMRG_ERR_ARG, "env_vjp: bad arguments");
+  return guarded(nullptr, [&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    const int D = d * d;
+    const size_t site = (size_t)Dl * Dr * D;
+    TempMpo W(Dl, Dr, d, W_host);
+    const std::vector<double> Wt = transpose_conj_ops(W_host, Dl, Dr, d);
+    TempMpo Wc(Dl, Dr, d, Wt.data());
+    const int Me = side == 0 ? Ml : Mr, De = side == 0 ? Dl : Dr;   // E (environment in)
+    const int Mg = side == 0 ? Mr : Ml, Dg = side == 0 ? Dr : Dl;   // G (environment out)
+    const long long ne = (long long)De * Me * Me, ng = (long long)Dg * Mg * Mg;
+    DevBufs buf;
+    cplx* Eh = buf.get(ne);     // E^dagger per channel
+    cplx* Gt = buf.get(ng);     // G^T per channel
+    cplx* Gc = buf.get(ng);     // conj G
+    cplx* tmp = buf.get(ng);
+    cplx* part = buf.get(257);
+    for (int w = 0; w < De; ++w)
+      CK(tdmrg::ztranspose(Me, Me, (const cplx*)E + (size_t)w * Me * Me, Eh + (size_t)w * Me * Me,
+                           1, s));
+    for (int w = 0; w < Dg; ++w)
+      CK(tdmrg::ztranspose(Mg, Mg, (const cplx*)G + (size_t)w * Mg * Mg, Gt + (size_t)w * Mg * Mg,
+                           0, s));
+    CK(cudaMemcpyAsync(Gc, G, sizeof(cplx) * (size_t)ng, cudaMemcpyDeviceToDevice, s));
+    CK(tdmrg::zconj(ng, Gc, s));
+    tdmrg::Ctx c{s, (cplx*)X, (cplx*)Y};
+    const cplx* Ed = (const cplx*)E;
+    const cplx* Bd = (const cplx*)bra;
+    const cplx* Kd = (const cplx*)ket;
+    if (side == 0) {
+      // ketbar = H_eff(E^dagger, W^T conj, G^T) bra,  brabar = H_eff(E, W, conj G) ket,
+      // Ebar = conj(env_right(conj G, bra, W, ket))
+      tdmrg::heff_f64(c, Wc.m.s[0], Ml, Mr, D, d, Eh, Gt, Bd, (cplx*)ketbar, nullptr);
+      tdmrg::heff_f64(c, W.m.s[0], Ml, Mr, D, d, Ed, Gc, Kd, (cplx*)brabar, nullptr);
+      tdmrg::env_right_f64(c, W.m.s[0], Ml, Mr, Ml, Mr, D, d, Gc, Bd, Kd, (cplx*)Ebar);
+    } else {
+      // ketbar = H_eff(G^T, W^T conj, E^dagger) bra,  brabar = H_eff(conj G, W, E) ket,
+      // Ebar = conj(env_left(conj G, bra, W, ket))
+      tdmrg::heff_f64(c, Wc.m.s[0], Ml, Mr, D, d, Gt, Eh, Bd, (cplx*)ketbar, nullptr);
+      tdmrg::heff_f64(c, W.m.s[0], Ml, Mr, D, d, Gc, Ed, Kd, (cplx*)brabar, nullptr);
+      tdmrg::env_left_f64(c, W.m.s[0], Ml, Mr, Ml, Mr, D, d, Gc, Bd, Kd, (cplx*)Ebar);
+    }
+    CK(tdmrg::zconj(ne, (cplx*)Ebar, s));
+    // theta_bar[p] = Re <G, update(E, bra, dW_p, ket)>  (the update is linear in W)
+    for (int p = 0; p < nparam; ++p) {
+      const double* dW = dW_host + 2 * site * p;
+      if (!any_nonzero(dW, 2 * site)) {
+        theta_bar[p] = 0.0;
+        continue;
+      }
+      TempMpo dWp(Dl, Dr, d, dW);
+      if (side == 0)
+        tdmrg::env_left_f64(c, dWp.m.s[0], Ml, Mr, Ml, Mr, D, d, Ed, Bd, Kd, tmp);
+      else
+        tdmrg::env_right_f64(c, dWp.m.s[0], Ml, Mr, Ml, Mr, D, d, Ed, Bd, Kd, tmp);
+      theta_bar[p] = dot_re((const cplx*)G, tmp, ng, part, s);
+    }
+    CK(cudaStreamSynchronize(s));
+  });
+}
+
+int tdmrg_kernel_expansion_vjp(int side, int Ml, int Mr, int d, int Dl, int Dr,
+                               const double* W_host, int nparam, const double* dW_host,
+                               const void* E, const void* A, const void* Xbar, void* Ebar,
+                               void* Abar, double* theta_bar, void* X, void* Y, void* stream) {
+  if ((side != 0 && side != 1) || Ml < 1 || Mr < 1 || d < 1 || Dl < 1 || Dr < 1 || !W_host ||
+      nparam < 0 || (nparam > 0 && (!dW_host || !theta_bar)) || !E || !A || !Xbar || !Ebar ||
+      !Abar || !X || !Y)
+    return fail(nullptr, TDMRG_ERR_ARG, "expansion_vjp: bad arguments");
+  return guarded(nullptr, [&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    const int D = d * d;
+    const size_t site = (size_t)Dl * Dr * D;
+    const long long per = (long long)Ml * D * Mr;
+    const int Dmax = Dl > Dr ? Dl : Dr;
+    const std::vector<double> Wt = transpose_conj_ops(W_host, Dl, Dr, d);
+    TempMpo Wc(Dl, Dr, d, Wt.data());
+    DevBufs buf;
+    cplx* Pb = buf.get((long long)Dmax * per);    // Xbar in the channel-major partial layout
+    cplx* Z = buf.get((long long)Dmax * per);
+    cplx* tmp = buf.get((long long)Dmax * per);
+    cplx* part = buf.get(257);
+    tdmrg::Ctx c{s, (cplx*)X, (cplx*)Y};
+    const cplx one = {1.0, 0.0}, zero = {0.0, 0.0};
+    const cplx* Ed = (const cplx*)E;
+    const cplx* Ad = (const cplx*)A;
+    const int np = side == 0 ? Dr : Dl;           // channels of the partial contraction
+    if (side == 0) {
+      // Pb[v][(x,s,t)][c] = Xbar[(x,s,t)][(v,c)]
+      for (int v = 0; v < Dr; ++v)
+        CK(cudaMemcpy2DAsync(Pb + (size_t)v * per, sizeof(cplx) * Mr,
+                             (const cplx*)Xbar + (size_t)v * Mr, sizeof(cplx) * (size_t)Dr * Mr,
+                             sizeof(cplx) * Mr, (size_t)Ml * D, cudaMemcpyDeviceToDevice, s));
+      // Z[w][x][u][t][c] = sum_{v,s} conj(W[w,v,s,u]) Pb[v][x][s][t][c]
+      CK(tdmrg::mpo_mix(Wc.m.s[0].rl, Ml, d, Mr, Pb, per, Z, per, nullptr, s));
+      // Abar[y][(u,t,c)] = sum_{w,x} conj(L[w,x,y]) Z[w][x][(u,t,c)]
+      CK(tdmrg::zgemm(Ml, D * Mr, Ml, 1, Dl, one, mat(Ed, 1, Ml, 0, (long long)Ml * Ml, 1),
+                      mat(Z, (long long)D * Mr, 1, 0, per), zero, (cplx*)Abar, (long long)D * Mr,
+                      0, nullptr, s));
+      // Lbar[w][x][y] = sum_k Z[w][x][k] conj(A[y][k])
+      CK(tdmrg::zgemm(Ml, Ml, D * Mr, Dl, 1, one, mat(Z, (long long)D * Mr, 1, per),
+                      mat(Ad, 1, (long long)D * Mr, 0, 0, 1), zero, (cplx*)Ebar, Ml,
+                      (long long)Ml * Ml, nullptr, s));
+    } else {
+      // Pb[(w,y)][(s,t,b)] = conj(Xbar[(s,t,b)][(w,y)])   (X = P^H)
+      CK(tdmrg::ztranspose(D * Mr, Dl * Ml, (const cplx*)Xbar, Pb, 1, s));
+      // Z[v][y][u][t][b] = sum_{w,s} conj(W[w,v,s,u]) Pb[w][y][s][t][b]
+      CK(tdmrg::mpo_mix(Wc.m.s[0].lr, Ml, d, Mr, Pb, per, Z, per, nullptr, s));
+      // Abar[(y,u,t)][c] = sum_{v,b} Z[v][(y,u,t)][b] conj(R[v][b][c])
+      CK(tdmrg::zgemm(Ml * D, Mr, Mr, 1, Dr, one, mat(Z, Mr, 1, 0, per),
+                      mat(Ed, Mr, 1, 0, (long long)Mr * Mr, 1), zero, (cplx*)Abar, Mr, 0,
+                      nullptr, s));
+      // Rbar[v][b][c] = sum_k Z[v][k][b] conj(A[k][c])
+      CK(tdmrg::zgemm(Mr, Mr, Ml * D, Dr, 1, one, mat(Z, 1, Mr, per), mat(Ad, Mr, 1, 0, 0, 1),
+                      zero, (cplx*)Ebar, Mr, (long long)Mr * Mr, nullptr, s));
+    }
+    // theta_bar[p] = Re <Pb, partial(E, dW_p, A)>  (the candidates are linear in W)
+    for (int p = 0; p < nparam; ++p) {
+      const double* dW = dW_host + 2 * site * p;
+      if (!any_nonzero(dW, 2 * site)) {
+        theta_bar[p] = 0.0;
+        continue;
+      }
+      TempMpo dWp(Dl, Dr, d, dW);
+      if (side == 0)
+        tdmrg::left_partial_f64(c, dWp.m.s[0], Ml, Ml, D, d, Mr, Ed, Ad, tmp, nullptr);
+      else
+        tdmrg::right_partial_f64(c, dWp.m.s[0], Ml, D, d, Mr, Mr, Ed, Ad, tmp, nullptr);
+      theta_bar[p] = dot_re(Pb, tmp, (long long)np * per, part, s);
+    }
+    CK(cudaStreamSynchronize(s));
+  });
+}
+
+int tdmrg_kernel_qr_vjp_completed(int m, int n, const int* accepted, const void* Q, const void* R,
+                                  const void* Xsel, const void* Qbar, const void* Rbar,
+                                  void* Ybar, void* Xselbar, void* stream) {
+  if (m < 1 || n < 1 || m < n || !accepted || !Q || !R || !Qbar || !Rbar || !Ybar)
+    return fail(nullptr, TDMRG_ERR_ARG, "qr_vjp_completed: need m >= n >= 1 and non-NULL buffers");
+  std::vector<int> S, K;
+  for (int j = 0; j < n; ++j) (accepted[j] ? S : K).push_back(j);
+  const int ns = (int)S.size(), nk = (int)K.size();
+  if (nk > 0 && (!Xsel || !Xselbar))
+    return fail(nullptr, TDMRG_ERR_ARG, "qr_vjp_completed: completed columns need Xsel, Xselbar");
+  return guarded(nullptr, [&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    const cplx one = {1.0, 0.0}, mone = {-1.0, 0.0}, zero = {0.0, 0.0};
+    const size_t cb = sizeof(cplx);
+    const cudaMemcpyKind dd = cudaMemcpyDeviceToDevice;
+    std::vector<int> order(S);
+    order.insert(order.end(), K.begin(), K.end());
+    const long long mn = (long long)m * n, nn = (long long)n * n;
+    DevBufs buf;
+    cplx* Qp = buf.get(mn);
+    cplx* Z = buf.get(mn);
+    cplx* Yr = buf.get(mn);
+    cplx* Qbp = buf.get(mn);
+    cplx* rhs = buf.get(mn);
+    cplx* Zb = buf.get(mn);
+    cplx* T = buf.get(mn);
+    cplx* Rp = buf.get(nn);
+    cplx* Rb = buf.get(nn);
+    cplx* Mt = buf.get(nn);
+    cplx* Sh = buf.get(nn);
+    cplx* RS = buf.get((long long)(ns > 0 ? ns : 1) * n);
+    cplx* RbS = buf.get((long long)(ns > 0 ? ns : 1) * n);
+    // column scol of a row-major matrix with leading dimension sld -> column dcol of dst
+    auto col = [&](cplx* dst, long long dld, int dcol, const void* src, long long sld, int scol) {
+      CK(cudaMemcpy2DAsync(dst + dcol, cb * dld, (const cplx*)src + scol, cb * sld, cb, (size_t)m,
+                           dd, s));
+    };
+    // processing order: accepted columns S, then completed columns K
+    for (int i = 0; i < n; ++i) col(Qp, n, i, Q, n, order[i]);
+    for (int i = 0; i < n; ++i) col(Qbp, n, i, Qbar, n, order[i]);
+    CK(cudaMemcpyAsync(Rb, Rbar, cb * (size_t)nn, dd, s));
+    CK(tdmrg::triu_inplace(n, Rb, s));
+    for (int i = 0; i < ns; ++i) {
+      CK(cudaMemcpyAsync(RS + (size_t)i * n, (const cplx*)R + (size_t)S[i] * n, cb * n, dd, s));
+      CK(cudaMemcpyAsync(RbS + (size_t)i * n, Rb + (size_t)S[i] * n, cb * n, dd, s));
+    }
+    // the factorised matrix Y = Q_S R_S, and Z = [Y_S | Xsel]
+    CK(tdmrg::zgemm(m, n, ns, 1, 1, one, mat(Qp, n, 1), mat(RS, n, 1), zero, Yr, n, 0, nullptr, s));
+    for (int i = 0; i < ns; ++i) col(Z, n, i, Yr, n, S[i]);
+    for (int i = 0; i < nk; ++i) col(Z, n, ns + i, Xsel, nk, i);
+    // R_Z = triu(Qp^H Z) with its accepted block taken from R
+    CK(tdmrg::zgemm(n, n, m, 1, 1, one, mat(Qp, 1, n, 0, 0, 1), mat(Z, n, 1), zero, Rp, n, 0,
+                    nullptr, s));
+    CK(tdmrg::triu_inplace(n, Rp, s));
+    for (int j = 0; j < ns; ++j)
+      CK(cudaMemcpy2DAsync(Rp + j, cb * n, RS + S[j], cb * n, cb, (size_t)ns, dd, s));
+    // Qbar_S += Y Rbar_S^H  (the R_S = Q_S^H Y term)
+    if (ns > 0)
+      CK(tdmrg::zgemm(m, ns, n, 1, 1, one, mat(Yr, n, 1), mat(RbS, 1, n, 0, 0, 1), one, Qbp, n, 0,
+                      nullptr, s));
+    // Zbar = full-rank QR VJP of Z = Qp R_Z with Rbar_Z = 0:
+    //   M = -Qbp^H Qp, S = Hermitian fold of M, Zbar R_Z^H = Qbp + Qp S
+    CK(tdmrg::zgemm(n, n, m, 1, 1, mone, mat(Qbp, 1, n, 0, 0, 1), mat(Qp, n, 1), zero, Mt, n, 0,
+                    nullptr, s));
+    CK(tdmrg::herm_lower(n, Mt, Sh, s));
+    CK(cudaMemcpyAsync(rhs, Qbp, cb * (size_t)mn, dd, s));
+    CK(tdmrg::zgemm(m, n, n, 1, 1, one, mat(Qp, n, 1), mat(Sh, n, 1), one, rhs, n, 0, nullptr, s));
+    CK(tdmrg::solve_rh(m, n, Rp, rhs, Zb, s));
+    // Ybar = Q_S Rbar_S + Zbar_S scattered to the positions S;  Xselbar = Zbar_K
+    CK(tdmrg::zgemm(m, n, ns, 1, 1, one, mat(Qp, n, 1), mat(RbS, n, 1), zero, (cplx*)Ybar, n, 0,
+                    nullptr, s));
+    CK(cudaMemsetAsync(T, 0, cb * (size_t)mn, s));
+    for (int i = 0; i < ns; ++i) col(T, n, S[i], Zb, n, i);
+    CK(tdmrg::zaxpy(mn, one, T, (cplx*)Ybar, s));
+    for (int i = 0; i < nk; ++i) col((cplx*)Xselbar, nk, i, Zb, n, ns + i);
+    CK(cudaStreamSynchronize(s));
+  });
+}
+
 int tdmrg_kernel_krylov_dense(int n, const void* H, const void* v, void* out, double tau_re,
                               double tau_im, double tol, int kmax, int* kused, void* stream) {
   if (n < 1 || !H || !v || !out || kmax < 1 || kmax > tdmrg::KMAX || !(tol > 0.0))

@@ -725,3 +725,17 @@ def correlation_pipeline_gradient(model, beta, dtau, M, dt, nsteps, cbar, mpo_h,
     gH = step_parameter_gradient(model, Wb, mpo_h)
     gJ = step_parameter_gradient(model, Wjb, mpo_j)
     return C, {p: gH[p] + gJ[p] for p in gH}
+
+
+def mobility_pipeline_gradient(model, kT, dtau, M, dt, nsteps, mpo_h, mpo_j, every=2,
+                               tol=1e-14, rank_tol=RANK_TOL):
+    """mu of Eq. 2 from the oracle pipeline's C_n (t_n = n dt, n <= nsteps; trapezoid, cut off
+    at nsteps dt) and dmu/dtheta.  mu = (1 / 2kT) 2 int_0^{t_max} Re C dt is linear in Re C_n,
+    mu = sum_n w_n Re C_n with w_n = dt / kT (half at both ends), so dmu/dtheta is the
+    pipeline gradient for the real cotangent cbar_n = w_n."""
+    w = np.full(nsteps + 1, dt / kT)
+    w[0] *= 0.5
+    w[-1] *= 0.5
+    C, g = correlation_pipeline_gradient(model, 1.0 / kT, dtau, M, dt, nsteps, w + 0j, mpo_h,
+                                         mpo_j, every, tol, rank_tol)
+    return float(np.sum(w * C.real)), g

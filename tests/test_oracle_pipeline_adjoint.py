@@ -14,6 +14,9 @@ fit of j|Psi_beta>, both real-time evolutions and the overlaps of Eq. 6, reverse
   derivatives of dense exponentials) - an independent pin of the whole chain.  Bounds: C to
   1e-8 (measured 5e-10: residuals below 1e-8 dropped per gauge QR), the gradient to 1e-6
   relative (measured 5e-8).
+* Mobility and isotope derivative: mu of Eq. 2 and dmu/dtheta from the pipeline (cotangent =
+  the trapezoid weights), and dmu/dm for omega ~ m^{-1/2} at fixed g^2 omega, against exact
+  diagonalisation at full bond dimension.
 """
 import numpy as np
 
@@ -112,3 +115,27 @@ def test_full_bond_pipeline_gradient_equals_exact():
     assert np.abs(C - Cex).max() <= 1e-8 * np.abs(Cex).max()
     for p in gradient.parameters(model):
         _close(g[p], float(np.sum(np.conj(cbar) * G[p]).real), 1e-6)
+
+
+def test_mobility_and_isotope_derivative_equal_exact():
+    """mu (Eq. 2, trapezoid cut off at t_max) and its derivatives from the TD-DMRG pipeline at
+    full bond dimension (rank threshold 1e-8) equal exact diagonalisation, and so does the
+    isotope derivative dmu/dm for omega ~ m^{-1/2} at fixed g^2 omega (the chain rule
+    dmu/dm = -omega/2 dmu/domega + g/4 dmu/dg at m = 1)."""
+    from oracle import kubo
+    model = HolsteinModel(N=3, omega=[1.0], g=[0.7], nmax=[2], V=0.8)
+    kT, dt, ns = 5.0, 0.1, 3
+    mu, g = adjoint.mobility_pipeline_gradient(model, kT, 0.05, 64, dt, ns, mpo_hamiltonian,
+                                               mpo_current, rank_tol=1e-8)
+    t = np.arange(ns + 1) * dt
+    mu_ex, g_ex = gradient.mobility_gradient(model, kT, t)
+    Cex, _ = gradient.correlation_gradient(model, 1.0 / kT, t)
+    assert abs(mu_ex - kubo.mobility(t, Cex, kT)) < 1e-15
+    _close(mu, mu_ex, 1e-8)
+    # the rank threshold drops residuals of absolute size, so the components are bounded
+    # against the size of the whole gradient (measured: at most 1.9e-9 on a gradient of 0.23)
+    scale = max(abs(x) for x in g_ex.values())
+    for p in gradient.parameters(model):
+        assert abs(g[p] - g_ex[p]) <= 1e-6 * scale, p
+    iso, iso_ex = gradient.isotope_derivative(model, g), gradient.isotope_derivative(model, g_ex)
+    assert abs(iso - iso_ex) <= 1e-6 * scale

@@ -133,6 +133,27 @@ int tdmrg_realtime_observe(tdmrg_model* h, double* C_out, double* obs);
  * t_grid[nt], C[2*nt] host; pure host arithmetic, no handle needed. */
 int tdmrg_mobility(const double* t_grid, const double* C, int nt, double kT, double* mu_out);
 
+/* Number of model parameters theta (omega_m, g_m, V, then alpha, omega_p with a bond mode), the
+ * numbering of tdmrg_host_mpo_site and of the parameter cotangents below. */
+int tdmrg_parameter_count(const tdmrg_model* h, int* count);
+
+/* Reverse of one second-order projector-splitting step exp(tau H) (Eq. S1) in complex FP64
+ * (needs TDMRG_PREC_C128; no counterpart in the paper: a building block of the adjoint).
+ * The MPS has the bond dimensions tdmrg_thermal_prepare uses for M; A_in[L] are device pointers
+ * to its site tensors (Ml x d*d x Mr, sites 1.. right-orthonormal, the center at site 0, as the
+ * library's states are between steps).  The step is run again with its intermediates kept on
+ * the device, then reversed: with Abar_out[L] (device) the cotangents of the output sites it
+ * writes Abar_in[L] (device) and theta_bar[count] (host, tdmrg_parameter_count numbering) such
+ * that Re sum_k <Abar_out_k, dA_out_k> = Re sum_k <Abar_in_k, dA_in_k> + sum_p theta_bar_p
+ * dtheta_p, and the output sites to A_out[L] if A_out is not NULL.  The step is the one without
+ * renormalisation (imaginary time included); completed gauge columns follow their coupling
+ * candidates.  nodes: Gauss-Legendre nodes of the exponential VJPs (16 is rounding-accurate
+ * for |tau| times the spectral spread <= 5).  Allocates its tape (freed before return);
+ * synchronises the handle's stream. */
+int tdmrg_step_vjp(tdmrg_model* h, int M, const void* const* A_in, double tau_re, double tau_im,
+                   const void* const* Abar_out, void* const* A_out, void* const* Abar_in,
+                   double* theta_bar, int nodes);
+
 /* One site of an MPO of the chain, dense, built on the host (no handle, no GPU): the chain of
  * tdmrg_model_create (same arguments and checks) with, when nmax_p != 0, the bond mode of
  * tdmrg_model_set_peierls (alpha, omega_p, nmax_p in [2, 32]).  which: TDMRG_MPO_H (Eq. 1 /
@@ -225,6 +246,16 @@ int tdmrg_kernel_site_exp_vjp(int Ml, int Mr, int d, int Dl, int Dr, const doubl
                               const void* L, const void* R, const void* A, const void* ybar,
                               double tau_re, double tau_im, int nodes, double tol, void* Abar,
                               void* Lbar, void* Rbar, void* stream);
+
+/* tdmrg_kernel_site_exp_vjp plus parameter cotangents: for nparam derivative sites
+ * dW_host[nparam][Dl][Dr][d][d] (host, as tdmrg_host_mpo_site writes them) it also writes
+ * theta_bar[p] = Re<Hbar, H_eff(L, dW_p, R)> (host), Hbar the cotangent of the operator from the
+ * same quadrature; nparam = 0 is tdmrg_kernel_site_exp_vjp. */
+int tdmrg_kernel_site_exp_vjp_theta(int Ml, int Mr, int d, int Dl, int Dr, const double* W_host,
+                                    const void* L, const void* R, const void* A,
+                                    const void* ybar, double tau_re, double tau_im, int nodes,
+                                    double tol, int nparam, const double* dW_host, void* Abar,
+                                    void* Lbar, void* Rbar, double* theta_bar, void* stream);
 
 /* Vector-Jacobian product of the bond exponential of the projector-splitting step (Eq. S1,
  * zero-site term), y = exp(tau K) C with (K C)[a][b] = sum_w sum L[w][a][a'] C[a'][b']

@@ -32,6 +32,7 @@ _i = ctypes.c_int
 _p = ctypes.c_void_p
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
+_pp = ctypes.POINTER(ctypes.c_void_p)
 
 _SIGS = {
     "tdmrg_model_create": [_i, _i, _dp, _dp, _d, _ip, ctypes.POINTER(_p)],
@@ -74,6 +75,10 @@ _SIGS = {
     "tdmrg_kernel_expansion_vjp": [_i, _i, _i, _i, _i, _i, _dp, _i, _dp, _p, _p, _p, _p, _p, _dp,
                                    _p, _p, _p],
     "tdmrg_kernel_qr_vjp_completed": [_i, _i, _ip, _p, _p, _p, _p, _p, _p, _p, _p],
+    "tdmrg_kernel_site_exp_vjp_theta": [_i, _i, _i, _i, _i, _dp, _p, _p, _p, _p, _d, _d, _i, _d,
+                                        _i, _dp, _p, _p, _p, _dp, _p],
+    "tdmrg_parameter_count": [_p, _ip],
+    "tdmrg_step_vjp": [_p, _i, _pp, _d, _d, _pp, _pp, _pp, _dp, _i],
 }
 
 
@@ -206,6 +211,27 @@ class Model:
 
     def set_profiling(self, on=True):
         _check(self._lib.tdmrg_model_set_profiling(self._h, int(bool(on))), self._h)
+
+    def parameter_count(self):
+        """Number of parameters theta (omega_m, g_m, V, then alpha, omega_p with a bond mode)."""
+        n = ctypes.c_int()
+        _check(self._lib.tdmrg_parameter_count(self._h, ctypes.byref(n)), self._h)
+        return n.value
+
+    def step_vjp(self, M, A_in, tau, Abar_out, nodes=16):
+        """Reverse of one FP64 projector-splitting step exp(tau H) through tdmrg_step_vjp: the
+        site tensors A_in and the cotangents Abar_out of the output sites (lists of complex128
+        CUDA tensors) -> (A_out, Abar_in, theta_bar)."""
+        import torch
+        L = len(A_in)
+        A_out = [torch.empty_like(a) for a in A_in]
+        Abar_in = [torch.empty_like(a) for a in A_in]
+        arr = lambda ts: (ctypes.c_void_p * L)(*[t.data_ptr() for t in ts])   # noqa: E731
+        tb = np.zeros(self.parameter_count())
+        _check(self._lib.tdmrg_step_vjp(self._h, int(M), arr(A_in), float(np.real(tau)),
+                                        float(np.imag(tau)), arr(Abar_out), arr(A_out),
+                                        arr(Abar_in), _dptr(tb), int(nodes)), self._h)
+        return A_out, Abar_in, tb
 
     def reset_stats(self):
         _check(self._lib.tdmrg_reset_stats(self._h), self._h)

@@ -81,6 +81,80 @@ struct TempMpo {
   ~TempMpo() { Engine::free_mpo(m); }
 };
 
+using tdmrg::cplx;
+
+tdmrg::MatRef mat(const void* p, long long rs, long long cs, long long sb = 0, long long sr = 0,
+                  int conj = 0) {
+  return tdmrg::MatRef{(const cplx*)p, rs, cs, sb, sr, conj};
+}
+
+// device temporaries of one entry point, freed when it returns
+struct DevBufs {
+  std::vector<void*> p;
+  cplx* get(long long n) {
+    void* q = nullptr;
+    CK(cudaMalloc(&q, sizeof(cplx) * (size_t)(n > 0 ? n : 1)));
+    p.push_back(q);
+    return (cplx*)q;
+  }
+  ~DevBufs() {
+    for (void* q : p) cudaFree(q);
+  }
+};
+
+// op'[s][u] = conj(op[u][s]) for every channel pair of a dense site [Dl][Dr][d][d]
+std::vector<double> transpose_conj_ops(const double* W, int Dl, int Dr, int d) {
+  const int D = d * d;
+  std::vector<double> out((size_t)2 * Dl * Dr * D);
+  for (int b = 0; b < Dl * Dr; ++b)
+    for (int si = 0; si < d; ++si)
+      for (int ui = 0; ui < d; ++ui) {
+        const size_t dst = 2 * ((size_t)b * D + si * d + ui);
+        const size_t src = 2 * ((size_t)b * D + ui * d + si);
+        out[dst] = W[src];
+        out[dst + 1] = -W[src + 1];
+      }
+  return out;
+}
+
+bool any_nonzero(const double* x, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (x[i] != 0.0) return true;
+  return false;
+}
+
+// <g, x> = sum conj(g_i) x_i: 256 chunk sums by one batched GEMM plus the tail, added on the
+// host in a fixed order.  part: 257 device entries.  Synchronises s.
+cplx dot_c(const cplx* g, const cplx* x, long long n, cplx* part, cudaStream_t s) {
+  const int B = 256;
+  const long long kc = n / B, rem = n - kc * B;
+  const cplx one = {1.0, 0.0}, zero = {0.0, 0.0};
+  if (kc > 0)
+    CK(tdmrg::zgemm(1, 1, (int)kc, B, 1, one, mat(g, 0, 1, kc, 0, 1), mat(x, 1, 0, kc), zero,
+                    part, 1, 1, nullptr, s));
+  if (rem > 0)
+    CK(tdmrg::zgemm(1, 1, (int)rem, 1, 1, one, mat(g + kc * B, 0, 1, 0, 0, 1),
+                    mat(x + kc * B, 1, 0), zero, part + B, 1, 0, nullptr, s));
+  std::vector<cplx> h(B + 1);
+  CK(cudaMemcpyAsync(h.data(), part, sizeof(cplx) * (B + 1), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  cplx acc = {0.0, 0.0};
+  if (kc > 0)
+    for (int b = 0; b < B; ++b) {
+      acc.x += h[b].x;
+      acc.y += h[b].y;
+    }
+  if (rem > 0) {
+    acc.x += h[B].x;
+    acc.y += h[B].y;
+  }
+  return acc;
+}
+
+double dot_re(const cplx* g, const cplx* x, long long n, cplx* part, cudaStream_t s) {
+  return dot_c(g, x, n, part, s).x;
+}
+
 // the chain of Eq. 1 from the arguments of tdmrg_model_create; nullptr or the failed check
 const char* fill_params(int N, int modes, const double* omega, const double* g, double V,
                         const int* nmax, tdmrg::ModelParams& P) {
@@ -330,6 +404,25 @@ int tdmrg_host_mpo_site(int N, int modes, const double* omega, const double* g, 
         W_out[off] += b.op[e].real();
         W_out[off + 1] += b.op[e].imag();
       }
+  });
+}
+
+int tdmrg_parameter_count(const tdmrg_model* h, int* count) {
+  if (!h || !count) return fail(nullptr, TDMRG_ERR_ARG, "parameter_count: NULL argument");
+  *count = tdmrg::parameter_count(h->eng->P);
+  return TDMRG_OK;
+}
+
+int tdmrg_step_vjp(tdmrg_model* h, int M, const void* const* A_in, double tau_re, double tau_im,
+                   const void* const* Abar_out, void* const* A_out, void* const* Abar_in,
+                   double* theta_bar, int nodes) {
+  if (!h) return fail(nullptr, TDMRG_ERR_ARG, "NULL handle");
+  if (M < 1 || !A_in || !Abar_out || !Abar_in || !theta_bar || nodes < 1 || nodes > 64)
+    return fail(h, TDMRG_ERR_ARG, "step_vjp: bad arguments");
+  return guarded(h, [&] {
+    h->eng->step_vjp(M, (const tdmrg::cplx* const*)A_in, tau_re, tau_im,
+                     (const tdmrg::cplx* const*)Abar_out, (tdmrg::cplx* const*)A_out,
+                     (tdmrg::cplx* const*)Abar_in, theta_bar, nodes);
   });
 }
 
@@ -684,41 +777,47 @@ void gauss_legendre01(int n, std::vector<double>& s, std::vector<double>& w) {
 }
 }  // namespace
 
-int tdmrg_kernel_site_exp_vjp(int Ml, int Mr, int d, int Dl, int Dr, const double* W_host,
-                              const void* L, const void* R, const void* A, const void* ybar,
-                              double tau_re, double tau_im, int nodes, double tol, void* Abar,
-                              void* Lbar, void* Rbar, void* stream) {
+}  // extern "C"
+
+namespace {
+// exp(tau H_eff) VJP with, for nparam derivative sites, theta_bar[p] = Re<Hbar, H_eff(dW_p)>
+int site_exp_vjp_impl(int Ml, int Mr, int d, int Dl, int Dr, const double* W_host, const void* L,
+                      const void* R, const void* A, const void* ybar, double tau_re,
+                      double tau_im, int nodes, double tol, int nparam, const double* dW_host,
+                      void* Abar, void* Lbar, void* Rbar, double* theta_bar, void* stream) {
   if (Ml < 1 || Mr < 1 || d < 1 || Dl < 1 || Dr < 1 || !W_host || !L || !R || !A || !ybar ||
-      !Abar || !Lbar || !Rbar || nodes < 1 || nodes > 64 || !(tol > 0.0))
+      !Abar || !Lbar || !Rbar || nodes < 1 || nodes > 64 || !(tol > 0.0) || nparam < 0 ||
+      (nparam > 0 && (!dW_host || !theta_bar)))
     return fail(nullptr, TDMRG_ERR_ARG, "site_exp_vjp: bad arguments");
   return guarded(nullptr, [&] {
-    using tdmrg::cplx;
     cudaStream_t s = (cudaStream_t)stream;
     const int D = d * d;
+    const size_t site = (size_t)Dl * Dr * D;
     const long long n = (long long)Ml * D * Mr;
     const long long nl = (long long)Dl * Ml * Ml, nr = (long long)Dr * Mr * Mr;
     TempMpo W(Dl, Dr, d, W_host);
+    std::vector<std::unique_ptr<TempMpo>> dWs(nparam);
+    for (int p = 0; p < nparam; ++p) {
+      theta_bar[p] = 0.0;
+      if (any_nonzero(dW_host + 2 * site * p, 2 * site))
+        dWs[p].reset(new TempMpo(Dl, Dr, d, dW_host + 2 * site * p));
+    }
     tdmrg::ModelParams P;
     P.N = 3;
     Engine eng(P);
     eng.set_stream(s);
     eng.set_krylov(tol, tdmrg::KMAX, 0);
     eng.ensure_workspace(n, n, 1, 1);
-    cplx *X = nullptr, *Y = nullptr, *a = nullptr, *b = nullptr, *El = nullptr, *Er = nullptr;
-    struct Free {
-      cplx** p[6];
-      ~Free() {
-        for (auto q : p)
-          if (*q) cudaFree(*q);
-      }
-    } fr{{&X, &Y, &a, &b, &El, &Er}};
     const long long xy = (long long)std::max(Dl, Dr) * n;
-    CK(cudaMalloc(&X, sizeof(cplx) * (size_t)xy));
-    CK(cudaMalloc(&Y, sizeof(cplx) * (size_t)xy));
-    CK(cudaMalloc(&a, sizeof(cplx) * (size_t)n));
-    CK(cudaMalloc(&b, sizeof(cplx) * (size_t)n));
-    CK(cudaMalloc(&El, sizeof(cplx) * (size_t)nl));
-    CK(cudaMalloc(&Er, sizeof(cplx) * (size_t)nr));
+    DevBufs buf;
+    cplx* X = buf.get(xy);
+    cplx* Y = buf.get(xy);
+    cplx* a = buf.get(n);
+    cplx* b = buf.get(n);
+    cplx* El = buf.get(nl);
+    cplx* Er = buf.get(nr);
+    cplx* t = nparam > 0 ? buf.get(n) : nullptr;
+    cplx* part = nparam > 0 ? buf.get(257) : nullptr;
     tdmrg::Ctx c{s, X, Y};
     const cplx* Ld = (const cplx*)L;
     const cplx* Rd = (const cplx*)R;
@@ -730,7 +829,8 @@ int tdmrg_kernel_site_exp_vjp(int Ml, int Mr, int d, int Dl, int Dr, const doubl
     // Hbar = conj(tau) int_0^1 a(s) b(s)^H ds, a(s) = e^{(1-s) conj(tau) H} ybar,
     // b(s) = e^{s tau H} A; its L and R parts are conjugated environment updates with a(s)
     // as bra and b(s) as ket: Lbar = conj(sum_s conj(k_s) env_right(R, a_s, W, b_s)),
-    // k_s = w_s conj(tau), and the same for Rbar with env_left.
+    // k_s = w_s conj(tau), and the same for Rbar with env_left.  A parameter enters through
+    // W only: theta_bar = sum_s Re(conj(k_s) <a_s, H_eff(dW) b_s>).
     CK(cudaMemsetAsync(Lbar, 0, sizeof(cplx) * (size_t)nl, s));
     CK(cudaMemsetAsync(Rbar, 0, sizeof(cplx) * (size_t)nr, s));
     std::vector<double> sn, wn;
@@ -743,11 +843,37 @@ int tdmrg_kernel_site_exp_vjp(int Ml, int Mr, int d, int Dl, int Dr, const doubl
       CK(tdmrg::zaxpy(nl, kc, El, (cplx*)Lbar, s));
       tdmrg::env_left_f64(c, W.m.s[0], Ml, Mr, Ml, Mr, D, d, Ld, a, b, Er);
       CK(tdmrg::zaxpy(nr, kc, Er, (cplx*)Rbar, s));
+      for (int p = 0; p < nparam; ++p) {
+        if (!dWs[p]) continue;
+        tdmrg::heff_f64(c, dWs[p]->m.s[0], Ml, Mr, D, d, Ld, Rd, b, t, nullptr);
+        const cplx z = dot_c(a, t, n, part, s);
+        theta_bar[p] += kc.x * z.x - kc.y * z.y;
+      }
     }
     CK(tdmrg::zconj(nl, (cplx*)Lbar, s));
     CK(tdmrg::zconj(nr, (cplx*)Rbar, s));
     eng.sync_and_check();
   });
+}
+}  // namespace
+
+extern "C" {
+
+int tdmrg_kernel_site_exp_vjp(int Ml, int Mr, int d, int Dl, int Dr, const double* W_host,
+                              const void* L, const void* R, const void* A, const void* ybar,
+                              double tau_re, double tau_im, int nodes, double tol, void* Abar,
+                              void* Lbar, void* Rbar, void* stream) {
+  return site_exp_vjp_impl(Ml, Mr, d, Dl, Dr, W_host, L, R, A, ybar, tau_re, tau_im, nodes, tol,
+                           0, nullptr, Abar, Lbar, Rbar, nullptr, stream);
+}
+
+int tdmrg_kernel_site_exp_vjp_theta(int Ml, int Mr, int d, int Dl, int Dr, const double* W_host,
+                                    const void* L, const void* R, const void* A,
+                                    const void* ybar, double tau_re, double tau_im, int nodes,
+                                    double tol, int nparam, const double* dW_host, void* Abar,
+                                    void* Lbar, void* Rbar, double* theta_bar, void* stream) {
+  return site_exp_vjp_impl(Ml, Mr, d, Dl, Dr, W_host, L, R, A, ybar, tau_re, tau_im, nodes, tol,
+                           nparam, dW_host, Abar, Lbar, Rbar, theta_bar, stream);
 }
 
 int tdmrg_kernel_bond_exp_vjp(int M, int Dw, const void* L, const void* R, const void* C,
@@ -851,76 +977,6 @@ int tdmrg_kernel_qr_vjp(int m, int n, const void* Q, const void* R, const void* 
     CK(cudaStreamSynchronize(s));
   });
 }
-
-}  // extern "C"
-
-namespace {
-using tdmrg::cplx;
-
-tdmrg::MatRef mat(const void* p, long long rs, long long cs, long long sb = 0, long long sr = 0,
-                  int conj = 0) {
-  return tdmrg::MatRef{(const cplx*)p, rs, cs, sb, sr, conj};
-}
-
-// device temporaries of one entry point, freed when it returns
-struct DevBufs {
-  std::vector<void*> p;
-  cplx* get(long long n) {
-    void* q = nullptr;
-    CK(cudaMalloc(&q, sizeof(cplx) * (size_t)(n > 0 ? n : 1)));
-    p.push_back(q);
-    return (cplx*)q;
-  }
-  ~DevBufs() {
-    for (void* q : p) cudaFree(q);
-  }
-};
-
-// op'[s][u] = conj(op[u][s]) for every channel pair of a dense site [Dl][Dr][d][d]
-std::vector<double> transpose_conj_ops(const double* W, int Dl, int Dr, int d) {
-  const int D = d * d;
-  std::vector<double> out((size_t)2 * Dl * Dr * D);
-  for (int b = 0; b < Dl * Dr; ++b)
-    for (int si = 0; si < d; ++si)
-      for (int ui = 0; ui < d; ++ui) {
-        const size_t dst = 2 * ((size_t)b * D + si * d + ui);
-        const size_t src = 2 * ((size_t)b * D + ui * d + si);
-        out[dst] = W[src];
-        out[dst + 1] = -W[src + 1];
-      }
-  return out;
-}
-
-bool any_nonzero(const double* x, size_t n) {
-  for (size_t i = 0; i < n; ++i)
-    if (x[i] != 0.0) return true;
-  return false;
-}
-
-// Re <g, x> = Re sum conj(g_i) x_i: 256 chunk sums by one batched GEMM plus the tail, added
-// on the host in a fixed order.  part: 257 device entries.  Synchronises s.
-double dot_re(const cplx* g, const cplx* x, long long n, cplx* part, cudaStream_t s) {
-  const int B = 256;
-  const long long kc = n / B, rem = n - kc * B;
-  const cplx one = {1.0, 0.0}, zero = {0.0, 0.0};
-  if (kc > 0)
-    CK(tdmrg::zgemm(1, 1, (int)kc, B, 1, one, mat(g, 0, 1, kc, 0, 1), mat(x, 1, 0, kc), zero,
-                    part, 1, 1, nullptr, s));
-  if (rem > 0)
-    CK(tdmrg::zgemm(1, 1, (int)rem, 1, 1, one, mat(g + kc * B, 0, 1, 0, 0, 1),
-                    mat(x + kc * B, 1, 0), zero, part + B, 1, 0, nullptr, s));
-  std::vector<cplx> h(B + 1);
-  CK(cudaMemcpyAsync(h.data(), part, sizeof(cplx) * (B + 1), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  double acc = 0.0;
-  if (kc > 0)
-    for (int b = 0; b < B; ++b) acc += h[b].x;
-  if (rem > 0) acc += h[B].x;
-  return acc;
-}
-}  // namespace
-
-extern "C" {
 
 int tdmrg_kernel_env_vjp(int side, int Ml, int Mr, int d, int Dl, int Dr, const double* W_host,
                          int nparam, const double* dW_host, const void* E, const void* bra,

@@ -762,7 +762,7 @@ void Engine::check_status() {
 
 // Every gauge QR outside a graph capture is bracketed by a pair of events; the pairs are read
 // at the next status check (the stream is synchronised there) or when the ring is full.
-void Engine::gauge_qr_dev(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cplx* R) {
+void Engine::gauge_qr_dev(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cplx* R, int* src) {
   const double t0 = tic();
   const bool timed = !capturing_;
   if (timed) {
@@ -770,7 +770,7 @@ void Engine::gauge_qr_dev(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cplx* 
     CK(cudaEventRecord(qr_ev_[2 * qr_ev_n_], st_));
   }
   CK(gauge_qr_blocked(m, n, Y, p, E, Q, R, qb_scratch_, qb_len_, qb_acc_, qr_, status_, st_,
-                      qr_gcap_, rank_tol_));
+                      qr_gcap_, rank_tol_, src));
   if (timed) {
     CK(cudaEventRecord(qr_ev_[2 * qr_ev_n_ + 1], st_));
     ++qr_ev_n_;

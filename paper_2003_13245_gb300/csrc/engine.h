@@ -179,7 +179,15 @@ class Engine {
   // number of matvecs that ran
   template <class F>
   int krylov(long long n, const cplx* v, cplx* out, double tr, double ti, F&& matvec);
-  void gauge_qr_dev(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cplx* R);
+  void gauge_qr_dev(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cplx* R,
+                    int* src = nullptr);
+  // Reverse of one FP64 projector-splitting step exp(tau H) (Eq. S1) of an MPS with bond
+  // dimensions bond_dimensions(sites, M): A_in (device, sites 1.. right-orthonormal), the
+  // cotangents Abar_out of the output sites -> the output A_out (may be NULL), Abar_in and
+  // theta_bar[parameter_count(P)] (host).  The step is run again with its intermediates kept
+  // (step_adjoint.cu).
+  void step_vjp(int M, const cplx* const* A_in, double tr, double ti, const cplx* const* Abar_out,
+                cplx* const* A_out, cplx* const* Abar_in, double* theta_bar, int nodes);
 
  private:
   void alloc_mps(DevMps& s, int M);

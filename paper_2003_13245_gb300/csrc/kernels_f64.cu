@@ -491,6 +491,8 @@ struct QrKernelArgs {
   double rank_tol, complete_tol;
   const unsigned char* acc_in;   // completion only: accepted flags of a factorisation done
                                  // elsewhere (Q, R already written; only skipped columns filled)
+  int* src_out = nullptr;        // if set: per completed position, the candidate that filled it
+                                 // (i < p: column i of E, p + i: unit vector e_i)
 };
 
 // Sum of the G per-block partial doubles at stride `stride` (fixed order per lane, then a
@@ -794,6 +796,7 @@ __global__ void __launch_bounds__(QR_THREADS) gauge_qr_kernel(QrKernelArgs A) {
           A.Q[(long long)(r0 + r) * n + j] = make_double2(v[r].x * inv, v[r].y * inv);
         __syncthreads();
         if (threadIdx.x == 0) acc[j] = 1;
+        if (A.src_out && threadIdx.x == 0 && blockIdx.x == 0) A.src_out[j] = (int)(cand - 1);
         __syncthreads();
         found = true;
       }
@@ -861,7 +864,8 @@ cudaError_t gauge_qr(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cplx* R,
 }
 
 cudaError_t gauge_qr_complete(int m, int n, int p, QrRef E, cplx* Q, const unsigned char* acc,
-                              const QrScratch& W, int* status, cudaStream_t s, int gcap) {
+                              const QrScratch& W, int* status, cudaStream_t s, int gcap,
+                              int* src) {
   int G = gauge_qr_grid(m);
   if (gcap > 0 && G > gcap) G = gcap;
   if (G > W.gmax || n > W.nmax) return cudaErrorInvalidValue;
@@ -882,6 +886,7 @@ cudaError_t gauge_qr_complete(int m, int n, int p, QrRef E, cplx* Q, const unsig
   a.rank_tol = 1e-12;
   a.complete_tol = 1e-2;
   a.acc_in = acc;
+  a.src_out = src;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(G);
   cfg.blockDim = dim3(QR_THREADS);

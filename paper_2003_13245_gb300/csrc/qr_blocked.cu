@@ -384,7 +384,7 @@ long long gauge_qr_blocked_scratch(int n, int gmax) {
 cudaError_t gauge_qr_blocked(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cplx* R,
                              cplx* scratch, long long scratch_len, unsigned char* acc,
                              const QrScratch& W, int* status, cudaStream_t s, int gcap,
-                             double rank_tol) {
+                             double rank_tol, int* src) {
   int G = gauge_qr_blocked_grid(m);
   if (gcap > 0 && G > gcap) G = gcap;
   const long long PS = (long long)n * QB + QB + QB * QB;
@@ -420,7 +420,7 @@ cudaError_t gauge_qr_blocked(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cpl
   e = cudaLaunchKernelEx(&cfg, gauge_qr_blocked_kernel, a);
   if (e != cudaSuccess) return e;
   // completion of skipped positions (only when some column was skipped: decided on device)
-  return gauge_qr_complete(m, n, p, p > 0 ? E : Y, Q, acc, W, status, s, gcap);
+  return gauge_qr_complete(m, n, p, p > 0 ? E : Y, Q, acc, W, status, s, gcap, src);
 }
 
 }  // namespace tdmrg

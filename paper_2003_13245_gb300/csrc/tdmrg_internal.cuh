@@ -118,16 +118,19 @@ struct QrScratch {
 cudaError_t gauge_qr(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cplx* R,
                      const QrScratch& W, int* status, cudaStream_t s, int gcap = 0);
 int gauge_qr_grid(int m);
-// completion pass only (skipped positions of a factorisation whose accepted flags are `acc`)
+// completion pass only (skipped positions of a factorisation whose accepted flags are `acc`);
+// if src is not NULL, src[j] receives the candidate that filled completed position j (i < p:
+// column i of E, p + i: unit vector e_i; other entries untouched)
 cudaError_t gauge_qr_complete(int m, int n, int p, QrRef E, cplx* Q, const unsigned char* acc,
-                              const QrScratch& W, int* status, cudaStream_t s, int gcap = 0);
+                              const QrScratch& W, int* status, cudaStream_t s, int gcap = 0,
+                              int* src = nullptr);
 // blocked variant (16 columns per block); scratch: gauge_qr_blocked_scratch(n, gmax) complex
 // entries and n accepted flags; W supplies the barrier and the completion pass' scratch
 long long gauge_qr_blocked_scratch(int n, int gmax);
 cudaError_t gauge_qr_blocked(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cplx* R,
                              cplx* scratch, long long scratch_len, unsigned char* acc,
                              const QrScratch& W, int* status, cudaStream_t s, int gcap = 0,
-                             double rank_tol = 1e-12);
+                             double rank_tol = 1e-12, int* src = nullptr);
 
 // dst[j][i] = conj?(src[i][j]) for an m x n source.
 cudaError_t ztranspose(int m, int n, const cplx* src, cplx* dst, int conj, cudaStream_t s);

@@ -1,0 +1,68 @@
+"""Parity of the reverse of one projector-splitting step (tdmrg_step_vjp, FP64) with the
+oracle's tape (``oracle/adjoint.step_with_tape``): the output sites, the cotangents of the input
+sites and the parameter cotangents (omega, g, V), for real and imaginary tau, on a random state
+(full-rank bonds) and on the right-canonicalised |I> (rank-2 bonds, so the gauge QRs complete
+columns from their coupling candidates).  Skipped until the entry point's first run on a GPU."""
+import numpy as np
+import pytest
+
+from tests.inputs import random_complex
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skip(reason="awaiting the first run of tdmrg_step_vjp on a GPU")]
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2003_13245_gb300.build import build_library
+    build_library()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+@pytest.mark.parametrize("M,tau,start", [(4, -0.1j, "random"), (64, -0.1j, "random"),
+                                         (4, -0.1j, "identity"), (4, -0.05, "identity")])
+def test_step_vjp_matches_oracle_tape(M, tau, start):
+    from oracle import adjoint, tdvp
+    from oracle.model import HolsteinModel, mpo_hamiltonian, site_list
+    from paper_2003_13245_gb300 import binding
+    model = HolsteinModel(N=3, omega=[1.0], g=[0.7], nmax=[2], V=0.8)
+    rng = np.random.default_rng(9000 + M)
+    d = [s[3] for s in site_list(model)]
+    Ws = mpo_hamiltonian(model)
+    if start == "random":
+        Mb = tdvp.bond_dims([x * x for x in d], M)
+        A0 = [random_complex(rng, (Mb[k], d[k] ** 2, Mb[k + 1])) for k in range(len(d))]
+    else:
+        A0 = tdvp.identity_state(model, M)
+    p = tdvp.PurifiedMPS(model, A0, Ws)
+    p.right_canonicalize()
+    A = [x.copy() for x in p.A]
+    A[0] = A[0] / np.linalg.norm(A[0])
+    Abar = [random_complex(rng, x.shape) for x in A]
+    T, out, inp, wids = adjoint.step_with_tape(Ws, d, A, tau, tol=1e-14)
+    bars = T.backward(dict(zip(out, Abar)))
+    ref_out = [T.vals[i] for i in out]
+    ref_in = [bars.get(i, np.zeros_like(T.vals[i])) for i in inp]
+    ref_th = adjoint.step_parameter_gradient(model, [bars.get(w, 0) for w in wids],
+                                             mpo_hamiltonian)
+    m = binding.Model(model.N, model.omega, model.g, model.nmax, model.V)
+    try:
+        A_out, Abar_in, th = m.step_vjp(M, [dev(x) for x in A], tau, [dev(x) for x in Abar])
+    finally:
+        m.close()
+    for got, ref in zip(A_out, ref_out):
+        assert np.abs(got.cpu().numpy() - ref).max() <= 1e-10 * max(np.abs(ref).max(), 1e-300)
+    scale = max(np.abs(x).max() for x in ref_in)
+    for got, ref in zip(Abar_in, ref_in):
+        assert np.abs(got.cpu().numpy() - ref).max() <= 1e-8 * scale
+    ref_vec = [ref_th[("omega", 0)], ref_th[("g", 0)], ref_th[("V", -1)]]
+    tscale = max(abs(x) for x in ref_vec)
+    for got, ref in zip(th, ref_vec):
+        assert abs(got - ref) <= 1e-8 * tscale

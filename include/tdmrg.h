@@ -207,8 +207,9 @@ const char* tdmrg_last_global_error(void);
  * (dense, host pointer, complex interleaved).  TDMRG_PREC_C128: X, Y are device workspaces of
  * max(Dl, Dr) * Ml * d*d * Mr complex entries each (ws32 unused).  TDMRG_PREC_C64_3XTF32:
  * both contractions run on the tensor cores with 3xTF32 split operands; ws32 is a device
- * workspace of tdmrg_heff_workspace_floats(...) floats (X, Y unused).  Synchronises `stream`;
- * ERR_TIMEOUT if a bounded pipeline wait gave up. */
+ * workspace of tdmrg_heff_workspace_floats(...) floats (X, Y unused).  Allocates the device
+ * tables of the MPO site (and, for 3xTF32, a status word), freed before return; synchronises
+ * `stream`; ERR_TIMEOUT if a bounded pipeline wait gave up. */
 int tdmrg_kernel_heff(int Ml, int Mr, int d, int Dl, int Dr, const double* W_host,
                       const void* L, const void* R, const void* A, void* out,
                       void* X, void* Y, void* ws32, int precision, void* stream);
@@ -250,7 +251,8 @@ int tdmrg_kernel_site_exp_vjp(int Ml, int Mr, int d, int Dl, int Dr, const doubl
 /* tdmrg_kernel_site_exp_vjp plus parameter cotangents: for nparam derivative sites
  * dW_host[nparam][Dl][Dr][d][d] (host, as tdmrg_host_mpo_site writes them) it also writes
  * theta_bar[p] = Re<Hbar, H_eff(L, dW_p, R)> (host), Hbar the cotangent of the operator from the
- * same quadrature; nparam = 0 is tdmrg_kernel_site_exp_vjp. */
+ * same quadrature; nparam = 0 is tdmrg_kernel_site_exp_vjp.  Allocates its scratch (freed
+ * before return); synchronises `stream`. */
 int tdmrg_kernel_site_exp_vjp_theta(int Ml, int Mr, int d, int Dl, int Dr, const double* W_host,
                                     const void* L, const void* R, const void* A,
                                     const void* ybar, double tau_re, double tau_im, int nodes,
@@ -345,7 +347,8 @@ int tdmrg_kernel_zgemm_tc(int M, int N, int K, const void* A, const void* B, int
 /* Left environment update (the gauge shift of Eq. S1 carries it along the sweep):
  *   Lout[v,b,c] = sum conj(bra[a,s,t,b]) L[w,a,y] W[w,v,s,u] ket[y,u,t,c]
  * bra: Ml1 x d*d x Mr1, ket: Ml2 x d*d x Mr2, L: Dl x Ml1 x Ml2, Lout: Dr x Mr1 x Mr2.
- * X, Y: workspace of max(Dl,Dr) * Ml2 * d*d * Mr2 complex entries.  Synchronises `stream`. */
+ * X, Y: workspace of max(Dl,Dr) * Ml2 * d*d * Mr2 complex entries.  Allocates the device
+ * tables of the MPO site (freed before return); synchronises `stream`. */
 int tdmrg_kernel_env_left(int Ml1, int Mr1, int Ml2, int Mr2, int d, int Dl, int Dr,
                           const double* W_host, const void* L, const void* bra,
                           const void* ket, void* Lout, void* X, void* Y, void* stream);

@@ -1,8 +1,16 @@
 """Parity of the reverse of one projector-splitting step (tdmrg_step_vjp, FP64) with the
 oracle's tape (``oracle/adjoint.step_with_tape``): the output sites, the cotangents of the input
-sites and the parameter cotangents (omega, g, V), for real and imaginary tau, on a random state
-(full-rank bonds) and on the right-canonicalised |I> (rank-2 bonds, so the gauge QRs complete
-columns from their coupling candidates).  Skipped until the entry point's first run on a GPU."""
+sites and the parameter cotangents (omega, g, V).
+
+* A random state (full-rank bonds, no completed columns), real and imaginary tau: every part is
+  a smooth function of its inputs; bound 1e-8 of the largest entry (the Krylov tolerances).
+* The right-canonicalised |I> at M = 4, real tau: rank-2 bonds, so 12 gauge-QR columns per
+  step are completed from their coupling candidates, accepted with residuals down to 1e-2 of
+  their norm; two CPU rounding orders of the same algorithm differ by 2.6e-9 of the parameter
+  cotangents, so the bound there is 1e-7.  (Wider bonds around |I>, or imaginary tau from it,
+  put columns at the rank threshold and are not a parity case: two rounding orders differ by
+  1e-6 and more.)
+Skipped until the entry point's first run on a GPU."""
 import numpy as np
 import pytest
 
@@ -26,9 +34,11 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
 
 
-@pytest.mark.parametrize("M,tau,start", [(4, -0.1j, "random"), (64, -0.1j, "random"),
-                                         (4, -0.1j, "identity"), (4, -0.05, "identity")])
-def test_step_vjp_matches_oracle_tape(M, tau, start):
+@pytest.mark.parametrize("M,tau,start,bound", [(4, -0.1j, "random", 1e-8),
+                                               (4, -0.05, "random", 1e-8),
+                                               (64, -0.1j, "random", 1e-8),
+                                               (4, -0.1j, "identity", 1e-7)])
+def test_step_vjp_matches_oracle_tape(M, tau, start, bound):
     from oracle import adjoint, tdvp
     from oracle.model import HolsteinModel, mpo_hamiltonian, site_list
     from paper_2003_13245_gb300 import binding
@@ -61,8 +71,8 @@ def test_step_vjp_matches_oracle_tape(M, tau, start):
         assert np.abs(got.cpu().numpy() - ref).max() <= 1e-10 * max(np.abs(ref).max(), 1e-300)
     scale = max(np.abs(x).max() for x in ref_in)
     for got, ref in zip(Abar_in, ref_in):
-        assert np.abs(got.cpu().numpy() - ref).max() <= 1e-8 * scale
+        assert np.abs(got.cpu().numpy() - ref).max() <= bound * scale
     ref_vec = [ref_th[("omega", 0)], ref_th[("g", 0)], ref_th[("V", -1)]]
     tscale = max(abs(x) for x in ref_vec)
     for got, ref in zip(th, ref_vec):
-        assert abs(got - ref) <= 1e-8 * tscale
+        assert abs(got - ref) <= bound * tscale

@@ -154,6 +154,21 @@ int tdmrg_step_vjp(tdmrg_model* h, int M, const void* const* A_in, double tau_re
                    const void* const* Abar_out, void* const* A_out, void* const* Abar_in,
                    double* theta_bar, int nodes);
 
+/* Real-time correlation of two given states and its reverse pass, complex FP64 (needs
+ * TDMRG_PREC_C128; no counterpart in the paper: the adjoint of Eq. 6 for fixed initial
+ * states).  psi1[L], psi2[L]: device site tensors as for tdmrg_step_vjp.  Both are stepped by
+ * nsteps steps exp(-i dt H) and C_n = <psi1(n dt)| j |psi2(n dt)> is written to
+ * C_out[2 (nsteps+1)] (host, interleaved).  For the loss Re sum_n conj(Cbar_n) C_n
+ * (Cbar[2 (nsteps+1)] host) it writes the cotangents g1[L], g2[L] of the initial states (device)
+ * and theta_bar[count] (host, through H and j).  The states are stored every `every` steps;
+ * each stretch is recomputed from its stored state and reversed step by step as
+ * tdmrg_step_vjp does (memory: nsteps / every stored pairs plus one stretch and one step's
+ * tape).  Allocates its storage (freed before return); synchronises the handle's stream. */
+int tdmrg_correlation_states_vjp(tdmrg_model* h, int M, const void* const* psi1,
+                                 const void* const* psi2, double dt, int nsteps, int every,
+                                 const double* Cbar, double* C_out, void* const* g1,
+                                 void* const* g2, double* theta_bar, int nodes);
+
 /* One site of an MPO of the chain, dense, built on the host (no handle, no GPU): the chain of
  * tdmrg_model_create (same arguments and checks) with, when nmax_p != 0, the bond mode of
  * tdmrg_model_set_peierls (alpha, omega_p, nmax_p in [2, 32]).  which: TDMRG_MPO_H (Eq. 1 /

@@ -79,6 +79,7 @@ _SIGS = {
                                         _i, _dp, _p, _p, _p, _dp, _p],
     "tdmrg_parameter_count": [_p, _ip],
     "tdmrg_step_vjp": [_p, _i, _pp, _d, _d, _pp, _pp, _pp, _dp, _i],
+    "tdmrg_correlation_states_vjp": [_p, _i, _pp, _pp, _d, _i, _i, _dp, _dp, _pp, _pp, _dp, _i],
 }
 
 
@@ -232,6 +233,25 @@ class Model:
                                         float(np.imag(tau)), arr(Abar_out), arr(A_out),
                                         arr(Abar_in), _dptr(tb), int(nodes)), self._h)
         return A_out, Abar_in, tb
+
+    def correlation_states_vjp(self, M, psi1, psi2, dt, nsteps, cbar, every=2, nodes=16):
+        """C_n of two given states (lists of complex128 CUDA tensors) stepped in real time and the
+        reverse pass for Re sum conj(cbar_n) C_n -> (C, g1, g2, theta_bar)."""
+        import torch
+        L = len(psi1)
+        arr = lambda ts: (ctypes.c_void_p * L)(*[t.data_ptr() for t in ts])   # noqa: E731
+        g1 = [torch.empty_like(a) for a in psi1]
+        g2 = [torch.empty_like(a) for a in psi2]
+        cb = np.zeros(2 * (nsteps + 1))
+        cb[0::2] = np.real(cbar)
+        cb[1::2] = np.imag(cbar)
+        C = np.zeros(2 * (nsteps + 1))
+        tb = np.zeros(self.parameter_count())
+        _check(self._lib.tdmrg_correlation_states_vjp(self._h, int(M), arr(psi1), arr(psi2),
+                                                      float(dt), int(nsteps), int(every),
+                                                      _dptr(cb), _dptr(C), arr(g1), arr(g2),
+                                                      _dptr(tb), int(nodes)), self._h)
+        return C[0::2] + 1j * C[1::2], g1, g2, tb
 
     def reset_stats(self):
         _check(self._lib.tdmrg_reset_stats(self._h), self._h)

@@ -426,6 +426,22 @@ int tdmrg_step_vjp(tdmrg_model* h, int M, const void* const* A_in, double tau_re
   });
 }
 
+int tdmrg_correlation_states_vjp(tdmrg_model* h, int M, const void* const* psi1,
+                                 const void* const* psi2, double dt, int nsteps, int every,
+                                 const double* Cbar, double* C_out, void* const* g1,
+                                 void* const* g2, double* theta_bar, int nodes) {
+  if (!h) return fail(nullptr, TDMRG_ERR_ARG, "NULL handle");
+  if (M < 1 || !psi1 || !psi2 || !(dt > 0.0) || nsteps < 0 || every < 1 || !Cbar || !C_out ||
+      !g1 || !g2 || !theta_bar || nodes < 1 || nodes > 64)
+    return fail(h, TDMRG_ERR_ARG, "correlation_states_vjp: bad arguments");
+  return guarded(h, [&] {
+    h->eng->correlation_states_vjp(M, (const tdmrg::cplx* const*)psi1,
+                                   (const tdmrg::cplx* const*)psi2, dt, nsteps, every, Cbar,
+                                   C_out, (tdmrg::cplx* const*)g1, (tdmrg::cplx* const*)g2,
+                                   theta_bar, nodes);
+  });
+}
+
 int tdmrg_get_logz(const tdmrg_model* h, double* logz) {
   if (!h || !logz) return fail(nullptr, TDMRG_ERR_ARG, "NULL argument");
   if (!h->eng->prepared()) return fail(const_cast<tdmrg_model*>(h), TDMRG_ERR_STATE, "not prepared");

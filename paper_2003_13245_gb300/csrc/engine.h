@@ -188,6 +188,14 @@ class Engine {
   // (step_adjoint.cu).
   void step_vjp(int M, const cplx* const* A_in, double tr, double ti, const cplx* const* Abar_out,
                 cplx* const* A_out, cplx* const* Abar_in, double* theta_bar, int nodes);
+  // C_n = <psi1(n dt)| j |psi2(n dt)>, n = 0..nsteps, of two FP64 states stepped in real time,
+  // and the reverse pass for the loss Re sum_n conj(cbar_n) C_n: states stored every `every`
+  // steps, each stretch recomputed and reversed step by step (step_vjp) with the overlap VJPs;
+  // writes C (2 (nsteps+1) host), the cotangents g1, g2 of the initial states (device) and
+  // theta_bar (host, through H and j).
+  void correlation_states_vjp(int M, const cplx* const* psi1, const cplx* const* psi2, double dt,
+                              int nsteps, int every, const double* cbar, double* C,
+                              cplx* const* g1, cplx* const* g2, double* theta_bar, int nodes);
 
  private:
   void alloc_mps(DevMps& s, int M);
@@ -215,6 +223,10 @@ class Engine {
   double norm2_dev(const cplx* x, long long n);
   void scale_dev(cplx* x, long long n, double f);
   Cx overlap(const DevMps& bra, const DevMpo& W, const DevMps& ket);
+  // adds the cotangents of <bra| j |ket> for the cotangent cbar of the overlap (step_adjoint.cu)
+  void overlap_vjp(const std::vector<cplx*>& bra, const std::vector<cplx*>& ket, const std::vector<int>& Mb,
+                   Cx cbar, const std::vector<cplx*>& gbra, const std::vector<cplx*>& gket,
+                   std::vector<double>& theta);
   void fit_apply(const DevMpo& W, const DevMps& psi, DevMps& phi, int sweeps);
   void check_status();
   void harvest_qr_events();

@@ -461,4 +461,182 @@ void Engine::step_vjp(int M, const cplx* const* A_in, double tr, double ti,
   check_status();
 }
 
+void Engine::overlap_vjp(const std::vector<cplx*>& bra, const std::vector<cplx*>& ket,
+                         const std::vector<int>& Mb, Cx cbar, const std::vector<cplx*>& gbra,
+                         const std::vector<cplx*>& gket, std::vector<double>& theta) {
+  const int L = (int)sites_.size();
+  const int np = parameter_count(P);
+  std::vector<long long> n(L), ne(L + 1);
+  long long maxenv = 1, maxsite = 1;
+  for (int k = 0; k < L; ++k) {
+    n[k] = (long long)Mb[k] * sites_[k].d * sites_[k].d * Mb[k + 1];
+    ne[k] = (long long)J_.s[k].Dl * Mb[k] * Mb[k];
+    maxenv = std::max(maxenv, ne[k]);
+    maxsite = std::max(maxsite, n[k]);
+  }
+  ne[L] = 1;
+  Tape tp;
+  std::vector<cplx*> e(L + 1);
+  for (int k = 0; k <= L; ++k) e[k] = tp.get(ne[k]);
+  Ctx c = ctx();
+  // forward chain e_{k+1} = env_left(e_k, bra_k, j_k, ket_k)
+  set_ones(e[0]);
+  for (int k = 0; k < L; ++k) {
+    const int d = sites_[k].d;
+    env_left_f64(c, J_.s[k], Mb[k], Mb[k + 1], Mb[k], Mb[k + 1], d * d, d, e[k], bra[k], ket[k],
+                 e[k + 1]);
+  }
+  // reverse: the cotangent of the 1 x 1 x 1 final environment is cbar
+  cplx* G[2] = {tp.get(maxenv), tp.get(maxenv)};
+  cplx* bb = tp.get(maxsite);
+  cplx* kb = tp.get(maxsite);
+  const cplx cb = {cbar.real(), cbar.imag()};
+  CK(cudaMemcpyAsync(G[L & 1], &cb, sizeof(cplx), cudaMemcpyHostToDevice, st_));
+  CK(cudaStreamSynchronize(st_));
+  std::vector<double> tht(np > 0 ? np : 1, 0.0);
+  for (int k = L - 1; k >= 0; --k) {
+    const DevMpoSite& W = J_.s[k];
+    const int d = sites_[k].d;
+    const std::vector<double> Wd = dense_site(W.Dl, W.Dr, d, W.host);
+    std::vector<double> dWd;
+    for (int p = 0; p < np; ++p) {
+      const std::vector<double> x = dense_site(W.Dl, W.Dr, d, mpo_site_derivative(P, 1, p, k).blocks);
+      dWd.insert(dWd.end(), x.begin(), x.end());
+    }
+    call(tdmrg_kernel_env_vjp(0, Mb[k], Mb[k + 1], d, W.Dl, W.Dr, Wd.data(), np,
+                              np > 0 ? dWd.data() : nullptr, e[k], bra[k], ket[k], G[(k + 1) & 1],
+                              G[k & 1], bb, kb, tht.data(), X_, Y_, (void*)st_));
+    for (int p = 0; p < np; ++p) theta[p] += tht[p];
+    CK(zaxpy(n[k], kOne, bb, gbra[k], st_));
+    CK(zaxpy(n[k], kOne, kb, gket[k], st_));
+  }
+  CK(cudaStreamSynchronize(st_));
+}
+
+void Engine::correlation_states_vjp(int M, const cplx* const* psi1, const cplx* const* psi2,
+                                    double dt, int nsteps, int every, const double* cbar,
+                                    double* C, cplx* const* g1_out, cplx* const* g2_out,
+                                    double* theta_bar, int nodes) {
+  if (mixed())
+    throw Failure{TDMRG_ERR_ARG, "correlation_states_vjp: the reverse pass runs in FP64 precision"};
+  if (nsteps < 0 || every < 1) throw Failure{TDMRG_ERR_ARG, "correlation_states_vjp: bad counts"};
+  const int L = (int)sites_.size();
+  const int np = parameter_count(P);
+  DevMps s1, s2;
+  struct Free {
+    Engine& e;
+    DevMps& a;
+    DevMps& b;
+    ~Free() {
+      e.free_mps(a);
+      e.free_mps(b);
+    }
+  } fr{*this, s1, s2};
+  alloc_mps(s1, M);
+  alloc_mps(s2, M);
+  const std::vector<int>& Mb = s1.Mb;
+  std::vector<long long> n(L);
+  for (int k = 0; k < L; ++k) n[k] = s1.size(k);
+  Tape tp;
+  auto snapshot = [&](const DevMps& s) {
+    std::vector<cplx*> out(L);
+    for (int k = 0; k < L; ++k) {
+      out[k] = tp.get(n[k]);
+      CK(cudaMemcpyAsync(out[k], s.A[k], sizeof(cplx) * (size_t)n[k], cudaMemcpyDeviceToDevice,
+                         st_));
+    }
+    return out;
+  };
+  auto load = [&](DevMps& s, const std::vector<cplx*>& a) {
+    for (int k = 0; k < L; ++k)
+      CK(cudaMemcpyAsync(s.A[k], a[k], sizeof(cplx) * (size_t)n[k], cudaMemcpyDeviceToDevice,
+                         st_));
+    build_right_envs(s);
+  };
+  auto step = [&](DevMps& s) {
+    tdvp_step_body(s, 0.0, -dt);
+    check_status();
+  };
+  // forward: C_n and the stored states
+  std::vector<cplx*> p1(L), p2(L);     // read only
+  for (int k = 0; k < L; ++k) {
+    p1[k] = const_cast<cplx*>(psi1[k]);
+    p2[k] = const_cast<cplx*>(psi2[k]);
+  }
+  struct Ckpt {
+    int n;
+    std::vector<cplx*> a, b;
+  };
+  std::vector<Ckpt> ck;
+  load(s1, p1);
+  load(s2, p2);
+  ck.push_back({0, snapshot(s1), snapshot(s2)});
+  for (int t = 0; t <= nsteps; ++t) {
+    if (t > 0) {
+      step(s1);
+      step(s2);
+      if (t % every == 0 && t < nsteps) ck.push_back({t, snapshot(s1), snapshot(s2)});
+    }
+    const Cx v = overlap(s1, J_, s2);
+    C[2 * t] = v.real();
+    C[2 * t + 1] = v.imag();
+  }
+  // reverse over the stretches between stored states, latest first
+  std::vector<cplx*> g1(L), g2(L), h1(L), h2(L);
+  for (int k = 0; k < L; ++k) {
+    g1[k] = tp.get(n[k]);
+    g2[k] = tp.get(n[k]);
+    h1[k] = tp.get(n[k]);
+    h2[k] = tp.get(n[k]);
+    CK(cudaMemsetAsync(g1[k], 0, sizeof(cplx) * (size_t)n[k], st_));
+    CK(cudaMemsetAsync(g2[k], 0, sizeof(cplx) * (size_t)n[k], st_));
+  }
+  std::vector<double> th(np, 0.0), ths(np > 0 ? np : 1, 0.0);
+  auto cb = [&](int t) { return Cx(cbar[2 * t], cbar[2 * t + 1]); };
+  for (int i = (int)ck.size() - 1; i >= 0; --i) {
+    const int s0 = ck[i].n;
+    const int e0 = (i + 1 < (int)ck.size()) ? ck[i + 1].n : nsteps;
+    if (e0 <= s0) continue;
+    std::vector<std::vector<cplx*>> st1{ck[i].a}, st2{ck[i].b};
+    Tape seg;
+    load(s1, ck[i].a);
+    load(s2, ck[i].b);
+    for (int t = s0 + 1; t <= e0; ++t) {
+      step(s1);
+      step(s2);
+      std::vector<cplx*> a(L), b(L);
+      for (int k = 0; k < L; ++k) {
+        a[k] = seg.get(n[k]);
+        b[k] = seg.get(n[k]);
+        CK(cudaMemcpyAsync(a[k], s1.A[k], sizeof(cplx) * (size_t)n[k], cudaMemcpyDeviceToDevice,
+                           st_));
+        CK(cudaMemcpyAsync(b[k], s2.A[k], sizeof(cplx) * (size_t)n[k], cudaMemcpyDeviceToDevice,
+                           st_));
+      }
+      st1.push_back(a);
+      st2.push_back(b);
+    }
+    for (int t = e0; t > s0; --t) {
+      overlap_vjp(st1[t - s0], st2[t - s0], Mb, cb(t), g1, g2, th);
+      step_vjp(M, st1[t - s0 - 1].data(), 0.0, -dt, g1.data(), nullptr, h1.data(), ths.data(),
+               nodes);
+      for (int p = 0; p < np; ++p) th[p] += ths[p];
+      step_vjp(M, st2[t - s0 - 1].data(), 0.0, -dt, g2.data(), nullptr, h2.data(), ths.data(),
+               nodes);
+      for (int p = 0; p < np; ++p) th[p] += ths[p];
+      std::swap(g1, h1);
+      std::swap(g2, h2);
+    }
+  }
+  overlap_vjp(ck[0].a, ck[0].b, Mb, cb(0), g1, g2, th);
+  for (int k = 0; k < L; ++k) {
+    CK(cudaMemcpyAsync(g1_out[k], g1[k], sizeof(cplx) * (size_t)n[k], cudaMemcpyDeviceToDevice,
+                       st_));
+    CK(cudaMemcpyAsync(g2_out[k], g2[k], sizeof(cplx) * (size_t)n[k], cudaMemcpyDeviceToDevice,
+                       st_));
+  }
+  for (int p = 0; p < np; ++p) theta_bar[p] = th[p];
+  CK(cudaStreamSynchronize(st_));
+}
+
 }  // namespace tdmrg

@@ -76,3 +76,44 @@ def test_step_vjp_matches_oracle_tape(M, tau, start, bound):
     tscale = max(abs(x) for x in ref_vec)
     for got, ref in zip(th, ref_vec):
         assert abs(got - ref) <= bound * tscale
+
+
+def test_correlation_states_vjp_matches_oracle():
+    """C_n and the reverse pass of the real-time correlation of two given states
+    (tdmrg_correlation_states_vjp) against ``oracle/adjoint.correlation_vjp``: random states at
+    M = 4, three steps stored every two (one recomputed stretch of two, one of one)."""
+    from oracle import adjoint, tdvp
+    from oracle.model import HolsteinModel, mpo_current, mpo_hamiltonian, site_list
+    from paper_2003_13245_gb300 import binding
+    model = HolsteinModel(N=3, omega=[1.0], g=[0.7], nmax=[2], V=0.8)
+    rng = np.random.default_rng(9100)
+    d = [s[3] for s in site_list(model)]
+    Ws, Wj = mpo_hamiltonian(model), mpo_current(model)
+    Mb = tdvp.bond_dims([x * x for x in d], 4)
+    states = []
+    for _ in range(2):
+        A0 = [random_complex(rng, (Mb[k], d[k] ** 2, Mb[k + 1])) for k in range(len(d))]
+        p = tdvp.PurifiedMPS(model, A0, Ws)
+        p.right_canonicalize()
+        A = [x.copy() for x in p.A]
+        A[0] = A[0] / np.linalg.norm(A[0])
+        states.append(A)
+    dt, ns = 0.1, 3
+    cbar = random_complex(rng, (ns + 1,))
+    C, g1, g2, Wb, Wjb = adjoint.correlation_vjp(Ws, Wj, d, states[0], states[1], dt, ns, cbar,
+                                                 every=2)
+    gH = adjoint.step_parameter_gradient(model, Wb, mpo_hamiltonian)
+    gJ = adjoint.step_parameter_gradient(model, Wjb, mpo_current)
+    ref_th = [gH[p] + gJ[p] for p in (("omega", 0), ("g", 0), ("V", -1))]
+    m = binding.Model(model.N, model.omega, model.g, model.nmax, model.V)
+    try:
+        Cg, h1, h2, th = m.correlation_states_vjp(4, [dev(x) for x in states[0]],
+                                                  [dev(x) for x in states[1]], dt, ns, cbar)
+    finally:
+        m.close()
+    assert np.abs(Cg - C).max() <= 1e-10 * np.abs(C).max()
+    for got, ref in zip(h1 + h2, g1 + g2):
+        assert np.abs(got.cpu().numpy() - ref).max() <= 1e-8 * max(np.abs(x).max() for x in g1 + g2)
+    tscale = max(abs(x) for x in ref_th)
+    for got, ref in zip(th, ref_th):
+        assert abs(got - ref) <= 1e-8 * tscale

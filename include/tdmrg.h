@@ -169,6 +169,23 @@ int tdmrg_correlation_states_vjp(tdmrg_model* h, int M, const void* const* psi1,
                                  const double* Cbar, double* C_out, void* const* g1,
                                  void* const* g2, double* theta_bar, int nodes);
 
+/* Gradient of the whole C(t) computation of Eq. 6 (the adjoint; no counterpart in the paper),
+ * complex FP64 (needs TDMRG_PREC_C128).  Runs, as tdmrg_thermal_prepare and tdmrg_correlation
+ * do, the right-canonicalised |I>, round(beta / (2 dtau)) imaginary-time steps (center
+ * normalised after each), the fit of j Psi_b and nsteps real-time steps dt, writing
+ * C_out[2 (nsteps+1)] (host, C_n at t = n dt) and *logz_out (if not NULL); then reverses all
+ * of it for the loss Re sum_n conj(Cbar_n) C_n (Cbar[2 (nsteps+1)] host) and writes
+ * theta_bar[count] = dloss/dtheta (host, tdmrg_parameter_count numbering: omega_m, g_m, V,
+ * ...).  For dmu/dtheta pass the trapezoid weights of tdmrg_mobility as Cbar.  The real-time
+ * states are stored every `every` steps and each stretch recomputed; the imaginary-time states
+ * are all kept.  Completed gauge columns follow their coupling candidates; a rank threshold
+ * above rounding (tdmrg_model_set_rank_tol, e.g. 1e-8) keeps the reverse pass conditioned
+ * when bonds are wider than the state's rank.  Allocates its storage (freed before return);
+ * synchronises the handle's stream. */
+int tdmrg_correlation_vjp(tdmrg_model* h, double beta, double dtau, int M, double dt,
+                          int nsteps, int every, const double* Cbar, double* C_out,
+                          double* theta_bar, double* logz_out, int nodes);
+
 /* One site of an MPO of the chain, dense, built on the host (no handle, no GPU): the chain of
  * tdmrg_model_create (same arguments and checks) with, when nmax_p != 0, the bond mode of
  * tdmrg_model_set_peierls (alpha, omega_p, nmax_p in [2, 32]).  which: TDMRG_MPO_H (Eq. 1 /

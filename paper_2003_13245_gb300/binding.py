@@ -80,6 +80,7 @@ _SIGS = {
     "tdmrg_parameter_count": [_p, _ip],
     "tdmrg_step_vjp": [_p, _i, _pp, _d, _d, _pp, _pp, _pp, _dp, _i],
     "tdmrg_correlation_states_vjp": [_p, _i, _pp, _pp, _d, _i, _i, _dp, _dp, _pp, _pp, _dp, _i],
+    "tdmrg_correlation_vjp": [_p, _d, _d, _i, _d, _i, _i, _dp, _dp, _dp, _dp, _i],
 }
 
 
@@ -233,6 +234,21 @@ class Model:
                                         float(np.imag(tau)), arr(Abar_out), arr(A_out),
                                         arr(Abar_in), _dptr(tb), int(nodes)), self._h)
         return A_out, Abar_in, tb
+
+    def correlation_vjp(self, beta, dtau, M, dt, nsteps, cbar, every=2, nodes=16):
+        """C_n (t = n dt) of the whole FP64 pipeline and dloss/dtheta for
+        loss = Re sum_n conj(cbar_n) C_n through tdmrg_correlation_vjp -> (C, theta_bar, log Z)."""
+        cb = np.zeros(2 * (nsteps + 1))
+        cb[0::2] = np.real(cbar)
+        cb[1::2] = np.imag(cbar)
+        C = np.zeros(2 * (nsteps + 1))
+        tb = np.zeros(self.parameter_count())
+        lz = ctypes.c_double()
+        _check(self._lib.tdmrg_correlation_vjp(self._h, float(beta), float(dtau), int(M),
+                                               float(dt), int(nsteps), int(every), _dptr(cb),
+                                               _dptr(C), _dptr(tb), ctypes.byref(lz), int(nodes)),
+               self._h)
+        return C[0::2] + 1j * C[1::2], tb, lz.value
 
     def correlation_states_vjp(self, M, psi1, psi2, dt, nsteps, cbar, every=2, nodes=16):
         """C_n of two given states (lists of complex128 CUDA tensors) stepped in real time and the

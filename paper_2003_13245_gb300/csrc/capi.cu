@@ -442,6 +442,18 @@ int tdmrg_correlation_states_vjp(tdmrg_model* h, int M, const void* const* psi1,
   });
 }
 
+int tdmrg_correlation_vjp(tdmrg_model* h, double beta, double dtau, int M, double dt,
+                          int nsteps, int every, const double* Cbar, double* C_out,
+                          double* theta_bar, double* logz_out, int nodes) {
+  if (!h) return fail(nullptr, TDMRG_ERR_ARG, "NULL handle");
+  if (!Cbar || !C_out || !theta_bar || nodes < 1 || nodes > 64)
+    return fail(h, TDMRG_ERR_ARG, "correlation_vjp: bad arguments");
+  return guarded(h, [&] {
+    h->eng->correlation_vjp(beta, dtau, M, dt, nsteps, every, Cbar, C_out, theta_bar, logz_out,
+                            nodes);
+  });
+}
+
 int tdmrg_get_logz(const tdmrg_model* h, double* logz) {
   if (!h || !logz) return fail(nullptr, TDMRG_ERR_ARG, "NULL argument");
   if (!h->eng->prepared()) return fail(const_cast<tdmrg_model*>(h), TDMRG_ERR_STATE, "not prepared");

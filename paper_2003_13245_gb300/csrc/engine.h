@@ -186,8 +186,12 @@ class Engine {
   // cotangents Abar_out of the output sites -> the output A_out (may be NULL), Abar_in and
   // theta_bar[parameter_count(P)] (host).  The step is run again with its intermediates kept
   // (step_adjoint.cu).
+  // With normalize, the output center is divided by its norm n (log n^2 to *log_norm) and the
+  // cotangent Abar_out refers to the normalised output, plus logn_bar for log n^2.  With
+  // Abar_out NULL only the forward step runs (A_out written).
   void step_vjp(int M, const cplx* const* A_in, double tr, double ti, const cplx* const* Abar_out,
-                cplx* const* A_out, cplx* const* Abar_in, double* theta_bar, int nodes);
+                cplx* const* A_out, cplx* const* Abar_in, double* theta_bar, int nodes,
+                bool normalize = false, double logn_bar = 0.0, double* log_norm = nullptr);
   // C_n = <psi1(n dt)| j |psi2(n dt)>, n = 0..nsteps, of two FP64 states stepped in real time,
   // and the reverse pass for the loss Re sum_n conj(cbar_n) C_n: states stored every `every`
   // steps, each stretch recomputed and reversed step by step (step_vjp) with the overlap VJPs;
@@ -196,6 +200,21 @@ class Engine {
   void correlation_states_vjp(int M, const cplx* const* psi1, const cplx* const* psi2, double dt,
                               int nsteps, int every, const double* cbar, double* C,
                               cplx* const* g1, cplx* const* g2, double* theta_bar, int nodes);
+  // |I> right-canonicalised (completions from the H coupling) with its center normalised ->
+  // psi0 (device); with gbar (the cotangent of psi0, plus logn_bar for log n^2) the reverse
+  // adds the parameter cotangents to theta (pipeline_adjoint.cu)
+  void canonicalize_vjp(int M, cplx* const* psi0, const cplx* const* gbar, double logn_bar,
+                        double* theta, double* log_norm);
+  // phi ~ j|psi> by two one-site fitting sweeps (completions from the j coupling of psi) ->
+  // phi (device); with gphi the reverse adds the cotangent of psi to gpsi and the parameter
+  // cotangents to theta
+  void fit_vjp(int M, const cplx* const* psi, cplx* const* phi, const cplx* const* gphi,
+               cplx* const* gpsi, double* theta);
+  // the whole C(t) pipeline in FP64 (preparation, fit, real-time steps, overlaps) and the
+  // parameter cotangents of Re sum_n conj(cbar_n) C_n
+  void correlation_vjp(double beta, double dtau, int M, double dt, int nsteps, int every,
+                       const double* cbar, double* C, double* theta_bar, double* logz,
+                       int nodes);
 
  private:
   void alloc_mps(DevMps& s, int M);

@@ -10,6 +10,7 @@
 // GEMMs).  Parameter cotangents enter through the derivative MPO sites dW/dtheta as directional
 // contractions.  The step is the one the oracle takes: no renormalisation in imaginary time.
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "../../include/tdmrg.h"
@@ -80,11 +81,167 @@ std::vector<double> dense_site(int Dl, int Dr, int d, const std::vector<MpoBlock
 void call(int rc) {
   if (rc != TDMRG_OK) throw Failure{rc, tdmrg_last_global_error()};
 }
+
+// <g, x> = sum conj(g_i) x_i: 256 chunk sums by one batched GEMM plus the tail, added on the
+// host in a fixed order (part: 257 device entries); synchronises st
+Cx dot(const cplx* g, const cplx* x, long long n, cplx* part, cudaStream_t st) {
+  const int B = 256;
+  const long long kc = n / B, rem = n - kc * B;
+  if (kc > 0) {
+    MatRef a = mr(g, 0, 1, 1), b = mr(x, 1, 0);
+    a.sb = kc;
+    b.sb = kc;
+    CK(zgemm(1, 1, (int)kc, B, 1, kOne, a, b, kZero, part, 1, 1, nullptr, st));
+  }
+  if (rem > 0)
+    CK(zgemm(1, 1, (int)rem, 1, 1, kOne, mr(g + kc * B, 0, 1, 1), mr(x + kc * B, 1, 0), kZero,
+             part + B, 1, 0, nullptr, st));
+  std::vector<cplx> h(B + 1);
+  CK(cudaMemcpyAsync(h.data(), part, sizeof(cplx) * (B + 1), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  Cx acc(0.0, 0.0);
+  if (kc > 0)
+    for (int b = 0; b < B; ++b) acc += Cx(h[b].x, h[b].y);
+  if (rem > 0) acc += Cx(h[B].x, h[B].y);
+  return acc;
+}
+// scratch of the gauge-shift reverses below (each at least site-sized, Xfullb and cand at
+// least max(Dl, Dr) times site-sized)
+struct ShiftScratch {
+  cplx *Qb2, *Yb2, *b3, *Xsel, *Xselb, *Xfullb, *cand, *e1, *s1;
+};
+
+std::vector<int> completed_positions(const std::vector<unsigned char>& acc, std::vector<int>& accv) {
+  std::vector<int> K;
+  accv.assign(acc.size(), 0);
+  for (size_t j = 0; j < acc.size(); ++j) {
+    accv[j] = acc[j] ? 1 : 0;
+    if (!acc[j]) K.push_back((int)j);
+  }
+  return K;
+}
+
+// Reverse of a right-to-left gauge shift: Y = a^H (m = d^2 Mr rows, Ml columns) = Q2 R2 with
+// completions from X = P^H, P = right_partial(R, W, c).  Qs_bar: cotangent of the site Q2^H;
+// Cm_bar: cotangent of C = R2^H (NULL: none).  Writes abar (cotangent of a); adds the
+// candidates' cotangents to R (Rbar), c (cbar) and theta.
+void qr_left_reverse(const Ctx& ctx, const ShiftScratch& w, cplx* X, cplx* Y,
+                     const DevMpoSite& W, const double* Wd, int np, const double* dWd, int Ml,
+                     int Mr, int d, const cplx* R, const cplx* c, const cplx* Q2, const cplx* R2,
+                     const std::vector<unsigned char>& acc, const std::vector<int>& src,
+                     const cplx* Qs_bar, const cplx* Cm_bar, cplx* abar, cplx* Rbar, cplx* cbar,
+                     double* theta, std::vector<double>& tht) {
+  cudaStream_t st = ctx.st;
+  const int D = d * d;
+  const long long m = (long long)D * Mr, n = (long long)Ml * m;
+  const long long nr = (long long)W.Dr * Mr * Mr;
+  CK(ztranspose(Ml, (int)m, Qs_bar, w.Qb2, 1, st));
+  if (Cm_bar)
+    CK(ztranspose(Ml, Ml, Cm_bar, w.b3, 1, st));
+  else
+    CK(cudaMemsetAsync(w.b3, 0, sizeof(cplx) * (size_t)Ml * Ml, st));
+  std::vector<int> accv;
+  const std::vector<int> K = completed_positions(acc, accv);
+  const int p = W.Dl * Ml, nk = (int)K.size();
+  if (nk > 0) {
+    right_partial_f64(ctx, W, Ml, D, d, Mr, Mr, R, c, w.cand, nullptr);
+    CK(cudaMemsetAsync(w.Xsel, 0, sizeof(cplx) * (size_t)(m * nk), st));
+    for (int i = 0; i < nk; ++i) {
+      const int s = src[K[i]];
+      if (s < 0) throw Failure{TDMRG_ERR_CUDA, "gauge shift reverse: completion source not recorded"};
+      if (s < p) {
+        CK(cudaMemcpy2DAsync(w.Xsel + i, sizeof(cplx) * nk, w.cand + (long long)s * m,
+                             sizeof(cplx), sizeof(cplx), (size_t)m, cudaMemcpyDeviceToDevice, st));
+      } else {
+        const cplx one = kOne;
+        CK(cudaMemcpyAsync(w.Xsel + (long long)(s - p) * nk + i, &one, sizeof(cplx),
+                           cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+      }
+    }
+    CK(zconj(m * nk, w.Xsel, st));
+  }
+  call(tdmrg_kernel_qr_vjp_completed((int)m, Ml, accv.data(), Q2, R2, nk ? w.Xsel : nullptr,
+                                     w.Qb2, w.b3, w.Yb2, nk ? w.Xselb : nullptr, (void*)st));
+  CK(ztranspose((int)m, Ml, w.Yb2, abar, 1, st));
+  if (nk > 0) {
+    CK(cudaMemsetAsync(w.Xfullb, 0, sizeof(cplx) * (size_t)(m * p), st));
+    for (int i = 0; i < nk; ++i) {
+      const int s = src[K[i]];
+      if (s < p)
+        CK(cudaMemcpy2DAsync(w.Xfullb + s, sizeof(cplx) * p, w.Xselb + i, sizeof(cplx) * nk,
+                             sizeof(cplx), (size_t)m, cudaMemcpyDeviceToDevice, st));
+    }
+    call(tdmrg_kernel_expansion_vjp(1, Ml, Mr, d, W.Dl, W.Dr, Wd, np, dWd, R, c, w.Xfullb, w.e1,
+                                    w.s1, tht.data(), X, Y, (void*)st));
+    for (int q = 0; q < np; ++q) theta[q] += tht[q];
+    CK(zaxpy(nr, kOne, w.e1, Rbar, st));
+    CK(zaxpy(n, kOne, w.s1, cbar, st));
+  }
+}
+
+// Reverse of a left-to-right gauge shift: a (Ml d^2 x Mr) = Q R with completions from the
+// columns of left_partial(L, W, c).  Q_bar, R_bar (NULL: none) -> abar (written); adds the
+// candidates' cotangents to L (Lbar), c (cbar) and theta.
+void qr_right_reverse(const Ctx& ctx, const ShiftScratch& w, cplx* X, cplx* Y,
+                      const DevMpoSite& W, const double* Wd, int np, const double* dWd, int Ml,
+                      int Mr, int d, const cplx* L, const cplx* c, const cplx* Q, const cplx* R,
+                      const std::vector<unsigned char>& acc, const std::vector<int>& src,
+                      const cplx* Q_bar, const cplx* R_bar, cplx* abar, cplx* Lbar, cplx* cbar,
+                      double* theta, std::vector<double>& tht) {
+  cudaStream_t st = ctx.st;
+  const int D = d * d;
+  const long long m = (long long)Ml * D, n = m * Mr;
+  const long long nl = (long long)W.Dl * Ml * Ml;
+  if (R_bar)
+    CK(cudaMemcpyAsync(w.b3, R_bar, sizeof(cplx) * (size_t)Mr * Mr, cudaMemcpyDeviceToDevice, st));
+  else
+    CK(cudaMemsetAsync(w.b3, 0, sizeof(cplx) * (size_t)Mr * Mr, st));
+  std::vector<int> accv;
+  const std::vector<int> K = completed_positions(acc, accv);
+  const int p = W.Dr * Mr, nk = (int)K.size();
+  if (nk > 0) {
+    left_partial_f64(ctx, W, Ml, Ml, D, d, Mr, L, c, w.cand, nullptr);
+    CK(cudaMemsetAsync(w.Xsel, 0, sizeof(cplx) * (size_t)(m * nk), st));
+    for (int i = 0; i < nk; ++i) {
+      const int s = src[K[i]];
+      if (s < 0) throw Failure{TDMRG_ERR_CUDA, "gauge shift reverse: completion source not recorded"};
+      if (s < p) {
+        const long long v = s / Mr, cc = s % Mr;
+        CK(cudaMemcpy2DAsync(w.Xsel + i, sizeof(cplx) * nk, w.cand + v * n + cc,
+                             sizeof(cplx) * Mr, sizeof(cplx), (size_t)m, cudaMemcpyDeviceToDevice,
+                             st));
+      } else {
+        const cplx one = kOne;
+        CK(cudaMemcpyAsync(w.Xsel + (long long)(s - p) * nk + i, &one, sizeof(cplx),
+                           cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+      }
+    }
+  }
+  call(tdmrg_kernel_qr_vjp_completed((int)m, Mr, accv.data(), Q, R, nk ? w.Xsel : nullptr, Q_bar,
+                                     w.b3, abar, nk ? w.Xselb : nullptr, (void*)st));
+  if (nk > 0) {
+    CK(cudaMemsetAsync(w.Xfullb, 0, sizeof(cplx) * (size_t)(m * p), st));
+    for (int i = 0; i < nk; ++i) {
+      const int s = src[K[i]];
+      if (s < p)
+        CK(cudaMemcpy2DAsync(w.Xfullb + s, sizeof(cplx) * p, w.Xselb + i, sizeof(cplx) * nk,
+                             sizeof(cplx), (size_t)m, cudaMemcpyDeviceToDevice, st));
+    }
+    call(tdmrg_kernel_expansion_vjp(0, Ml, Mr, d, W.Dl, W.Dr, Wd, np, dWd, L, c, w.Xfullb, w.e1,
+                                    w.s1, tht.data(), X, Y, (void*)st));
+    for (int q = 0; q < np; ++q) theta[q] += tht[q];
+    CK(zaxpy(nl, kOne, w.e1, Lbar, st));
+    CK(zaxpy(n, kOne, w.s1, cbar, st));
+  }
+}
 }  // namespace
 
 void Engine::step_vjp(int M, const cplx* const* A_in, double tr, double ti,
                       const cplx* const* Abar_out, cplx* const* A_out, cplx* const* Abar_in,
-                      double* theta_bar, int nodes) {
+                      double* theta_bar, int nodes, bool normalize, double logn_bar,
+                      double* log_norm) {
   if (mixed()) throw Failure{TDMRG_ERR_ARG, "step_vjp: the reverse pass runs in FP64 precision"};
   const int L = (int)sites_.size();
   const std::vector<int> Mb = bond_dimensions(sites_, M);
@@ -236,15 +393,45 @@ void Engine::step_vjp(int M, const cplx* const* A_in, double tr, double ti,
              A[k - 1], Ml, 0, nullptr, st_));
     copy(A[k], Qs_rl[k], n[k]);
   }
+  // optional normalisation of the output center: A0 <- A0 / ||A0||, log ||A0||^2 reported
+  cplx* part = tp.get(257);
+  double nrm = 1.0;
+  cplx* A0raw = nullptr;
+  if (normalize) {
+    nrm = std::sqrt(dot(A[0], A[0], n[0], part, st_).real());
+    if (!std::isfinite(nrm) || nrm <= 0.0)
+      throw Failure{TDMRG_ERR_NONFINITE, "step_vjp: non-finite norm of the output center"};
+    A0raw = tp.get(n[0]);
+    copy(A0raw, A[0], n[0]);
+    scale_dev(A[0], n[0], 1.0 / nrm);
+    if (log_norm) *log_norm = 2.0 * std::log(nrm);
+  }
   if (A_out)
     for (int k = 0; k < L; ++k) copy(A_out[k], A[k], n[k]);
   check_status();
+  if (!Abar_out) {                       // forward only
+    CK(cudaStreamSynchronize(st_));
+    return;
+  }
 
   // ---- reverse ----
   std::vector<cplx*> ab(L), Lb(L), Rib(L), Rnb(L);
   for (int k = 0; k < L; ++k) {
     ab[k] = tp.get(n[k]);
     copy(ab[k], Abar_out[k], n[k]);
+  }
+  if (normalize) {
+    // A0n = A0 / n:  abar0 <- (g - Re<A0n, g> A0n) / n  (+ logn_bar * 2 A0 / n^2 for log n^2)
+    const double re = dot(A[0], ab[0], n[0], part, st_).real();
+    const cplx f = {-re, 0.0};
+    CK(zaxpy(n[0], f, A[0], ab[0], st_));
+    scale_dev(ab[0], n[0], 1.0 / nrm);
+    if (logn_bar != 0.0) {
+      const cplx lf = {2.0 * logn_bar / (nrm * nrm), 0.0};
+      CK(zaxpy(n[0], lf, A0raw, ab[0], st_));
+    }
+  }
+  for (int k = 0; k < L; ++k) {
     Lb[k] = tp.get(nL[k]);
     Rib[k] = tp.get(nR[k]);
     Rnb[k] = tp.get(nR[k]);
@@ -619,10 +806,10 @@ void Engine::correlation_states_vjp(int M, const cplx* const* psi1, const cplx* 
     for (int t = e0; t > s0; --t) {
       overlap_vjp(st1[t - s0], st2[t - s0], Mb, cb(t), g1, g2, th);
       step_vjp(M, st1[t - s0 - 1].data(), 0.0, -dt, g1.data(), nullptr, h1.data(), ths.data(),
-               nodes);
+               nodes, false, 0.0, nullptr);
       for (int p = 0; p < np; ++p) th[p] += ths[p];
       step_vjp(M, st2[t - s0 - 1].data(), 0.0, -dt, g2.data(), nullptr, h2.data(), ths.data(),
-               nodes);
+               nodes, false, 0.0, nullptr);
       for (int p = 0; p < np; ++p) th[p] += ths[p];
       std::swap(g1, h1);
       std::swap(g2, h2);
@@ -635,6 +822,452 @@ void Engine::correlation_states_vjp(int M, const cplx* const* psi1, const cplx* 
     CK(cudaMemcpyAsync(g2_out[k], g2[k], sizeof(cplx) * (size_t)n[k], cudaMemcpyDeviceToDevice,
                        st_));
   }
+  for (int p = 0; p < np; ++p) theta_bar[p] = th[p];
+  CK(cudaStreamSynchronize(st_));
+}
+
+namespace {
+// sizes of one call's MPS: bond dimensions, local dimensions, site sizes
+struct Dims {
+  std::vector<int> Mb, D, d;
+  std::vector<long long> n;
+  long long maxsite = 1, maxxy = 1, maxenv = 1;
+  int maxbond = 1;
+};
+}  // namespace
+
+static Dims make_dims(const std::vector<SiteInfo>& sites, int M, int Dmax) {
+  Dims z;
+  const int L = (int)sites.size();
+  z.Mb = bond_dimensions(sites, M);
+  z.D.resize(L);
+  z.d.resize(L);
+  z.n.resize(L);
+  for (int k = 0; k < L; ++k) {
+    z.d[k] = sites[k].d;
+    z.D[k] = z.d[k] * z.d[k];
+    z.n[k] = (long long)z.Mb[k] * z.D[k] * z.Mb[k + 1];
+    z.maxsite = std::max(z.maxsite, z.n[k]);
+    z.maxxy = std::max(z.maxxy, (long long)Dmax * z.n[k]);
+    z.maxenv = std::max(z.maxenv, (long long)Dmax * z.Mb[k] * z.Mb[k]);
+    z.maxenv = std::max(z.maxenv, (long long)Dmax * z.Mb[k + 1] * z.Mb[k + 1]);
+    z.maxbond = std::max(z.maxbond, z.Mb[k + 1]);
+  }
+  z.maxxy = std::max(z.maxxy, (long long)Dmax * z.maxbond * z.maxbond);
+  return z;
+}
+
+void Engine::canonicalize_vjp(int M, cplx* const* psi0, const cplx* const* gbar, double logn_bar,
+                              double* theta, double* log_norm) {
+  const int L = (int)sites_.size();
+  const Dims z = make_dims(sites_, M, std::max(H_.maxD, J_.maxD));
+  ensure_workspace(z.maxsite, z.maxxy, z.maxbond, z.maxbond);
+  const int np = parameter_count(P);
+  std::vector<std::vector<double>> Wd(L), dWd(L);
+  for (int k = 0; k < L; ++k) {
+    const DevMpoSite& W = H_.s[k];
+    Wd[k] = dense_site(W.Dl, W.Dr, W.d, W.host);
+    for (int p = 0; p < np; ++p) {
+      const auto x = dense_site(W.Dl, W.Dr, W.d, mpo_site_derivative(P, 0, p, k).blocks);
+      dWd[k].insert(dWd[k].end(), x.begin(), x.end());
+    }
+  }
+  auto copy = [&](cplx* dst, const cplx* src, long long cnt) {
+    CK(cudaMemcpyAsync(dst, src, sizeof(cplx) * (size_t)cnt, cudaMemcpyDeviceToDevice, st_));
+  };
+  Ctx c = ctx();
+  Tape tp;
+  std::vector<cplx*> A(L), Renv(L), ain(L), Q2(L), R2(L), Qs(L), Cm(L), nxt(L);
+  std::vector<std::vector<unsigned char>> acc(L);
+  std::vector<std::vector<int>> src(L);
+  std::vector<long long> nR(L);
+  // |I> on the one-carrier sector
+  const auto ent = identity_state_entries(P);
+  size_t maxe = 1;
+  for (auto& e : ent) maxe = std::max(maxe, e.size());
+  int* d_ent = tp.geti((long long)maxe);
+  for (int k = 0; k < L; ++k) {
+    A[k] = tp.get(z.n[k]);
+    nR[k] = (long long)H_.s[k].Dr * z.Mb[k + 1] * z.Mb[k + 1];
+    Renv[k] = tp.get(nR[k]);
+    CK(cudaMemcpy(d_ent, ent[k].data(), sizeof(int) * ent[k].size(), cudaMemcpyHostToDevice));
+    CK(zfill_identity_mps(A[k], z.Mb[k], z.D[k], z.Mb[k + 1], d_ent, (int)ent[k].size() / 3, st_));
+    CK(cudaStreamSynchronize(st_));
+  }
+  int* src_dev = tp.geti(z.maxbond);
+  set_ones(Renv[L - 1]);
+  for (int k = L - 1; k > 0; --k) {
+    const DevMpoSite& W = H_.s[k];
+    const int Ml = z.Mb[k], Mr = z.Mb[k + 1];
+    const long long m = (long long)z.D[k] * Mr;
+    ain[k] = tp.get(z.n[k]);
+    copy(ain[k], A[k], z.n[k]);
+    right_partial_f64(c, W, Ml, z.D[k], z.d[k], Mr, Mr, Renv[k], A[k], Y_, nullptr);
+    CK(cudaMemsetAsync(src_dev, 0xff, sizeof(int) * (size_t)Ml, st_));
+    Q2[k] = tp.get(z.n[k]);
+    R2[k] = tp.get((long long)Ml * Ml);
+    gauge_qr_dev((int)m, Ml, qr(A[k], 1, m, kNoSplit, 0, 1), W.Dl * Ml, qr(Y_, 1, m, kNoSplit, 0, 1),
+                 Q2[k], R2[k], src_dev);
+    acc[k].resize(Ml);
+    src[k].resize(Ml);
+    CK(cudaMemcpyAsync(acc[k].data(), qb_acc_, (size_t)Ml, cudaMemcpyDeviceToHost, st_));
+    CK(cudaMemcpyAsync(src[k].data(), src_dev, sizeof(int) * (size_t)Ml, cudaMemcpyDeviceToHost,
+                       st_));
+    CK(cudaStreamSynchronize(st_));
+    Qs[k] = tp.get(z.n[k]);
+    Cm[k] = tp.get((long long)Ml * Ml);
+    CK(ztranspose((int)m, Ml, Q2[k], Qs[k], 1, st_));
+    CK(ztranspose(Ml, Ml, R2[k], Cm[k], 1, st_));
+    env_right_f64(c, W, Ml, Mr, Ml, Mr, z.D[k], z.d[k], Renv[k], Qs[k], Qs[k], Renv[k - 1]);
+    nxt[k] = tp.get(z.n[k - 1]);
+    copy(nxt[k], A[k - 1], z.n[k - 1]);
+    const long long nrows = (long long)z.Mb[k - 1] * z.D[k - 1];
+    CK(zgemm((int)nrows, Ml, Ml, 1, 1, kOne, mr(nxt[k], Ml, 1), mr(Cm[k], Ml, 1), kZero, A[k - 1],
+             Ml, 0, nullptr, st_));
+    copy(A[k], Qs[k], z.n[k]);
+  }
+  cplx* part = tp.get(257);
+  const double nrm = std::sqrt(dot(A[0], A[0], z.n[0], part, st_).real());
+  if (!std::isfinite(nrm) || nrm <= 0.0)
+    throw Failure{TDMRG_ERR_NONFINITE, "canonicalize_vjp: non-finite norm"};
+  cplx* A0raw = tp.get(z.n[0]);
+  copy(A0raw, A[0], z.n[0]);
+  scale_dev(A[0], z.n[0], 1.0 / nrm);
+  if (log_norm) *log_norm = 2.0 * std::log(nrm);
+  for (int k = 0; k < L; ++k) copy(psi0[k], A[k], z.n[k]);
+  check_status();
+  if (!gbar) {
+    CK(cudaStreamSynchronize(st_));
+    return;
+  }
+  // ---- reverse ----
+  std::vector<cplx*> ab(L), Rb(L);
+  for (int k = 0; k < L; ++k) {
+    ab[k] = tp.get(z.n[k]);
+    copy(ab[k], gbar[k], z.n[k]);
+    Rb[k] = tp.get(nR[k]);
+    CK(cudaMemsetAsync(Rb[k], 0, sizeof(cplx) * (size_t)nR[k], st_));
+  }
+  {
+    const double re = dot(A[0], ab[0], z.n[0], part, st_).real();
+    const cplx f = {-re, 0.0};
+    CK(zaxpy(z.n[0], f, A[0], ab[0], st_));
+    scale_dev(ab[0], z.n[0], 1.0 / nrm);
+    if (logn_bar != 0.0) {
+      const cplx lf = {2.0 * logn_bar / (nrm * nrm), 0.0};
+      CK(zaxpy(z.n[0], lf, A0raw, ab[0], st_));
+    }
+  }
+  ShiftScratch w{tp.get(z.maxsite), tp.get(z.maxsite), tp.get((long long)z.maxbond * z.maxbond),
+                 tp.get(z.maxsite), tp.get(z.maxsite), tp.get(z.maxxy), tp.get(z.maxxy),
+                 tp.get(z.maxenv), tp.get(z.maxsite)};
+  cplx* bb = tp.get(z.maxsite);
+  cplx* kb = tp.get(z.maxsite);
+  cplx* qsb = tp.get(z.maxsite);
+  cplx* t1 = tp.get(z.maxsite);
+  cplx* a1b = tp.get(z.maxsite);
+  cplx* e1 = tp.get(z.maxenv);
+  cplx* cmb = tp.get((long long)z.maxbond * z.maxbond);
+  std::vector<double> tht(np > 0 ? np : 1, 0.0);
+  for (int k = 1; k < L; ++k) {
+    const DevMpoSite& W = H_.s[k];
+    const int Ml = z.Mb[k], Mr = z.Mb[k + 1];
+    const long long nrows = (long long)z.Mb[k - 1] * z.D[k - 1];
+    // A[k-1] = nxt Cm:  Cmbar = nxt^H abar,  abar <- abar Cm^H
+    CK(zgemm(Ml, Ml, (int)nrows, 1, 1, kOne, mr(nxt[k], 1, Ml, 1), mr(ab[k - 1], Ml, 1), kZero,
+             cmb, Ml, 0, nullptr, st_));
+    CK(zgemm((int)nrows, Ml, Ml, 1, 1, kOne, mr(ab[k - 1], Ml, 1), mr(Cm[k], 1, Ml, 1), kZero, t1,
+             Ml, 0, nullptr, st_));
+    copy(ab[k - 1], t1, z.n[k - 1]);
+    // Renv[k-1] = env_right(Renv[k], Qs, W, Qs)
+    call(tdmrg_kernel_env_vjp(1, Ml, Mr, z.d[k], W.Dl, W.Dr, Wd[k].data(), np,
+                              np > 0 ? dWd[k].data() : nullptr, Renv[k], Qs[k], Qs[k], Rb[k - 1],
+                              e1, bb, kb, tht.data(), X_, Y_, (void*)st_));
+    for (int q = 0; q < np; ++q) theta[q] += tht[q];
+    CK(zaxpy(nR[k], kOne, e1, Rb[k], st_));
+    copy(qsb, ab[k], z.n[k]);
+    CK(zaxpy(z.n[k], kOne, bb, qsb, st_));
+    CK(zaxpy(z.n[k], kOne, kb, qsb, st_));
+    // LQ of ain with completions from right_partial(Renv[k], W, ain)
+    qr_left_reverse(c, w, X_, Y_, W, Wd[k].data(), np, np > 0 ? dWd[k].data() : nullptr, Ml, Mr,
+                    z.d[k], Renv[k], ain[k], Q2[k], R2[k], acc[k], src[k], qsb, cmb, a1b, Rb[k],
+                    a1b, theta, tht);
+    copy(ab[k], a1b, z.n[k]);
+  }
+  CK(cudaStreamSynchronize(st_));
+  check_status();
+}
+
+void Engine::fit_vjp(int M, const cplx* const* psi, cplx* const* phi, const cplx* const* gphi,
+                     cplx* const* gpsi, double* theta) {
+  const int L = (int)sites_.size();
+  const Dims z = make_dims(sites_, M, std::max(H_.maxD, J_.maxD));
+  ensure_workspace(z.maxsite, z.maxxy, z.maxbond, z.maxbond);
+  const int np = parameter_count(P);
+  constexpr int S = 2;   // sweeps, as in realtime_init
+  std::vector<std::vector<double>> Jd(L), dJd(L);
+  for (int k = 0; k < L; ++k) {
+    const DevMpoSite& W = J_.s[k];
+    Jd[k] = dense_site(W.Dl, W.Dr, W.d, W.host);
+    for (int p = 0; p < np; ++p) {
+      const auto x = dense_site(W.Dl, W.Dr, W.d, mpo_site_derivative(P, 1, p, k).blocks);
+      dJd[k].insert(dJd[k].end(), x.begin(), x.end());
+    }
+  }
+  auto dJ = [&](int k) { return np > 0 ? dJd[k].data() : nullptr; };
+  auto copy = [&](cplx* dst, const cplx* src, long long cnt) {
+    CK(cudaMemcpyAsync(dst, src, sizeof(cplx) * (size_t)cnt, cudaMemcpyDeviceToDevice, st_));
+  };
+  std::vector<long long> nLj(L), nRj(L);
+  for (int k = 0; k < L; ++k) {
+    nLj[k] = (long long)J_.s[k].Dl * z.Mb[k] * z.Mb[k];
+    nRj[k] = (long long)J_.s[k].Dr * z.Mb[k + 1] * z.Mb[k + 1];
+  }
+  Ctx c = ctx();
+  Tape tp;
+  int* src_dev = tp.geti(z.maxbond);
+  auto flags = [&](int cols, std::vector<unsigned char>& acc, std::vector<int>& src) {
+    acc.resize(cols);
+    src.resize(cols);
+    CK(cudaMemcpyAsync(acc.data(), qb_acc_, (size_t)cols, cudaMemcpyDeviceToHost, st_));
+    CK(cudaMemcpyAsync(src.data(), src_dev, sizeof(int) * (size_t)cols, cudaMemcpyDeviceToHost,
+                       st_));
+    CK(cudaStreamSynchronize(st_));
+  };
+  // initial right environments, phi = psi: Rf0[k-1] = env_right(Rf0[k], psi, j, psi)
+  std::vector<cplx*> Rf0(L);
+  for (int k = 0; k < L; ++k) Rf0[k] = tp.get(nRj[k]);
+  set_ones(Rf0[L - 1]);
+  for (int k = L - 1; k > 0; --k)
+    env_right_f64(c, J_.s[k], z.Mb[k], z.Mb[k + 1], z.Mb[k], z.Mb[k + 1], z.D[k], z.d[k], Rf0[k],
+                  psi[k], psi[k], Rf0[k - 1]);
+  struct Sweep {
+    std::vector<cplx*> Lf, Rn, a_lr, Q_lr, R_lr, a_rl, Q2_rl, R2_rl, Qs_rl;
+    std::vector<std::vector<unsigned char>> acc_lr, acc_rl;
+    std::vector<std::vector<int>> src_lr, src_rl;
+  };
+  std::vector<Sweep> sw(S);
+  std::vector<cplx*> ph(L);
+  for (int s = 0; s < S; ++s) {
+    Sweep& q = sw[s];
+    for (auto* v : {&q.Lf, &q.Rn, &q.a_lr, &q.Q_lr, &q.R_lr, &q.a_rl, &q.Q2_rl, &q.R2_rl, &q.Qs_rl})
+      v->assign(L, nullptr);
+    q.acc_lr.resize(L);
+    q.acc_rl.resize(L);
+    q.src_lr.resize(L);
+    q.src_rl.resize(L);
+    const std::vector<cplx*>& Rin = s == 0 ? Rf0 : sw[s - 1].Rn;
+    for (int k = 0; k < L; ++k) q.Lf[k] = tp.get(nLj[k]);
+    set_ones(q.Lf[0]);
+    for (int k = 0; k < L; ++k) {
+      const DevMpoSite& W = J_.s[k];
+      const int Ml = z.Mb[k], Mr = z.Mb[k + 1];
+      q.a_lr[k] = tp.get(z.n[k]);
+      heff_f64(c, W, Ml, Mr, z.D[k], z.d[k], q.Lf[k], Rin[k], psi[k], q.a_lr[k], nullptr);
+      if (k == L - 1) {
+        ph[k] = q.a_lr[k];
+        continue;
+      }
+      left_partial_f64(c, W, Ml, Ml, z.D[k], z.d[k], Mr, q.Lf[k], psi[k], Y_, nullptr);
+      CK(cudaMemsetAsync(src_dev, 0xff, sizeof(int) * (size_t)Mr, st_));
+      q.Q_lr[k] = tp.get(z.n[k]);
+      q.R_lr[k] = tp.get((long long)Mr * Mr);
+      gauge_qr_dev(Ml * z.D[k], Mr, qr(q.a_lr[k], Mr, 1, kNoSplit, 0, 0), W.Dr * Mr,
+                   qr(Y_, Mr, 1, Mr, z.n[k], 0), q.Q_lr[k], q.R_lr[k], src_dev);
+      flags(Mr, q.acc_lr[k], q.src_lr[k]);
+      env_left_f64(c, W, Ml, Mr, Ml, Mr, z.D[k], z.d[k], q.Lf[k], q.Q_lr[k], psi[k], q.Lf[k + 1]);
+      ph[k] = q.Q_lr[k];
+    }
+    for (int k = 0; k < L; ++k) q.Rn[k] = tp.get(nRj[k]);
+    set_ones(q.Rn[L - 1]);
+    for (int k = L - 1; k >= 0; --k) {
+      const DevMpoSite& W = J_.s[k];
+      const int Ml = z.Mb[k], Mr = z.Mb[k + 1];
+      const long long m = (long long)z.D[k] * Mr;
+      q.a_rl[k] = tp.get(z.n[k]);
+      heff_f64(c, W, Ml, Mr, z.D[k], z.d[k], q.Lf[k], q.Rn[k], psi[k], q.a_rl[k], nullptr);
+      if (k == 0) {
+        ph[0] = q.a_rl[0];
+        continue;
+      }
+      right_partial_f64(c, W, Ml, z.D[k], z.d[k], Mr, Mr, q.Rn[k], psi[k], Y_, nullptr);
+      CK(cudaMemsetAsync(src_dev, 0xff, sizeof(int) * (size_t)Ml, st_));
+      q.Q2_rl[k] = tp.get(z.n[k]);
+      q.R2_rl[k] = tp.get((long long)Ml * Ml);
+      gauge_qr_dev((int)m, Ml, qr(q.a_rl[k], 1, m, kNoSplit, 0, 1), W.Dl * Ml,
+                   qr(Y_, 1, m, kNoSplit, 0, 1), q.Q2_rl[k], q.R2_rl[k], src_dev);
+      flags(Ml, q.acc_rl[k], q.src_rl[k]);
+      q.Qs_rl[k] = tp.get(z.n[k]);
+      CK(ztranspose((int)m, Ml, q.Q2_rl[k], q.Qs_rl[k], 1, st_));
+      env_right_f64(c, W, Ml, Mr, Ml, Mr, z.D[k], z.d[k], q.Rn[k], q.Qs_rl[k], psi[k],
+                    q.Rn[k - 1]);
+      ph[k] = q.Qs_rl[k];
+    }
+  }
+  for (int k = 0; k < L; ++k) copy(phi[k], ph[k], z.n[k]);
+  check_status();
+  if (!gphi) {
+    CK(cudaStreamSynchronize(st_));
+    return;
+  }
+  // ---- reverse ----
+  std::vector<std::vector<cplx*>> Lb(S, std::vector<cplx*>(L)), Rnb(S, std::vector<cplx*>(L));
+  std::vector<cplx*> R0b(L);
+  for (int k = 0; k < L; ++k) {
+    R0b[k] = tp.get(nRj[k]);
+    CK(cudaMemsetAsync(R0b[k], 0, sizeof(cplx) * (size_t)nRj[k], st_));
+    for (int s = 0; s < S; ++s) {
+      Lb[s][k] = tp.get(nLj[k]);
+      Rnb[s][k] = tp.get(nRj[k]);
+      CK(cudaMemsetAsync(Lb[s][k], 0, sizeof(cplx) * (size_t)nLj[k], st_));
+      CK(cudaMemsetAsync(Rnb[s][k], 0, sizeof(cplx) * (size_t)nRj[k], st_));
+    }
+  }
+  ShiftScratch w{tp.get(z.maxsite), tp.get(z.maxsite), tp.get((long long)z.maxbond * z.maxbond),
+                 tp.get(z.maxsite), tp.get(z.maxsite), tp.get(z.maxxy), tp.get(z.maxxy),
+                 tp.get(z.maxenv), tp.get(z.maxsite)};
+  cplx* phib = tp.get(z.maxsite);
+  cplx* ab = tp.get(z.maxsite);
+  cplx* bb = tp.get(z.maxsite);
+  cplx* kb = tp.get(z.maxsite);
+  cplx* tA = tp.get(z.maxsite);
+  cplx* e1 = tp.get(z.maxenv);
+  cplx* tL = tp.get(z.maxenv);
+  cplx* tR = tp.get(z.maxenv);
+  cplx* part = tp.get(257);
+  std::vector<double> tht(np > 0 ? np : 1, 0.0);
+  // a = H_eff(L, j, R) psi with cotangent abar: psi, L, R cotangents and the parameters
+  auto heff_reverse = [&](int k, const cplx* Le, const cplx* Re, const cplx* abar, cplx* Lbar,
+                          cplx* Rbar) {
+    const DevMpoSite& W = J_.s[k];
+    const int Ml = z.Mb[k], Mr = z.Mb[k + 1];
+    call(tdmrg_kernel_heff_vjp(Ml, Mr, z.d[k], W.Dl, W.Dr, Jd[k].data(), Le, Re, psi[k], abar, tA,
+                               tL, tR, X_, Y_, (void*)st_));
+    CK(zaxpy(z.n[k], kOne, tA, gpsi[k], st_));
+    CK(zaxpy(nLj[k], kOne, tL, Lbar, st_));
+    CK(zaxpy(nRj[k], kOne, tR, Rbar, st_));
+    for (int p = 0; p < np; ++p) {
+      const MpoSite dW = mpo_site_derivative(P, 1, p, k);
+      if (dW.blocks.empty()) continue;
+      DevMpo dm;
+      upload_mpo({dW}, dm);
+      struct FreeMpo {
+        DevMpo& m;
+        ~FreeMpo() { free_mpo(m); }
+      } fm{dm};
+      heff_f64(c, dm.s[0], Ml, Mr, z.D[k], z.d[k], Le, Re, psi[k], bb, nullptr);
+      theta[p] += dot(abar, bb, z.n[k], part, st_).real();
+    }
+  };
+  for (int s = S - 1; s >= 0; --s) {
+    Sweep& q = sw[s];
+    std::vector<cplx*>& Rinb = s == 0 ? R0b : Rnb[s - 1];
+    const std::vector<cplx*>& Rin = s == 0 ? Rf0 : sw[s - 1].Rn;
+    // right-to-left half, last update first; the output phi is this half's last sweep
+    for (int k = 0; k < L; ++k) {
+      const DevMpoSite& W = J_.s[k];
+      const int Ml = z.Mb[k], Mr = z.Mb[k + 1];
+      if (s == S - 1)
+        copy(phib, gphi[k], z.n[k]);
+      else
+        CK(cudaMemsetAsync(phib, 0, sizeof(cplx) * (size_t)z.n[k], st_));
+      if (k > 0) {
+        // Rn[k-1] = env_right(Rn[k], Qs (bra), j, psi (ket))
+        call(tdmrg_kernel_env_vjp(1, Ml, Mr, z.d[k], W.Dl, W.Dr, Jd[k].data(), np, dJ(k),
+                                  q.Rn[k], q.Qs_rl[k], psi[k], Rnb[s][k - 1], e1, bb, kb,
+                                  tht.data(), X_, Y_, (void*)st_));
+        for (int p = 0; p < np; ++p) theta[p] += tht[p];
+        CK(zaxpy(nRj[k], kOne, e1, Rnb[s][k], st_));
+        CK(zaxpy(z.n[k], kOne, bb, phib, st_));
+        CK(zaxpy(z.n[k], kOne, kb, gpsi[k], st_));
+        qr_left_reverse(c, w, X_, Y_, W, Jd[k].data(), np, dJ(k), Ml, Mr, z.d[k], q.Rn[k], psi[k],
+                        q.Q2_rl[k], q.R2_rl[k], q.acc_rl[k], q.src_rl[k], phib, nullptr, ab,
+                        Rnb[s][k], gpsi[k], theta, tht);
+      } else {
+        copy(ab, phib, z.n[0]);
+      }
+      heff_reverse(k, q.Lf[k], q.Rn[k], ab, Lb[s][k], Rnb[s][k]);
+    }
+    // left-to-right half, last update first (its last site is overwritten unread)
+    for (int k = L - 2; k >= 0; --k) {
+      const DevMpoSite& W = J_.s[k];
+      const int Ml = z.Mb[k], Mr = z.Mb[k + 1];
+      // Lf[k+1] = env_left(Lf[k], Q (bra), j, psi (ket))
+      call(tdmrg_kernel_env_vjp(0, Ml, Mr, z.d[k], W.Dl, W.Dr, Jd[k].data(), np, dJ(k), q.Lf[k],
+                                q.Q_lr[k], psi[k], Lb[s][k + 1], e1, phib, kb, tht.data(), X_, Y_,
+                                (void*)st_));
+      for (int p = 0; p < np; ++p) theta[p] += tht[p];
+      CK(zaxpy(nLj[k], kOne, e1, Lb[s][k], st_));
+      CK(zaxpy(z.n[k], kOne, kb, gpsi[k], st_));
+      qr_right_reverse(c, w, X_, Y_, W, Jd[k].data(), np, dJ(k), Ml, Mr, z.d[k], q.Lf[k], psi[k],
+                       q.Q_lr[k], q.R_lr[k], q.acc_lr[k], q.src_lr[k], phib, nullptr, ab,
+                       Lb[s][k], gpsi[k], theta, tht);
+      heff_reverse(k, q.Lf[k], Rin[k], ab, Lb[s][k], Rinb[k]);
+    }
+  }
+  // the initial right environments (bra and ket both psi)
+  for (int k = 1; k < L; ++k) {
+    const DevMpoSite& W = J_.s[k];
+    call(tdmrg_kernel_env_vjp(1, z.Mb[k], z.Mb[k + 1], z.d[k], W.Dl, W.Dr, Jd[k].data(), np,
+                              dJ(k), Rf0[k], psi[k], psi[k], R0b[k - 1], e1, bb, kb, tht.data(),
+                              X_, Y_, (void*)st_));
+    for (int p = 0; p < np; ++p) theta[p] += tht[p];
+    CK(zaxpy(nRj[k], kOne, e1, R0b[k], st_));
+    CK(zaxpy(z.n[k], kOne, bb, gpsi[k], st_));
+    CK(zaxpy(z.n[k], kOne, kb, gpsi[k], st_));
+  }
+  CK(cudaStreamSynchronize(st_));
+  check_status();
+}
+
+void Engine::correlation_vjp(double beta, double dtau, int M, double dt, int nsteps, int every,
+                             const double* cbar, double* C, double* theta_bar, double* logz,
+                             int nodes) {
+  if (mixed()) throw Failure{TDMRG_ERR_ARG, "correlation_vjp: the reverse pass runs in FP64 precision"};
+  if (!(beta > 0.0) || !(dtau > 0.0) || M < 2 || !(dt > 0.0) || nsteps < 0 || every < 1)
+    throw Failure{TDMRG_ERR_ARG, "correlation_vjp: bad arguments"};
+  const long long ntau = std::llround(beta / (2.0 * dtau));
+  if (ntau < 1 || std::fabs(ntau * 2.0 * dtau - beta) > 1e-9 * std::max(1.0, beta))
+    throw Failure{TDMRG_ERR_ARG, "correlation_vjp: beta must be an even multiple of dtau"};
+  const int L = (int)sites_.size();
+  const int np = parameter_count(P);
+  const Dims z = make_dims(sites_, M, std::max(H_.maxD, J_.maxD));
+  Tape tp;
+  auto state = [&]() {
+    std::vector<cplx*> a(L);
+    for (int k = 0; k < L; ++k) a[k] = tp.get(z.n[k]);
+    return a;
+  };
+  std::vector<double> th(np, 0.0), ths(np > 0 ? np : 1, 0.0);
+  // forward: |I> canonicalised and normalised, imaginary-time steps each normalised, the fit
+  std::vector<std::vector<cplx*>> psi(ntau + 1);
+  psi[0] = state();
+  double lz = 0.0, ln = 0.0;
+  canonicalize_vjp(M, psi[0].data(), nullptr, 0.0, nullptr, &ln);
+  lz += ln;
+  for (long long i = 1; i <= ntau; ++i) {
+    psi[i] = state();
+    step_vjp(M, psi[i - 1].data(), -dtau, 0.0, nullptr, psi[i].data(), nullptr, ths.data(), nodes,
+             true, 0.0, &ln);
+    lz += ln;
+  }
+  if (logz) *logz = lz;
+  std::vector<cplx*> phi = state(), g1 = state(), g2 = state(), h = state();
+  fit_vjp(M, psi[ntau].data(), phi.data(), nullptr, nullptr, nullptr);
+  // real time with its reverse
+  correlation_states_vjp(M, psi[ntau].data(), phi.data(), dt, nsteps, every, cbar, C, g1.data(),
+                         g2.data(), ths.data(), nodes);
+  for (int p = 0; p < np; ++p) th[p] += ths[p];
+  // the fit: psi_beta receives the cotangent through phi
+  fit_vjp(M, psi[ntau].data(), h.data(), g2.data(), g1.data(), th.data());
+  // the preparation, last step first
+  for (long long i = ntau; i >= 1; --i) {
+    step_vjp(M, psi[i - 1].data(), -dtau, 0.0, g1.data(), nullptr, h.data(), ths.data(), nodes,
+             true, 0.0, nullptr);
+    for (int p = 0; p < np; ++p) th[p] += ths[p];
+    std::swap(g1, h);
+  }
+  canonicalize_vjp(M, h.data(), g1.data(), 0.0, th.data(), nullptr);
   for (int p = 0; p < np; ++p) theta_bar[p] = th[p];
   CK(cudaStreamSynchronize(st_));
 }

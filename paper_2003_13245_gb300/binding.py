@@ -521,3 +521,57 @@ def kernel_krylov_dense(H, v, out, tau, tol=1e-13, kmax=32, stream=None):
                                          float(np.real(tau)), float(np.imag(tau)), float(tol),
                                          int(kmax), ctypes.byref(k), _stream_ptr(stream)))
     return k.value
+
+
+# --- differentiable C(t) ----------------------------------------------------------------------
+
+def _correlation_function():
+    import torch
+
+    class CorrelationFunction(torch.autograd.Function):
+        """C(t_n), t_n = n dt (n = 0..nsteps), of the chain as a differentiable function of the
+        parameters theta = (omega_0.., g_0.., V) (a float64 tensor): forward through
+        tdmrg_thermal_prepare / tdmrg_correlation, backward through tdmrg_correlation_vjp
+        (FP64).  spec: dict with N, nmax, beta, dtau, M, dt, nsteps and optionally every,
+        rank_tol, nodes.  PyTorch's gradient of a real loss with respect to a complex output,
+        dl/dRe C + i dl/dIm C, is the cotangent Cbar of dl = Re sum conj(Cbar_n) dC_n."""
+
+        @staticmethod
+        def forward(ctx, theta, spec):
+            K = len(spec["nmax"])
+            th = theta.detach().cpu().numpy().astype(np.float64)
+            m = Model(spec["N"], th[:K], th[K:2 * K], spec["nmax"], float(th[2 * K]))
+            try:
+                if spec.get("rank_tol") is not None:
+                    m.set_rank_tol(spec["rank_tol"])
+                m.thermal_prepare(spec["beta"], spec["dtau"], spec["M"])
+                t = np.arange(spec["nsteps"] + 1) * spec["dt"]
+                C = m.correlation(t, spec["dt"])
+            finally:
+                m.close()
+            ctx.spec = spec
+            ctx.theta = th
+            return torch.as_tensor(np.asarray(C), dtype=torch.complex128)
+
+        @staticmethod
+        def backward(ctx, gC):
+            spec, th = ctx.spec, ctx.theta
+            K = len(spec["nmax"])
+            m = Model(spec["N"], th[:K], th[K:2 * K], spec["nmax"], float(th[2 * K]))
+            try:
+                if spec.get("rank_tol") is not None:
+                    m.set_rank_tol(spec["rank_tol"])
+                cbar = gC.detach().cpu().numpy().astype(np.complex128)
+                _, tb, _ = m.correlation_vjp(spec["beta"], spec["dtau"], spec["M"], spec["dt"],
+                                             spec["nsteps"], cbar, every=spec.get("every", 2),
+                                             nodes=spec.get("nodes", 16))
+            finally:
+                m.close()
+            return torch.as_tensor(tb, dtype=torch.float64), None
+
+    return CorrelationFunction
+
+
+def correlation_autograd(theta, spec):
+    """C(t) as a differentiable function of theta (see _correlation_function)."""
+    return _correlation_function().apply(theta, spec)

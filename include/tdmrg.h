@@ -204,6 +204,14 @@ int tdmrg_host_mpo_site(int N, int modes, const double* omega, const double* g, 
                         const int* nmax, double alpha, double omega_p, int nmax_p, int which,
                         int param, int site, int* dims, double* W_out);
 
+/* exp(z_s T) e_1, s < nz, for the real symmetric tridiagonal Lanczos matrix T = tridiag(beta,
+ * alpha, beta) (alpha[k] diagonal, beta[k-1] off-diagonal, 1 <= k <= 64), from one cyclic
+ * Jacobi eigendecomposition of T on the host (no handle, no GPU): z[2 nz] interleaved complex,
+ * out[2 k nz] interleaved, layout [s][k].  The small exponentials a reverse pass needs at many
+ * points of [0, tau] from one Krylov basis. */
+int tdmrg_host_tridiag_exp(int k, const double* alpha, const double* beta, int nz,
+                           const double* z, double* out);
+
 /* log Z = log Tr[exp(-beta H) P_1] accumulated by tdmrg_thermal_prepare. */
 int tdmrg_get_logz(const tdmrg_model* h, double* logz);
 

@@ -81,6 +81,7 @@ _SIGS = {
     "tdmrg_step_vjp": [_p, _i, _pp, _d, _d, _pp, _pp, _pp, _dp, _i],
     "tdmrg_correlation_states_vjp": [_p, _i, _pp, _pp, _d, _i, _i, _dp, _dp, _pp, _pp, _dp, _i],
     "tdmrg_correlation_vjp": [_p, _d, _d, _i, _d, _i, _i, _dp, _dp, _dp, _dp, _i],
+    "tdmrg_host_tridiag_exp": [_i, _dp, _dp, _i, _dp, _dp],
 }
 
 
@@ -311,6 +312,18 @@ def mobility(t_grid, C, kT):
     mu = ctypes.c_double()
     _check(lib.tdmrg_mobility(_dptr(t), _dptr(c), int(t.size), float(kT), ctypes.byref(mu)))
     return mu.value
+
+
+def host_tridiag_exp(alpha, beta, z):
+    """exp(z_s T) e_1 for T = tridiag(beta, alpha, beta) at the complex points z (host only);
+    returns an array [len(z), len(alpha)]."""
+    a = np.ascontiguousarray(alpha, dtype=np.float64)
+    b = np.ascontiguousarray(beta, dtype=np.float64) if len(beta) else np.zeros(1)
+    zz = np.ascontiguousarray(np.asarray(z, dtype=np.complex128)).view(np.float64)
+    out = np.zeros(2 * a.size * (zz.size // 2))
+    _check(load().tdmrg_host_tridiag_exp(int(a.size), _dptr(a), _dptr(b), int(zz.size // 2),
+                                         _dptr(zz), _dptr(out)))
+    return (out[0::2] + 1j * out[1::2]).reshape(-1, a.size)
 
 
 MPO_H, MPO_J, MPO_IDENTITY = 0, 1, 2

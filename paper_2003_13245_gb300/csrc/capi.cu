@@ -9,6 +9,7 @@
 
 #include "../../include/tdmrg.h"
 #include "engine.h"
+#include "small_exp.h"
 #include "tc.cuh"
 
 using tdmrg::Engine;
@@ -451,6 +452,24 @@ int tdmrg_correlation_vjp(tdmrg_model* h, double beta, double dtau, int M, doubl
   return guarded(h, [&] {
     h->eng->correlation_vjp(beta, dtau, M, dt, nsteps, every, Cbar, C_out, theta_bar, logz_out,
                             nodes);
+  });
+}
+
+int tdmrg_host_tridiag_exp(int k, const double* alpha, const double* beta, int nz,
+                           const double* z, double* out) {
+  if (k < 1 || k > 64 || nz < 0 || !alpha || (k > 1 && !beta) || (nz > 0 && (!z || !out)))
+    return fail(nullptr, TDMRG_ERR_ARG, "host_tridiag_exp: need 1 <= k <= 64 and non-NULL arrays");
+  for (int i = 0; i < k; ++i)
+    if (!std::isfinite(alpha[i]) || (i + 1 < k && !std::isfinite(beta[i])))
+      return fail(nullptr, TDMRG_ERR_ARG, "host_tridiag_exp: non-finite entry");
+  return guarded(nullptr, [&] {
+    std::vector<tdmrg::Cx> zz(nz), o((size_t)nz * k);
+    for (int s = 0; s < nz; ++s) zz[s] = tdmrg::Cx(z[2 * s], z[2 * s + 1]);
+    tdmrg::tridiag_exp_e1(k, alpha, beta, nz, zz.data(), o.data());
+    for (size_t i = 0; i < o.size(); ++i) {
+      out[2 * i] = o[i].real();
+      out[2 * i + 1] = o[i].imag();
+    }
   });
 }
 

@@ -1,0 +1,18 @@
+// Small exponentials of a Lanczos matrix on the host (small_exp.cpp; no CUDA).
+#pragma once
+#include <complex>
+#include <vector>
+
+namespace tdmrg {
+
+typedef std::complex<double> Cx;
+
+// Eigendecomposition of a dense real symmetric k x k matrix A (row-major, destroyed) by cyclic
+// Jacobi rotations: eigenvalues w[k], eigenvectors in the columns of Z (row-major k x k).
+void symmetric_eigen(int k, std::vector<double>& A, std::vector<double>& w, std::vector<double>& Z);
+
+// out[s][0..k) = exp(z_s T) e_1 for T = tridiag(beta, alpha, beta) (alpha[k] diagonal,
+// beta[k-1] off-diagonal), s < nz.
+void tridiag_exp_e1(int k, const double* alpha, const double* beta, int nz, const Cx* z, Cx* out);
+
+}  // namespace tdmrg

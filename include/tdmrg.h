@@ -81,6 +81,13 @@ int tdmrg_model_set_krylov(tdmrg_model* h, double tol, int kmax, int fixed_k);
  * precisions). */
 int tdmrg_model_set_rank_tol(tdmrg_model* h, double rank_tol);
 
+/* Quadrature of the exponential VJPs in the reverse passes (tdmrg_step_vjp and the calls built
+ * on it): 0 (default) evaluates exp(s tau H) v and exp((1-s) conj(tau) H) ybar by a fresh
+ * Lanczos exponential at every Gauss-Legendre node; 1 builds every node vector from the two
+ * Krylov bases of v and ybar (small exponentials on the host, one GEMM with each basis), which
+ * keeps the Krylov tolerance and needs two Lanczos runs instead of 1 + 2 nodes. */
+int tdmrg_model_set_adjoint_krylov_basis(tdmrg_model* h, int on);
+
 /* Work stream (a cudaStream_t passed as void*; NULL = legacy default stream). */
 int tdmrg_model_set_stream(tdmrg_model* h, void* stream);
 

@@ -82,6 +82,7 @@ _SIGS = {
     "tdmrg_correlation_states_vjp": [_p, _i, _pp, _pp, _d, _i, _i, _dp, _dp, _pp, _pp, _dp, _i],
     "tdmrg_correlation_vjp": [_p, _d, _d, _i, _d, _i, _i, _dp, _dp, _dp, _dp, _i],
     "tdmrg_host_tridiag_exp": [_i, _dp, _dp, _i, _dp, _dp],
+    "tdmrg_model_set_adjoint_krylov_basis": [_p, _i],
 }
 
 
@@ -214,6 +215,11 @@ class Model:
 
     def set_profiling(self, on=True):
         _check(self._lib.tdmrg_model_set_profiling(self._h, int(bool(on))), self._h)
+
+    def set_adjoint_krylov_basis(self, on=True):
+        """Node vectors of the exponential VJPs from the Krylov bases (True) or from fresh
+        Lanczos exponentials at every node (False, the default)."""
+        _check(self._lib.tdmrg_model_set_adjoint_krylov_basis(self._h, int(bool(on))), self._h)
 
     def parameter_count(self):
         """Number of parameters theta (omega_m, g_m, V, then alpha, omega_p with a bond mode)."""

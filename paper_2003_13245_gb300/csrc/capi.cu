@@ -240,6 +240,12 @@ int tdmrg_model_set_rank_tol(tdmrg_model* h, double rank_tol) {
   return TDMRG_OK;
 }
 
+int tdmrg_model_set_adjoint_krylov_basis(tdmrg_model* h, int on) {
+  if (!h) return fail(nullptr, TDMRG_ERR_ARG, "NULL handle");
+  h->eng->set_adjoint_krylov_basis(on != 0);
+  return TDMRG_OK;
+}
+
 int tdmrg_model_set_graphs(tdmrg_model* h, int on) {
   if (!h) return fail(nullptr, TDMRG_ERR_ARG, "NULL handle");
   return guarded(h, [&] { h->eng->set_graphs(on != 0, 0); });
@@ -795,34 +801,6 @@ int tdmrg_kernel_bond_exp(int M, int Dw, const void* L, const void* R, const voi
   });
 }
 
-namespace {
-// Gauss-Legendre nodes and weights on [0, 1] (n <= 64): Newton iteration on the three-term
-// recurrence of the Legendre polynomials from the usual cosine first guesses.
-void gauss_legendre01(int n, std::vector<double>& s, std::vector<double>& w) {
-  s.assign(n, 0.0);
-  w.assign(n, 0.0);
-  const double pi = 3.14159265358979323846;
-  for (int i = 0; i < (n + 1) / 2; ++i) {
-    double z = std::cos(pi * (i + 0.75) / (n + 0.5)), pp = 1.0;
-    for (int it = 0; it < 100; ++it) {
-      double p1 = 1.0, p2 = 0.0;
-      for (int j = 1; j <= n; ++j) {
-        const double p3 = p2;
-        p2 = p1;
-        p1 = ((2.0 * j - 1.0) * z * p2 - (j - 1.0) * p3) / j;
-      }
-      pp = n * (z * p1 - p2) / (z * z - 1.0);
-      const double dz = p1 / pp;
-      z -= dz;
-      if (std::fabs(dz) < 1e-16) break;
-    }
-    const double wi = 2.0 / ((1.0 - z * z) * pp * pp);
-    s[i] = 0.5 * (1.0 - z);            // ascending on [0, 1]
-    s[n - 1 - i] = 0.5 * (1.0 + z);
-    w[i] = w[n - 1 - i] = 0.5 * wi;
-  }
-}
-}  // namespace
 
 }  // extern "C"
 
@@ -881,7 +859,7 @@ int site_exp_vjp_impl(int Ml, int Mr, int d, int Dl, int Dr, const double* W_hos
     CK(cudaMemsetAsync(Lbar, 0, sizeof(cplx) * (size_t)nl, s));
     CK(cudaMemsetAsync(Rbar, 0, sizeof(cplx) * (size_t)nr, s));
     std::vector<double> sn, wn;
-    gauss_legendre01(nodes, sn, wn);
+    tdmrg::gauss_legendre01(nodes, sn, wn);
     for (int q = 0; q < nodes; ++q) {
       eng.krylov(n, (const cplx*)A, b, sn[q] * tau_re, sn[q] * tau_im, heff);
       eng.krylov(n, (const cplx*)ybar, a, (1.0 - sn[q]) * tau_re, -(1.0 - sn[q]) * tau_im, heff);
@@ -965,7 +943,7 @@ int tdmrg_kernel_bond_exp_vjp(int M, int Dw, const void* L, const void* R, const
     CK(cudaMemsetAsync(Lbar, 0, sizeof(cplx) * (size_t)Dw * mm, s));
     CK(cudaMemsetAsync(Rbar, 0, sizeof(cplx) * (size_t)Dw * mm, s));
     std::vector<double> sn, wn;
-    gauss_legendre01(nodes, sn, wn);
+    tdmrg::gauss_legendre01(nodes, sn, wn);
     const cplx one = {1.0, 0.0}, zero = {0.0, 0.0};
     for (int q = 0; q < nodes; ++q) {
       eng.krylov(mm, (const cplx*)C, b, sn[q] * tau_re, sn[q] * tau_im, kmv);

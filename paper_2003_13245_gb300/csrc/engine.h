@@ -215,6 +215,17 @@ class Engine {
   void correlation_vjp(double beta, double dtau, int M, double dt, int nsteps, int every,
                        const double* cbar, double* C, double* theta_bar, double* logz,
                        int nodes);
+  // Quadrature of the exponential VJPs in the reverse passes: from fresh Lanczos
+  // exponentials at every node (false, the default) or from the two Krylov bases of v and
+  // vbar (true: the node vectors as basis combinations, small exponentials on the host).
+  void set_adjoint_krylov_basis(bool on) { adjoint_basis_ = on; }
+  // Krylov-basis reverse of y = exp(tau H) v: vbar = exp(conj(tau) H) ybar, and the node
+  // vectors a_q (rows of Aq) and b_q (rows of Bq), q < nodes, with Hbar = sum_q k_q a_q b_q^H,
+  // k_q = w_q conj(tau) returned in kq (step_adjoint.cu)
+  template <class F>
+  void exp_vjp_nodes(long long n, const cplx* v, const cplx* ybar, double tr, double ti,
+                     int nodes, cplx* vbar, cplx* Aq, cplx* Bq, cplx* basis,
+                     std::vector<Cx>& kq, F&& matvec);
 
  private:
   void alloc_mps(DevMps& s, int M);
@@ -274,6 +285,7 @@ class Engine {
   void tdvp_step_body(DevMps& s, double tr, double ti);
   const StepGraph& step_graph(DevMps& s, double tr, double ti);
   int kmax_ = 32, fixed_k_ = 0;
+  bool adjoint_basis_ = false;
   bool prepared_ = false, rt_ready_ = false;
   double logZ_ = 0.0;
   std::vector<SiteInfo> sites_;

@@ -77,4 +77,31 @@ void tridiag_exp_e1(int k, const double* alpha, const double* beta, int nz, cons
   }
 }
 
+// Gauss-Legendre nodes and weights on [0, 1] (n <= 64): Newton iteration on the three-term
+// recurrence of the Legendre polynomials from the usual cosine first guesses.
+void gauss_legendre01(int n, std::vector<double>& s, std::vector<double>& w) {
+  s.assign(n, 0.0);
+  w.assign(n, 0.0);
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < (n + 1) / 2; ++i) {
+    double z = std::cos(pi * (i + 0.75) / (n + 0.5)), pp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p1 = 1.0, p2 = 0.0;
+      for (int j = 1; j <= n; ++j) {
+        const double p3 = p2;
+        p2 = p1;
+        p1 = ((2.0 * j - 1.0) * z * p2 - (j - 1.0) * p3) / j;
+      }
+      pp = n * (z * p1 - p2) / (z * z - 1.0);
+      const double dz = p1 / pp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    const double wi = 2.0 / ((1.0 - z * z) * pp * pp);
+    s[i] = 0.5 * (1.0 - z);            // ascending on [0, 1]
+    s[n - 1 - i] = 0.5 * (1.0 + z);
+    w[i] = w[n - 1 - i] = 0.5 * wi;
+  }
+}
+
 }  // namespace tdmrg

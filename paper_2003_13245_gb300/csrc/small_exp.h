@@ -15,4 +15,7 @@ void symmetric_eigen(int k, std::vector<double>& A, std::vector<double>& w, std:
 // beta[k-1] off-diagonal), s < nz.
 void tridiag_exp_e1(int k, const double* alpha, const double* beta, int nz, const Cx* z, Cx* out);
 
+// Gauss-Legendre nodes s[n] (ascending) and weights w[n] on [0, 1], n <= 64.
+void gauss_legendre01(int n, std::vector<double>& s, std::vector<double>& w);
+
 }  // namespace tdmrg

@@ -15,6 +15,7 @@
 
 #include "../../include/tdmrg.h"
 #include "engine.h"
+#include "small_exp.h"
 
 namespace tdmrg {
 
@@ -31,6 +32,12 @@ MatRef mr(const cplx* p, long long rs, long long cs, int conj = 0) {
   r.sb = 0;
   r.sr = 0;
   r.conj = conj;
+  return r;
+}
+
+MatRef mrb(const cplx* p, long long rs, long long cs, long long sb, int conj = 0) {
+  MatRef r = mr(p, rs, cs, conj);
+  r.sb = sb;
   return r;
 }
 
@@ -237,6 +244,67 @@ void qr_right_reverse(const Ctx& ctx, const ShiftScratch& w, cplx* X, cplx* Y,
   }
 }
 }  // namespace
+
+template <class F>
+void Engine::exp_vjp_nodes(long long n, const cplx* v, const cplx* ybar, double tr, double ti,
+                           int nodes, cplx* vbar, cplx* Aq, cplx* Bq, cplx* basis,
+                           std::vector<Cx>& kq, F&& matvec) {
+  std::vector<double> sq, wq;
+  gauss_legendre01(nodes, sq, wq);
+  kq.resize(nodes);
+  for (int q = 0; q < nodes; ++q) kq[q] = wq[q] * std::conj(Cx(tr, ti));
+  auto read_state = [&](int& k, double& b0, std::vector<double>& al, std::vector<double>& be) {
+    LzState h;
+    CK(cudaMemcpyAsync(&h, lz_, sizeof(LzState), cudaMemcpyDeviceToHost, st_));
+    CK(cudaStreamSynchronize(st_));
+    k = h.k;
+    b0 = h.b0;
+    al.assign(h.alpha, h.alpha + (k > 0 ? k : 0));
+    be.assign(k > 1 ? h.beta + 1 : h.beta, k > 1 ? h.beta + k : h.beta);   // beta_1 .. beta_{k-1}
+  };
+  // forward Lanczos of v: its basis is kept for the b_q
+  int k1 = 0, k2 = 0;
+  double b1 = 0.0, b2 = 0.0;
+  std::vector<double> a1, e1, a2, e2;
+  krylov(n, v, Kout_, tr, ti, matvec);
+  read_state(k1, b1, a1, e1);
+  if (k1 > 0)
+    CK(cudaMemcpyAsync(basis, V_, sizeof(cplx) * (size_t)k1 * n, cudaMemcpyDeviceToDevice, st_));
+  // Lanczos of ybar with conj(tau): vbar, and its basis (left in V_) for the a_q
+  krylov(n, ybar, vbar, tr, -ti, matvec);
+  read_state(k2, b2, a2, e2);
+  std::vector<Cx> zb(nodes), za(nodes), cb((size_t)nodes * std::max(k1, 1)),
+      ca((size_t)nodes * std::max(k2, 1));
+  for (int q = 0; q < nodes; ++q) {
+    zb[q] = sq[q] * Cx(tr, ti);
+    za[q] = (1.0 - sq[q]) * Cx(tr, -ti);
+  }
+  Tape tp;
+  if (k1 > 0 && b1 > 0.0) {
+    tridiag_exp_e1(k1, a1.data(), e1.data(), nodes, zb.data(), cb.data());
+    std::vector<cplx> h((size_t)nodes * k1);
+    for (size_t i = 0; i < h.size(); ++i) h[i] = {b1 * cb[i].real(), b1 * cb[i].imag()};
+    cplx* d = tp.get((long long)h.size());
+    CK(cudaMemcpyAsync(d, h.data(), sizeof(cplx) * h.size(), cudaMemcpyHostToDevice, st_));
+    CK(zgemm(nodes, (int)n, k1, 1, 1, kOne, mr(d, k1, 1), mr(basis, n, 1), kZero, Bq, n, 0,
+             nullptr, st_));
+    CK(cudaStreamSynchronize(st_));
+  } else {
+    CK(cudaMemsetAsync(Bq, 0, sizeof(cplx) * (size_t)nodes * n, st_));
+  }
+  if (k2 > 0 && b2 > 0.0) {
+    tridiag_exp_e1(k2, a2.data(), e2.data(), nodes, za.data(), ca.data());
+    std::vector<cplx> h((size_t)nodes * k2);
+    for (size_t i = 0; i < h.size(); ++i) h[i] = {b2 * ca[i].real(), b2 * ca[i].imag()};
+    cplx* d = tp.get((long long)h.size());
+    CK(cudaMemcpyAsync(d, h.data(), sizeof(cplx) * h.size(), cudaMemcpyHostToDevice, st_));
+    CK(zgemm(nodes, (int)n, k2, 1, 1, kOne, mr(d, k2, 1), mr(V_, n, 1), kZero, Aq, n, 0,
+             nullptr, st_));
+    CK(cudaStreamSynchronize(st_));
+  } else {
+    CK(cudaMemsetAsync(Aq, 0, sizeof(cplx) * (size_t)nodes * n, st_));
+  }
+}
 
 void Engine::step_vjp(int M, const cplx* const* A_in, double tr, double ti,
                       const cplx* const* Abar_out, cplx* const* A_out, cplx* const* Abar_in,
@@ -457,6 +525,98 @@ void Engine::step_vjp(int M, const cplx* const* A_in, double tr, double ti,
   std::vector<double> th(np, 0.0), tht(np > 0 ? np : 1, 0.0);
   const double tol = ktol_;
   void* sv = (void*)st_;
+  // exponential VJPs: the entry points (fresh Lanczos exponentials at every node) or the
+  // Krylov-basis quadrature on this engine (node vectors from the bases of v and vbar)
+  cplx *Aq = nullptr, *Bq = nullptr, *basis = nullptr, *tq = nullptr, *El = nullptr;
+  std::vector<std::vector<DevMpo>> dWdev;
+  struct FreeDev {
+    std::vector<std::vector<DevMpo>>& m;
+    ~FreeDev() {
+      for (auto& row : m)
+        for (auto& x : row) Engine::free_mpo(x);
+    }
+  } free_dev{dWdev};
+  if (adjoint_basis_) {
+    Aq = tp.get((long long)nodes * maxsite);
+    Bq = tp.get((long long)nodes * maxsite);
+    basis = tp.get((long long)KMAX * maxsite);
+    tq = tp.get(maxsite);
+    El = tp.get(maxenv);
+    dWdev.assign(L, std::vector<DevMpo>(np));
+    for (int k = 0; k < L; ++k)
+      for (int p = 0; p < np; ++p) {
+        const MpoSite dW = mpo_site_derivative(P, 0, p, k);
+        if (!dW.blocks.empty()) upload_mpo({dW}, dWdev[k][p]);
+      }
+  }
+  auto site_vjp = [&](int k, const cplx* Le, const cplx* Re, const cplx* ain, const cplx* ybar,
+                      cplx* Abar, cplx* Lbar, cplx* Rbar) {
+    const DevMpoSite& W = H_.s[k];
+    const int Ml = Mb[k], Mr = Mb[k + 1];
+    if (!adjoint_basis_) {
+      call(tdmrg_kernel_site_exp_vjp_theta(Ml, Mr, dd[k], W.Dl, W.Dr, Wd[k].data(), Le, Re, ain,
+                                           ybar, hr, hi, nodes, tol, np, dWp(k), Abar, Lbar, Rbar,
+                                           tht.data(), sv));
+      return;
+    }
+    std::vector<Cx> kq;
+    exp_vjp_nodes(n[k], ain, ybar, hr, hi, nodes, Abar, Aq, Bq, basis, kq,
+                  [&](const cplx* in, cplx* out, const int* skip) {
+                    heff_f64(c, W, Ml, Mr, D[k], dd[k], Le, Re, in, out, skip);
+                  });
+    CK(cudaMemsetAsync(Lbar, 0, sizeof(cplx) * (size_t)nL[k], st_));
+    CK(cudaMemsetAsync(Rbar, 0, sizeof(cplx) * (size_t)nR[k], st_));
+    for (int p = 0; p < np; ++p) tht[p] = 0.0;
+    for (int q = 0; q < nodes; ++q) {
+      const cplx* a = Aq + (size_t)q * n[k];
+      const cplx* b = Bq + (size_t)q * n[k];
+      const Cx kc = std::conj(kq[q]);                 // w_q tau
+      const cplx kcc = {kc.real(), kc.imag()};
+      // Lbar = conj(sum_q conj(k_q) env_right(R, a_q, W, b_q)), Rbar likewise with env_left
+      env_right_f64(c, W, Ml, Mr, Ml, Mr, D[k], dd[k], Re, a, b, El);
+      CK(zaxpy(nL[k], kcc, El, Lbar, st_));
+      env_left_f64(c, W, Ml, Mr, Ml, Mr, D[k], dd[k], Le, a, b, El);
+      CK(zaxpy(nR[k], kcc, El, Rbar, st_));
+      for (int p = 0; p < np; ++p) {
+        if (dWdev[k][p].s.empty()) continue;
+        heff_f64(c, dWdev[k][p].s[0], Ml, Mr, D[k], dd[k], Le, Re, b, tq, nullptr);
+        tht[p] += (kc * dot(a, tq, n[k], part, st_)).real();
+      }
+    }
+    CK(zconj(nL[k], Lbar, st_));
+    CK(zconj(nR[k], Rbar, st_));
+  };
+  auto bond_vjp = [&](int M, int Dw, const cplx* Le, const cplx* Re, const cplx* C0,
+                      const cplx* ybar, cplx* Cbar, cplx* Lbar, cplx* Rbar) {
+    if (!adjoint_basis_) {
+      call(tdmrg_kernel_bond_exp_vjp(M, Dw, Le, Re, C0, ybar, -hr, -hi, nodes, tol, Cbar, Lbar,
+                                     Rbar, sv));
+      return;
+    }
+    const long long mm = (long long)M * M;
+    std::vector<Cx> kq;
+    exp_vjp_nodes(mm, C0, ybar, -hr, -hi, nodes, Cbar, Aq, Bq, basis, kq,
+                  [&](const cplx* in, cplx* out, const int* skip) {
+                    bond_f64(c, M, Dw, Le, Re, in, out, skip);
+                  });
+    CK(cudaMemsetAsync(Lbar, 0, sizeof(cplx) * (size_t)(Dw * mm), st_));
+    CK(cudaMemsetAsync(Rbar, 0, sizeof(cplx) * (size_t)(Dw * mm), st_));
+    for (int q = 0; q < nodes; ++q) {
+      const cplx* a = Aq + (size_t)q * mm;
+      const cplx* b = Bq + (size_t)q * mm;
+      const cplx kk = {kq[q].real(), kq[q].imag()};  // w_q conj(tau)
+      // Lbar_w += k a conj(R_w) b^H;  Rbar_w += k a^T conj(L_w) conj(b)
+      CK(zgemm(M, M, M, Dw, 1, kOne, mrb(Re, M, 1, mm, 1), mr(b, 1, M, 1), kZero, El, M, mm,
+               nullptr, st_));
+      CK(zgemm(M, M, M, Dw, 1, kk, mr(a, M, 1), mrb(El, M, 1, mm), kOne, Lbar, M, mm, nullptr,
+               st_));
+      CK(zgemm(M, M, M, Dw, 1, kOne, mrb(Le, M, 1, mm, 1), mr(b, M, 1, 1), kZero, El, M, mm,
+               nullptr, st_));
+      CK(zgemm(M, M, M, Dw, 1, kk, mr(a, 1, M), mrb(El, M, 1, mm), kOne, Rbar, M, mm, nullptr,
+               st_));
+    }
+    CK(cudaStreamSynchronize(st_));
+  };
   auto add = [&](cplx* dst, const cplx* src, long long cnt) {
     CK(zaxpy(cnt, kOne, src, dst, st_));
   };
@@ -516,8 +676,7 @@ void Engine::step_vjp(int M, const cplx* const* A_in, double tr, double ti,
                s1, Ml, 0, nullptr, st_));
       copy(ab[k - 1], s1, n[k - 1]);
       // c = exp(-h K(Lenv[k], Rnew[k-1])) Cm
-      call(tdmrg_kernel_bond_exp_vjp(Ml, Dl, Lenv[k], Rnew[k - 1], Cm_rl[k], b1, -hr, -hi, nodes,
-                                     tol, b2, e1, e2, sv));
+      bond_vjp(Ml, Dl, Lenv[k], Rnew[k - 1], Cm_rl[k], b1, b2, e1, e2);
       add(Lb[k], e1, nL[k]);
       add(Rnb[k - 1], e2, nR[k - 1]);
       // Rnew[k-1] = env_right(Rnew[k], Qs, W, Qs)
@@ -562,9 +721,7 @@ void Engine::step_vjp(int M, const cplx* const* A_in, double tr, double ti,
       copy(a1b, ab[0], n[0]);
     }
     // a1 = exp(h H_eff(Lenv[k], W, Rnew[k])) ain
-    call(tdmrg_kernel_site_exp_vjp_theta(Ml, Mr, dd[k], Dl, Dr, Wd[k].data(), Lenv[k], Rnew[k],
-                                         ain_rl[k], a1b, hr, hi, nodes, tol, np, dWp(k), ab[k],
-                                         e1, e2, tht.data(), sv));
+    site_vjp(k, Lenv[k], Rnew[k], ain_rl[k], a1b, ab[k], e1, e2);
     take_theta();
     add(Lb[k], e1, nL[k]);
     add(Rnb[k], e2, nR[k]);
@@ -583,8 +740,7 @@ void Engine::step_vjp(int M, const cplx* const* A_in, double tr, double ti,
                kZero, s1, ncols, 0, nullptr, st_));
       copy(ab[k + 1], s1, n[k + 1]);
       // c = exp(-h K(Lenv[k+1], Rin[k])) R
-      call(tdmrg_kernel_bond_exp_vjp(Mr, Dr, Lenv[k + 1], Rin[k], R_lr[k], b1, -hr, -hi, nodes,
-                                     tol, b2, e1, e2, sv));
+      bond_vjp(Mr, Dr, Lenv[k + 1], Rin[k], R_lr[k], b1, b2, e1, e2);
       add(Lb[k + 1], e1, nL[k + 1]);
       add(Rib[k], e2, nR[k]);
       // Lenv[k+1] = env_left(Lenv[k], Q, W, Q)
@@ -624,9 +780,7 @@ void Engine::step_vjp(int M, const cplx* const* A_in, double tr, double ti,
       copy(a1b, ab[L - 1], n[L - 1]);
     }
     // a1 = exp(h H_eff(Lenv[k], W, Rin[k])) ain
-    call(tdmrg_kernel_site_exp_vjp_theta(Ml, Mr, dd[k], Dl, Dr, Wd[k].data(), Lenv[k], Rin[k],
-                                         ain_lr[k], a1b, hr, hi, nodes, tol, np, dWp(k), ab[k],
-                                         e1, e2, tht.data(), sv));
+    site_vjp(k, Lenv[k], Rin[k], ain_lr[k], a1b, ab[k], e1, e2);
     take_theta();
     add(Lb[k], e1, nL[k]);
     add(Rib[k], e2, nR[k]);

@@ -34,11 +34,12 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
 
 
+@pytest.mark.parametrize("basis", [False, True])
 @pytest.mark.parametrize("M,tau,start,bound", [(4, -0.1j, "random", 1e-8),
                                                (4, -0.05, "random", 1e-8),
                                                (64, -0.1j, "random", 1e-8),
                                                (4, -0.1j, "identity", 1e-7)])
-def test_step_vjp_matches_oracle_tape(M, tau, start, bound):
+def test_step_vjp_matches_oracle_tape(M, tau, start, bound, basis):
     from oracle import adjoint, tdvp
     from oracle.model import HolsteinModel, mpo_hamiltonian, site_list
     from paper_2003_13245_gb300 import binding
@@ -64,6 +65,7 @@ def test_step_vjp_matches_oracle_tape(M, tau, start, bound):
                                              mpo_hamiltonian)
     m = binding.Model(model.N, model.omega, model.g, model.nmax, model.V)
     try:
+        m.set_adjoint_krylov_basis(basis)
         A_out, Abar_in, th = m.step_vjp(M, [dev(x) for x in A], tau, [dev(x) for x in Abar])
     finally:
         m.close()
@@ -119,8 +121,9 @@ def test_correlation_states_vjp_matches_oracle():
         assert abs(got - ref) <= 1e-8 * tscale
 
 
+@pytest.mark.parametrize("basis", [False, True])
 @pytest.mark.parametrize("M,rank_tol", [(4, None), (64, 1e-8)])
-def test_correlation_vjp_matches_oracle_pipeline(M, rank_tol):
+def test_correlation_vjp_matches_oracle_pipeline(M, rank_tol, basis):
     """The gradient of the whole C(t) computation (tdmrg_correlation_vjp) against the oracle's
     reverse pass of its pipeline: below full bond dimension (M = 4, completed gauge columns
     everywhere; the oracle matches central differences to 2e-9 there) and at full bond
@@ -140,6 +143,7 @@ def test_correlation_vjp_matches_oracle_pipeline(M, rank_tol):
     try:
         if rank_tol is not None:
             m.set_rank_tol(rank_tol)
+        m.set_adjoint_krylov_basis(basis)
         Cg, th, _ = m.correlation_vjp(beta, dtau, M, dt, ns, cbar)
     finally:
         m.close()

@@ -211,6 +211,10 @@ int tdmrg_host_mpo_site(int N, int modes, const double* omega, const double* g, 
                         const int* nmax, double alpha, double omega_p, int nmax_p, int which,
                         int param, int site, int* dims, double* W_out);
 
+/* Gauss-Legendre nodes s[n] (ascending) and weights w[n] on [0, 1] (1 <= n <= 64), on the host:
+ * the quadrature of the exponential VJPs' Frechet integrals. */
+int tdmrg_host_gauss_legendre(int n, double* s, double* w);
+
 /* exp(z_s T) e_1, s < nz, for the real symmetric tridiagonal Lanczos matrix T = tridiag(beta,
  * alpha, beta) (alpha[k] diagonal, beta[k-1] off-diagonal, 1 <= k <= 64), from one cyclic
  * Jacobi eigendecomposition of T on the host (no handle, no GPU): z[2 nz] interleaved complex,

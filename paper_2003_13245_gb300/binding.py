@@ -83,6 +83,7 @@ _SIGS = {
     "tdmrg_correlation_vjp": [_p, _d, _d, _i, _d, _i, _i, _dp, _dp, _dp, _dp, _i],
     "tdmrg_host_tridiag_exp": [_i, _dp, _dp, _i, _dp, _dp],
     "tdmrg_model_set_adjoint_krylov_basis": [_p, _i],
+    "tdmrg_host_gauss_legendre": [_i, _dp, _dp],
 }
 
 
@@ -318,6 +319,13 @@ def mobility(t_grid, C, kT):
     mu = ctypes.c_double()
     _check(lib.tdmrg_mobility(_dptr(t), _dptr(c), int(t.size), float(kT), ctypes.byref(mu)))
     return mu.value
+
+
+def host_gauss_legendre(n):
+    """Gauss-Legendre nodes and weights on [0, 1] (host only)."""
+    sn, wn = np.zeros(int(n)), np.zeros(int(n))
+    _check(load().tdmrg_host_gauss_legendre(int(n), _dptr(sn), _dptr(wn)))
+    return sn, wn
 
 
 def host_tridiag_exp(alpha, beta, z):

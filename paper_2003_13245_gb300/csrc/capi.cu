@@ -461,6 +461,19 @@ int tdmrg_correlation_vjp(tdmrg_model* h, double beta, double dtau, int M, doubl
   });
 }
 
+int tdmrg_host_gauss_legendre(int n, double* s, double* w) {
+  if (n < 1 || n > 64 || !s || !w)
+    return fail(nullptr, TDMRG_ERR_ARG, "host_gauss_legendre: need 1 <= n <= 64");
+  return guarded(nullptr, [&] {
+    std::vector<double> sv, wv;
+    tdmrg::gauss_legendre01(n, sv, wv);
+    for (int i = 0; i < n; ++i) {
+      s[i] = sv[i];
+      w[i] = wv[i];
+    }
+  });
+}
+
 int tdmrg_host_tridiag_exp(int k, const double* alpha, const double* beta, int nz,
                            const double* z, double* out) {
   if (k < 1 || k > 64 || nz < 0 || !alpha || (k > 1 && !beta) || (nz > 0 && (!z || !out)))

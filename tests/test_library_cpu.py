@@ -140,3 +140,16 @@ def test_host_tridiagonal_exponential_rejects_bad_input(lib):
         binding.host_tridiag_exp(np.zeros(65), np.zeros(64), [0.1])
     with pytest.raises(binding.TdmrgError):
         binding.host_tridiag_exp([1.0, float("nan")], [0.5], [0.1])
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 16, 64])
+def test_host_gauss_legendre_rule(lib, n):
+    """The quadrature of the exponential VJPs: nodes and weights on [0, 1] equal numpy's
+    Gauss-Legendre rule mapped from [-1, 1], and the rule integrates polynomials of degree
+    2n - 1 exactly."""
+    from paper_2003_13245_gb300 import binding
+    s, w = binding.host_gauss_legendre(n)
+    x, v = np.polynomial.legendre.leggauss(n)
+    assert np.abs(s - 0.5 * (x + 1)).max() < 1e-14 and np.abs(w - 0.5 * v).max() < 1e-14
+    for deg in (0, n, 2 * n - 1):
+        assert abs(np.sum(w * s ** deg) - 1.0 / (deg + 1)) < 1e-13

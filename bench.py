@@ -45,6 +45,9 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=20.0,
                    help="CPU time budget of the oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--adjoint-quadrature", default="basis", choices=["basis", "nodes"],
+                   help="c4-adjoint: node vectors of the exponential VJPs from the Krylov bases "
+                        "(basis) or from a Lanczos exponential at every node (nodes)")
     p.add_argument("--workload", default="c2", choices=["c2", "c3-batch", "c5", "c4-adjoint"],
                    help="c2: the headline chain; c3-batch: 36 independent instances stepped "
                         "together; c5: Holstein-Peierls N=32, 4 modes, M=256; c4-adjoint: the "
@@ -492,6 +495,7 @@ def run_c4_adjoint(args):
     ns = args.steps
     m = Model(12, omega, g, nmax, V)
     m.set_rank_tol(1e-8)
+    m.set_adjoint_krylov_basis(args.adjoint_quadrature == "basis")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     m.thermal_prepare(1.0 / kT, 0.05, 96)
@@ -514,7 +518,8 @@ def run_c4_adjoint(args):
             "steps": ns, "forward_s": fwd, "gradient_over_forward": grad / fwd,
             "mu": float(np.sum(w * np.real(Cg))), "dmu_dtheta": dmu, "dmu_dm": iso,
             "max_abs_C_diff_forward_vs_gradient_run": float(np.abs(np.asarray(C) - Cg).max()),
-            "logZ": logz, "dtype": "c128", "data": "synthetic",
+            "logZ": logz, "quadrature": args.adjoint_quadrature, "dtype": "c128",
+            "data": "synthetic",
             "config": {"N": 12, "omega": omega, "g": g, "nmax": nmax, "V": V, "kT": kT, "M": 96,
                        "dt": dt, "checkpoint_every": 20}}
     print(json.dumps(line))

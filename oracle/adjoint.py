@@ -22,7 +22,17 @@ conjugate pairing is taken accordingly.
   Hbar = sum_s c_s b_s^H, which the caller maps to L, W, R through the VJPs above.  The
   energy offset of H cancels between a(s) and b(s), so the integrand varies on the scale of
   |tau| times the spread of the spectrum; 16 nodes integrate it to rounding for
-  |tau| spread <= 5.
+  |tau| spread <= 5;
+* ``qr_vjp`` / ``qr_vjp_completed`` / ``qr_vjp_selected`` -- the gauge QR at full column rank,
+  with completed columns following their candidates, and with the completed columns fixed.
+
+Reverse passes on tapes (``Tape``: values and the VJPs of the operations that made them):
+``step_with_tape`` (one projector-splitting step, Eq. S1), ``correlation_vjp`` (C_n of two given
+states, Eq. 6, stored every k steps), ``thermal_logz_gradient`` (the imaginary-time
+preparation, Eq. 5), ``fit_with_tape`` (the variational j fit) and
+``correlation_pipeline_gradient`` / ``mobility_pipeline_gradient`` (the whole C(t) and mu of
+Eq. 2 as functions of omega_m, g_m, V through the MPO coefficients,
+``step_parameter_gradient``).
 """
 from typing import Callable, List, Tuple
 

@@ -17,7 +17,7 @@ bond mode p_n of bond (n, n+1 mod N).
 MPO convention: W[wl, wr, s, s'] with s the output (bra) and s' the input (ket) level of
 the physical (P) index.  The first site only uses row 0, the last only the last column.
 """
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 from typing import List, Optional, Tuple
 
 import numpy as np

@@ -1,6 +1,5 @@
 """Pins for the exact-diagonalisation oracle: closed forms, limits and invariants of Eq. 2-7."""
 import numpy as np
-import pytest
 import scipy.linalg
 
 from oracle import kubo

@@ -1,18 +1,13 @@
 """Parity of the remaining building blocks of a reverse sweep through the C ABI against the
 oracle's VJPs (FP64): environment updates (both sides, with parameter cotangents through
 derivative MPO sites), gauge-completion candidates (both sides) and the gauge QR with completed
-columns.  Sizes span several 64-wide tiles with ragged tails.
-
-The host orchestration of these entry points (sizes, strides, channel tables, column gathers)
-was checked against the oracle by emulating every device primitive on the CPU; their first run
-on a GPU is still to come, so they are skipped until then."""
+columns.  Sizes span several 64-wide tiles with ragged tails."""
 import numpy as np
 import pytest
 
 from tests.inputs import random_complex, random_mpo_site
 
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skip(reason="awaiting the first run of these entry points on a GPU")]
+pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 

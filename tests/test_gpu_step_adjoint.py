@@ -10,14 +10,13 @@ sites and the parameter cotangents (omega, g, V).
   cotangents, so the bound there is 1e-7.  (Wider bonds around |I>, or imaginary tau from it,
   put columns at the rank threshold and are not a parity case: two rounding orders differ by
   1e-6 and more.)
-Skipped until the entry point's first run on a GPU."""
+"""
 import numpy as np
 import pytest
 
 from tests.inputs import random_complex
 
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skip(reason="awaiting the first run of tdmrg_step_vjp on a GPU")]
+pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 

@@ -45,10 +45,16 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=20.0,
                    help="CPU time budget of the oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--accuracy-steps", type=int, default=2,
+                   help="real-time steps of the plain FP64 GPU path run beside the mixed path "
+                        "(its throughput and the C(t) error of the mixed path against it); 0 "
+                        "skips the leg")
     p.add_argument("--adjoint-quadrature", default="basis", choices=["basis", "nodes"],
                    help="c4-adjoint: node vectors of the exponential VJPs from the Krylov bases "
                         "(basis) or from a Lanczos exponential at every node (nodes)")
-    p.add_argument("--workload", default="c2", choices=["c2", "c3-batch", "c5", "c4-adjoint"],
+    p.add_argument("--workload", default="c2",
+                   choices=["c2", "c3-batch", "c5", "c4-adjoint", "c2-accuracy", "hp-sweep",
+                            "isotope"],
                    help="c2: the headline chain; c3-batch: 36 independent instances stepped "
                         "together; c5: Holstein-Peierls N=32, 4 modes, M=256; c4-adjoint: the "
                         "gradient of mu on the N=12 chain, M=96, FP64")
@@ -120,9 +126,23 @@ class _Budget(Exception):
     pass
 
 
+def workload_config(world=1):
+    """The `config` object of both arms' JSON lines (same workload, same keys)."""
+    w = WORKLOAD
+    return {"workload": w["name"], "N": w["N"], "modes": len(w["omega"]), "omega": w["omega"],
+            "g": w["g"], "nmax": w["nmax"], "V": w["V"], "kT": w["kT"], "M": w["M"],
+            "dt": w["dt"], "sites": w["N"] * (1 + len(w["omega"])),
+            "site_updates_per_step": 4 * w["N"] * (1 + len(w["omega"])),
+            "parallelism": "replicas x%d" % world,
+            "l2": "inputs larger than L2: site tensors + environments of both states exceed "
+                  "129 MB"}
+
+
 def oracle_sample(budget_s):
     """Site updates/s of the FP64 CPU oracle on the same chain and bond dimension: the
-    right-canonicalised |I> (not timed), then imaginary-time site updates until the budget."""
+    right-canonicalised |I> at M=128 (not timed), then real-time site updates exp(-i dt/2
+    H_eff) with their gauge shifts and bond steps (projector-splitting steps of dt) until the
+    budget.  A site update costs the same from |I> as from Psi_beta (same bond dimensions)."""
     from oracle import tdvp
     from oracle.model import HolsteinModel, mpo_hamiltonian
     w = WORKLOAD
@@ -139,11 +159,15 @@ def oracle_sample(budget_s):
 
     try:
         while True:
-            psi.step(-w["dtau"], tdvp.KrylovOpts(), on_site=tick)
+            psi.step(-1j * w["dt"], tdvp.KrylovOpts(), on_site=tick)
     except _Budget:
         pass
     el = time.perf_counter() - t0
     return count[0], el
+
+
+ORACLE_SAMPLE = ("FP64 numpy oracle: real-time projector-splitting site updates (dt = 0.05) of "
+                 "the same chain at M=128 from the right-canonicalised |I>")
 
 
 def cpu_threads():
@@ -174,13 +198,10 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * secs / max(1, args.steps), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-            "config": {"workload": WORKLOAD["name"], **{k: WORKLOAD[k] for k in
-                                                         ("N", "omega", "g", "nmax", "V", "kT", "M", "dt")}},
+            "config": workload_config(args.gpus),
             "cpu_baseline": {"value": v, "unit": "site-updates/s", "cores": cpu_threads(),
                              "kind": "oracle",
-                             "sample": "FP64 numpy oracle, imaginary-time site updates of the "
-                                       "same chain at M=128 from the right-canonicalised |I>, "
-                                       "%.0f s per step" % per},
+                             "sample": ORACLE_SAMPLE + ", %.0f s per step" % per},
             "e2e": {"value": v, "unit": "site-updates/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -238,9 +259,10 @@ def run_ours(args):
     m = Model(w["N"], w["omega"], w["g"], w["nmax"], w["V"], precision=prec, stream=stream)
     m.thermal_prepare(1.0 / w["kT"], w["dtau"], w["M"])
     m.realtime_init()
+    C_warm = [m.realtime_observe()]
     for _ in range(args.warmup):
         m.realtime_step(1, w["dt"])
-        m.realtime_observe()
+        C_warm.append(m.realtime_observe())
     pre = m.stats()
     m.reset_stats()
     barrier()
@@ -287,6 +309,10 @@ def run_ours(args):
                   "matvecs": ps["matvecs"], "bond_matvecs": ps["bond_matvecs"],
                   "qrs": ps["qrs"]}
     m.close()
+    fp64_peak = measure_fp64_rate(stream) if rank == 0 else None
+    accuracy = None
+    if rank == 0 and prec != PREC_C128 and args.accuracy_steps > 0:
+        accuracy = fp64_path_leg(w, stream, C_warm[:min(args.accuracy_steps, args.warmup) + 1])
 
     site_updates = st["site_updates"]
     total_units = site_updates
@@ -330,7 +356,9 @@ def run_ours(args):
         qr_tflops = st["qr_flops"] / (st["qr_ms"] / 1e3) / 1e12 if st["qr_ms"] > 0 else None
         roof = {"bound": "alu", "achieved": qr_tflops, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": qr_tflops / FP64_PEAK_TFLOPS if qr_tflops else None,
-                "traffic": None,
+                "traffic": None, "peak_measured": fp64_peak,
+                "frac_of_measured": (qr_tflops / fp64_peak["tflops"]
+                                     if qr_tflops and fp64_peak else None),
                 "kernel": "gauge_qr_blocked_kernel (FP64 gauge QR, cooperative, 16-column blocks)",
                 "share_of_step": st["qr_ms"] / ms_max if ms_max > 0 else None,
                 "peak_source": "GB300 FP64 rate from unit counts and clock: 152 SMs x 2 DFMA/clk "
@@ -349,13 +377,7 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "c128" if prec == PREC_C128 else "c64-3xtf32", "data": "synthetic",
-        "config": {"workload": w["name"], "N": w["N"], "modes": len(w["omega"]),
-                   "omega": w["omega"], "g": w["g"], "nmax": w["nmax"], "V": w["V"],
-                   "kT": w["kT"], "M": w["M"], "dt": w["dt"], "sites": 48,
-                   "site_updates_per_step": site_updates / args.steps,
-                   "parallelism": "replicas x%d" % world,
-                   "l2": "inputs larger than L2: site tensors + environments of both states "
-                         "exceed 129 MB"},
+        "config": workload_config(world),
         "roofline": roof,
         "heff_roofline": heff_roof if prec != PREC_C128 else None,
         "heff": {"tflops": heff_tflops, "matvecs": st["matvecs"], "flops": st["heff_flops"]},
@@ -370,17 +392,82 @@ def run_ours(args):
     }
     if phases is not None:
         line["phases"] = phases
+    if accuracy is not None:
+        line["fp64_path"] = accuracy["fp64_path"]
+        line["ct_err"] = accuracy["ct_err"]
     if world == 1 and not args.no_cpu_baseline:
         u, s = oracle_sample(args.cpu_seconds)
         line["cpu_baseline"] = {"value": u / s, "unit": "site-updates/s", "cores": cpu_threads(),
                                 "kind": "oracle",
-                                "sample": "FP64 numpy oracle: %d imaginary-time site updates of "
-                                          "the same chain at M=128 from the right-canonicalised "
-                                          "|I> in %.1f s" % (u, s)}
+                                "sample": ORACLE_SAMPLE + ": %d site updates in %.1f s" % (u, s)}
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def measure_fp64_rate(stream):
+    """FP64 FMA rate of this GPU: the library's DFMA probe (8 independent FMA chains per
+    thread, 4 blocks of 256 threads per SM), best of three event-timed launches."""
+    import torch
+    from paper_2003_13245_gb300 import binding
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    blocks, iters = 4 * sms, 1 << 17
+    sink = torch.empty(blocks * 256, dtype=torch.float64, device="cuda")
+    binding.kernel_dfma_loop(blocks, 1 << 10, sink, stream)
+    best = None
+    for _ in range(3):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fl = binding.kernel_dfma_loop(blocks, iters, sink, stream)
+        e1.record(stream)
+        e1.synchronize()
+        tf = fl / (e0.elapsed_time(e1) / 1e3) / 1e12
+        best = tf if best is None else max(best, tf)
+    return {"tflops": best, "how": "tdmrg_kernel_dfma_loop: %d blocks x 256 threads x 8 FMA "
+                                  "chains x %d, best of 3, CUDA events" % (blocks, iters)}
+
+
+def fp64_path_leg(w, stream, C_mixed):
+    """The plain FP64 GPU path on the same chain: its own thermal preparation, then
+    len(C_mixed) - 1 real-time steps with C(t) after each.  Returns its site-updates/s
+    (event-timed steps) and the error of the mixed path, max_t |C_mixed - C_FP64| / |C_FP64(0)|,
+    over those steps (C_mixed from the mixed run's first steps after its own preparation)."""
+    import torch
+    from paper_2003_13245_gb300 import Model, PREC_C128
+    n = len(C_mixed) - 1
+    m = Model(w["N"], w["omega"], w["g"], w["nmax"], w["V"], precision=PREC_C128, stream=stream)
+    t0 = time.perf_counter()
+    m.thermal_prepare(1.0 / w["kT"], w["dtau"], w["M"])
+    m.realtime_init()
+    prep_s = time.perf_counter() - t0
+    C = [m.realtime_observe()]
+    m.reset_stats()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    ms = 0.0
+    for _ in range(n):
+        e0.record(stream)
+        m.realtime_step(1, w["dt"])
+        e1.record(stream)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+        C.append(m.realtime_observe())
+    su = m.stats()["site_updates"]
+    m.close()
+    C = np.array(C)
+    Cm = np.array(C_mixed)
+    err = np.abs(Cm - C) / abs(C[0])
+    return {"fp64_path": {"value": su / (ms / 1e3) if ms > 0 else None, "unit": "site-updates/s",
+                          "dtype": "c128", "steps": n, "prep_s": prep_s,
+                          "what": "the same chain and step on the plain FP64 GPU path (every "
+                                  "contraction complex FP64), event-timed real-time steps"},
+            "ct_err": {"max": float(err.max()), "per_t": [float(x) for x in err],
+                       "t": [i * w["dt"] for i in range(n + 1)],
+                       "logZ_note": "both paths prepared independently at kT=%g" % w["kT"],
+                       "definition": "max_t |C_c64-3xtf32(t) - C_c128(t)| / |C_c128(0)|, both on "
+                                     "the GPU from their own thermal preparations"}}
 
 
 # ----------------------------------------------------------------------------------------
@@ -439,6 +526,172 @@ def run_c3_batch(args):
     b.close()
     for m in models:
         m.close()
+    return 0
+
+
+def run_c2_accuracy(args):
+    """C(t) error of the mixed path against the plain FP64 GPU path on the c2 chain at every
+    (V, kBT) in {0.5, 2} x {0.5, 1, 2}, M = 128: both prepared independently (dtau = 0.05),
+    then `steps` real-time steps dt = 0.05; per point max_t |C_mixed - C_FP64| / |C_FP64(0)|,
+    |log Z_mixed - log Z_FP64| and both paths' event-timed site-updates/s."""
+    import torch
+    from paper_2003_13245_gb300 import Model, PREC_C128, PREC_C64_3XTF32
+    from paper_2003_13245_gb300.build import build_library
+    build_library()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    base = dict(WORKLOAD)
+    rows = []
+    for V in (0.5, 2.0):
+        for kT in (0.5, 1.0, 2.0):
+            res = {}
+            for name, prec in (("c64", PREC_C64_3XTF32), ("c128", PREC_C128)):
+                m = Model(base["N"], base["omega"], base["g"], base["nmax"], V, precision=prec,
+                          stream=stream)
+                t0 = time.perf_counter()
+                m.thermal_prepare(1.0 / kT, base["dtau"], base["M"])
+                m.realtime_init()
+                prep = time.perf_counter() - t0
+                C = [m.realtime_observe()]
+                m.reset_stats()
+                ms = 0.0
+                for _ in range(args.steps):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    m.realtime_step(1, base["dt"])
+                    e1.record(stream)
+                    e1.synchronize()
+                    ms += e0.elapsed_time(e1)
+                    C.append(m.realtime_observe())
+                res[name] = dict(C=np.array(C), logz=m.logz(), prep_s=prep,
+                                 rate=m.stats()["site_updates"] / (ms / 1e3))
+                m.close()
+            err = np.abs(res["c64"]["C"] - res["c128"]["C"]) / abs(res["c128"]["C"][0])
+            rows.append({"V": V, "kT": kT, "ct_err": float(err.max()),
+                         "logZ_err": abs(res["c64"]["logz"] - res["c128"]["logz"]),
+                         "C0": [res["c128"]["C"][0].real, res["c128"]["C"][0].imag],
+                         "mixed_site_updates_per_s": res["c64"]["rate"],
+                         "fp64_site_updates_per_s": res["c128"]["rate"],
+                         "prep_s": {"c64": res["c64"]["prep_s"], "c128": res["c128"]["prep_s"]}})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    line = {"metric": "C(t) error of c64-3xtf32 against the FP64 GPU path, c2 chain, M=128",
+            "workload": "c2-accuracy", "steps": args.steps, "dt": base["dt"],
+            "horizon_t": args.steps * base["dt"], "rows": rows,
+            "max_ct_err": max(r["ct_err"] for r in rows), "data": "synthetic"}
+    print(json.dumps(line))
+    return 0
+
+
+def _batch_mobilities(models, steps, dt, kT):
+    """C(t) of prepared models advanced together (tdmrg_batch_correlation) on t = 0..steps*dt
+    and their mobilities (Eq. 2, tdmrg_mobility); returns (t, C, mu, seconds)."""
+    import torch
+    from paper_2003_13245_gb300 import Batch, binding
+    for m in models:
+        m.realtime_init()
+    b = Batch(models)
+    t = np.arange(steps + 1) * dt
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    C = b.correlation(t, dt)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    b.close()
+    kTs = kT if np.ndim(kT) else [kT] * len(models)
+    mu = [binding.mobility(t, c, k) for c, k in zip(C, kTs)]
+    return t, C, mu, el
+
+
+def run_hp_sweep(args):
+    """Holstein-Peierls three-paradigm sweep (Eq. 10): mu_H (local coupling only), mu_P
+    (Peierls coupling only) and mu_HP (both) against DV/V, with Matthiessen's rule
+    1/mu_M = 1/mu_H + 1/mu_P.  Synthetic chain: N = 8, two local modes (w, g, nmax) =
+    (0.2, 1.5, 4) and (1.0, 0.8, 3), one bond mode per bond (w_p = 0.2, nmax_p = 8) with
+    V_n = V (1 + alpha (b + b^+)), V = kT = 1, M = 64, 3xTF32, fixed Krylov dimension 8; DV is
+    the thermal spread of V_n, DV/V = alpha sqrt(coth(w_p / 2 kT)).  All instances advance
+    together on the batched path."""
+    import torch
+    from paper_2003_13245_gb300 import Model, PREC_C64_3XTF32
+    from paper_2003_13245_gb300.build import build_library
+    build_library()
+    torch.cuda.set_device(0)
+    N, omega, g, nmax, V, kT, wp, nmp, M, dt = 8, [0.2, 1.0], [1.5, 0.8], [4, 3], 1.0, 1.0, 0.2, 8, 64, 0.05
+    ratios = [0.2, 0.4, 0.8, 1.6]
+    spread = np.sqrt(1.0 / np.tanh(wp / (2 * kT)))
+    specs = [("H", 0.0, g)] + [("P", r / spread, [0.0, 0.0]) for r in ratios] + \
+            [("HP", r / spread, g) for r in ratios]
+    models = []
+    t0 = time.perf_counter()
+    for _, alpha, gg in specs:
+        m = Model(N, omega, gg, nmax, V, peierls=(alpha, wp, nmp), precision=PREC_C64_3XTF32,
+                  krylov=(1e-7, 32, 8))
+        m.thermal_prepare(1.0 / kT, 0.05, M)
+        models.append(m)
+    prep = time.perf_counter() - t0
+    t, C, mu, el = _batch_mobilities(models, args.steps, dt, kT)
+    su = sum(m.stats()["site_updates"] for m in models)
+    for m in models:
+        m.close()
+    mu_H = mu[0]
+    rows = []
+    for i, r in enumerate(ratios):
+        mu_P, mu_HP = mu[1 + i], mu[1 + len(ratios) + i]
+        rows.append({"dV_over_V": r, "alpha": r / spread, "mu_H": mu_H, "mu_P": mu_P,
+                     "mu_HP": mu_HP, "mu_Matthiessen": 1.0 / (1.0 / mu_H + 1.0 / mu_P)})
+    line = {"metric": "Holstein-Peierls paradigms mu_H, mu_P, mu_HP vs DV/V with Matthiessen's "
+                      "rule, batched TD-DMRG", "workload": "hp-sweep", "rows": rows,
+            "instances": len(models), "steps": args.steps, "t_max": float(t[-1]),
+            "seconds": el, "prep_s": prep, "site_updates_per_s": su / el,
+            "config": {"N": N, "omega": omega, "g": g, "nmax": nmax, "V": V, "kT": kT,
+                       "omega_p": wp, "nmax_p": nmp, "M": M, "dt": dt},
+            "dtype": "c64-3xtf32", "data": "synthetic"}
+    print(json.dumps(line))
+    return 0
+
+
+def run_isotope(args):
+    """Frequency-scaling isotope scan (isotope approach 2: every w_m scaled by m^-1/2 with
+    g_m^2 w_m fixed): mu(m) and the coherence length L(m) of Eq. 9 from batched TD-DMRG, and
+    the hopping-limit mu_FGR(m) from the batched Eq. 7 kernel, at three temperatures.
+    Synthetic chain: N = 8, modes (0.2, 1.5, 6) and (1.0, 0.8, 4), V = 0.5, M = 64, 3xTF32,
+    fixed Krylov dimension 8, dt = 0.05."""
+    import torch
+    from paper_2003_13245_gb300 import Model, PREC_C64_3XTF32, binding
+    from paper_2003_13245_gb300.build import build_library
+    build_library()
+    torch.cuda.set_device(0)
+    N, omega, g, nmax, V, M, dt = 8, [0.2, 1.0], [1.5, 0.8], [6, 4], 0.5, 64, 0.05
+    masses = [1.0, 13.0 / 12.0, 1.25, 1.5, 2.0]
+    temps = [0.8, 1.0, 1.2]
+    specs, models, Ls = [], [], []
+    t0 = time.perf_counter()
+    for kT in temps:
+        for ms in masses:
+            w = [x / np.sqrt(ms) for x in omega]
+            gg = [x * ms ** 0.25 for x in g]
+            m = Model(N, w, gg, nmax, V, precision=PREC_C64_3XTF32, krylov=(1e-7, 32, 8))
+            m.thermal_prepare(1.0 / kT, 0.05, M)
+            Ls.append(binding.coherence_length(m.reduced_density()))
+            models.append(m)
+            specs.append((kT, ms, w, gg))
+    prep = time.perf_counter() - t0
+    t, C, mu, el = _batch_mobilities(models, args.steps, dt, [s[0] for s in specs])
+    for m in models:
+        m.close()
+    fgr = binding.fgr_mobility_batch([s[2] for s in specs], [s[3] for s in specs], V,
+                                     [s[0] for s in specs], dt, args.steps + 1)
+    rows = []
+    for i, (kT, ms, w, gg) in enumerate(specs):
+        ref = mu[temps.index(kT) * len(masses)]
+        rows.append({"kT": kT, "m": ms, "mu": mu[i], "isotope_effect": mu[i] / ref - 1.0,
+                     "L": Ls[i], "mu_fgr": float(fgr[i])})
+    line = {"metric": "isotope scan mu(m), L(m), mu_FGR(m), batched TD-DMRG + Eq. 7 kernel",
+            "workload": "isotope", "rows": rows, "instances": len(models), "steps": args.steps,
+            "t_max": float(t[-1]), "seconds": el, "prep_s": prep,
+            "config": {"N": N, "omega": omega, "g": g, "nmax": nmax, "V": V, "M": M, "dt": dt},
+            "dtype": "c64-3xtf32", "data": "synthetic"}
+    print(json.dumps(line))
     return 0
 
 
@@ -538,6 +791,12 @@ def main():
         return run_c5(args)
     if args.workload == "c4-adjoint":
         return run_c4_adjoint(args)
+    if args.workload == "c2-accuracy":
+        return run_c2_accuracy(args)
+    if args.workload == "hp-sweep":
+        return run_hp_sweep(args)
+    if args.workload == "isotope":
+        return run_isotope(args)
     return run_ours(args)
 
 

@@ -39,9 +39,10 @@ extern "C" {
 #define TDMRG_ERR_CUDA      -2   /* a CUDA runtime call failed                           */
 #define TDMRG_ERR_OOM       -3   /* device allocation failed                             */
 #define TDMRG_ERR_NONFINITE -4   /* NaN/Inf detected in a norm after a half-sweep        */
-#define TDMRG_ERR_NOCONV    -5   /* reserved: a Krylov exponential that stopped at kmax with
-                                    its error estimate above 1e3 tol; the device records this
-                                    in its Lanczos state, no entry point returns it yet   */
+#define TDMRG_ERR_NOCONV    -5   /* a site Krylov exponential stopped at kmax with its
+                                    a-posteriori error estimate above 1e3 tol (not in
+                                    fixed-k mode); the step's result is kept, the handle
+                                    stays usable                                          */
 #define TDMRG_ERR_TIMEOUT   -6   /* a bounded device-side wait (grid barrier) gave up    */
 #define TDMRG_ERR_STATE     -7   /* call out of order (e.g. correlation before prepare)  */
 
@@ -107,7 +108,30 @@ int tdmrg_model_set_graphs(tdmrg_model* h, int on);
 typedef struct tdmrg_batch tdmrg_batch;
 int tdmrg_batch_create(tdmrg_model* const* models, int n, tdmrg_batch** out);
 int tdmrg_batch_realtime_step(tdmrg_batch* b, int nsteps, double dt);
+
+/* One half of the second-order projector-splitting step (Eq. S1) of both real-time states of
+ * every instance: the first call runs the left-to-right half-sweeps (half a step dt/2 on every
+ * site with the backward bond steps), the next call the right-to-left ones, which completes the
+ * step; calls alternate.  All instances' half-step graphs are launched before any is waited
+ * for.  tdmrg_batch_realtime_step returns TDMRG_ERR_STATE while a second half is pending. */
+int tdmrg_batch_step_half(tdmrg_batch* b, double dt);
+
+/* C(t) of Eq. 6 for every instance of the batch on one grid (t_grid[nt] host, ascending,
+ * t_grid[0] = 0, integer multiples of dt, as tdmrg_correlation): re-forms Psi_1 = Psi_b and
+ * Psi_2 = j Psi_b of every instance (each must be prepared), advances all of them together by
+ * half-steps and writes C_out[n][2 nt] (host, instance-major, interleaved re, im) in the
+ * order the models were given to tdmrg_batch_create. */
+int tdmrg_batch_correlation(tdmrg_batch* b, const double* t_grid, int nt, double dt,
+                            double* C_out);
 int tdmrg_batch_destroy(tdmrg_batch* b);
+
+/* Limit of every bounded grid-barrier wait of the handle's cooperative kernels (gauge QRs,
+ * Lanczos steps, fused bond exponentials) in SM clock cycles; 0 (default) is about 2 s.  A
+ * barrier that gives up sets a status word, every block of the launch leaves at its next
+ * barrier, and the call returns TDMRG_ERR_TIMEOUT with the status cleared (the handle stays
+ * usable; the interrupted state is not: prepare again).  Lowering the limit is how the timeout
+ * path is tested without a stuck GPU. */
+int tdmrg_model_set_wait_cycles(tdmrg_model* h, long long cycles);
 
 /* Phase timers: when on, the library synchronises its stream at every phase boundary and
  * accumulates host wall time per phase into the stats (slightly slower; off by default). */
@@ -139,6 +163,42 @@ int tdmrg_realtime_observe(tdmrg_model* h, double* C_out, double* obs);
  * mu = (1 / (2 kT)) * 2 int_0^{t_max} Re C dt by the trapezoid rule (C(-t) = C(t)^*).
  * t_grid[nt], C[2*nt] host; pure host arithmetic, no handle needed. */
 int tdmrg_mobility(const double* t_grid, const double* C, int nt, double kT, double* mu_out);
+
+/* Hopping-limit mobility from the Fermi-golden-rule correlation function of Eq. 7 for a batch
+ * of P parameter sets (the frequency-scaling isotope scan and other sweeps): for the current
+ * of Eq. 3 on the ring and one carrier, to second order in V,
+ *   C(t) = 2 V^2 exp{-sum_m 2 g_m^2 [(2 n_m + 1) - n_m e^{i w_m t} - (n_m + 1) e^{-i w_m t}]},
+ * n_m = 1 / (e^{w_m / kT} - 1) (the printed Eq. 7 differs by these conventions: two molecules'
+ * modes relax per hop, two neighbours, opposite time phase), and mu = (1 / kT) int_0^{t_max}
+ * Re C dt by the trapezoid rule on t_i = i dt, i < nt (Eq. 2 cut off at t_max = (nt-1) dt).
+ * omega[P K], g[P K] (row p = parameter set, K <= 64 modes), V[P], kT[P], mu_out[P]: host.
+ * One GPU block per parameter set, fixed summation order.  Allocates its device copies (freed
+ * before return); synchronises `stream`. */
+int tdmrg_fgr_mobility_batch(int P, int K, const double* omega, const double* g,
+                             const double* V, const double* kT, double dt, int nt, double* mu_out,
+                             void* stream);
+
+/* Reduced electronic density matrix of the prepared thermal state (Eq. 9): sigma = Tr_ph
+ * rho_beta, rho_beta = Tr_Q |Psi_b><Psi_b| / Z, so sigma_ij = Tr[rho_beta c+_j c_i] on the
+ * one-carrier sector (Tr sigma = 1).  All N^2 entries come from one left-to-right pass of
+ * transfer contractions over Psi_b (right-orthonormal beyond its center, so every right
+ * environment is the identity), in the model's precision.  Writes sigma_out[2 N N] (host,
+ * row-major sigma_ij at 2 (i N + j), interleaved re, im).  Requires tdmrg_thermal_prepare;
+ * allocates its environments (freed before return); synchronises the handle's stream. */
+int tdmrg_reduced_density(tdmrg_model* h, double* sigma_out);
+
+/* Coherence length of Eq. 9, L = (sum_ij |sigma_ij|)^2 / (N sum_ij |sigma_ij|^2): 1 for a
+ * fully localised state (sigma = I / N), N for a fully delocalised one (|sigma_ij| = 1 / N).
+ * sigma[2 N N] as tdmrg_reduced_density writes it (host).  Pure host arithmetic. */
+int tdmrg_coherence_length(int N, const double* sigma, double* L_out);
+
+/* Mean free path of Eq. 8 from a computed C(t): group velocity v = sqrt(<j(0) j(0)>) =
+ * sqrt(Re C(0)), relaxation time tau = 1/2 int |Re C(t) / Re C(0)| dt over (-t_max, t_max) =
+ * int_0^{t_max} |Re C| dt / Re C(0) (Re C is even), trapezoid rule on the grid values of |Re C|,
+ * cut off at t_max = t_grid[nt-1]; l = v tau (in units of the lattice spacing R = 1).
+ * t_grid[nt] (ascending, t_grid[0] = 0), C[2*nt] interleaved (host); writes vtl_out[3] =
+ * {v, tau, l}.  TDMRG_ERR_ARG unless nt >= 2 and Re C(0) > 0.  Pure host arithmetic. */
+int tdmrg_mean_free_path(const double* t_grid, const double* C, int nt, double* vtl_out);
 
 /* Number of model parameters theta (omega_m, g_m, V, then alpha, omega_p with a bond mode), the
  * numbering of tdmrg_host_mpo_site and of the parameter cotangents below. */
@@ -409,34 +469,40 @@ int tdmrg_kernel_env_left(int Ml1, int Mr1, int Ml2, int Mr2, int d, int Dl, int
  * 1e-12 ||Y||_F; skipped positions are filled from the columns of E (m x p row-major, may
  * be NULL with p = 0) then unit vectors, each taken when its residual exceeds 1e-2 of its
  * norm.  Q (m x n) and R (n x n) row-major outputs; R rows of completed positions are 0.
- * status (device int, may be NULL): set to 1 if the bounded grid barrier timed out.
- * Allocates its scratch (freed before return); synchronises `stream`. */
+ * status (device int, may be NULL): set to 1 if the bounded grid barrier timed out, 2 if the
+ * completion ran out of vectors; either way the call returns TDMRG_ERR_TIMEOUT (1) or
+ * TDMRG_ERR_CUDA (2).  Each block stages ceil(m / blocks) rows in at most 200 KB of shared
+ * memory (blocks = one per SM): about 12,500 rows per block, m ~ 1.9 million on 152 SMs;
+ * larger m returns TDMRG_ERR_CUDA.  Allocates its scratch (freed before return);
+ * synchronises `stream`. */
 int tdmrg_kernel_gauge_qr(int m, int n, const void* Y, int p, const void* E, void* Q,
                           void* R, int* status, void* stream);
 
-/* Blocked gauge QR (the factorisation the engine uses): same definition, arguments and
- * outputs as tdmrg_kernel_gauge_qr, computed 16 columns at a time (block Gram-Schmidt
- * projections, Gram-form factorisation inside the block with a cancellation guard that
- * restarts the block at any column whose residual lost more than half its norm).
+/* Blocked gauge QR (the factorisation the engine uses): same definition, arguments, outputs
+ * and status handling as tdmrg_kernel_gauge_qr, computed 16 columns at a time (block
+ * Gram-Schmidt projections, Gram-form factorisation inside the block with a cancellation
+ * guard that restarts the block at any column whose residual lost more than half its norm).
  * Allocates and frees its scratch; synchronises `stream`. */
 int tdmrg_kernel_gauge_qr_blocked(int m, int n, const void* Y, int p, const void* E, void* Q,
                                   void* R, int* status, void* stream);
 
 /* Gauge QR that allocates nothing.  The paper has no counterpart: this entry point exists for
- * callers that cannot allocate device memory -- code running inside a CUDA graph capture
- * (cudaMalloc would invalidate the capture), callers that must not fail on memory once set up,
- * and hosts whose memory is owned by another runtime.  Same arguments, same result and same
- * layouts as tdmrg_kernel_gauge_qr; Y, E, Q, R (and status, if not NULL) are the caller's.
- * The scratch (cross-block partial sums, barrier counters, status word) is one fixed
- * file-scope device array of about 1.6 MB that every GPU loading the library keeps until exit.
- * Limits: n <= 256 and a grid of <= 192 blocks (m up to any size on GPUs with <= 192 SMs);
- * larger sizes return TDMRG_ERR_ARG with a message.  The first call on each device looks up
- * the array's device address (cudaGetSymbolAddress, with that device current): make that first
- * call before any stream capture.  All calls share the array and it keeps the last call's
- * contents (the barrier counters and the status word are cleared at the start of every call),
- * so calls that overlap on the GPU race: issue them on one stream or synchronise between them.
- * Synchronises `stream`; TDMRG_ERR_TIMEOUT if the bounded grid barrier gave up (when status
- * is NULL; otherwise the caller reads *status: 1 timeout, 2 out of completion vectors). */
+ * callers that cannot allocate device memory -- programs that hand all device memory to
+ * another runtime or pool and may not allocate behind its back, and callers that must not fail
+ * for lack of memory (or wait on the synchronisation an allocation can bring) once set up.
+ * Same arguments, same result, same layouts and same status handling as tdmrg_kernel_gauge_qr;
+ * Y, E, Q, R (and status, if not NULL) are the caller's.  The scratch (cross-block partial
+ * sums, barrier counters, status word) is one fixed file-scope device array of about 1.6 MB
+ * that every GPU loading the library keeps until exit.
+ * Limits: n <= 256, a grid of <= 192 blocks, and m small enough that one block's slice of
+ * ceil(m / blocks) rows fits 200 KB of shared memory (about 12,500 rows per block, m ~ 1.9
+ * million on 152 SMs); larger sizes return TDMRG_ERR_ARG with a message naming the limit.
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress,
+ * with that device current).  All calls share the array and it keeps the last call's contents
+ * (the barrier counters and the status word are cleared at the start of every call), so calls
+ * that overlap on the GPU race: issue them on one stream or synchronise between them.
+ * Synchronises `stream` and reads the status word; TDMRG_ERR_TIMEOUT if the bounded grid
+ * barrier gave up, TDMRG_ERR_CUDA if the completion ran out of vectors. */
 int tdmrg_kernel_gauge_qr_noalloc(int m, int n, const void* Y, int p, const void* E, void* Q,
                                   void* R, int* status, void* stream);
 
@@ -455,6 +521,14 @@ int tdmrg_kernel_gauge_qr_noalloc(int m, int n, const void* Y, int p, const void
 int tdmrg_kernel_bond_exp(int M, int Dw, const void* L, const void* R, const void* C, void* out,
                           double tau_re, double tau_im, double tol, int kmax, int* kused,
                           void* stream);
+
+/* FP64 FMA throughput probe (measurement only; no counterpart in the paper): blocks x 256
+ * threads each run 8 independent chains of `iters` fused multiply-adds and write their sum to
+ * sink[blocks * 256] (device).  *flops_out (host, may be NULL) receives the flop count
+ * 2 * 8 * 256 * blocks * iters.  Asynchronous on `stream` (time it with events there): the
+ * measured FP64 rate that the FP64 kernels' roofline fractions are quoted beside. */
+int tdmrg_kernel_dfma_loop(int blocks, long long iters, double* sink, double* flops_out,
+                           void* stream);
 
 /* Krylov exponential of a dense Hermitian matrix H (n x n, device) -- the site and bond
  * exponentials of Eq. S1 on an explicit matrix:

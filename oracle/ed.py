@@ -110,6 +110,14 @@ class ED:
     def rho(self) -> np.ndarray:
         return (self.U * self.p) @ self.U.conj().T
 
+    def reduced_density(self) -> np.ndarray:
+        """sigma = Tr_ph rho (Eq. 9): the thermal density matrix of the sector with every phonon
+        traced out, sigma_nm = sum_ph rho[(n, ph), (m, ph)] = Tr[rho c+_m c_n]."""
+        N = self.model.N
+        Dph = self.H.shape[0] // N
+        r = self.rho().reshape(N, Dph, N, Dph)
+        return np.einsum("apbp->ab", r)
+
     def correlation_direct(self, t: float) -> complex:
         """Tr[rho e^{iHt} j e^{-iHt} j] with matrix exponentials (no eigen-sum)."""
         Ut = (self.U * np.exp(-1j * self.E * t)) @ self.U.conj().T

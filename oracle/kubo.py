@@ -1,4 +1,5 @@
-"""Kubo mobility (Eq. 2) and the hopping-limit correlation function (Eq. 7).
+"""Kubo mobility (Eq. 2), the hopping-limit correlation function (Eq. 7), the mean free
+path (Eq. 8) and the coherence length (Eq. 9).
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 """
@@ -48,3 +49,46 @@ def free_band_correlation(N: int, V: float, beta: float) -> float:
     p = np.exp(-beta * (eps - eps.min()))
     p /= p.sum()
     return float(np.sum(p * (2.0 * V * np.sin(ks)) ** 2))
+
+
+def mean_free_path(t: np.ndarray, C: np.ndarray):
+    """Eq. 8: group velocity v = sqrt(<j(0) j(0)>) = sqrt(Re C(0)), relaxation time
+    tau = 1/2 int_{-inf}^{inf} |Re C(t) / Re C(0)| dt, mean free path l = v tau.
+
+    Re C is even in t (C(-t) = C(t)^*), so tau = int_0^{t_max} |Re C(t)| dt / Re C(0), cut off
+    at the end of the grid and taken by the trapezoid rule on the grid values of |Re C|
+    (the grid must start at t = 0).  Returns (v, tau, l)."""
+    t = np.asarray(t, dtype=float)
+    C = np.asarray(C)
+    if t[0] != 0.0:
+        raise ValueError("grid must start at t = 0")
+    c0 = float(np.real(C[0]))
+    if not c0 > 0.0:
+        raise ValueError("Re C(0) = <j j> must be positive")
+    area = 0.0
+    for i in range(len(t) - 1):
+        area += 0.5 * (t[i + 1] - t[i]) * (abs(C[i].real) + abs(C[i + 1].real))
+    v = np.sqrt(c0)
+    tau = area / c0
+    return float(v), float(tau), float(v * tau)
+
+
+def coherence_length(sigma: np.ndarray) -> float:
+    """Eq. 9: L = (sum_ij |sigma_ij|)^2 / (N sum_ij |sigma_ij|^2) of the reduced electronic
+    density matrix sigma = Tr_ph rho_beta (N x N)."""
+    a = np.abs(np.asarray(sigma))
+    N = a.shape[0]
+    return float(a.sum() ** 2 / (N * (a * a).sum()))
+
+
+def free_band_density(N: int, V: float, beta: float) -> np.ndarray:
+    """g = 0: sigma = exp(-beta h) / Tr exp(-beta h) with h the N x N hopping matrix of Eq. 1
+    (h_{n,n+1} = h_{n+1,n} = V on the ring)."""
+    h = np.zeros((N, N))
+    for n in range(N):
+        h[n, (n + 1) % N] += V
+        h[(n + 1) % N, n] += V
+    e, u = np.linalg.eigh(h)
+    w = np.exp(-beta * (e - e.min()))
+    rho = (u * w) @ u.T
+    return rho / np.trace(rho)

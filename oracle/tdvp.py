@@ -392,6 +392,33 @@ def overlap(bra: List[np.ndarray], Ws: List[np.ndarray], ket: List[np.ndarray], 
     return complex(E[0, 0, 0])
 
 
+def reduced_density(model: HolsteinModel, mps: List[np.ndarray]) -> np.ndarray:
+    """sigma_ij = <psi| c+_j c_i |psi> / <psi|psi> (Eq. 9 from a purified MPS), one overlap with
+    an operator MPO per entry: c_i and c+_j on the P index of the electronic sites of molecules
+    i and j (n_i when i = j), the identity elsewhere (hard-core carrier: no string)."""
+    sites = site_list(model)
+    d = [s[3] for s in sites]
+    I = identity_mpo(model)
+    norm = overlap(mps, I, mps, d)
+    c = np.array([[0.0, 1.0], [0.0, 0.0]])          # |1> -> |0>
+    N = model.N
+    sig = np.zeros((N, N), dtype=complex)
+    for i in range(N):
+        for j in range(N):
+            W = [w.copy() for w in I]
+            for k, (kind, n, _, _) in enumerate(sites):
+                if kind != "e":
+                    continue
+                op = np.eye(2)
+                if n == i:
+                    op = c @ op
+                if n == j:
+                    op = c.T @ op
+                W[k] = op.astype(complex)[None, None]
+            sig[i, j] = overlap(mps, W, mps, d) / norm
+    return sig
+
+
 def identity_mpo(model: HolsteinModel) -> List[np.ndarray]:
     return [np.eye(s[3], dtype=complex)[None, None] for s in site_list(model)]
 

@@ -42,11 +42,19 @@ _SIGS = {
     "tdmrg_model_set_stream": [_p, _p],
     "tdmrg_model_destroy": [_p],
     "tdmrg_model_set_profiling": [_p, _i],
+    "tdmrg_model_set_wait_cycles": [_p, ctypes.c_longlong],
     "tdmrg_model_set_graphs": [_p, _i],
     "tdmrg_model_set_rank_tol": [_p, _d],
     "tdmrg_batch_create": [ctypes.POINTER(_p), _i, ctypes.POINTER(_p)],
     "tdmrg_batch_realtime_step": [_p, _i, _d],
+    "tdmrg_batch_step_half": [_p, _d],
+    "tdmrg_batch_correlation": [_p, _dp, _i, _d, _dp],
     "tdmrg_batch_destroy": [_p],
+    "tdmrg_mean_free_path": [_dp, _dp, _i, _dp],
+    "tdmrg_reduced_density": [_p, _dp],
+    "tdmrg_kernel_dfma_loop": [_i, ctypes.c_longlong, _p, _dp, _p],
+    "tdmrg_fgr_mobility_batch": [_i, _i, _dp, _dp, _dp, _dp, _d, _i, _dp, _p],
+    "tdmrg_coherence_length": [_i, _dp, _dp],
     "tdmrg_thermal_prepare": [_p, _d, _d, _i],
     "tdmrg_correlation": [_p, _dp, _i, _d, _dp],
     "tdmrg_realtime_init": [_p],
@@ -149,6 +157,7 @@ class Model:
                                       nm.ctypes.data_as(_ip), ctypes.byref(h)))
         self._h = h
         self._lib = lib
+        self.N = int(N)
         if peierls is not None:
             alpha, omega_p, nmax_p = peierls
             _check(lib.tdmrg_model_set_peierls(h, float(alpha), float(omega_p), int(nmax_p)), h)
@@ -199,6 +208,14 @@ class Model:
         _check(self._lib.tdmrg_get_logz(self._h, ctypes.byref(v)), self._h)
         return v.value
 
+    def reduced_density(self):
+        """sigma = Tr_ph rho_beta (Eq. 9) of the prepared state: complex N x N, sigma_ij =
+        <c+_j c_i>."""
+        N = self.N
+        out = np.zeros(2 * N * N)
+        _check(self._lib.tdmrg_reduced_density(self._h, _dptr(out)), self._h)
+        return (out[0::2] + 1j * out[1::2]).reshape(N, N)
+
     def stats(self):
         s = np.zeros(21)
         _check(self._lib.tdmrg_get_stats(self._h, _dptr(s), 21), self._h)
@@ -216,6 +233,15 @@ class Model:
 
     def set_profiling(self, on=True):
         _check(self._lib.tdmrg_model_set_profiling(self._h, int(bool(on))), self._h)
+
+    def set_krylov(self, tol, kmax, fixed_k=0):
+        """Krylov stopping tolerance, largest dimension and (if > 0) a fixed dimension."""
+        _check(self._lib.tdmrg_model_set_krylov(self._h, float(tol), int(kmax), int(fixed_k)),
+               self._h)
+
+    def set_wait_cycles(self, cycles):
+        """Limit of the bounded grid-barrier waits in clock cycles (0: default, ~2 s)."""
+        _check(self._lib.tdmrg_model_set_wait_cycles(self._h, int(cycles)), self._h)
 
     def set_adjoint_krylov_basis(self, on=True):
         """Node vectors of the exponential VJPs from the Krylov bases (True) or from fresh
@@ -297,6 +323,19 @@ class Batch:
     def realtime_step(self, nsteps, dt):
         _check(self._lib.tdmrg_batch_realtime_step(self._h, int(nsteps), float(dt)))
 
+    def step_half(self, dt):
+        """One half-step of every instance (left-to-right, then right-to-left on the next call)."""
+        _check(self._lib.tdmrg_batch_step_half(self._h, float(dt)))
+
+    def correlation(self, t_grid, dt):
+        """C(t) of every instance on one grid: a complex array [instances][len(t_grid)]."""
+        t = np.ascontiguousarray(t_grid, dtype=np.float64)
+        out = np.zeros(2 * t.size * len(self.models))
+        _check(self._lib.tdmrg_batch_correlation(self._h, _dptr(t), int(t.size), float(dt),
+                                                 _dptr(out)))
+        out = out.reshape(len(self.models), t.size, 2)
+        return out[..., 0] + 1j * out[..., 1]
+
     def close(self):
         if getattr(self, "_h", None):
             self._lib.tdmrg_batch_destroy(self._h)
@@ -319,6 +358,56 @@ def mobility(t_grid, C, kT):
     mu = ctypes.c_double()
     _check(lib.tdmrg_mobility(_dptr(t), _dptr(c), int(t.size), float(kT), ctypes.byref(mu)))
     return mu.value
+
+
+def kernel_dfma_loop(blocks, iters, sink, stream=None):
+    """Launch the FP64 FMA throughput probe on `stream`; returns its flop count."""
+    lib = load()
+    fl = ctypes.c_double()
+    _check(lib.tdmrg_kernel_dfma_loop(int(blocks), int(iters), _ptr(sink), ctypes.byref(fl),
+                                      _stream_ptr(stream)))
+    return fl.value
+
+
+def fgr_mobility_batch(omega, g, V, kT, dt, nt, stream=None):
+    """Hopping-limit mobilities (Eq. 7 in Eq. 2) of P parameter sets on the GPU:
+    omega, g: P x K, V, kT: P; returns mu[P]."""
+    lib = load()
+    om = np.ascontiguousarray(np.atleast_2d(omega), dtype=np.float64)
+    gg = np.ascontiguousarray(np.atleast_2d(g), dtype=np.float64)
+    P, K = om.shape
+    VV = np.ascontiguousarray(np.broadcast_to(V, (P,)), dtype=np.float64)
+    TT = np.ascontiguousarray(np.broadcast_to(kT, (P,)), dtype=np.float64)
+    mu = np.zeros(P)
+    _check(lib.tdmrg_fgr_mobility_batch(int(P), int(K), _dptr(om), _dptr(gg), _dptr(VV),
+                                        _dptr(TT), float(dt), int(nt), _dptr(mu),
+                                        _stream_ptr(stream)))
+    return mu
+
+
+def coherence_length(sigma):
+    """Eq. 9 through tdmrg_coherence_length for an N x N complex sigma."""
+    lib = load()
+    sig = np.ascontiguousarray(sigma, dtype=np.complex128)
+    N = sig.shape[0]
+    flat = np.empty(2 * N * N)
+    flat[0::2] = sig.real.ravel()
+    flat[1::2] = sig.imag.ravel()
+    out = ctypes.c_double()
+    _check(lib.tdmrg_coherence_length(int(N), _dptr(flat), ctypes.byref(out)))
+    return out.value
+
+
+def mean_free_path(t_grid, C):
+    """Eq. 8 through tdmrg_mean_free_path: (v, tau, l)."""
+    lib = load()
+    t = np.ascontiguousarray(t_grid, dtype=np.float64)
+    c = np.empty(2 * t.size)
+    c[0::2] = np.real(C)
+    c[1::2] = np.imag(C)
+    out = np.zeros(3)
+    _check(lib.tdmrg_mean_free_path(_dptr(t), _dptr(c), int(t.size), _dptr(out)))
+    return float(out[0]), float(out[1]), float(out[2])
 
 
 def host_gauss_legendre(n):
@@ -521,8 +610,8 @@ def kernel_gauge_qr_blocked(Y, Q, R, E=None, status=None, stream=None):
 
 def kernel_gauge_qr_noalloc(Y, Q, R, E=None, status=None, stream=None):
     """tdmrg_kernel_gauge_qr with the scratch in the library's fixed device array: no device
-    allocation happens in the call (for callers inside a graph capture or without an
-    allocator); the first call on a device must come before any stream capture."""
+    allocation happens in the call (for callers whose device memory is owned by another runtime
+    or that may not allocate once set up); calls that overlap on the GPU race."""
     lib = load()
     m, n = Y.shape
     p = 0 if E is None else E.shape[1]
@@ -578,7 +667,8 @@ def _correlation_function():
                 m.close()
             ctx.spec = spec
             ctx.theta = th
-            return torch.as_tensor(np.asarray(C), dtype=torch.complex128)
+            ctx.device = theta.device
+            return torch.as_tensor(np.asarray(C), dtype=torch.complex128, device=theta.device)
 
         @staticmethod
         def backward(ctx, gC):
@@ -594,7 +684,7 @@ def _correlation_function():
                                              nodes=spec.get("nodes", 16))
             finally:
                 m.close()
-            return torch.as_tensor(tb, dtype=torch.float64), None
+            return torch.as_tensor(tb, dtype=torch.float64, device=ctx.device), None
 
     return CorrelationFunction
 

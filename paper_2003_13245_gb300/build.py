@@ -14,7 +14,8 @@ OBJ = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libtdmrg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["kernels_f64.cu", "qr_blocked.cu", "kernels_tc.cu", "bond_krylov.cu",
-              "lanczos_step.cu", "engine.cu", "step_adjoint.cu", "capi.cu", "noalloc.cu"]
+              "lanczos_step.cu", "engine.cu", "step_adjoint.cu", "capi.cu", "noalloc.cu",
+              "fgr.cu"]
 CXX_SOURCES = ["model.cpp", "small_exp.cpp"]
 
 

@@ -49,6 +49,7 @@ struct BondArgs {
   double* partn;       // G
   unsigned* bar;
   int* status;
+  long long wait;      // grid-barrier wait limit (clock cycles)
   unsigned long long* mv;
   double tr, ti, tol;
 };
@@ -146,7 +147,7 @@ __global__ void __launch_bounds__(BT, 1) bond_exp_kernel(BondArgs A) {
   for (int e = threadIdx.x; e < len; e += BT) ws[e] = A.v[e0 + e];
   __syncthreads();
   lzc::slice_norm(ws, len, red, A.partn);
-  if (!lzc::barrier(A.bar, A.G, epoch, A.status)) return;
+  if (!lzc::barrier(A.bar, A.G, epoch, A.status, A.wait)) return;
   lzc::reduce_norm(A.partn, A.G, &s_nrm);
   const double b0 = sqrt(s_nrm);
   if (threadIdx.x == 0) {
@@ -196,7 +197,7 @@ __global__ void __launch_bounds__(BT, 1) bond_exp_kernel(BondArgs A) {
           if (a < M && b < M) Tw[(size_t)a * M + b] = acc[i][jj];
         }
     }
-    if (!lzc::barrier(A.bar, A.G, epoch, A.status)) return;
+    if (!lzc::barrier(A.bar, A.G, epoch, A.status, A.wait)) return;
     // ---- B: P_w = T_w R_w^T
     for (int it = blockIdx.x; it < items; it += A.G) {
       const int w = it / (nt * nt), rem = it - w * nt * nt;
@@ -226,7 +227,7 @@ __global__ void __launch_bounds__(BT, 1) bond_exp_kernel(BondArgs A) {
           if (a < M && b < M) Pw[(size_t)a * M + b] = acc[i][jj];
         }
     }
-    if (!lzc::barrier(A.bar, A.G, epoch, A.status)) return;
+    if (!lzc::barrier(A.bar, A.G, epoch, A.status, A.wait)) return;
     // ---- C1: w = sum_w P_w (FP64, channel order); dots against q_lo .. q_j
     for (int e = threadIdx.x; e < len; e += BT) {
       double x = 0.0, y = 0.0;
@@ -240,18 +241,18 @@ __global__ void __launch_bounds__(BT, 1) bond_exp_kernel(BondArgs A) {
     __syncthreads();
     const int lo = j > 0 ? j - 1 : 0;
     lzc::slice_dots(A.V, n, ws, e0, len, lo, j + 1, part1);
-    if (!lzc::barrier(A.bar, A.G, epoch, A.status)) return;
+    if (!lzc::barrier(A.bar, A.G, epoch, A.status, A.wait)) return;
     // ---- C2: first projection; dots against q_0 .. q_j
     lzc::reduce_dots(part1, A.G, lo, j + 1, h1);
     lzc::slice_project(A.V, n, ws, e0, len, lo, j + 1, h1);
     lzc::slice_dots(A.V, n, ws, e0, len, 0, j + 1, part2);
-    if (!lzc::barrier(A.bar, A.G, epoch, A.status)) return;
+    if (!lzc::barrier(A.bar, A.G, epoch, A.status, A.wait)) return;
     // ---- C3: second projection; ||w||^2
     lzc::reduce_dots(part2, A.G, 0, j + 1, h2);
     lzc::slice_project(A.V, n, ws, e0, len, 0, j + 1, h2);
     for (int e = threadIdx.x; e < len; e += BT) A.W[e0 + e] = ws[e];
     lzc::slice_norm(ws, len, red, A.partn);
-    if (!lzc::barrier(A.bar, A.G, epoch, A.status)) return;
+    if (!lzc::barrier(A.bar, A.G, epoch, A.status, A.wait)) return;
     // ---- C4: tridiagonal bookkeeping and the small exponential (warp 0 of every CTA)
     lzc::reduce_norm(A.partn, A.G, &s_nrm);
     if (threadIdx.x < 32) {
@@ -333,6 +334,7 @@ cudaError_t bond_exp_fused(int M, int Dw, const cplx* L, const cplx* R, const cp
   a.L = L; a.R = R; a.v = C; a.out = out; a.V = V;
   a.W = W.W; a.T = W.T; a.P = W.P; a.part = W.part; a.partn = W.partn; a.bar = W.bar;
   a.status = status; a.mv = W.mv;
+  a.wait = W.wait > 0 ? W.wait : kBarrierWaitCycles;
   a.tr = tr; a.ti = ti; a.tol = tol;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(G);

@@ -22,6 +22,7 @@ struct tdmrg_model {
 
 struct tdmrg_batch {
   std::vector<tdmrg_model*> models;
+  int phase = 0;   // 1 after a left-to-right half-step (the step is completed by the next one)
 };
 
 static thread_local std::string g_err;
@@ -227,6 +228,12 @@ int tdmrg_model_set_stream(tdmrg_model* h, void* stream) {
   return TDMRG_OK;
 }
 
+int tdmrg_model_set_wait_cycles(tdmrg_model* h, long long cycles) {
+  if (!h) return fail(nullptr, TDMRG_ERR_ARG, "NULL handle");
+  if (cycles < 0) return fail(h, TDMRG_ERR_ARG, "wait_cycles: need cycles >= 0");
+  return guarded(h, [&] { h->eng->set_wait_cycles(cycles); });
+}
+
 int tdmrg_model_set_profiling(tdmrg_model* h, int on) {
   if (!h) return fail(nullptr, TDMRG_ERR_ARG, "NULL handle");
   h->eng->set_profiling(on != 0);
@@ -284,8 +291,90 @@ int tdmrg_batch_create(tdmrg_model* const* models, int n, tdmrg_batch** out) {
   return TDMRG_OK;
 }
 
+namespace {
+// the grid of tdmrg_correlation: t_grid[0] = 0, ascending integer multiples of dt -> step counts
+const char* grid_steps(const double* t_grid, int nt, double dt, std::vector<long long>& steps) {
+  if (!t_grid || nt < 1 || !(dt > 0.0)) return "bad grid arguments";
+  if (t_grid[0] != 0.0) return "t_grid[0] must be 0";
+  steps.assign(nt, 0);
+  for (int i = 0; i < nt; ++i) {
+    const double q = t_grid[i] / dt;
+    const long long r = std::llround(q);
+    if (std::fabs(q - r) > 1e-9 * std::max(1.0, std::fabs(q)))
+      return "t_grid points must be integer multiples of dt";
+    if (i > 0 && r <= steps[i - 1]) return "t_grid must be ascending";
+    steps[i] = r;
+  }
+  return nullptr;
+}
+
+// launches one half-step (half 1 or 2) of every instance, then waits for all of them
+int batch_half(tdmrg_batch* b, double dt, int half) {
+  for (tdmrg_model* h : b->models) {
+    const int rc = guarded(h, [&] { h->eng->realtime_half_launch(dt, half); });
+    if (rc != TDMRG_OK) {
+      g_err = h->err;
+      return rc;
+    }
+  }
+  for (tdmrg_model* h : b->models) {
+    const int rc = guarded(h, [&] { h->eng->sync_and_check(); });
+    if (rc != TDMRG_OK) {
+      g_err = h->err;
+      return rc;
+    }
+  }
+  return TDMRG_OK;
+}
+}  // namespace
+
+int tdmrg_batch_step_half(tdmrg_batch* b, double dt) {
+  if (!b || !(dt > 0.0)) return fail(nullptr, TDMRG_ERR_ARG, "batch half-step: bad arguments");
+  const int rc = batch_half(b, dt, b->phase == 0 ? 1 : 2);
+  if (rc == TDMRG_OK) b->phase ^= 1;
+  return rc;
+}
+
+int tdmrg_batch_correlation(tdmrg_batch* b, const double* t_grid, int nt, double dt,
+                            double* C_out) {
+  if (!b || !C_out) return fail(nullptr, TDMRG_ERR_ARG, "batch correlation: bad arguments");
+  std::vector<long long> steps;
+  if (const char* msg = grid_steps(t_grid, nt, dt, steps))
+    return fail(nullptr, TDMRG_ERR_ARG, msg);
+  const int n = (int)b->models.size();
+  for (tdmrg_model* h : b->models) {
+    const int rc = guarded(h, [&] { h->eng->realtime_init(); });
+    if (rc != TDMRG_OK) {
+      g_err = h->err;
+      return rc;
+    }
+  }
+  b->phase = 0;
+  long long at = 0;
+  for (int i = 0; i < nt; ++i) {
+    for (; at < steps[i]; ++at) {
+      int rc = batch_half(b, dt, 1);
+      if (rc == TDMRG_OK) rc = batch_half(b, dt, 2);
+      if (rc != TDMRG_OK) return rc;
+    }
+    for (int j = 0; j < n; ++j) {
+      tdmrg_model* h = b->models[j];
+      const int rc = guarded(h, [&] {
+        h->eng->realtime_observe(C_out + 2 * ((size_t)j * nt + i), nullptr);
+      });
+      if (rc != TDMRG_OK) {
+        g_err = h->err;
+        return rc;
+      }
+    }
+  }
+  return TDMRG_OK;
+}
+
 int tdmrg_batch_realtime_step(tdmrg_batch* b, int nsteps, double dt) {
   if (!b || nsteps < 0 || !(dt > 0.0)) return fail(nullptr, TDMRG_ERR_ARG, "batch step: bad arguments");
+  if (b->phase != 0)
+    return fail(nullptr, TDMRG_ERR_STATE, "batch step: a half-step is pending (call tdmrg_batch_step_half)");
   for (int st = 0; st < nsteps; ++st) {
     for (tdmrg_model* h : b->models) {
       const int rc = guarded(h, [&] { h->eng->realtime_step_launch(dt); });
@@ -339,17 +428,9 @@ int tdmrg_realtime_observe(tdmrg_model* h, double* C_out, double* obs) {
 
 int tdmrg_correlation(tdmrg_model* h, const double* t_grid, int nt, double dt, double* C_out) {
   if (!h) return fail(nullptr, TDMRG_ERR_ARG, "NULL handle");
-  if (!t_grid || !C_out || nt < 1 || !(dt > 0.0)) return fail(h, TDMRG_ERR_ARG, "bad grid arguments");
-  if (t_grid[0] != 0.0) return fail(h, TDMRG_ERR_ARG, "t_grid[0] must be 0");
-  std::vector<long long> steps(nt);
-  for (int i = 0; i < nt; ++i) {
-    const double q = t_grid[i] / dt;
-    const long long r = std::llround(q);
-    if (std::fabs(q - r) > 1e-9 * std::max(1.0, std::fabs(q)))
-      return fail(h, TDMRG_ERR_ARG, "t_grid points must be integer multiples of dt");
-    if (i > 0 && r <= steps[i - 1]) return fail(h, TDMRG_ERR_ARG, "t_grid must be ascending");
-    steps[i] = r;
-  }
+  if (!C_out) return fail(h, TDMRG_ERR_ARG, "bad grid arguments");
+  std::vector<long long> steps;
+  if (const char* msg = grid_steps(t_grid, nt, dt, steps)) return fail(h, TDMRG_ERR_ARG, msg);
   return guarded(h, [&] {
     h->eng->realtime_init();
     long long at = 0;
@@ -372,6 +453,81 @@ int tdmrg_mobility(const double* t_grid, const double* C, int nt, double kT, dou
     integral += 0.5 * h * (C[2 * i] + C[2 * i + 2]);
   }
   *mu_out = 2.0 * integral / (2.0 * kT);
+  return TDMRG_OK;
+}
+
+int tdmrg_fgr_mobility_batch(int P, int K, const double* omega, const double* g,
+                             const double* V, const double* kT, double dt, int nt, double* mu_out,
+                             void* stream) {
+  if (P < 1 || K < 1 || K > 64 || !omega || !g || !V || !kT || !mu_out || nt < 2 || !(dt > 0.0))
+    return fail(nullptr, TDMRG_ERR_ARG,
+                "fgr_mobility_batch: need P >= 1, 1 <= K <= 64, nt >= 2, dt > 0, host arrays");
+  for (long long i = 0; i < (long long)P * K; ++i)
+    if (!std::isfinite(omega[i]) || !(omega[i] > 0.0) || !std::isfinite(g[i]))
+      return fail(nullptr, TDMRG_ERR_ARG, "fgr_mobility_batch: need finite g and omega > 0");
+  for (int p = 0; p < P; ++p)
+    if (!std::isfinite(V[p]) || !(kT[p] > 0.0) || !std::isfinite(kT[p]))
+      return fail(nullptr, TDMRG_ERR_ARG, "fgr_mobility_batch: need finite V and kT > 0");
+  return guarded(nullptr, [&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t nk = (size_t)P * K;
+    double* d = nullptr;
+    struct Free {
+      double*& p;
+      ~Free() {
+        if (p) cudaFree(p);
+      }
+    } fr{d};
+    CK(cudaMalloc(&d, sizeof(double) * (2 * nk + 3 * (size_t)P)));
+    double *dw = d, *dg = d + nk, *dV = d + 2 * nk, *dT = dV + P, *dmu = dT + P;
+    CK(cudaMemcpyAsync(dw, omega, sizeof(double) * nk, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(dg, g, sizeof(double) * nk, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(dV, V, sizeof(double) * P, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(dT, kT, sizeof(double) * P, cudaMemcpyHostToDevice, s));
+    CK(tdmrg::fgr_mobility(P, K, dw, dg, dV, dT, dt, nt, dmu, s));
+    CK(cudaMemcpyAsync(mu_out, dmu, sizeof(double) * P, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  });
+}
+
+int tdmrg_reduced_density(tdmrg_model* h, double* sigma_out) {
+  if (!h) return fail(nullptr, TDMRG_ERR_ARG, "NULL handle");
+  if (!sigma_out) return fail(h, TDMRG_ERR_ARG, "reduced_density: sigma_out is NULL");
+  return guarded(h, [&] { h->eng->reduced_density(sigma_out); });
+}
+
+int tdmrg_coherence_length(int N, const double* sigma, double* L_out) {
+  if (N < 1 || !sigma || !L_out)
+    return fail(nullptr, TDMRG_ERR_ARG, "coherence_length: need N >= 1 and non-NULL arrays");
+  double s1 = 0.0, s2 = 0.0;
+  for (long long e = 0; e < (long long)N * N; ++e) {
+    const double a = std::hypot(sigma[2 * e], sigma[2 * e + 1]);
+    s1 += a;
+    s2 += a * a;
+  }
+  if (!(s2 > 0.0) || !std::isfinite(s1))
+    return fail(nullptr, TDMRG_ERR_ARG, "coherence_length: sigma is zero or not finite");
+  *L_out = s1 * s1 / (N * s2);
+  return TDMRG_OK;
+}
+
+int tdmrg_mean_free_path(const double* t_grid, const double* C, int nt, double* vtl_out) {
+  if (!t_grid || !C || !vtl_out || nt < 2)
+    return fail(nullptr, TDMRG_ERR_ARG, "mean_free_path: need nt >= 2 and non-NULL arrays");
+  if (t_grid[0] != 0.0) return fail(nullptr, TDMRG_ERR_ARG, "mean_free_path: t_grid[0] must be 0");
+  const double c0 = C[0];
+  if (!(c0 > 0.0) || !std::isfinite(c0))
+    return fail(nullptr, TDMRG_ERR_ARG, "mean_free_path: Re C(0) = <j j> must be positive");
+  double area = 0.0;
+  for (int i = 0; i + 1 < nt; ++i) {
+    const double h = t_grid[i + 1] - t_grid[i];
+    if (!(h > 0.0)) return fail(nullptr, TDMRG_ERR_ARG, "mean_free_path: t_grid must be ascending");
+    area += 0.5 * h * (std::fabs(C[2 * i]) + std::fabs(C[2 * i + 2]));
+  }
+  const double v = std::sqrt(c0), tau = area / c0;
+  vtl_out[0] = v;
+  vtl_out[1] = tau;
+  vtl_out[2] = v * tau;
   return TDMRG_OK;
 }
 
@@ -702,7 +858,21 @@ int tdmrg_kernel_gauge_qr(int m, int n, const void* Y, int p, const void* E, voi
     tdmrg::QrRef y{(const tdmrg::cplx*)Y, n, 1, 1LL << 60, 0, 0};
     tdmrg::QrRef e{(const tdmrg::cplx*)(p > 0 ? E : Y), p > 0 ? p : n, 1, 1LL << 60, 0, 0};
     CK(tdmrg::gauge_qr(m, n, y, p, e, (tdmrg::cplx*)Q, (tdmrg::cplx*)R, W, st, s));
+    int hs = 0;
+    CK(cudaMemcpyAsync(&hs, st, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (hs == 1) throw Failure{TDMRG_ERR_TIMEOUT, "gauge QR grid barrier timed out"};
+    if (hs == 2) throw Failure{TDMRG_ERR_CUDA, "gauge QR ran out of completion vectors"};
+  });
+}
+
+int tdmrg_kernel_dfma_loop(int blocks, long long iters, double* sink, double* flops_out,
+                           void* stream) {
+  if (blocks < 1 || iters < 1 || !sink)
+    return fail(nullptr, TDMRG_ERR_ARG, "dfma_loop: need blocks >= 1, iters >= 1, a sink");
+  return guarded(nullptr, [&] {
+    CK(tdmrg::dfma_loop(blocks, iters, sink, (cudaStream_t)stream));
+    if (flops_out) *flops_out = 2.0 * 8.0 * 256.0 * (double)blocks * (double)iters;
   });
 }
 

@@ -399,6 +399,7 @@ Engine::Engine(const ModelParams& p) : P(p) {
   rebuild_mpos();
   CK(cudaMalloc(&status_, sizeof(int) * 4));
   CK(cudaMemset(status_, 0, sizeof(int) * 4));
+  bs_.noconv = status_ + 3;
   CK(cudaMalloc(&lz_, sizeof(LzState)));
   CK(cudaMalloc(&scal_, sizeof(double) * 8));
   CK(cudaMalloc(&part_d_, sizeof(double) * NBLK));
@@ -741,7 +742,8 @@ void Engine::bond_exp(int M, int Dw, const cplx* Le, const cplx* Re, double tr, 
 
 void Engine::check_status() {
   CK(cudaMemcpyAsync(h_pinned_ + 1, status_, 3 * sizeof(int), cudaMemcpyDeviceToHost, st_));
-  stats.d2h_bytes += 3 * sizeof(int);
+  CK(cudaMemcpyAsync(h_pinned_ + 7, status_ + 3, sizeof(int), cudaMemcpyDeviceToHost, st_));
+  stats.d2h_bytes += 4 * sizeof(int);
   if (bs_.mv) {
     CK(cudaMemcpyAsync(h_mv_, bs_.mv, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st_));
     stats.d2h_bytes += sizeof(unsigned long long);
@@ -754,10 +756,20 @@ void Engine::check_status() {
     stats.bond_matvecs += used;
     stats.krylov_vectors += used;
   }
-  if (h_pinned_[1] == 1) throw Failure{TDMRG_ERR_TIMEOUT, "gauge QR grid barrier timed out"};
-  if (h_pinned_[2] == 1) throw Failure{TDMRG_ERR_TIMEOUT, "Lanczos grid barrier timed out"};
-  if (h_pinned_[1] == 2) throw Failure{TDMRG_ERR_CUDA, "gauge QR ran out of completion vectors"};
-  if (h_pinned_[3] != 0) throw Failure{TDMRG_ERR_TIMEOUT, "tensor-core pipeline wait timed out"};
+  const int qr = h_pinned_[1], lz = h_pinned_[2], tc = h_pinned_[3], nc = h_pinned_[7];
+  if (qr || lz || tc || nc) {
+    // the state of this step is not usable, but the handle is: clear the words so that the
+    // next call (a new preparation) starts from a clean status
+    CK(cudaMemsetAsync(status_, 0, 4 * sizeof(int), st_));
+    CK(cudaStreamSynchronize(st_));
+  }
+  if (qr == 1) throw Failure{TDMRG_ERR_TIMEOUT, "gauge QR grid barrier timed out"};
+  if (lz == 1) throw Failure{TDMRG_ERR_TIMEOUT, "Lanczos grid barrier timed out"};
+  if (qr == 2) throw Failure{TDMRG_ERR_CUDA, "gauge QR ran out of completion vectors"};
+  if (tc != 0) throw Failure{TDMRG_ERR_TIMEOUT, "tensor-core pipeline wait timed out"};
+  if (nc != 0)
+    throw Failure{TDMRG_ERR_NOCONV,
+                  "a Krylov exponential stopped at kmax with its error estimate above 1e3 tol"};
 }
 
 // Every gauge QR outside a graph capture is bracketed by a pair of events; the pairs are read
@@ -982,16 +994,16 @@ void Engine::clear_graphs() {
   step_graphs_.clear();
 }
 
-const Engine::StepGraph& Engine::step_graph(DevMps& s, double tr, double ti) {
+const Engine::StepGraph& Engine::step_graph(DevMps& s, double tr, double ti, int half) {
   for (const auto& g : step_graphs_)
-    if (g.state == &s && g.tr == tr && g.ti == ti) return g;
+    if (g.state == &s && g.tr == tr && g.ti == ti && g.half == half) return g;
   const Stats before = stats;
   const long long launches0 = launch_count();
   capturing_ = true;
   CK(cudaStreamBeginCapture(st_, cudaStreamCaptureModeThreadLocal));
   cudaGraph_t graph = nullptr;
   try {
-    tdvp_step_body(s, tr, ti);
+    tdvp_step_body(s, tr, ti, half);
   } catch (...) {
     cudaStreamEndCapture(st_, &graph);
     if (graph) cudaGraphDestroy(graph);
@@ -1001,7 +1013,7 @@ const Engine::StepGraph& Engine::step_graph(DevMps& s, double tr, double ti) {
   }
   capturing_ = false;
   CK(cudaStreamEndCapture(st_, &graph));
-  StepGraph g{&s, tr, ti, nullptr, stats_diff(stats, before)};
+  StepGraph g{&s, tr, ti, half, nullptr, stats_diff(stats, before)};
   g.delta.replayed_launches = (double)(launch_count() - launches0);
   // the captured launches did not run: the counter keeps counting real launches only
   count_launch(-(int)(launch_count() - launches0));
@@ -1036,6 +1048,18 @@ void Engine::realtime_step_launch(double dt) {
   stats_add(stats, g2.delta);
 }
 
+void Engine::realtime_half_launch(double dt, int half) {
+  if (!rt_ready_) throw Failure{TDMRG_ERR_STATE, "realtime half-step before realtime_init"};
+  if (!graphs_) throw Failure{TDMRG_ERR_STATE, "batched stepping needs graph mode"};
+  if (half != 1 && half != 2) throw Failure{TDMRG_ERR_ARG, "half-step: half must be 1 or 2"};
+  const StepGraph& g1 = step_graph(psi1_, 0.0, -dt, half);
+  CK(cudaGraphLaunch(g1.exec, st_));
+  stats_add(stats, g1.delta);
+  const StepGraph& g2 = step_graph(psi2_, 0.0, -dt, half);
+  CK(cudaGraphLaunch(g2.exec, st_));
+  stats_add(stats, g2.delta);
+}
+
 void Engine::sync_and_check() { check_status(); }
 
 void Engine::reset_stats() {
@@ -1054,13 +1078,13 @@ void Engine::renormalize(cplx* A, long long n) {
   CK(znormalize_log(n, A, scal_ + 2, scal_ + 3, st_));
 }
 
-void Engine::tdvp_step_body(DevMps& s, double tr, double ti) {
+void Engine::tdvp_step_body(DevMps& s, double tr, double ti, int half) {
   const double hr = 0.5 * tr, hi = 0.5 * ti;
   const bool imag = (ti == 0.0);
   const int L = s.L();
   Ctx c = ctx();
   double t0;
-  for (int k = 0; k < L; ++k) {
+  for (int k = 0; k < L && half != 2; ++k) {
     t0 = tic();
     site_update(s, k, hr, hi);
     toc(stats.t_site, t0);
@@ -1094,7 +1118,7 @@ void Engine::tdvp_step_body(DevMps& s, double tr, double ti) {
                          cudaMemcpyDeviceToDevice, st_));
     }
   }
-  for (int k = L - 1; k >= 0; --k) {
+  for (int k = L - 1; k >= 0 && half != 1; --k) {
     t0 = tic();
     site_update(s, k, hr, hi);
     toc(stats.t_site, t0);
@@ -1237,7 +1261,7 @@ void Engine::thermal_prepare(double beta, double dtau, int M) {
     throw Failure{TDMRG_ERR_ARG, "thermal_prepare: beta must be an even multiple of dtau"};
   prepared_ = false;
   rt_ready_ = false;
-  CK(cudaMemsetAsync(status_, 0, sizeof(int), st_));
+  CK(cudaMemsetAsync(status_, 0, 4 * sizeof(int), st_));
   alloc_mps(psi_b_, M);
   // |I> on the one-carrier sector
   const auto ent = identity_state_entries(P);
@@ -1306,6 +1330,103 @@ void Engine::realtime_observe(double* C, double* obs) {
     obs[0] = overlap(psi1_, I_, psi1_).real();
     obs[1] = overlap(psi2_, I_, psi2_).real();
     obs[2] = overlap(psi1_, H_, psi1_).real();
+  }
+}
+
+
+// sigma_ij = <Psi_b| c+_j c_i |Psi_b> (Eq. 9; the ancilla and every phonon traced out), all N^2
+// entries in one left-to-right pass of transfer contractions.  Psi_b is normalised with its
+// center at site 0 and sites 1.. right-orthonormal, so the right transfer environment of every
+// bond is the identity and an entry is the trace of a left environment.  Carried along the
+// chain: the identity-transfer environment E and, for every molecule p already passed, the
+// environments with c_p or c+_p inserted at its electronic site.  At the electronic site of
+// molecule q each of those is closed with c+_q or c_q (one transfer and a trace), E gives the
+// diagonal entry with n_q, and two new ones start from E.
+void Engine::reduced_density(double* sigma) {
+  if (!prepared_) throw Failure{TDMRG_ERR_STATE, "reduced_density before thermal_prepare"};
+  const DevMps& s = psi_b_;
+  const int L = s.L(), N = P.N;
+  auto one_site = [](int which) {
+    MpoSite m;
+    m.Dl = m.Dr = 1;
+    m.d = 2;
+    std::vector<Cx> op(4, Cx(0, 0));
+    if (which == 0) op[0 * 2 + 1] = Cx(1, 0);        // c  : |1> -> |0>
+    else if (which == 1) op[1 * 2 + 0] = Cx(1, 0);   // c+ : |0> -> |1>
+    else op[1 * 2 + 1] = Cx(1, 0);                   // n
+    m.blocks.push_back({0, 0, op});
+    return m;
+  };
+  DevMpo ops;
+  upload_mpo({one_site(0), one_site(1), one_site(2)}, ops);
+  long long maxe = 1;
+  for (int k = 0; k <= L; ++k) maxe = std::max(maxe, (long long)s.Mb[k] * s.Mb[k]);
+  const int nbuf = 2 * (2 * N + 1);
+  std::vector<cplx*> buf(nbuf, nullptr);
+  cplx* tr = nullptr;
+  struct Guard {
+    DevMpo& o;
+    std::vector<cplx*>& b;
+    cplx*& t;
+    ~Guard() {
+      free_mpo(o);
+      for (cplx* p : b)
+        if (p) cudaFree(p);
+      if (t) cudaFree(t);
+    }
+  } guard{ops, buf, tr};
+  for (auto& p : buf) CK(cudaMalloc(&p, sizeof(cplx) * (size_t)maxe));
+  CK(cudaMalloc(&tr, sizeof(cplx) * (size_t)N * N));
+  CK(cudaMemsetAsync(tr, 0, sizeof(cplx) * (size_t)N * N, st_));
+  // slot 0: E; slots 1 + 2p, 2 + 2p: c_p and c+_p inserted; two banks (current, next)
+  int bank = 0;
+  auto slot = [&](int b, int i) { return buf[b * (2 * N + 1) + i]; };
+  std::vector<char> open(2 * N + 1, 0);
+  set_ones(slot(0, 0));
+  open[0] = 1;
+  const DevMpoSite& Cop = ops.s[0];
+  const DevMpoSite& Cdag = ops.s[1];
+  const DevMpoSite& Nop = ops.s[2];
+  for (int k = 0; k < L; ++k) {
+    const int Ml = s.Mb[k], Mr = s.Mb[k + 1], D = s.D[k], d = s.d[k];
+    const bool elec = sites_[k].kind == SiteInfo::ELEC;
+    const int q = sites_[k].mol;
+    auto transfer = [&](const DevMpoSite& W, const cplx* in, cplx* out) {
+      env_left_any(W, Ml, Mr, Ml, Mr, D, d, in, s.A[k], s.A[k], out);
+    };
+    // scratch for closings: slot 0 of the other bank is free until E is advanced below
+    cplx* scratch = slot(bank ^ 1, 0);
+    if (elec) {
+      for (int p = 0; p < q; ++p) {
+        // c_p ... c+_q: <c+_q c_p> = sigma_pq;  c+_p ... c_q: <c+_p c_q> = sigma_qp
+        transfer(Cdag, slot(bank, 1 + 2 * p), scratch);
+        CK(ztrace(scratch, Mr, tr + (size_t)p * N + q, st_));
+        transfer(Cop, slot(bank, 2 + 2 * p), scratch);
+        CK(ztrace(scratch, Mr, tr + (size_t)q * N + p, st_));
+      }
+      transfer(Nop, slot(bank, 0), scratch);
+      CK(ztrace(scratch, Mr, tr + (size_t)q * N + q, st_));
+    }
+    // advance every open environment through site k (identity), start the two new ones
+    for (int i = 0; i < 2 * N + 1; ++i)
+      if (open[i]) transfer(I_.s[k], slot(bank, i), slot(bank ^ 1, i));
+    if (elec) {
+      transfer(Cop, slot(bank, 0), slot(bank ^ 1, 1 + 2 * q));
+      transfer(Cdag, slot(bank, 0), slot(bank ^ 1, 2 + 2 * q));
+      open[1 + 2 * q] = open[2 + 2 * q] = 1;
+    }
+    bank ^= 1;
+  }
+  std::vector<cplx> h((size_t)N * N);
+  CK(cudaMemcpyAsync(h.data(), tr, sizeof(cplx) * h.size(), cudaMemcpyDeviceToHost, st_));
+  CK(cudaStreamSynchronize(st_));
+  stats.d2h_bytes += sizeof(cplx) * h.size();
+  check_status();
+  for (size_t e = 0; e < h.size(); ++e) {
+    if (!std::isfinite(h[e].x) || !std::isfinite(h[e].y))
+      throw Failure{TDMRG_ERR_NONFINITE, "non-finite reduced density matrix"};
+    sigma[2 * e] = h[e].x;
+    sigma[2 * e + 1] = h[e].y;
   }
 }
 

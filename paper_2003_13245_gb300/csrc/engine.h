@@ -154,14 +154,27 @@ class Engine {
   bool graphs() const { return graphs_; }
   // launch both real-time graphs of one step without waiting (batched use)
   void realtime_step_launch(double dt);
+  // launch both real-time graphs of one half-step without waiting: half 1 is the left-to-right
+  // half-sweep of the second-order step, half 2 the right-to-left one (batched use)
+  void realtime_half_launch(double dt, int half);
   void sync_and_check();
   void reset_stats();   // reads pending QR timings first, then zeroes the counters
   void set_profiling(bool on) { prof_ = on; }
+  // limit of every bounded grid-barrier wait in clock cycles (0: the default, ~2 s); lowering
+  // it makes the barriers give up, which is how the timeout path is tested
+  void set_wait_cycles(long long c) {
+    qr_.wait = c;
+    bs_.wait = c;
+    clear_graphs();
+  }
   void rebuild_mpos();
   void thermal_prepare(double beta, double dtau, int M);
   void realtime_init();
   void realtime_step(int nsteps, double dt);
   void realtime_observe(double* C, double* obs);
+  // sigma = Tr_ph rho_beta of the prepared thermal state (Eq. 9): sigma_ij = <c+_j c_i>,
+  // written to sigma[2 (i N + j)] (interleaved re, im; host)
+  void reduced_density(double* sigma);
   double logz() const { return logZ_; }
   bool prepared() const { return prepared_; }
   bool rt_ready() const { return rt_ready_; }
@@ -277,13 +290,14 @@ class Engine {
   struct StepGraph {
     const DevMps* state;
     double tr, ti;
+    int half;             // 0: the whole step, 1: left-to-right half, 2: right-to-left half
     cudaGraphExec_t exec;
     Stats delta;
   };
   std::vector<StepGraph> step_graphs_;
   void clear_graphs();
-  void tdvp_step_body(DevMps& s, double tr, double ti);
-  const StepGraph& step_graph(DevMps& s, double tr, double ti);
+  void tdvp_step_body(DevMps& s, double tr, double ti, int half = 0);
+  const StepGraph& step_graph(DevMps& s, double tr, double ti, int half = 0);
   int kmax_ = 32, fixed_k_ = 0;
   bool adjoint_basis_ = false;
   bool prepared_ = false, rt_ready_ = false;

@@ -439,10 +439,10 @@ cudaError_t zcombine(long long n, const LzState* S, const cplx* V, long long ldv
 // of the working vector, so the only cross-CTA traffic is the partial dot products and
 // norms, exchanged through double-buffered global arrays and a bounded grid barrier.
 // ------------------------------------------------------------------------------------
-constexpr long long BARRIER_TIMEOUT_CYCLES = 4000000000LL;   // about 2 s at 2 GHz
 constexpr int QR_THREADS = 256;
 
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* status) {
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* status,
+                                             long long limit) {
   __syncthreads();
   __shared__ int s_ok;
   if (threadIdx.x == 0) {
@@ -460,7 +460,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, in
       const long long t0 = clock64();
       while (*vgen == gen) {
         if (*vstat) { ok = 0; break; }
-        if (clock64() - t0 > BARRIER_TIMEOUT_CYCLES) {
+        if (clock64() - t0 > limit) {
           atomicExch(status, 1);
           ok = 0;
           break;
@@ -488,6 +488,7 @@ struct QrKernelArgs {
   double* partn;
   unsigned* bar;
   int* status;
+  long long wait;                // grid-barrier wait limit (clock cycles)
   double rank_tol, complete_tol;
   const unsigned char* acc_in;   // completion only: accepted flags of a factorisation done
                                  // elsewhere (Q, R already written; only skipped columns filled)
@@ -564,7 +565,7 @@ __device__ bool qr_pass(const QrKernelArgs& A, int r0, int nr, int lim, cplx* v,
     for (int w = 0; w < (T >> 5); ++w) t += red[w];
     A.part[((long long)buf * G + g) * (n + 1) + n] = make_double2(t, 0.0);
   }
-  if (!grid_barrier(A.bar, G, A.status)) return false;
+  if (!grid_barrier(A.bar, G, A.status, A.wait)) return false;
   // (2) reduce the G partials of every column: P threads per column, 2 accumulators each
   {
     const cplx* base = A.part + (long long)buf * G * (n + 1);
@@ -660,7 +661,7 @@ __device__ bool qr_norm(const QrKernelArgs& A, int nr, const cplx* v, double& ou
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
     A.partn[buf * G + blockIdx.x] = t;
   }
-  if (!grid_barrier(A.bar, G, A.status)) return false;
+  if (!grid_barrier(A.bar, G, A.status, A.wait)) return false;
   qr_sum_partials(A.partn + buf * G, 1, G, red, 32);   // reads through L2 (other CTAs)
   __syncthreads();
   out = sqrt(red[32]);
@@ -735,7 +736,7 @@ __global__ void __launch_bounds__(QR_THREADS) gauge_qr_kernel(QrKernelArgs A) {
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
     A.partn[buf * G + blockIdx.x] = t;
   }
-  if (!grid_barrier(A.bar, G, A.status)) return;
+  if (!grid_barrier(A.bar, G, A.status, A.wait)) return;
   qr_sum_partials(A.partn + buf * G, 1, G, red, 33);
   __syncthreads();
   const double thr = A.rank_tol * sqrt(red[33]);
@@ -804,22 +805,44 @@ __global__ void __launch_bounds__(QR_THREADS) gauge_qr_kernel(QrKernelArgs A) {
   }
 }
 
-static int g_qr_coop_blocks = -1;
+// per device: the SM count (one CTA per SM keeps the barrier cheap) and whether the kernel's
+// shared-memory limit has been raised on that device
+constexpr int kQrMaxDevices = 64;
+static int g_qr_coop_blocks[kQrMaxDevices];
+static bool g_qr_attr_set[kQrMaxDevices];
+
+static int qr_device() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return (dev >= 0 && dev < kQrMaxDevices) ? dev : 0;
+}
 
 int gauge_qr_grid(int m) {
-  if (g_qr_coop_blocks < 0) {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
+  const int dev = qr_device();
+  if (g_qr_coop_blocks[dev] < 1) {
+    int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // shared memory is at most ~20 KB: one CTA per SM is always co-resident
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gauge_qr_kernel, QR_THREADS, 48 * 1024);
-    if (per < 1) per = 1;
-    g_qr_coop_blocks = sms;   // one CTA per SM keeps the barrier cheap
+    g_qr_coop_blocks[dev] = sms > 0 ? sms : 1;
   }
   int g = (m + 15) / 16;
-  if (g > g_qr_coop_blocks) g = g_qr_coop_blocks;
+  if (g > g_qr_coop_blocks[dev]) g = g_qr_coop_blocks[dev];
   if (g < 1) g = 1;
   return g;
+}
+
+size_t gauge_qr_smem(int m, int n, int G) {
+  const int rows = (m + G - 1) / G;
+  return (size_t)rows * sizeof(cplx) + 2 * (size_t)n * sizeof(cplx) + 34 * sizeof(double) +
+         QR_THREADS * sizeof(cplx) + (size_t)n + 16;
+}
+
+static cudaError_t qr_allow_smem() {
+  const int dev = qr_device();
+  if (g_qr_attr_set[dev]) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(
+      gauge_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kQrMaxSmem);
+  if (e == cudaSuccess) g_qr_attr_set[dev] = true;
+  return e;
 }
 
 cudaError_t gauge_qr(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cplx* R,
@@ -827,17 +850,11 @@ cudaError_t gauge_qr(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cplx* R,
   int G = gauge_qr_grid(m);
   if (gcap > 0 && G > gcap) G = gcap;
   if (G > W.gmax || n > W.nmax) return cudaErrorInvalidValue;
-  const int rows = (m + G - 1) / G;
-  const size_t smem = (size_t)rows * sizeof(cplx) + 2 * (size_t)n * sizeof(cplx) +
-                      34 * sizeof(double) + QR_THREADS * sizeof(cplx) + (size_t)n + 16;
-  if (smem > 200 * 1024) return cudaErrorInvalidValue;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(gauge_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         200 * 1024);
-    attr_set = true;
-  }
-  cudaError_t e = cudaMemsetAsync(W.bar, 0, 2 * sizeof(unsigned), s);
+  const size_t smem = gauge_qr_smem(m, n, G);
+  if (smem > kQrMaxSmem) return cudaErrorInvalidValue;
+  cudaError_t e = qr_allow_smem();
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(W.bar, 0, 2 * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   QrKernelArgs a;
   a.m = m; a.n = n; a.p = p;
@@ -845,6 +862,7 @@ cudaError_t gauge_qr(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cplx* R,
   if (p == 0) { a.E = Y; }
   a.Q = Q; a.R = R;
   a.part = W.part; a.partn = W.partn; a.bar = W.bar; a.status = status;
+  a.wait = W.wait > 0 ? W.wait : kBarrierWaitCycles;
   a.rank_tol = 1e-12;
   a.complete_tol = 1e-2;
   a.acc_in = nullptr;
@@ -869,12 +887,9 @@ cudaError_t gauge_qr_complete(int m, int n, int p, QrRef E, cplx* Q, const unsig
   int G = gauge_qr_grid(m);
   if (gcap > 0 && G > gcap) G = gcap;
   if (G > W.gmax || n > W.nmax) return cudaErrorInvalidValue;
-  const int rows = (m + G - 1) / G;
-  const size_t smem = (size_t)rows * sizeof(cplx) + 2 * (size_t)n * sizeof(cplx) +
-                      34 * sizeof(double) + QR_THREADS * sizeof(cplx) + (size_t)n + 16;
-  if (smem > 200 * 1024) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(gauge_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       200 * 1024);
+  const size_t smem = gauge_qr_smem(m, n, G);
+  if (smem > kQrMaxSmem) return cudaErrorInvalidValue;
+  cudaError_t e = qr_allow_smem();
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(W.bar, 0, 2 * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
@@ -883,6 +898,7 @@ cudaError_t gauge_qr_complete(int m, int n, int p, QrRef E, cplx* Q, const unsig
   a.Y = E; a.E = E;
   a.Q = Q; a.R = nullptr;
   a.part = W.part; a.partn = W.partn; a.bar = W.bar; a.status = status;
+  a.wait = W.wait > 0 ? W.wait : kBarrierWaitCycles;
   a.rank_tol = 1e-12;
   a.complete_tol = 1e-2;
   a.acc_in = acc;
@@ -939,6 +955,55 @@ cudaError_t zfill_identity_mps(cplx* A, int Ml, int D, int Mr, const int* entrie
   if (e != cudaSuccess) return e;
   if (nent > 0) count_launch();
   if (nent > 0) fill_entries_kernel<<<(nent + 255) / 256, 256, 0, s>>>(A, D, Mr, entries, nent);
+  return cudaGetLastError();
+}
+
+
+// out = sum_b E[b][b] of an M x M matrix (one block, fixed summation order)
+__global__ void __launch_bounds__(256) ztrace_kernel(const cplx* E, int M, cplx* out) {
+  __shared__ double sr[256], si[256];
+  double re = 0.0, im = 0.0;
+  for (int b = threadIdx.x; b < M; b += 256) {
+    const cplx e = E[(long long)b * M + b];
+    re += e.x;
+    im += e.y;
+  }
+  sr[threadIdx.x] = re;
+  si[threadIdx.x] = im;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      sr[threadIdx.x] += sr[threadIdx.x + w];
+      si[threadIdx.x] += si[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = make_double2(sr[0], si[0]);
+}
+
+cudaError_t ztrace(const cplx* E, int M, cplx* out, cudaStream_t s) {
+  count_launch();
+  ztrace_kernel<<<1, 256, 0, s>>>(E, M, out);
+  return cudaGetLastError();
+}
+
+
+// FP64 FMA throughput probe: every thread runs 8 independent chains of `iters` FMAs
+// (x <- x * a + b with |a| < 1, so the chains stay finite) and stores their sum.
+__global__ void __launch_bounds__(256) dfma_loop_kernel(long long iters, double a, double b,
+                                                        double* sink) {
+  double x0 = threadIdx.x * 1e-3, x1 = x0 + 0.1, x2 = x0 + 0.2, x3 = x0 + 0.3;
+  double x4 = x0 + 0.4, x5 = x0 + 0.5, x6 = x0 + 0.6, x7 = x0 + 0.7;
+  for (long long i = 0; i < iters; ++i) {
+    x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+    x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+  }
+  sink[blockIdx.x * (long long)blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+}
+
+cudaError_t dfma_loop(int blocks, long long iters, double* sink, cudaStream_t s) {
+  count_launch();
+  dfma_loop_kernel<<<blocks, 256, 0, s>>>(iters, 0.999999, 1e-6, sink);
   return cudaGetLastError();
 }
 

@@ -13,7 +13,6 @@ namespace tdmrg {
 namespace lzc {
 
 constexpr int NV = KMAX + 1;                      // partial-dot slots per CTA
-constexpr long long TIMEOUT_CYCLES = 4000000000LL;   // about 2 s at 2 GHz
 
 __device__ __forceinline__ double wsum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -22,9 +21,10 @@ __device__ __forceinline__ double wsum(double v) {
 
 // Grid barrier on one monotonic counter: barrier number e is passed once the counter reaches
 // e * nblocks (one atomic per CTA; the launcher clears the counter).  Bounded: gives up after
-// ~2 s, sets *status = 1, and every CTA then leaves.
+// `limit` clock cycles (kBarrierWaitCycles, ~2 s, unless a test lowers it), sets *status = 1,
+// and every CTA then leaves.
 __device__ __forceinline__ bool barrier(unsigned* bar, unsigned nblocks, unsigned& epoch,
-                                        int* status) {
+                                        int* status, long long limit) {
   __syncthreads();
   __shared__ int s_ok;
   ++epoch;
@@ -38,7 +38,7 @@ __device__ __forceinline__ bool barrier(unsigned* bar, unsigned nblocks, unsigne
     const long long t0 = clock64();
     while (*vbar < target) {
       if (*vstat) { ok = 0; break; }
-      if (clock64() - t0 > TIMEOUT_CYCLES) {
+      if (clock64() - t0 > limit) {
         atomicExch(status, 1);
         ok = 0;
         break;

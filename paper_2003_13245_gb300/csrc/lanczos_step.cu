@@ -26,6 +26,8 @@ struct LzStepArgs {
   double* partn;     // G
   unsigned* bar;
   int* status;
+  long long wait;    // grid-barrier wait limit (clock cycles)
+  int* noconv;       // sticky flag of unconverged runs (may be NULL)
   double tr, ti, tol;
 };
 
@@ -51,15 +53,15 @@ __global__ void __launch_bounds__(LT) lz_step_kernel(LzStepArgs A) {
 
   const int lo = j > 0 ? j - 1 : 0;
   lzc::slice_dots_block(A.V, n, w, e0, len, lo, j + 1, part1, red);
-  if (!lzc::barrier(A.bar, A.G, epoch, A.status)) return;
+  if (!lzc::barrier(A.bar, A.G, epoch, A.status, A.wait)) return;
   lzc::reduce_dots(part1, A.G, lo, j + 1, h1);
   lzc::slice_project(A.V, n, w, e0, len, lo, j + 1, h1);
   lzc::slice_dots_block(A.V, n, w, e0, len, 0, j + 1, part2, red);
-  if (!lzc::barrier(A.bar, A.G, epoch, A.status)) return;
+  if (!lzc::barrier(A.bar, A.G, epoch, A.status, A.wait)) return;
   lzc::reduce_dots(part2, A.G, 0, j + 1, h2);
   lzc::slice_project(A.V, n, w, e0, len, 0, j + 1, h2);
   lzc::slice_norm(w, len, red, A.partn);
-  if (!lzc::barrier(A.bar, A.G, epoch, A.status)) return;
+  if (!lzc::barrier(A.bar, A.G, epoch, A.status, A.wait)) return;
   lzc::reduce_norm(A.partn, A.G, &s_nrm);
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
@@ -84,6 +86,7 @@ __global__ void __launch_bounds__(LT) lz_step_kernel(LzStepArgs A) {
           S->k = j + 1;
           S->err = err;
           S->noconv = (!bd && !A.fixed && err > 1e3 * A.tol) ? 1 : 0;
+          if (S->noconv && A.noconv) atomicExch(A.noconv, 1);
           __threadfence();
           S->done = 1;
         }
@@ -122,6 +125,8 @@ cudaError_t lz_step(long long n, int j, cplx* V, LzState* S, const BondScratch& 
   a.S = (int)((n + g - 1) / g);
   a.kcap = kcap; a.fixed = fixed;
   a.V = V; a.st = S; a.part = W.part; a.partn = W.partn; a.bar = W.bar; a.status = status;
+  a.wait = W.wait > 0 ? W.wait : kBarrierWaitCycles;
+  a.noconv = W.noconv;
   a.tr = tr; a.ti = ti; a.tol = tol;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)g);

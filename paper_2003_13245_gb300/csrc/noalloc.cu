@@ -1,11 +1,12 @@
 // Gauge QR without any device allocation.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is being captured
-// (an allocation would break the capture), callers that must never fail for lack of memory
-// once set up, and host programs that hand all memory management to another runtime.  This
-// entry point serves them: the caller passes Y, E, Q and R, and the scratch the QR kernel
-// needs (the cross-block partial sums, the grid-barrier counters and a status word) lives in
-// one fixed file-scope device array that every GPU loading the library holds until exit.
+// Some callers cannot call cudaMalloc: programs that hand all device memory to another
+// runtime or pool and may not allocate behind its back, and callers that must not fail for
+// lack of memory (or wait on the implicit synchronisation an allocation can bring) once they
+// are set up.  This entry point serves them: the caller passes Y, E, Q and R, and the scratch
+// the QR kernel needs (the cross-block partial sums, the grid-barrier counters and a status
+// word) lives in one fixed file-scope device array that every GPU loading the library holds
+// until exit.
 #include <cstdio>
 #include <mutex>
 
@@ -41,11 +42,16 @@ extern "C" int tdmrg_kernel_gauge_qr_noalloc(int m, int n, const void* Y, int p,
     return na_fail(TDMRG_ERR_ARG, "gauge_qr_noalloc: need m >= n >= 1 and non-NULL buffers");
   if (n > NA_MAX_N)
     return na_fail(TDMRG_ERR_ARG, "gauge_qr_noalloc: n exceeds the fixed scratch (n <= 256)");
-  if (tdmrg::gauge_qr_grid(m) > NA_MAX_G)
-    return na_fail(TDMRG_ERR_ARG, "gauge_qr_noalloc: grid exceeds the fixed scratch (<= 192 blocks)");
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES)
     return na_fail(TDMRG_ERR_CUDA, "gauge_qr_noalloc: no usable current device");
+  const int G = tdmrg::gauge_qr_grid(m);
+  if (G > NA_MAX_G)
+    return na_fail(TDMRG_ERR_ARG, "gauge_qr_noalloc: grid exceeds the fixed scratch (<= 192 blocks)");
+  if (tdmrg::gauge_qr_smem(m, n, G) > tdmrg::kQrMaxSmem)
+    return na_fail(TDMRG_ERR_ARG,
+                   "gauge_qr_noalloc: m too large: each block stages ceil(m / blocks) rows of 16 "
+                   "bytes in at most 200 KB of shared memory (about 12,500 rows per block)");
   void* base = nullptr;
   {
     // set-up, once per device, with that device current
@@ -79,12 +85,10 @@ extern "C" int tdmrg_kernel_gauge_qr_noalloc(int m, int n, const void* Y, int p,
   if (err != cudaSuccess) return na_fail(TDMRG_ERR_CUDA, cudaGetErrorString(err));
   if (cudaStreamSynchronize(s) != cudaSuccess)
     return na_fail(TDMRG_ERR_CUDA, "gauge_qr_noalloc: stream synchronisation failed");
-  if (!status) {
-    int hs = 0;
-    if (cudaMemcpy(&hs, st, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
-      return na_fail(TDMRG_ERR_CUDA, "gauge_qr_noalloc: reading the status word failed");
-    if (hs == 1) return na_fail(TDMRG_ERR_TIMEOUT, "gauge_qr_noalloc: grid barrier timed out");
-    if (hs == 2) return na_fail(TDMRG_ERR_CUDA, "gauge_qr_noalloc: ran out of completion vectors");
-  }
+  int hs = 0;
+  if (cudaMemcpy(&hs, st, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return na_fail(TDMRG_ERR_CUDA, "gauge_qr_noalloc: reading the status word failed");
+  if (hs == 1) return na_fail(TDMRG_ERR_TIMEOUT, "gauge_qr_noalloc: grid barrier timed out");
+  if (hs == 2) return na_fail(TDMRG_ERR_CUDA, "gauge_qr_noalloc: ran out of completion vectors");
   return TDMRG_OK;
 }

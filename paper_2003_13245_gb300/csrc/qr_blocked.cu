@@ -24,7 +24,7 @@ namespace {
 constexpr int QB = 16;                 // columns per block
 constexpr int QB_THREADS = 256;
 static_assert(QB * QB == QB_THREADS, "the in-block update gives one Gram entry to each thread");
-constexpr long long QB_TIMEOUT = 4000000000LL;
+
 
 __device__ __forceinline__ double wsum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -34,7 +34,8 @@ __device__ __forceinline__ double wsum(double v) {
 // Grid barrier on one monotonic counter: barrier number e is passed once the counter reaches
 // e * nblocks (one atomic per CTA; the launcher clears the counter).  Bounded: gives up after
 // ~2 s, sets *status = 1, and every CTA then leaves.
-__device__ bool qb_barrier(unsigned* bar, unsigned nblocks, int* status, unsigned& epoch) {
+__device__ bool qb_barrier(unsigned* bar, unsigned nblocks, int* status, unsigned& epoch,
+                           long long limit) {
   __syncthreads();
   __shared__ int s_ok;
   ++epoch;
@@ -48,7 +49,7 @@ __device__ bool qb_barrier(unsigned* bar, unsigned nblocks, int* status, unsigne
     const long long t0 = clock64();
     while (*vbar < target) {
       if (*vstat) { ok = 0; break; }
-      if (clock64() - t0 > QB_TIMEOUT) {
+      if (clock64() - t0 > limit) {
         atomicExch(status, 1);
         ok = 0;
         break;
@@ -71,6 +72,7 @@ struct QbArgs {
   int PS;            // n*QB + QB + QB*QB
   unsigned* bar;
   int* status;
+  long long wait;           // grid-barrier wait limit (clock cycles)
   unsigned char* acc_out;   // [n] accepted flags (for the completion pass)
   double rank_tol;
 };
@@ -85,7 +87,7 @@ __device__ __forceinline__ cplx qb_load(const QrRef& Y, long long r, long long c
 // fin[off..off+cnt): CTA g sums the slice it owns -- one warp per entry, every lane loading its
 // share of the G partials at once -- then a barrier, then everyone may read fin.
 __device__ bool qb_reduce(const QbArgs& A, int off, int cnt, unsigned G, unsigned& ep) {
-  if (!qb_barrier(A.bar, G, A.status, ep)) return false;
+  if (!qb_barrier(A.bar, G, A.status, ep, A.wait)) return false;
   const int per = (cnt + (int)G - 1) / (int)G;
   const int lo = blockIdx.x * per, hi = min(cnt, lo + per);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -100,7 +102,7 @@ __device__ bool qb_reduce(const QbArgs& A, int off, int cnt, unsigned G, unsigne
     ay = wsum(ay);
     if (lane == 0) A.fin[off + e] = make_double2(ax, ay);
   }
-  return qb_barrier(A.bar, G, A.status, ep);
+  return qb_barrier(A.bar, G, A.status, ep, A.wait);
 }
 
 }  // namespace
@@ -406,6 +408,7 @@ cudaError_t gauge_qr_blocked(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cpl
   a.m = m; a.n = n; a.Y = Y; a.Q = Q; a.R = R;
   a.part = scratch; a.fin = scratch + (long long)G * PS; a.PS = (int)PS;
   a.bar = W.bar; a.status = status; a.acc_out = acc; a.rank_tol = rank_tol;
+  a.wait = W.wait > 0 ? W.wait : kBarrierWaitCycles;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(G);
   cfg.blockDim = dim3(QB_THREADS);

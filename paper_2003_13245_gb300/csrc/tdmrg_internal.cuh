@@ -92,6 +92,8 @@ struct BondScratch {
   unsigned long long* mv = nullptr;  // Krylov vectors used, accumulated over launches
   long long maxn = 0;
   int maxDw = 0, gmax = 0;
+  long long wait = 0;                // grid-barrier wait limit in clock cycles (0: ~2 s)
+  int* noconv = nullptr;             // lz_step: set to 1 when a Krylov run stops unconverged
 };
 // One orthogonalisation step of the host-driven Lanczos (lanczos_step.cu): w = V[j+1] holds
 // H q_j; both Gram-Schmidt passes, the norm, the small exponential, the stop test and the
@@ -108,16 +110,23 @@ cudaError_t bond_exp_fused(int M, int Dw, const cplx* L, const cplx* R, const cp
                            double tol, int kcap, int fixed, int gcap, cudaStream_t s);
 
 struct QrScratch {
-  cplx* part;          // 2 * gmax * (nmax + 1)
-  double* partn;       // 2 * gmax
-  unsigned* bar;       // 2
-  int gmax;
-  int nmax;
+  cplx* part = nullptr;       // 2 * gmax * (nmax + 1)
+  double* partn = nullptr;    // 2 * gmax
+  unsigned* bar = nullptr;    // 2
+  int gmax = 0;
+  int nmax = 0;
+  long long wait = 0;         // grid-barrier wait limit in clock cycles (0: ~2 s)
 };
+// the default limit of every bounded grid-barrier wait: about 2 s at 2 GHz
+constexpr long long kBarrierWaitCycles = 4000000000LL;
 // gcap > 0 caps the cooperative grid (several QRs of concurrent instances can then co-reside)
 cudaError_t gauge_qr(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cplx* R,
                      const QrScratch& W, int* status, cudaStream_t s, int gcap = 0);
 int gauge_qr_grid(int m);
+// dynamic shared memory of the column-wise QR on a grid of G blocks (each block stages its
+// ceil(m / G) rows); launches above kQrMaxSmem are refused
+constexpr size_t kQrMaxSmem = 200 * 1024;
+size_t gauge_qr_smem(int m, int n, int G);
 // completion pass only (skipped positions of a factorisation whose accepted flags are `acc`);
 // if src is not NULL, src[j] receives the candidate that filled completed position j (i < p:
 // column i of E, p + i: unit vector e_i; other entries untouched)
@@ -134,6 +143,15 @@ cudaError_t gauge_qr_blocked(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cpl
 
 // dst[j][i] = conj?(src[i][j]) for an m x n source.
 cudaError_t ztranspose(int m, int n, const cplx* src, cplx* dst, int conj, cudaStream_t s);
+// FP64 FMA throughput probe: blocks x 256 threads x 8 chains x iters FMAs, results to sink
+// (blocks * 256 doubles)
+cudaError_t dfma_loop(int blocks, long long iters, double* sink, cudaStream_t s);
+// hopping-limit mobility of Eq. 7 for P parameter sets (device arrays omega[P K], g[P K],
+// V[P], kT[P] -> mu[P]); K <= 64 (fgr.cu)
+cudaError_t fgr_mobility(int P, int K, const double* omega, const double* g, const double* V,
+                         const double* kT, double dt, int nt, double* mu, cudaStream_t s);
+// *out = trace of the M x M matrix E (one launch)
+cudaError_t ztrace(const cplx* E, int M, cplx* out, cudaStream_t s);
 // x <- conj(x)
 cudaError_t zconj(long long n, cplx* x, cudaStream_t s);
 // y <- y + alpha x

@@ -62,5 +62,36 @@ def c1_prefix():
         json.dump(p, f, indent=1)
 
 
+def c2_modes_prefix():
+    """The c2 chain's two modes per molecule, (w, g, nmax) = (0.2, 1.5, 8) and (1.0, 0.8, 4),
+    on N = 3 molecules at V = 0.5, kT = 2 (5 imaginary steps of dtau = 0.05), M = 128: the bulk
+    sites are 128 x 64 x 128 as in the N = 16 benchmark chain, so every kernel path of the
+    benchmark runs (split-K tensor-core H_eff, fused bond exponential at M = 128, blocked QR of
+    8192 x 128).  The oracle's C(t) on the first 10 real-time steps (dt = 0.05), with the
+    tolerances set to 10x the oracle's spread under 1e-14 relative perturbations."""
+    p = dict(N=3, omega=[0.2, 1.0], g=[1.5, 0.8], nmax=[8, 4], V=0.5, beta=0.5, dtau=0.05, M=128,
+             dt=0.05)
+    m = HolsteinModel(N=p["N"], omega=p["omega"], g=p["g"], nmax=p["nmax"], V=p["V"])
+
+    def run():
+        r = tdvp.correlation(m, p["beta"], p["dtau"], p["M"], p["dt"], 10, every=2)
+        run.last = r
+        return r.logZ, r.C
+
+    dz, dc = perturbed_spread(run, seeds=(1, 2))
+    logz, C = run()
+    r = run.last
+    p.update(t=r.t.tolist(), C_re=C.real.tolist(), C_im=C.imag.tolist(), logZ=logz,
+             spread_logZ=dz, spread_C=dc, tol=max(1e-10, 10 * dc), logz_tol=max(1e-10, 10 * dz),
+             source="oracle.tdvp.correlation; spread: 2 runs with 1e-14 relative noise on every "
+                    "gauge-QR input")
+    with open(os.path.join(HERE, "c2modes_N3_M128_prefix.json"), "w") as f:
+        json.dump(p, f, indent=1)
+
+
 if __name__ == "__main__":
-    c1_prefix()
+    which = sys.argv[1:] or ["c1"]
+    if "c1" in which:
+        c1_prefix()
+    if "c2modes" in which:
+        c2_modes_prefix()

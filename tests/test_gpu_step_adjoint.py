@@ -7,7 +7,9 @@ sites and the parameter cotangents (omega, g, V).
 * The right-canonicalised |I> at M = 4, real tau: rank-2 bonds, so 12 gauge-QR columns per
   step are completed from their coupling candidates, accepted with residuals down to 1e-2 of
   their norm; two CPU rounding orders of the same algorithm differ by 2.6e-9 of the parameter
-  cotangents, so the bound there is 1e-7.  (Wider bonds around |I>, or imaginary tau from it,
+  cotangents, so the bound there is 1e-7; 1e-14 relative noise on the input sites moves the
+  oracle's own output sites by 3.7e-9 of their largest entry, so they are held to 4e-8 there
+  (10x that spread; measured on GB300: 4e-10).  (Wider bonds around |I>, or imaginary tau from it,
   put columns at the rank threshold and are not a parity case: two rounding orders differ by
   1e-6 and more.)
 """
@@ -34,11 +36,11 @@ def dev(a):
 
 
 @pytest.mark.parametrize("basis", [False, True])
-@pytest.mark.parametrize("M,tau,start,bound", [(4, -0.1j, "random", 1e-8),
-                                               (4, -0.05, "random", 1e-8),
-                                               (64, -0.1j, "random", 1e-8),
-                                               (4, -0.1j, "identity", 1e-7)])
-def test_step_vjp_matches_oracle_tape(M, tau, start, bound, basis):
+@pytest.mark.parametrize("M,tau,start,bound,out_bound", [(4, -0.1j, "random", 1e-8, 1e-10),
+                                                         (4, -0.05, "random", 1e-8, 1e-10),
+                                                         (64, -0.1j, "random", 1e-8, 1e-10),
+                                                         (4, -0.1j, "identity", 1e-7, 4e-8)])
+def test_step_vjp_matches_oracle_tape(M, tau, start, bound, out_bound, basis):
     from oracle import adjoint, tdvp
     from oracle.model import HolsteinModel, mpo_hamiltonian, site_list
     from paper_2003_13245_gb300 import binding
@@ -69,7 +71,7 @@ def test_step_vjp_matches_oracle_tape(M, tau, start, bound, basis):
     finally:
         m.close()
     for got, ref in zip(A_out, ref_out):
-        assert np.abs(got.cpu().numpy() - ref).max() <= 1e-10 * max(np.abs(ref).max(), 1e-300)
+        assert np.abs(got.cpu().numpy() - ref).max() <= out_bound * max(np.abs(ref).max(), 1e-300)
     scale = max(np.abs(x).max() for x in ref_in)
     for got, ref in zip(Abar_in, ref_in):
         assert np.abs(got.cpu().numpy() - ref).max() <= bound * scale

@@ -164,3 +164,81 @@ def test_mixed_precision_sector_norm_beyond_fp32():
     assert np.isfinite(lz1) and lz0 > 200.0
     assert abs(lz1 - lz0) < 2e-3
     assert abs(c1 - c0) < 2e-4 * abs(c0)
+
+
+def test_mobility_from_gpu_correlation_matches_ed():
+    """Eq. 2 end to end: mu from the GPU's C(t) of the c1 chain at full bond dimension (M=256)
+    through tdmrg_mobility equals mu from the exact-diagonalisation C(t) on the same grid
+    (t = 0..5, dt = 0.05, trapezoid) to 1e-10 of C(0) t_max / kT, the bound the 1e-10 C(t)
+    parity implies; the 3xTF32 path stays within 2e-4 of the same scale."""
+    from oracle import kubo
+    from paper_2003_13245_gb300 import PREC_C64_3XTF32, binding
+    ed = _ed(3, [1.0], [1.0], [4], 1.0, 1.0)
+    t = np.arange(0, 101) * 0.05
+    ref = ed.correlation(t)
+    mu_ed = kubo.mobility(t, ref, 1.0)
+    scale = abs(ref[0]) * t[-1] / 1.0
+    for prec, bound in ((None, 1e-10), (PREC_C64_3XTF32, 2e-4)):
+        kw = {} if prec is None else dict(precision=prec)
+        m = _model(3, [1.0], [1.0], [4], 1.0, **kw)
+        m.thermal_prepare(1.0, 0.05, 256)
+        C = m.correlation(t, 0.05)
+        m.close()
+        mu = binding.mobility(t, C, 1.0)
+        assert abs(mu - mu_ed) <= bound * scale
+
+
+def test_reduced_density_and_coherence_length():
+    """Eq. 9 on the GPU (tdmrg_reduced_density: one pass of transfer contractions over Psi_b):
+    at full bond dimension sigma equals exact diagonalisation to 1e-10 and so does L; the
+    3xTF32 path within 1e-5 (contractions at ~2^-21); the limits L = 1 at V = 0 and L -> N on
+    the even free ring at low temperature (g = 0, N = 4, beta = 40, whose state has Schmidt
+    rank <= 4 so M = 16 is exact)."""
+    from oracle import kubo
+    from paper_2003_13245_gb300 import PREC_C64_3XTF32, binding
+    ref = _ed(3, [1.0], [1.0], [4], 1.0, 1.0).reduced_density()
+    for prec, bound in ((None, 1e-10), (PREC_C64_3XTF32, 1e-5)):
+        kw = {} if prec is None else dict(precision=prec)
+        m = _model(3, [1.0], [1.0], [4], 1.0, **kw)
+        m.thermal_prepare(1.0, 0.05, 256)
+        sig = m.reduced_density()
+        m.close()
+        assert np.abs(sig - ref).max() < bound
+        L = binding.coherence_length(sig)
+        assert abs(L - kubo.coherence_length(ref)) < 10 * bound
+    m = _model(3, [1.0], [1.0], [3], 0.0)
+    m.thermal_prepare(1.0, 0.1, 16)
+    assert abs(binding.coherence_length(m.reduced_density()) - 1.0) < 1e-12
+    m.close()
+    m = _model(4, [1.0], [0.0], [2], 1.0)
+    m.thermal_prepare(40.0, 0.1, 16)
+    assert abs(binding.coherence_length(m.reduced_density()) - 4.0) < 1e-8
+    m.close()
+
+
+def test_c2_shaped_sites_match_oracle_golden():
+    """The c2 chain's two modes per molecule on N = 3 at M = 128 (bulk sites 128 x 64 x 128,
+    the benchmark's kernel paths: split-K tensor-core H_eff, fused bond exponential at M = 128,
+    blocked QR of 8192 x 128): preparation at kT = 2 plus ten real-time steps against the
+    oracle's stored values (tests/golden/make_golden.py, oracle only).  FP64 within 10x the
+    oracle's own perturbation spread; 3xTF32 within 5e-4 of C(0) and 5e-4 in log Z (the
+    precision of the complex-FP32 contractions accumulated over the sweep)."""
+    from paper_2003_13245_gb300 import PREC_C64_3XTF32
+    path = os.path.join(GOLDEN, "c2modes_N3_M128_prefix.json")
+    g = json.load(open(path))
+    t = np.array(g["t"])
+    ref = np.array(g["C_re"]) + 1j * np.array(g["C_im"])
+    for prec in (None, PREC_C64_3XTF32):
+        kw = {} if prec is None else dict(precision=prec)
+        m = _model(g["N"], g["omega"], g["g"], g["nmax"], g["V"], **kw)
+        m.thermal_prepare(g["beta"], g["dtau"], g["M"])
+        C = m.correlation(t, g["dt"])
+        lz = m.logz()
+        m.close()
+        err = np.abs(C - ref).max() / abs(ref[0])
+        if prec is None:
+            assert abs(lz - g["logZ"]) < g["logz_tol"]
+            assert err < g["tol"]
+        else:
+            assert abs(lz - g["logZ"]) < 5e-4
+            assert err < 5e-4

@@ -32,6 +32,19 @@ def test_mobility_matches_oracle(lib):
     assert abs(binding.mobility(t, C, 0.7) - kubo.mobility(t, C, 0.7)) < 1e-14
 
 
+def test_mean_free_path_matches_oracle(lib):
+    """Eq. 8 through the C ABI equals the oracle's quadrature on a sign-changing Re C."""
+    from oracle import kubo
+    from paper_2003_13245_gb300 import binding
+    t = np.linspace(0, 8, 161)
+    C = np.exp(-0.3 * t) * (1.7 * np.cos(2.1 * t) + 0.2j * np.sin(t))
+    got = binding.mean_free_path(t, C)
+    ref = kubo.mean_free_path(t, C)
+    assert max(abs(a - b) for a, b in zip(got, ref)) < 1e-14
+    with pytest.raises(binding.TdmrgError):
+        binding.mean_free_path(t, -C)          # <j j> must be positive
+
+
 def test_argument_errors_are_reported(lib):
     from paper_2003_13245_gb300 import binding
     with pytest.raises(binding.TdmrgError) as e:

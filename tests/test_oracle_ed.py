@@ -87,3 +87,43 @@ def test_kubo_trapezoid():
     t = np.array([0.0, 1.0, 3.0])
     C = np.array([2.0, 1.0, 0.0]) + 1j
     assert abs(kubo.mobility(t, C, 1.0) - (1.5 + 1.0)) < 1e-15
+
+
+# ---- mean free path (Eq. 8) -------------------------------------------------------------------
+
+def test_mean_free_path_gaussian_closed_form():
+    """C(t) = C0 exp(-t^2 / (2 s^2)): v = sqrt(C0), tau = s sqrt(pi / 2) (t_max = 12 s)."""
+    from oracle import kubo
+    C0, s = 2.5, 0.7
+    t = np.linspace(0.0, 12 * s, 4001)
+    C = C0 * np.exp(-t ** 2 / (2 * s * s)) * (1 + 0.3j * t)     # Im C does not enter
+    v, tau, l = kubo.mean_free_path(t, C)
+    assert abs(v - np.sqrt(C0)) < 1e-15
+    assert abs(tau - s * np.sqrt(np.pi / 2)) < 1e-9
+    assert abs(l - v * tau) < 1e-15
+
+
+def test_mean_free_path_free_band_grows_with_cutoff():
+    """g = 0: C is constant (free band), so tau equals the cut-off t_max."""
+    from oracle import kubo
+    c = kubo.free_band_correlation(3, 1.0, 1.0)
+    t = np.arange(0, 201) * 0.05
+    v, tau, l = kubo.mean_free_path(t, np.full(t.size, c + 0j))
+    assert abs(tau - t[-1]) < 1e-12 and abs(v - np.sqrt(c)) < 1e-15
+
+
+def test_mean_free_path_takes_absolute_values():
+    """Re C = cos(w t) exp(-g t) changes sign: tau = int_0^T |cos w t| e^{-g t} dt (adaptive
+    quadrature split at the zeros of the cosine) -- dropping the absolute value fails this."""
+    import scipy.integrate
+    from oracle import kubo
+    w, gam, T = 3.0, 0.4, 12.0
+    t = np.linspace(0.0, T, 24001)
+    C = np.cos(w * t) * np.exp(-gam * t) + 0j
+    zeros = [(k + 0.5) * np.pi / w for k in range(int(T * w / np.pi) + 1) if (k + 0.5) * np.pi / w < T]
+    ref = scipy.integrate.quad(lambda x: abs(np.cos(w * x)) * np.exp(-gam * x), 0.0, T,
+                               points=zeros, limit=200, epsabs=1e-13)[0]
+    _, tau, _ = kubo.mean_free_path(t, C)
+    assert abs(tau - ref) < 1e-6
+    signed = np.trapezoid(C.real, t)
+    assert abs(signed - ref) > 0.1

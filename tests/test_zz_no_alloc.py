@@ -1,6 +1,7 @@
 """The allocation-free gauge QR (tdmrg_kernel_gauge_qr_noalloc) against the allocating one.
 
-It serves callers that cannot allocate device memory (graph capture, fixed-memory hosts);
+It serves callers that cannot allocate device memory (all device memory owned by another
+runtime or pool, or no allocation allowed once set up);
 two calls in a row must give the same Q and R as tdmrg_kernel_gauge_qr, which also shows that
 the shared scratch left by one call does not leak into the next."""
 import numpy as np
@@ -51,3 +52,16 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     with pytest.raises(binding.TdmrgError) as e:
         binding.kernel_gauge_qr_noalloc(Y, Q, R)
     assert "n <= 256" in str(e.value)
+
+
+def test_noalloc_rejects_rows_beyond_shared_memory():
+    """m so large that one block's row slice exceeds the kernel's 200 KB of shared memory is
+    refused on the host with a message, before any launch (no buffer is touched)."""
+    import ctypes
+    from paper_2003_13245_gb300 import binding
+    lib = binding.load()
+    Y = torch.zeros((1, 1), dtype=torch.complex128, device="cuda")
+    p = ctypes.c_void_p(Y.data_ptr())
+    rc = lib.tdmrg_kernel_gauge_qr_noalloc(4_200_000, 1, p, 0, None, p, p, None, None)
+    assert rc == -1
+    assert "shared memory" in lib.tdmrg_last_global_error().decode()

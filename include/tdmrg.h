@@ -99,12 +99,14 @@ int tdmrg_model_set_stream(tdmrg_model* h, void* stream);
 int tdmrg_model_set_graphs(tdmrg_model* h, int on);
 
 /* Batched real-time stepping of several independent instances (the (V, T, N) parameter sweep):
- * every model must have been prepared and passed tdmrg_realtime_init.  tdmrg_batch_create puts
- * each model in graph mode on its own stream (with a QR grid capped to a quarter of the SMs
- * so that instances run side by side; the models keep their own data), and
- * tdmrg_batch_realtime_step launches one step of every instance before waiting for any of
- * them.  Results are those of the individual models (tdmrg_realtime_observe on each).  The
- * batch does not own the models; destroy it before them. */
+ * every model must have been prepared and passed tdmrg_realtime_init with a fixed Krylov
+ * dimension.  tdmrg_batch_create puts each model in graph mode on its own stream (with its
+ * cooperative grids capped to a quarter of the SMs so that instances run side by side; the
+ * models keep their own data).  A half-step of the whole batch is ONE CUDA graph launch: the
+ * graph, captured at the first use of a time step, holds every instance's half-sweeps of both
+ * states as independent branches.  tdmrg_batch_realtime_step runs whole steps (two half-step
+ * graphs each).  Results are those of the individual models (tdmrg_realtime_observe on each).
+ * The batch does not own the models; destroy it before them. */
 typedef struct tdmrg_batch tdmrg_batch;
 int tdmrg_batch_create(tdmrg_model* const* models, int n, tdmrg_batch** out);
 int tdmrg_batch_realtime_step(tdmrg_batch* b, int nsteps, double dt);
@@ -132,6 +134,14 @@ int tdmrg_batch_destroy(tdmrg_batch* b);
  * usable; the interrupted state is not: prepare again).  Lowering the limit is how the timeout
  * path is tested without a stuck GPU. */
 int tdmrg_model_set_wait_cycles(tdmrg_model* h, long long cycles);
+
+/* Real-time propagation of the two states of Eq. 6 side by side (on by default): Psi_2 = j Psi_b
+ * is stepped by a second set of workspaces on its own stream and host thread while Psi_1 is
+ * stepped on the handle's stream; the cooperative grids of both are capped to half of the SMs
+ * meanwhile.  Results equal the one-after-the-other order up to rounding (the capped grids sum
+ * in other partitions).  Takes effect at the next tdmrg_realtime_init; not used in graph mode.
+ * The second set of workspaces roughly doubles the device memory of the real-time phase. */
+int tdmrg_model_set_concurrent(tdmrg_model* h, int on);
 
 /* Phase timers: when on, the library synchronises its stream at every phase boundary and
  * accumulates host wall time per phase into the stats (slightly slower; off by default). */
@@ -324,6 +334,16 @@ const char* tdmrg_last_global_error(void);
 int tdmrg_kernel_heff(int Ml, int Mr, int d, int Dl, int Dr, const double* W_host,
                       const void* L, const void* R, const void* A, void* out,
                       void* X, void* Y, void* ws32, int precision, void* stream);
+
+/* The H_eff product of tdmrg_kernel_heff as the engine runs it in the sweep (same definition
+ * and layouts), timed: the environments are prepared once, one warm-up product, then `reps`
+ * products between two CUDA events on `stream`; *ms_per_matvec (host) receives the average.
+ * TDMRG_PREC_C64_3XTF32 uses the engine's tensor-core path (split, L.A contraction with
+ * split-K, MPO mixing into split planes, contraction with R); TDMRG_PREC_C128 the FP64 path.
+ * Allocates its workspaces (freed before return); synchronises `stream`. */
+int tdmrg_kernel_heff_timed(int Ml, int Mr, int d, int Dl, int Dr, const double* W_host,
+                            const void* L, const void* R, const void* A, void* out, int precision,
+                            int reps, double* ms_per_matvec, void* stream);
 
 /* Vector-Jacobian product of the H_eff product of the one-site step (Eq. S1) -- the building
  * block an adjoint of the step needs (the adjoint itself has no counterpart in the paper).
@@ -529,6 +549,26 @@ int tdmrg_kernel_bond_exp(int M, int Dw, const void* L, const void* R, const voi
  * measured FP64 rate that the FP64 kernels' roofline fractions are quoted beside. */
 int tdmrg_kernel_dfma_loop(int blocks, long long iters, double* sink, double* flops_out,
                            void* stream);
+
+/* Split-K tuning of the tensor-core contractions (no counterpart in the paper).  Every
+ * contraction of the mixed-precision path is one tcgen05 GEMM of shape (M, N, K) summed over
+ * nred operand pairs for nbatch outputs; its K loop may be split over CTAs.  The split of each
+ * shape is read from tc_splitk_table.txt beside libtdmrg.so (or the file named by the
+ * environment variable TDMRG_SPLITK_TABLE), lines "M N K nred nbatch ksplit"; shapes not listed
+ * use an occupancy rule.  The table is written by paper_2003_13245_gb300/tune_splitk.py, which
+ * records a workload's shapes and times every candidate split:
+ *   tdmrg_tune_record_shapes(1) starts recording the shapes tc_gemm sees (0 stops);
+ *   tdmrg_tune_recorded_shapes writes up to `capacity` shapes as 5 ints each to shapes[] and
+ *     their number to *count (host);
+ *   tdmrg_tune_reload_table makes the next contraction read the table file again;
+ *   tdmrg_kernel_tc_gemm_timed runs one shape with split ksplit (0: the table / rule) on
+ *     synthetic operands, one warm-up then `reps` launches between CUDA events on `stream`,
+ *     and writes the average milliseconds to *ms_out (allocates and frees its operands). */
+int tdmrg_tune_record_shapes(int on);
+int tdmrg_tune_recorded_shapes(int* shapes, int capacity, int* count);
+int tdmrg_tune_reload_table(void);
+int tdmrg_kernel_tc_gemm_timed(int M, int N, int K, int nred, int nbatch, int ksplit, int reps,
+                               double* ms_out, void* stream);
 
 /* Krylov exponential of a dense Hermitian matrix H (n x n, device) -- the site and bond
  * exponentials of Eq. S1 on an explicit matrix:

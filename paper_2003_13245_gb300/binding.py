@@ -43,6 +43,8 @@ _SIGS = {
     "tdmrg_model_destroy": [_p],
     "tdmrg_model_set_profiling": [_p, _i],
     "tdmrg_model_set_wait_cycles": [_p, ctypes.c_longlong],
+    "tdmrg_model_set_concurrent": [_p, _i],
+    "tdmrg_kernel_heff_timed": [_i, _i, _i, _i, _i, _dp, _p, _p, _p, _p, _i, _i, _dp, _p],
     "tdmrg_model_set_graphs": [_p, _i],
     "tdmrg_model_set_rank_tol": [_p, _d],
     "tdmrg_batch_create": [ctypes.POINTER(_p), _i, ctypes.POINTER(_p)],
@@ -53,6 +55,10 @@ _SIGS = {
     "tdmrg_mean_free_path": [_dp, _dp, _i, _dp],
     "tdmrg_reduced_density": [_p, _dp],
     "tdmrg_kernel_dfma_loop": [_i, ctypes.c_longlong, _p, _dp, _p],
+    "tdmrg_tune_record_shapes": [_i],
+    "tdmrg_tune_recorded_shapes": [_ip, _i, _ip],
+    "tdmrg_tune_reload_table": [],
+    "tdmrg_kernel_tc_gemm_timed": [_i, _i, _i, _i, _i, _i, _i, _dp, _p],
     "tdmrg_fgr_mobility_batch": [_i, _i, _dp, _dp, _dp, _dp, _d, _i, _dp, _p],
     "tdmrg_coherence_length": [_i, _dp, _dp],
     "tdmrg_thermal_prepare": [_p, _d, _d, _i],
@@ -239,6 +245,10 @@ class Model:
         _check(self._lib.tdmrg_model_set_krylov(self._h, float(tol), int(kmax), int(fixed_k)),
                self._h)
 
+    def set_concurrent(self, on=True):
+        """Step the two real-time states side by side (default) or one after the other."""
+        _check(self._lib.tdmrg_model_set_concurrent(self._h, int(bool(on))), self._h)
+
     def set_wait_cycles(self, cycles):
         """Limit of the bounded grid-barrier waits in clock cycles (0: default, ~2 s)."""
         _check(self._lib.tdmrg_model_set_wait_cycles(self._h, int(cycles)), self._h)
@@ -385,6 +395,35 @@ def fgr_mobility_batch(omega, g, V, kT, dt, nt, stream=None):
     return mu
 
 
+def tune_record_shapes(on):
+    """Start (True) or stop recording the tensor-core contraction shapes."""
+    load().tdmrg_tune_record_shapes(int(bool(on)))
+
+
+def tune_recorded_shapes():
+    """The recorded shapes as a list of (M, N, K, nred, nbatch)."""
+    lib = load()
+    n = ctypes.c_int()
+    _check(lib.tdmrg_tune_recorded_shapes(None, 0, ctypes.byref(n)))
+    buf = np.zeros(5 * max(n.value, 1), dtype=np.int32)
+    _check(lib.tdmrg_tune_recorded_shapes(buf.ctypes.data_as(_ip), n.value, ctypes.byref(n)))
+    return [tuple(int(x) for x in buf[5 * i:5 * i + 5]) for i in range(n.value)]
+
+
+def tune_reload_table():
+    load().tdmrg_tune_reload_table()
+
+
+def kernel_tc_gemm_timed(M, N, K, nred, nbatch, ksplit, reps=10, stream=None):
+    """Average milliseconds of one tensor-core contraction shape with split ksplit."""
+    lib = load()
+    ms = ctypes.c_double()
+    _check(lib.tdmrg_kernel_tc_gemm_timed(int(M), int(N), int(K), int(nred), int(nbatch),
+                                          int(ksplit), int(reps), ctypes.byref(ms),
+                                          _stream_ptr(stream)))
+    return ms.value
+
+
 def coherence_length(sigma):
     """Eq. 9 through tdmrg_coherence_length for an N x N complex sigma."""
     lib = load()
@@ -471,6 +510,19 @@ def kernel_heff(L, W, R, A, out, X, Y, d, precision=PREC_C128, ws32=None, stream
     _check(lib.tdmrg_kernel_heff(Ml, Mr, d, Dl, Dr, _dptr(Wc), _ptr(L), _ptr(R), _ptr(A),
                                  _ptr(out), _ptr(X), _ptr(Y), _ptr(ws32), int(precision),
                                  _stream_ptr(stream)))
+
+
+def kernel_heff_timed(L, W, R, A, out, d, precision=PREC_C64_3XTF32, reps=20, stream=None):
+    """Average milliseconds of the sweep's H_eff product (tdmrg_kernel_heff_timed)."""
+    lib = load()
+    Dl, Ml, _ = L.shape
+    Dr, Mr, _ = R.shape
+    Wc = np.ascontiguousarray(W, dtype=np.complex128).view(np.float64)
+    ms = ctypes.c_double()
+    _check(lib.tdmrg_kernel_heff_timed(Ml, Mr, d, Dl, Dr, _dptr(Wc), _ptr(L), _ptr(R), _ptr(A),
+                                       _ptr(out), int(precision), int(reps), ctypes.byref(ms),
+                                       _stream_ptr(stream)))
+    return ms.value
 
 
 def kernel_heff_vjp(L, W, R, A, ybar, Abar, Lbar, Rbar, X, Y, d, stream=None):

@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(BT, 1) bond_exp_kernel(BondArgs A) {
   __shared__ cplx h1[NV], h2[NV], cc[KMAX];
   __shared__ double alpha[KMAX], beta[KMAX + 1], red[BT / 32];
   __shared__ double s_nrm, s_b0, s_scale;
-  __shared__ int s_done, s_k;
+  __shared__ int s_done, s_k, s_second;
 
   const int M = A.M, Dw = A.Dw;
   const long long n = A.n;
@@ -241,15 +241,30 @@ __global__ void __launch_bounds__(BT, 1) bond_exp_kernel(BondArgs A) {
     __syncthreads();
     const int lo = j > 0 ? j - 1 : 0;
     lzc::slice_dots(A.V, n, ws, e0, len, lo, j + 1, part1);
+    lzc::slice_norm(ws, len, red, A.partn + A.G);     // ||w||^2 before the projection
     if (!lzc::barrier(A.bar, A.G, epoch, A.status, A.wait)) return;
-    // ---- C2: first projection; dots against q_0 .. q_j
+    // ---- C2: first projection; then, only if it cancelled more than half of ||w||^2
+    // (the criterion of Daniel, Gragg, Kaufman and Stewart), the second one against q_0 .. q_j
     lzc::reduce_dots(part1, A.G, lo, j + 1, h1);
+    lzc::reduce_norm(A.partn + A.G, A.G, &s_nrm);
     lzc::slice_project(A.V, n, ws, e0, len, lo, j + 1, h1);
-    lzc::slice_dots(A.V, n, ws, e0, len, 0, j + 1, part2);
-    if (!lzc::barrier(A.bar, A.G, epoch, A.status, A.wait)) return;
-    // ---- C3: second projection; ||w||^2
-    lzc::reduce_dots(part2, A.G, 0, j + 1, h2);
-    lzc::slice_project(A.V, n, ws, e0, len, 0, j + 1, h2);
+    if (threadIdx.x == 0) {
+      double rem = s_nrm;
+      for (int i = lo; i <= j; ++i) rem -= h1[i].x * h1[i].x + h1[i].y * h1[i].y;
+      s_second = (rem < 0.5 * s_nrm) ? 1 : 0;
+    }
+    __syncthreads();
+    if (s_second) {
+      lzc::slice_dots(A.V, n, ws, e0, len, 0, j + 1, part2);
+      if (!lzc::barrier(A.bar, A.G, epoch, A.status, A.wait)) return;
+      // ---- C3: second projection
+      lzc::reduce_dots(part2, A.G, 0, j + 1, h2);
+      lzc::slice_project(A.V, n, ws, e0, len, 0, j + 1, h2);
+    } else {
+      for (int i = threadIdx.x; i <= j; i += blockDim.x) h2[i] = make_double2(0.0, 0.0);
+      __syncthreads();
+    }
+    // ---- ||w||^2
     for (int e = threadIdx.x; e < len; e += BT) A.W[e0 + e] = ws[e];
     lzc::slice_norm(ws, len, red, A.partn);
     if (!lzc::barrier(A.bar, A.G, epoch, A.status, A.wait)) return;

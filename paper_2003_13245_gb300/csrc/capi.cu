@@ -23,6 +23,25 @@ struct tdmrg_model {
 struct tdmrg_batch {
   std::vector<tdmrg_model*> models;
   int phase = 0;   // 1 after a left-to-right half-step (the step is completed by the next one)
+  // one CUDA graph per half-step over every instance (each instance a branch on its own
+  // stream), captured at the first use of a time step dt
+  cudaStream_t s0 = nullptr;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  double dt[2] = {0.0, 0.0};
+  std::vector<tdmrg::Stats> delta[2];
+  ~tdmrg_batch() {
+    for (auto& e : exec)
+      if (e) cudaGraphExecDestroy(e);
+    for (auto& e : join)
+      if (e) cudaEventDestroy(e);
+    if (fork) cudaEventDestroy(fork);
+    if (s0) {
+      cudaStreamSynchronize(s0);
+      cudaStreamDestroy(s0);
+    }
+  }
 };
 
 static thread_local std::string g_err;
@@ -308,15 +327,58 @@ const char* grid_steps(const double* t_grid, int nt, double dt, std::vector<long
   return nullptr;
 }
 
-// launches one half-step (half 1 or 2) of every instance, then waits for all of them
-int batch_half(tdmrg_batch* b, double dt, int half) {
-  for (tdmrg_model* h : b->models) {
-    const int rc = guarded(h, [&] { h->eng->realtime_half_launch(dt, half); });
-    if (rc != TDMRG_OK) {
-      g_err = h->err;
-      return rc;
-    }
+// the graph of one half-step of every instance: captured from a fork on the batch stream, each
+// instance's engine recording its work on its own stream, joined back before the capture ends
+void batch_capture(tdmrg_batch* b, double dt, int half) {
+  const int n = (int)b->models.size();
+  if (!b->s0) CK(cudaStreamCreateWithFlags(&b->s0, cudaStreamNonBlocking));
+  if (!b->fork) CK(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+  while ((int)b->join.size() < n) {
+    cudaEvent_t e = nullptr;
+    CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    b->join.push_back(e);
   }
+  cudaGraphExec_t& ex = b->exec[half - 1];
+  if (ex) {
+    cudaGraphExecDestroy(ex);
+    ex = nullptr;
+  }
+  std::vector<tdmrg::Stats> delta(n);
+  CK(cudaStreamBeginCapture(b->s0, cudaStreamCaptureModeThreadLocal));
+  cudaGraph_t graph = nullptr;
+  try {
+    CK(cudaEventRecord(b->fork, b->s0));
+    for (int i = 0; i < n; ++i) {
+      Engine& e = *b->models[i]->eng;
+      CK(cudaStreamWaitEvent(e.stream(), b->fork, 0));
+      delta[i] = e.capture_realtime_half(dt, half);
+      CK(cudaEventRecord(b->join[i], e.stream()));
+      CK(cudaStreamWaitEvent(b->s0, b->join[i], 0));
+    }
+  } catch (...) {
+    cudaStreamEndCapture(b->s0, &graph);
+    if (graph) cudaGraphDestroy(graph);
+    throw;
+  }
+  CK(cudaStreamEndCapture(b->s0, &graph));
+  const cudaError_t e = cudaGraphInstantiate(&ex, graph, 0);
+  cudaGraphDestroy(graph);
+  CK(e);
+  b->dt[half - 1] = dt;
+  b->delta[half - 1] = delta;
+}
+
+// one half-step (half 1 or 2) of every instance: a single graph launch, then each instance's
+// status words are read
+int batch_half(tdmrg_batch* b, double dt, int half) {
+  const int rc0 = guarded(nullptr, [&] {
+    if (!b->exec[half - 1] || b->dt[half - 1] != dt) batch_capture(b, dt, half);
+    CK(cudaGraphLaunch(b->exec[half - 1], b->s0));
+    for (size_t i = 0; i < b->models.size(); ++i)
+      b->models[i]->eng->add_stats(b->delta[half - 1][i]);
+    CK(cudaStreamSynchronize(b->s0));
+  });
+  if (rc0 != TDMRG_OK) return rc0;
   for (tdmrg_model* h : b->models) {
     const int rc = guarded(h, [&] { h->eng->sync_and_check(); });
     if (rc != TDMRG_OK) {
@@ -376,20 +438,9 @@ int tdmrg_batch_realtime_step(tdmrg_batch* b, int nsteps, double dt) {
   if (b->phase != 0)
     return fail(nullptr, TDMRG_ERR_STATE, "batch step: a half-step is pending (call tdmrg_batch_step_half)");
   for (int st = 0; st < nsteps; ++st) {
-    for (tdmrg_model* h : b->models) {
-      const int rc = guarded(h, [&] { h->eng->realtime_step_launch(dt); });
-      if (rc != TDMRG_OK) {
-        g_err = h->err;
-        return rc;
-      }
-    }
-    for (tdmrg_model* h : b->models) {
-      const int rc = guarded(h, [&] { h->eng->sync_and_check(); });
-      if (rc != TDMRG_OK) {
-        g_err = h->err;
-        return rc;
-      }
-    }
+    int rc = batch_half(b, dt, 1);
+    if (rc == TDMRG_OK) rc = batch_half(b, dt, 2);
+    if (rc != TDMRG_OK) return rc;
   }
   return TDMRG_OK;
 }
@@ -657,7 +708,7 @@ int tdmrg_get_logz(const tdmrg_model* h, double* logz) {
 
 int tdmrg_get_stats(const tdmrg_model* h, double* stats, int n) {
   if (!h || !stats || n < 0) return fail(nullptr, TDMRG_ERR_ARG, "NULL argument");
-  const auto& s = h->eng->stats;
+  const tdmrg::Stats s = h->eng->total_stats();
   const double v[21] = {s.site_updates, s.matvecs, s.heff_flops, s.krylov_vectors,
                         s.bond_matvecs, s.qrs, s.completions, s.env_updates, s.heff_ms,
                         s.h2d_bytes, s.d2h_bytes,
@@ -716,6 +767,162 @@ int tdmrg_kernel_heff(int Ml, int Mr, int d, int Dl, int Dr, const double* W_hos
       if (hs) throw Failure{TDMRG_ERR_TIMEOUT, "tensor-core pipeline wait timed out"};
     }
     CK(cudaStreamSynchronize(s));
+  });
+}
+
+int tdmrg_kernel_heff_timed(int Ml, int Mr, int d, int Dl, int Dr, const double* W_host,
+                            const void* L, const void* R, const void* A, void* out, int precision,
+                            int reps, double* ms_per_matvec, void* stream) {
+  if (Ml < 1 || Mr < 1 || d < 1 || Dl < 1 || Dr < 1 || !W_host || !L || !R || !A || !out ||
+      reps < 1 || !ms_per_matvec)
+    return fail(nullptr, TDMRG_ERR_ARG, "heff_timed: bad arguments");
+  if (precision != TDMRG_PREC_C128 && precision != TDMRG_PREC_C64_3XTF32)
+    return fail(nullptr, TDMRG_ERR_ARG, "heff_timed: unknown precision");
+  return guarded(nullptr, [&] {
+    using tdmrg::cplx;
+    using tdmrg::pad4;
+    TempMpo W(Dl, Dr, d, W_host);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int D = d * d;
+    const long long site = (long long)Ml * D * Mr;
+    std::vector<void*> mem;
+    struct Free {
+      std::vector<void*>& m;
+      ~Free() {
+        for (void* p : m) cudaFree(p);
+      }
+    } fr{mem};
+    auto get = [&](size_t bytes) {
+      void* p = nullptr;
+      CK(cudaMalloc(&p, bytes > 0 ? bytes : 16));
+      mem.push_back(p);
+      return p;
+    };
+    int* st = (int*)get(sizeof(int));
+    CK(cudaMemsetAsync(st, 0, sizeof(int), s));
+    const int Dm = Dl > Dr ? Dl : Dr;
+    tdmrg::TcBufs b{};
+    cplx *X = nullptr, *Y = nullptr;
+    if (precision == TDMRG_PREC_C64_3XTF32) {
+      b.envA = (float*)get(sizeof(float) * 4 * (size_t)Dl * Ml * pad4(Ml));
+      b.envB = (float*)get(sizeof(float) * 4 * (size_t)Dr * Mr * pad4(Mr));
+      b.siteA = (float*)get(sizeof(float) * 4 * (size_t)D * Mr * pad4(Ml));
+      b.x32 = (float*)get(sizeof(float) * 2 * (size_t)Dm * site);
+      b.mix = (float*)get(sizeof(float) * 4 * (size_t)Dr * Ml * D * pad4(Mr));
+      b.kpart_len = 4LL << 20;
+      b.kpart = (float*)get(sizeof(float) * (size_t)b.kpart_len);
+      b.status = st;
+      tdmrg::heff_tc_prepare(s, b, Ml, Mr, Dl, Dr, (const cplx*)L, (const cplx*)R);
+    } else {
+      X = (cplx*)get(sizeof(cplx) * (size_t)Dm * site);
+      Y = (cplx*)get(sizeof(cplx) * (size_t)Dm * site);
+    }
+    auto once = [&] {
+      if (precision == TDMRG_PREC_C64_3XTF32)
+        tdmrg::heff_tc_apply(s, b, W.m.s[0], Ml, Mr, D, d, (const cplx*)A, (cplx*)out);
+      else
+        tdmrg::heff_f64(tdmrg::Ctx{s, X, Y}, W.m.s[0], Ml, Mr, D, d, (const cplx*)L,
+                        (const cplx*)R, (const cplx*)A, (cplx*)out, nullptr);
+    };
+    once();   // warm-up
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, s));
+    for (int r = 0; r < reps; ++r) once();
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int hs = 0;
+    CK(cudaMemcpyAsync(&hs, st, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hs) throw Failure{TDMRG_ERR_TIMEOUT, "tensor-core pipeline wait timed out"};
+    *ms_per_matvec = ms / reps;
+  });
+}
+
+int tdmrg_model_set_concurrent(tdmrg_model* h, int on) {
+  if (!h) return fail(nullptr, TDMRG_ERR_ARG, "NULL handle");
+  return guarded(h, [&] { h->eng->set_concurrent(on != 0); });
+}
+
+int tdmrg_tune_record_shapes(int on) {
+  tdmrg::tc_record_shapes(on != 0);
+  return TDMRG_OK;
+}
+
+int tdmrg_tune_recorded_shapes(int* shapes, int capacity, int* count) {
+  if (!count || capacity < 0 || (capacity > 0 && !shapes))
+    return fail(nullptr, TDMRG_ERR_ARG, "recorded_shapes: bad arguments");
+  const auto v = tdmrg::tc_recorded_shapes();
+  *count = (int)v.size();
+  for (int i = 0; i < (int)v.size() && i < capacity; ++i)
+    for (int j = 0; j < 5; ++j) shapes[5 * i + j] = v[i][j];
+  return TDMRG_OK;
+}
+
+int tdmrg_tune_reload_table(void) {
+  tdmrg::tc_reload_table();
+  return TDMRG_OK;
+}
+
+int tdmrg_kernel_tc_gemm_timed(int M, int N, int K, int nred, int nbatch, int ksplit, int reps,
+                               double* ms_out, void* stream) {
+  if (M < 1 || N < 1 || K < 1 || nred < 1 || nbatch < 1 || ksplit < 0 || reps < 1 || !ms_out)
+    return fail(nullptr, TDMRG_ERR_ARG, "tc_gemm_timed: bad arguments");
+  return guarded(nullptr, [&] {
+    using tdmrg::pad4;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<void*> mem;
+    struct Free {
+      std::vector<void*>& m;
+      ~Free() {
+        for (void* p : m) cudaFree(p);
+      }
+    } fr{mem};
+    auto get = [&](size_t bytes) {
+      void* p = nullptr;
+      CK(cudaMalloc(&p, bytes));
+      mem.push_back(p);
+      return p;
+    };
+    tdmrg::TcOperand A{nullptr, M, K, pad4(K), nred};
+    tdmrg::TcOperand B{nullptr, N, K, pad4(K), nred * nbatch};
+    A.p = (float*)get(sizeof(float) * (size_t)A.floats());
+    B.p = (float*)get(sizeof(float) * (size_t)B.floats());
+    CK(cudaMemsetAsync(A.p, 0, sizeof(float) * (size_t)A.floats(), s));
+    CK(cudaMemsetAsync(B.p, 0, sizeof(float) * (size_t)B.floats(), s));
+    const long long mn = (long long)nbatch * M * N;
+    float* C = (float*)get(sizeof(float) * 2 * (size_t)mn);
+    int* st = (int*)get(sizeof(int));
+    CK(cudaMemsetAsync(st, 0, sizeof(int), s));
+    tdmrg::TcGemm g{};
+    g.M = M; g.N = N; g.K = K; g.nred = nred; g.nbatch = nbatch;
+    g.a_red = nred > 1 ? 1 : 0; g.b_red = nred > 1 ? 1 : 0; g.b_bat = nbatch > 1 ? nred : 0;
+    g.out_mode = 1; g.C = C; g.ldc = N; g.sbc = (long long)M * N; g.plane = mn;
+    g.status = st; g.ksplit = ksplit;
+    g.part_len = 4LL << 20;           // the engine's split-K scratch
+    g.part = (float*)get(sizeof(float) * (size_t)g.part_len);
+    CK(tdmrg::tc_gemm(A, B, g, s));   // warm-up
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, s));
+    for (int r = 0; r < reps; ++r) CK(tdmrg::tc_gemm(A, B, g, s));
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int hs = 0;
+    CK(cudaMemcpyAsync(&hs, st, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hs) throw Failure{TDMRG_ERR_TIMEOUT, "tensor-core pipeline wait timed out"};
+    *ms_out = ms / reps;
   });
 }
 
@@ -964,7 +1171,7 @@ int tdmrg_kernel_bond_exp(int M, int Dw, const void* L, const void* R, const voi
     CK(cudaMalloc(&W.T, sizeof(float2) * (size_t)Dw * n));
     CK(cudaMalloc(&W.P, sizeof(float2) * (size_t)Dw * n));
     CK(cudaMalloc(&W.part, sizeof(tdmrg::cplx) * 2 * (size_t)sms * (tdmrg::KMAX + 1)));
-    CK(cudaMalloc(&W.partn, sizeof(double) * (size_t)sms));
+    CK(cudaMalloc(&W.partn, sizeof(double) * 2 * (size_t)sms));   // 2 * gmax
     CK(cudaMalloc(&W.bar, sizeof(unsigned) * 2));
     CK(cudaMalloc(&W.mv, sizeof(unsigned long long)));
     CK(cudaMalloc(&V, sizeof(tdmrg::cplx) * (size_t)kcap * n));

@@ -8,7 +8,9 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <exception>
 #include <string>
+#include <thread>
 
 #include "../../include/tdmrg.h"
 
@@ -213,10 +215,18 @@ void right_x_tc(cudaStream_t st, const TcBufs& b, int Dr, int Ml2, int D, int Mr
 
 void heff_tc_apply(cudaStream_t st, const TcBufs& b, const DevMpoSite& W, int Ml, int Mr, int D,
                    int d, const cplx* in, cplx* out) {
-  left_x_tc(st, b, W.Dl, Ml, Ml, D, Mr, in);
   TcOperand Yp{b.mix, Ml * D, Mr, pad4(Mr), W.Dr};
-  CK(mix_split(W.lr, Ml, d, Mr, b.x32, (long long)Ml * D * Mr, (long long)W.Dl * Ml * D * Mr, Yp, 0,
-               st));
+  if (heff_left_mix_supported(d, W.Dl, W.lr)) {
+    // L . A with the MPO mixing in the epilogue: the FP32 intermediate stays on chip
+    TcOperand Lp{b.envA, W.Dl * Ml, Ml, pad4(Ml), 1};
+    TcOperand Bt{b.siteA, D * Mr, Ml, pad4(Ml), 1};
+    CK(split_f64_t(in, 0, (long long)D * Mr, 0, Bt, st));
+    CK(heff_left_mix(Lp, Bt, W.lr, Ml, Mr, d, W.Dl, Yp, b.status, st));
+  } else {
+    left_x_tc(st, b, W.Dl, Ml, Ml, D, Mr, in);
+    CK(mix_split(W.lr, Ml, d, Mr, b.x32, (long long)Ml * D * Mr, (long long)W.Dl * Ml * D * Mr, Yp,
+                 0, st));
+  }
   TcOperand Rp{b.envB, Mr, Mr, pad4(Mr), W.Dr};
   TcGemm g{};
   g.M = Ml * D; g.N = Mr; g.K = Mr; g.nred = W.Dr; g.nbatch = 1; g.a_red = 1; g.b_red = 1;
@@ -395,6 +405,7 @@ void Engine::free_mpo(DevMpo& m) {
 // construction / workspace
 // ------------------------------------------------------------------------------------
 Engine::Engine(const ModelParams& p) : P(p) {
+  CK(cudaGetDevice(&dev_));
   sites_ = chain_sites(P);
   rebuild_mpos();
   CK(cudaMalloc(&status_, sizeof(int) * 4));
@@ -454,6 +465,8 @@ Engine::~Engine() {
 }
 
 void Engine::rebuild_mpos() {
+  twin_.reset();     // built from the old parameters; made again at the next realtime_init
+  twin_on_ = false;
   sites_ = chain_sites(P);
   upload_mpo(hamiltonian_mpo(P), H_);
   upload_mpo(current_mpo(P), J_);
@@ -720,7 +733,7 @@ void Engine::ensure_bond_scratch(int maxbond) {
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     bs_.gmax = sms;
     CK(cudaMalloc(&bs_.part, sizeof(cplx) * 2 * (size_t)sms * (KMAX + 1)));
-    CK(cudaMalloc(&bs_.partn, sizeof(double) * (size_t)sms));
+    CK(cudaMalloc(&bs_.partn, sizeof(double) * 2 * (size_t)sms));   // 2 * gmax: lz_step
     CK(cudaMalloc(&bs_.bar, sizeof(unsigned) * 2));
     CK(cudaMalloc(&bs_.mv, sizeof(unsigned long long)));
     CK(cudaMemset(bs_.mv, 0, sizeof(unsigned long long)));
@@ -1037,35 +1050,38 @@ void Engine::tdvp_step(DevMps& s, double tr, double ti) {
   check_status();
 }
 
-void Engine::realtime_step_launch(double dt) {
-  if (!rt_ready_) throw Failure{TDMRG_ERR_STATE, "realtime_step before realtime_init"};
-  if (!graphs_) throw Failure{TDMRG_ERR_STATE, "batched stepping needs graph mode"};
-  const StepGraph& g1 = step_graph(psi1_, 0.0, -dt);
-  CK(cudaGraphLaunch(g1.exec, st_));
-  stats_add(stats, g1.delta);
-  const StepGraph& g2 = step_graph(psi2_, 0.0, -dt);
-  CK(cudaGraphLaunch(g2.exec, st_));
-  stats_add(stats, g2.delta);
-}
+void Engine::sync_and_check() { check_status(); }
 
-void Engine::realtime_half_launch(double dt, int half) {
+Stats Engine::capture_realtime_half(double dt, int half) {
   if (!rt_ready_) throw Failure{TDMRG_ERR_STATE, "realtime half-step before realtime_init"};
   if (!graphs_) throw Failure{TDMRG_ERR_STATE, "batched stepping needs graph mode"};
   if (half != 1 && half != 2) throw Failure{TDMRG_ERR_ARG, "half-step: half must be 1 or 2"};
-  const StepGraph& g1 = step_graph(psi1_, 0.0, -dt, half);
-  CK(cudaGraphLaunch(g1.exec, st_));
-  stats_add(stats, g1.delta);
-  const StepGraph& g2 = step_graph(psi2_, 0.0, -dt, half);
-  CK(cudaGraphLaunch(g2.exec, st_));
-  stats_add(stats, g2.delta);
+  const Stats before = stats;
+  const long long launches0 = launch_count();
+  capturing_ = true;
+  try {
+    tdvp_step_body(psi1_, 0.0, -dt, half);
+    tdvp_step_body(psi2_, 0.0, -dt, half);
+  } catch (...) {
+    capturing_ = false;
+    stats = before;
+    throw;
+  }
+  capturing_ = false;
+  Stats d = stats_diff(stats, before);
+  d.replayed_launches = (double)(launch_count() - launches0);
+  count_launch(-(int)(launch_count() - launches0));
+  stats = before;
+  return d;
 }
 
-void Engine::sync_and_check() { check_status(); }
+void Engine::add_stats(const Stats& d) { stats_add(stats, d); }
 
 void Engine::reset_stats() {
   harvest_qr_events();
   stats = Stats();
   stats.launches_at_reset = (double)launch_count();
+  if (twin_) twin_->reset_stats();
 }
 
 // Imaginary time: the center is multiplied by exp(-tau H_eff / 2) at every site and by
@@ -1298,29 +1314,118 @@ void Engine::thermal_prepare(double beta, double dtau, int M) {
   prepared_ = true;
 }
 
+void Engine::sync_twin_settings() {
+  Engine& t = *twin_;
+  if (t.precision_ != precision_) t.set_precision(precision_);
+  t.ktol_ = ktol_;
+  t.ktol_user_ = true;
+  t.kmax_ = kmax_;
+  t.fixed_k_ = fixed_k_;
+  t.rank_tol_ = rank_tol_;
+  t.rank_tol_user_ = true;
+  t.prof_ = prof_;
+  t.qr_.wait = qr_.wait;
+  t.bs_.wait = bs_.wait;
+}
+
+// the twin's first state becomes a copy of src (an MPS of this engine, complete on src_stream)
+// with its right environments built on the twin's stream
+void Engine::adopt_state(const DevMps& src, cudaStream_t src_stream) {
+  CK(cudaStreamSynchronize(src_stream));
+  if (psi1_.A.size() != src.A.size() || psi1_.Mb != src.Mb) {
+    clear_graphs();
+    free_mps(psi1_);
+    alloc_mps(psi1_, *std::max_element(src.Mb.begin(), src.Mb.end()));
+    if (psi1_.Mb != src.Mb) throw Failure{TDMRG_ERR_STATE, "twin: bond dimensions differ"};
+  }
+  for (int k = 0; k < src.L(); ++k)
+    CK(cudaMemcpyAsync(psi1_.A[k], src.A[k], sizeof(cplx) * (size_t)src.size(k),
+                       cudaMemcpyDeviceToDevice, st_));
+  build_right_envs(psi1_);
+  CK(cudaStreamSynchronize(st_));
+  prepared_ = true;
+  rt_ready_ = true;
+}
+
 void Engine::realtime_init() {
   if (!prepared_) throw Failure{TDMRG_ERR_STATE, "realtime_init before thermal_prepare"};
+  twin_on_ = false;
   copy_mps(psi_b_, psi1_);
   build_right_envs(psi1_);
   fit_apply(J_, psi_b_, psi2_, 2);
   build_right_envs(psi2_);
   CK(cudaStreamSynchronize(st_));
+  if (concurrent_ && !graphs_) {
+    if (!twin_) {
+      twin_.reset(new Engine(P));
+      twin_->concurrent_ = false;
+      cudaStream_t ts = nullptr;
+      CK(cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking));
+      twin_->own_stream_ = ts;
+      twin_->st_ = ts;
+    }
+    sync_twin_settings();
+    twin_->adopt_state(psi2_, st_);
+    twin_on_ = true;
+  }
   rt_ready_ = true;
 }
 
 void Engine::realtime_step(int nsteps, double dt) {
   if (!rt_ready_) throw Failure{TDMRG_ERR_STATE, "realtime_step before realtime_init"};
   if (nsteps < 0 || !(dt > 0.0)) throw Failure{TDMRG_ERR_ARG, "realtime_step: need dt > 0"};
-  for (int i = 0; i < nsteps; ++i) {
-    tdvp_step(psi1_, 0.0, -dt);
-    tdvp_step(psi2_, 0.0, -dt);
+  if (!twin_on_) {
+    for (int i = 0; i < nsteps; ++i) {
+      tdvp_step(psi1_, 0.0, -dt);
+      tdvp_step(psi2_, 0.0, -dt);
+    }
+    return;
   }
+  // two lanes: cooperative grids capped to half of the SMs so that both co-reside
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_));
+  const int cap = std::max(8, sms / 2);
+  const int cap0 = qr_gcap_, tcap0 = twin_->qr_gcap_;
+  qr_gcap_ = cap;
+  twin_->qr_gcap_ = cap;
+  sync_twin_settings();
+  std::exception_ptr err;
+  Engine* tw = twin_.get();
+  const int dev = dev_;
+  try {
+    for (int i = 0; i < nsteps; ++i) {
+      std::thread lane([tw, dev, dt, &err] {
+        try {
+          CK(cudaSetDevice(dev));
+          tw->tdvp_step(tw->psi1_, 0.0, -dt);
+        } catch (...) {
+          err = std::current_exception();
+        }
+      });
+      try {
+        tdvp_step(psi1_, 0.0, -dt);
+      } catch (...) {
+        lane.join();
+        throw;
+      }
+      lane.join();
+      if (err) std::rethrow_exception(err);
+    }
+  } catch (...) {
+    qr_gcap_ = cap0;
+    twin_->qr_gcap_ = tcap0;
+    throw;
+  }
+  qr_gcap_ = cap0;
+  twin_->qr_gcap_ = tcap0;
 }
 
 void Engine::realtime_observe(double* C, double* obs) {
   if (!rt_ready_) throw Failure{TDMRG_ERR_STATE, "realtime_observe before realtime_init"};
+  // the twin's steps ended with a synchronisation of its stream: its state is complete
+  const DevMps& second = twin_on_ ? twin_->psi1_ : psi2_;
   const double t0 = tic();
-  const Cx c = overlap(psi1_, J_, psi2_);
+  const Cx c = overlap(psi1_, J_, second);
   toc(stats.t_observe, t0);
   if (!std::isfinite(c.real()) || !std::isfinite(c.imag()))
     throw Failure{TDMRG_ERR_NONFINITE, "non-finite C(t)"};
@@ -1328,9 +1433,37 @@ void Engine::realtime_observe(double* C, double* obs) {
   C[1] = c.imag();
   if (obs) {
     obs[0] = overlap(psi1_, I_, psi1_).real();
-    obs[1] = overlap(psi2_, I_, psi2_).real();
+    obs[1] = overlap(second, I_, second).real();
     obs[2] = overlap(psi1_, H_, psi1_).real();
   }
+}
+
+Stats Engine::total_stats() const {
+  Stats s = stats;
+  if (twin_) {
+    const Stats& t = twin_->stats;
+    s.site_updates += t.site_updates;
+    s.matvecs += t.matvecs;
+    s.heff_flops += t.heff_flops;
+    s.krylov_vectors += t.krylov_vectors;
+    s.bond_matvecs += t.bond_matvecs;
+    s.qrs += t.qrs;
+    s.completions += t.completions;
+    s.env_updates += t.env_updates;
+    s.heff_ms += t.heff_ms;
+    s.qr_ms += t.qr_ms;
+    s.qr_flops += t.qr_flops;
+    s.lz_ms += t.lz_ms;
+    s.t_site += t.t_site;
+    s.t_qr += t.t_qr;
+    s.t_env += t.t_env;
+    s.t_bond += t.t_bond;
+    s.t_absorb += t.t_absorb;
+    s.h2d_bytes += t.h2d_bytes;
+    s.d2h_bytes += t.d2h_bytes;
+    s.replayed_launches += t.replayed_launches;
+  }
+  return s;
 }
 
 

@@ -1,5 +1,6 @@
 // TDVP engine: device MPS/MPO storage and the one-site projector-splitting sweep.
 #pragma once
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -152,13 +153,21 @@ class Engine {
   // once into a CUDA graph and replayed.  qr_cap > 0 caps the QR grid (batched instances).
   void set_graphs(bool on, int qr_cap = 0);
   bool graphs() const { return graphs_; }
-  // launch both real-time graphs of one step without waiting (batched use)
-  void realtime_step_launch(double dt);
-  // launch both real-time graphs of one half-step without waiting: half 1 is the left-to-right
-  // half-sweep of the second-order step, half 2 the right-to-left one (batched use)
-  void realtime_half_launch(double dt, int half);
   void sync_and_check();
+  // Records one half-step (half 1: left-to-right, 2: right-to-left) of both real-time states
+  // into the stream capture the caller has started and joined this engine's stream to (one
+  // graph over several instances); returns the counters one replay adds.  Graph mode only.
+  Stats capture_realtime_half(double dt, int half);
+  void add_stats(const Stats& d);
   void reset_stats();   // reads pending QR timings first, then zeroes the counters
+  // Real-time propagation of the two states side by side: j Psi_b is stepped by a twin engine
+  // (own workspaces, stream and host thread) while this engine steps Psi_b; cooperative grids
+  // of both are capped to half of the SMs meanwhile so that the two lanes co-reside.  Off in
+  // graph mode (batched instances already run side by side).  On by default.
+  void set_concurrent(bool on) { concurrent_ = on; }
+  bool concurrent() const { return concurrent_; }
+  // counters of this engine plus those of its twin
+  Stats total_stats() const;
   void set_profiling(bool on) { prof_ = on; }
   // limit of every bounded grid-barrier wait in clock cycles (0: the default, ~2 s); lowering
   // it makes the barriers give up, which is how the timeout path is tested
@@ -300,6 +309,12 @@ class Engine {
   const StepGraph& step_graph(DevMps& s, double tr, double ti, int half = 0);
   int kmax_ = 32, fixed_k_ = 0;
   bool adjoint_basis_ = false;
+  bool concurrent_ = true;
+  int dev_ = 0;
+  std::unique_ptr<Engine> twin_;     // steps the second real-time state when concurrent
+  bool twin_on_ = false;             // the twin holds the current second state
+  void sync_twin_settings();
+  void adopt_state(const DevMps& src, cudaStream_t src_stream);
   bool prepared_ = false, rt_ready_ = false;
   double logZ_ = 0.0;
   std::vector<SiteInfo> sites_;

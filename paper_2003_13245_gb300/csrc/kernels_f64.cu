@@ -4,13 +4,14 @@
 // gauge QR (completion pass and kernel-level entry points).
 #include "tdmrg_internal.cuh"
 
+#include <atomic>
 #include <cooperative_groups.h>
 #include <cmath>
 
 namespace tdmrg {
 
-static long long g_launches = 0;
-long long launch_count() { return g_launches; }
+static std::atomic<long long> g_launches{0};
+long long launch_count() { return g_launches.load(); }
 void count_launch(int n) { g_launches += n; }
 
 __device__ __forceinline__ cplx cmul(cplx a, cplx b) {
@@ -1004,6 +1005,77 @@ __global__ void __launch_bounds__(256) dfma_loop_kernel(long long iters, double 
 cudaError_t dfma_loop(int blocks, long long iters, double* sink, cudaStream_t s) {
   count_launch();
   dfma_loop_kernel<<<blocks, 256, 0, s>>>(iters, 0.999999, 1e-6, sink);
+  return cudaGetLastError();
+}
+
+
+// Parameter cotangent of a site operator H_eff(L, W, R) between a and b:
+//   G[w][v][s][u] += k * sum_{x,t,c} U[w][x][u][t][c] V[v][x][s][t][c],
+//   U[w][x][u][t][c] = sum_y L[w,x,y] b[y,u,t,c],  V[v][x][s][t][c] = sum_b' conj(a[x,s,t,b']) R[v,b',c],
+// so that <a, H_eff(L, dW, R) b> = sum dW[w,v,s,u] G[w,v,s,u].  One block per (w, v, s), the
+// threads striding over (x, t, c) with c fastest (coalesced), d accumulators per thread, a
+// fixed-order block reduction and one writer per entry.
+constexpr int GRAM_MAX_D = 16;
+__global__ void __launch_bounds__(256) param_gram_kernel(int Dl, int Dr, int Ml, int d, int Mr,
+                                                         const cplx* U, const cplx* V, cplx k,
+                                                         cplx* G) {
+  __shared__ double red[2 * GRAM_MAX_D][8];
+  const int s = blockIdx.x % d;
+  const int v = (blockIdx.x / d) % Dr;
+  const int w = blockIdx.x / (d * Dr);
+  const long long D = (long long)d * d;
+  const long long K = (long long)Ml * d * Mr;
+  double ar[GRAM_MAX_D], ai[GRAM_MAX_D];
+#pragma unroll
+  for (int u = 0; u < GRAM_MAX_D; ++u) ar[u] = ai[u] = 0.0;
+  for (long long e = threadIdx.x; e < K; e += blockDim.x) {
+    const long long x = e / ((long long)d * Mr);
+    const int t = (int)((e / Mr) % d);
+    const int c = (int)(e % Mr);
+    const cplx vv = V[(((long long)v * Ml + x) * D + (long long)s * d + t) * Mr + c];
+    const cplx* up = U + (((long long)w * Ml + x) * D + t) * Mr + c;
+#pragma unroll
+    for (int u = 0; u < GRAM_MAX_D; ++u) {
+      if (u < d) {
+        const cplx uu = up[(long long)u * d * Mr];
+        ar[u] = fma(uu.x, vv.x, fma(-uu.y, vv.y, ar[u]));
+        ai[u] = fma(uu.x, vv.y, fma(uu.y, vv.x, ai[u]));
+      }
+    }
+  }
+  const int lane = threadIdx.x & 31, wv = threadIdx.x >> 5;
+#pragma unroll
+  for (int u = 0; u < GRAM_MAX_D; ++u) {
+    if (u < d) {
+      double x = ar[u], y = ai[u];
+      for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_xor_sync(0xffffffffu, x, o);
+        y += __shfl_xor_sync(0xffffffffu, y, o);
+      }
+      if (lane == 0) {
+        red[2 * u][wv] = x;
+        red[2 * u + 1][wv] = y;
+      }
+    }
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < d) {
+    const int u = threadIdx.x;
+    double x = 0.0, y = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+      x += red[2 * u][q];
+      y += red[2 * u + 1][q];
+    }
+    cplx& g = G[(((long long)w * Dr + v) * d + s) * d + u];
+    g = make_double2(g.x + k.x * x - k.y * y, g.y + k.x * y + k.y * x);
+  }
+}
+
+cudaError_t param_gram(int Dl, int Dr, int Ml, int d, int Mr, const cplx* U, const cplx* V,
+                       cplx k, cplx* G, cudaStream_t s) {
+  if (d > GRAM_MAX_D || d < 1) return cudaErrorInvalidValue;
+  count_launch();
+  param_gram_kernel<<<Dl * Dr * d, 256, 0, s>>>(Dl, Dr, Ml, d, Mr, U, V, k, G);
   return cudaGetLastError();
 }
 

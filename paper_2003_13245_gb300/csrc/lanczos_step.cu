@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(LT) lz_step_kernel(LzStepArgs A) {
   __shared__ double red[8 * (LT / 32)];
   __shared__ double alpha[KMAX], beta[KMAX + 1];
   __shared__ double s_nrm, s_inv;
-  __shared__ int s_done;
+  __shared__ int s_done, s_second;
   const long long n = A.n;
   const int j = A.j;
   const long long e0 = (long long)blockIdx.x * A.S;
@@ -53,13 +53,30 @@ __global__ void __launch_bounds__(LT) lz_step_kernel(LzStepArgs A) {
 
   const int lo = j > 0 ? j - 1 : 0;
   lzc::slice_dots_block(A.V, n, w, e0, len, lo, j + 1, part1, red);
+  lzc::slice_norm(w, len, red, A.partn + A.G);      // ||w||^2 before the projection
   if (!lzc::barrier(A.bar, A.G, epoch, A.status, A.wait)) return;
   lzc::reduce_dots(part1, A.G, lo, j + 1, h1);
+  lzc::reduce_norm(A.partn + A.G, A.G, &s_nrm);
   lzc::slice_project(A.V, n, w, e0, len, lo, j + 1, h1);
-  lzc::slice_dots_block(A.V, n, w, e0, len, 0, j + 1, part2, red);
-  if (!lzc::barrier(A.bar, A.G, epoch, A.status, A.wait)) return;
-  lzc::reduce_dots(part2, A.G, 0, j + 1, h2);
-  lzc::slice_project(A.V, n, w, e0, len, 0, j + 1, h2);
+  // Re-orthogonalisation against every Krylov vector only when the three-term projection
+  // removed more than half of ||w||^2 (the criterion of Daniel, Gragg, Kaufman and Stewart):
+  // without such cancellation w stays orthogonal to the basis to rounding.  The decision is
+  // taken from grid-wide reduced values, so every CTA takes the same branch.
+  if (threadIdx.x == 0) {
+    double rem = s_nrm;
+    for (int i = lo; i <= j; ++i) rem -= h1[i].x * h1[i].x + h1[i].y * h1[i].y;
+    s_second = (rem < 0.5 * s_nrm) ? 1 : 0;
+  }
+  __syncthreads();
+  if (s_second) {
+    lzc::slice_dots_block(A.V, n, w, e0, len, 0, j + 1, part2, red);
+    if (!lzc::barrier(A.bar, A.G, epoch, A.status, A.wait)) return;
+    lzc::reduce_dots(part2, A.G, 0, j + 1, h2);
+    lzc::slice_project(A.V, n, w, e0, len, 0, j + 1, h2);
+  } else {
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) h2[i] = make_double2(0.0, 0.0);
+    __syncthreads();
+  }
   lzc::slice_norm(w, len, red, A.partn);
   if (!lzc::barrier(A.bar, A.G, epoch, A.status, A.wait)) return;
   lzc::reduce_norm(A.partn, A.G, &s_nrm);

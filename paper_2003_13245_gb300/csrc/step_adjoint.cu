@@ -528,6 +528,7 @@ void Engine::step_vjp(int M, const cplx* const* A_in, double tr, double ti,
   // exponential VJPs: the entry points (fresh Lanczos exponentials at every node) or the
   // Krylov-basis quadrature on this engine (node vectors from the bases of v and vbar)
   cplx *Aq = nullptr, *Bq = nullptr, *basis = nullptr, *tq = nullptr, *El = nullptr;
+  cplx* Gacc = nullptr;      // parameter cotangent of one site operator, Dl x Dr x d x d
   std::vector<std::vector<DevMpo>> dWdev;
   struct FreeDev {
     std::vector<std::vector<DevMpo>>& m;
@@ -542,6 +543,7 @@ void Engine::step_vjp(int M, const cplx* const* A_in, double tr, double ti,
     basis = tp.get((long long)KMAX * maxsite);
     tq = tp.get(maxsite);
     El = tp.get(maxenv);
+    Gacc = tp.get((long long)Dmax * Dmax * 256);
     dWdev.assign(L, std::vector<DevMpo>(np));
     for (int k = 0; k < L; ++k)
       for (int p = 0; p < np; ++p) {
@@ -567,6 +569,9 @@ void Engine::step_vjp(int M, const cplx* const* A_in, double tr, double ti,
     CK(cudaMemsetAsync(Lbar, 0, sizeof(cplx) * (size_t)nL[k], st_));
     CK(cudaMemsetAsync(Rbar, 0, sizeof(cplx) * (size_t)nR[k], st_));
     for (int p = 0; p < np; ++p) tht[p] = 0.0;
+    const int gsz = W.Dl * W.Dr * D[k];
+    const bool gram = np > 0 && dd[k] <= 16;
+    if (gram) CK(cudaMemsetAsync(Gacc, 0, sizeof(cplx) * (size_t)gsz, st_));
     for (int q = 0; q < nodes; ++q) {
       const cplx* a = Aq + (size_t)q * n[k];
       const cplx* b = Bq + (size_t)q * n[k];
@@ -577,10 +582,33 @@ void Engine::step_vjp(int M, const cplx* const* A_in, double tr, double ti,
       CK(zaxpy(nL[k], kcc, El, Lbar, st_));
       env_left_f64(c, W, Ml, Mr, Ml, Mr, D[k], dd[k], Le, a, b, El);
       CK(zaxpy(nR[k], kcc, El, Rbar, st_));
+      if (gram) {
+        // theta_p = Re sum_q k_q <a_q, H_eff(dW_p) b_q> = Re sum dW_p . G, G accumulated over
+        // the nodes: U = L b_q, V = conj(a_q) R, then one contraction over (x, t, c)
+        CK(zgemm(W.Dl * Ml, D[k] * Mr, Ml, 1, 1, kOne, mr(Le, Ml, 1), mr(b, (long long)D[k] * Mr, 1),
+                 kZero, X_, (long long)D[k] * Mr, 0, nullptr, st_));
+        CK(zgemm(Ml * D[k], Mr, Mr, W.Dr, 1, kOne, mr(a, Mr, 1, 1),
+                 mrb(Re, Mr, 1, (long long)Mr * Mr), kZero, Y_, Mr, (long long)Ml * D[k] * Mr,
+                 nullptr, st_));
+        CK(param_gram(W.Dl, W.Dr, Ml, dd[k], Mr, X_, Y_, kcc, Gacc, st_));
+      } else {
+        for (int p = 0; p < np; ++p) {
+          if (dWdev[k][p].s.empty()) continue;
+          heff_f64(c, dWdev[k][p].s[0], Ml, Mr, D[k], dd[k], Le, Re, b, tq, nullptr);
+          tht[p] += (kc * dot(a, tq, n[k], part, st_)).real();
+        }
+      }
+    }
+    if (gram) {
+      std::vector<cplx> gh(gsz);
+      CK(cudaMemcpyAsync(gh.data(), Gacc, sizeof(cplx) * (size_t)gsz, cudaMemcpyDeviceToHost,
+                         st_));
+      CK(cudaStreamSynchronize(st_));
       for (int p = 0; p < np; ++p) {
-        if (dWdev[k][p].s.empty()) continue;
-        heff_f64(c, dWdev[k][p].s[0], Ml, Mr, D[k], dd[k], Le, Re, b, tq, nullptr);
-        tht[p] += (kc * dot(a, tq, n[k], part, st_)).real();
+        const double* dw = dWd[k].data() + 2 * (size_t)gsz * p;
+        double acc = 0.0;
+        for (int e = 0; e < gsz; ++e) acc += dw[2 * e] * gh[e].x - dw[2 * e + 1] * gh[e].y;
+        tht[p] = acc;
       }
     }
     CK(zconj(nL[k], Lbar, st_));

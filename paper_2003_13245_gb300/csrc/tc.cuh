@@ -1,5 +1,8 @@
 // Tensor-core contraction interface (3xTF32 split complex operands, tcgen05).
 #pragma once
+#include <array>
+#include <vector>
+
 #include "tdmrg_internal.cuh"
 
 namespace tdmrg {
@@ -32,10 +35,17 @@ struct TcGemm {
   // is split over CTAs into partial sums that a second kernel adds up
   float* part;
   long long part_len;
-  int ksplit;          // set by tc_gemm
+  int ksplit;          // 0: tuned table / occupancy rule; > 0: forced (tc_gemm sets the one used)
 };
 
+// g.ksplit on input: 0 = the tuned table's split for the shape (else the occupancy rule),
+// > 0 = that split (capped by the K loop and the scratch)
 cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, const TcGemm& g, cudaStream_t s);
+// shapes (M, N, K, nred, nbatch) seen by tc_gemm while recording is on
+void tc_record_shapes(bool on);
+std::vector<std::array<int, 5>> tc_recorded_shapes();
+// forget the loaded split-K table (read again at the next tc_gemm)
+void tc_reload_table();
 // dst(b, row, k) = conj?(src[b*sb + row*rs + k*ks])
 cudaError_t split_f64(const cplx* src, long long sb, long long rs, long long ks, int conj,
                       const TcOperand& dst, cudaStream_t s);
@@ -47,5 +57,12 @@ cudaError_t split_f64_t(const cplx* src, long long sb, long long kstride, int co
 cudaError_t mix_split(const MixTable& T, int Ma, int d, int Mb, const float* X, long long xs,
                       long long xplane, const TcOperand& dst, int trans, cudaStream_t s);
 cudaError_t planes_to_f64(const TcOperand& P, cplx* out, cudaStream_t s);
+// First contraction of H_eff fused with the MPO mixing: Yp (split planes, rows (a, s, t),
+// K = c, nb = T.Dout) = mix_T(L . A) with L as Lp (rows (w, a), K = Ml) and A^T as Bt (rows
+// (u, t, c), K = Ml).  Supported for 2 <= d <= 10 and Dl <= 8 (heff_left_mix_supported).
+bool heff_left_mix_supported(int d, int Dl, const MixTable& T);
+cudaError_t heff_left_mix(const TcOperand& Lp, const TcOperand& Bt, const MixTable& T, int Ml,
+                          int Mr, int d, int Dl, const TcOperand& Yp, int* status,
+                          cudaStream_t s);
 
 }  // namespace tdmrg

@@ -87,7 +87,7 @@ struct BondScratch {
   float2* T = nullptr;               // maxDw * maxn
   float2* P = nullptr;               // maxDw * maxn
   cplx* part = nullptr;              // 2 * gmax * (KMAX + 1)
-  double* partn = nullptr;           // gmax
+  double* partn = nullptr;           // 2 * gmax (lz_step: the norms before and after)
   unsigned* bar = nullptr;           // 2 (barrier counter, generation)
   unsigned long long* mv = nullptr;  // Krylov vectors used, accumulated over launches
   long long maxn = 0;
@@ -150,6 +150,10 @@ cudaError_t dfma_loop(int blocks, long long iters, double* sink, cudaStream_t s)
 // V[P], kT[P] -> mu[P]); K <= 64 (fgr.cu)
 cudaError_t fgr_mobility(int P, int K, const double* omega, const double* g, const double* V,
                          const double* kT, double dt, int nt, double* mu, cudaStream_t s);
+// G[w][v][s][u] += k sum_{x,t,c} U[w][x][u][t][c] V[v][x][s][t][c] (Dl x Dr x d x d, d <= 16):
+// the parameter cotangent of a site operator from U = L b and V = conj(a) R (kernels_f64.cu)
+cudaError_t param_gram(int Dl, int Dr, int Ml, int d, int Mr, const cplx* U, const cplx* V,
+                       cplx k, cplx* G, cudaStream_t s);
 // *out = trace of the M x M matrix E (one launch)
 cudaError_t ztrace(const cplx* E, int M, cplx* out, cudaStream_t s);
 // x <- conj(x)

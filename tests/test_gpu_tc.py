@@ -65,3 +65,49 @@ def test_heff_tc_matches_oracle(Ml, Mr, d, Dl, Dr):
     got = out.cpu().numpy().reshape(ref.shape)
     err = np.abs(got - ref).max() / np.abs(ref).max()
     assert err < TOL, err
+
+
+@pytest.mark.parametrize("ksplit", [1, 3, 8])
+def test_splitk_table_is_applied_and_exact(ksplit, tmp_path, monkeypatch):
+    """A split-K table entry for a contraction shape changes only the summation order: with the
+    split forced through a table file, C = A B^T still matches FP64 to the 3xTF32 bound, and
+    the timed entry point runs that shape at every candidate split."""
+    from paper_2003_13245_gb300 import binding
+    M, N, K = 128, 64, 4096
+    table = tmp_path / "table.txt"
+    table.write_text("# test\n%d %d %d 1 1 %d\n" % (M, N, K, ksplit))
+    monkeypatch.setenv("TDMRG_SPLITK_TABLE", str(table))
+    binding.tune_reload_table()
+    try:
+        rng = np.random.default_rng(77 + ksplit)
+        A = random_complex(rng, (M, K))
+        B = random_complex(rng, (N, K))
+        C = torch.zeros((M, N), dtype=torch.complex128, device="cuda")
+        binding.kernel_zgemm_tc(dev(A), dev(B), C, 0, 0)
+        ref = A @ B.T
+        assert np.abs(C.cpu().numpy() - ref).max() / np.abs(ref).max() < TOL
+        assert binding.kernel_tc_gemm_timed(M, N, K, 1, 1, ksplit, reps=2) > 0.0
+    finally:
+        monkeypatch.delenv("TDMRG_SPLITK_TABLE")
+        binding.tune_reload_table()
+
+
+@pytest.mark.parametrize("Ml,Mr,d,Dl,Dr", HEFF_CASES + [(128, 128, 6, 7, 7), (50, 130, 10, 8, 3)])
+def test_sweep_heff_path_matches_oracle(Ml, Mr, d, Dl, Dr):
+    """The H_eff product as the sweep runs it (tdmrg_kernel_heff_timed: the first contraction
+    fused with the MPO mixing in its epilogue for 2 <= d <= 10 and Dl <= 8, then the
+    contraction with R) against the oracle, 3xTF32 bound; ragged row and column tiles."""
+    from oracle import tdvp
+    from paper_2003_13245_gb300 import binding
+    rng = np.random.default_rng(3000 + Ml + Mr + d)
+    L = random_complex(rng, (Dl, Ml, Ml))
+    R = random_complex(rng, (Dr, Mr, Mr))
+    W = random_mpo_site(rng, Dl, Dr, d)
+    A = random_complex(rng, (Ml, d * d, Mr))
+    ref = tdvp.heff(L, W, R, A, d)
+    out = torch.zeros((Ml, d * d, Mr), dtype=torch.complex128, device="cuda")
+    ms = binding.kernel_heff_timed(dev(L), W, dev(R), dev(A), out, d, binding.PREC_C64_3XTF32,
+                                   reps=1)
+    assert ms > 0.0
+    err = np.abs(out.cpu().numpy() - ref).max() / np.abs(ref).max()
+    assert err < TOL, err

@@ -307,8 +307,9 @@ int tdmrg_get_logz(const tdmrg_model* h, double* logz);
  * [17] C(t) overlaps; [18] event-timed milliseconds of the gauge QRs run outside graph
  * captures and [19] their algorithmic FP64 flops (one Gram-Schmidt pass, 8 m n^2 per QR of an
  * m x n matrix), [20] event-timed milliseconds of the Lanczos orthogonalisation steps of the
- * host-driven Krylov exponentials (site updates; also bond steps of the FP64 path).
- * n = entries wanted (<= 21). */
+ * host-driven Krylov exponentials (site updates; also bond steps of the FP64 path), [21] event-timed
+ * milliseconds, [22] algorithmic flops and [23] number of the gauge QRs with m >= 4096 rows.
+ * n = entries wanted (<= 24). */
 int tdmrg_get_stats(const tdmrg_model* h, double* stats, int n);
 int tdmrg_reset_stats(tdmrg_model* h);
 

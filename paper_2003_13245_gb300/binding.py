@@ -223,12 +223,12 @@ class Model:
         return (out[0::2] + 1j * out[1::2]).reshape(N, N)
 
     def stats(self):
-        s = np.zeros(21)
-        _check(self._lib.tdmrg_get_stats(self._h, _dptr(s), 21), self._h)
+        s = np.zeros(24)
+        _check(self._lib.tdmrg_get_stats(self._h, _dptr(s), 24), self._h)
         keys = ["site_updates", "matvecs", "heff_flops", "krylov_vectors", "bond_matvecs", "qrs",
                 "completions", "env_updates", "heff_ms", "h2d_bytes", "d2h_bytes", "launches",
                 "t_site", "t_qr", "t_env", "t_bond", "t_absorb", "t_observe", "qr_ms",
-                "qr_flops", "lz_ms"]
+                "qr_flops", "lz_ms", "qr_bulk_ms", "qr_bulk_flops", "qr_bulk_n"]
         return dict(zip(keys, s.tolist()))
 
     def set_rank_tol(self, tol):

@@ -709,13 +709,13 @@ int tdmrg_get_logz(const tdmrg_model* h, double* logz) {
 int tdmrg_get_stats(const tdmrg_model* h, double* stats, int n) {
   if (!h || !stats || n < 0) return fail(nullptr, TDMRG_ERR_ARG, "NULL argument");
   const tdmrg::Stats s = h->eng->total_stats();
-  const double v[21] = {s.site_updates, s.matvecs, s.heff_flops, s.krylov_vectors,
+  const double v[24] = {s.site_updates, s.matvecs, s.heff_flops, s.krylov_vectors,
                         s.bond_matvecs, s.qrs, s.completions, s.env_updates, s.heff_ms,
                         s.h2d_bytes, s.d2h_bytes,
                         (double)tdmrg::launch_count() - s.launches_at_reset + s.replayed_launches,
                         s.t_site, s.t_qr, s.t_env, s.t_bond, s.t_absorb, s.t_observe,
-                        s.qr_ms, s.qr_flops, s.lz_ms};
-  for (int i = 0; i < n && i < 21; ++i) stats[i] = v[i];
+                        s.qr_ms, s.qr_flops, s.lz_ms, s.qr_bulk_ms, s.qr_bulk_flops, s.qr_bulk_n};
+  for (int i = 0; i < n && i < 24; ++i) stats[i] = v[i];
   return TDMRG_OK;
 }
 

@@ -215,18 +215,10 @@ void right_x_tc(cudaStream_t st, const TcBufs& b, int Dr, int Ml2, int D, int Mr
 
 void heff_tc_apply(cudaStream_t st, const TcBufs& b, const DevMpoSite& W, int Ml, int Mr, int D,
                    int d, const cplx* in, cplx* out) {
+  left_x_tc(st, b, W.Dl, Ml, Ml, D, Mr, in);
   TcOperand Yp{b.mix, Ml * D, Mr, pad4(Mr), W.Dr};
-  if (heff_left_mix_supported(d, W.Dl, W.lr)) {
-    // L . A with the MPO mixing in the epilogue: the FP32 intermediate stays on chip
-    TcOperand Lp{b.envA, W.Dl * Ml, Ml, pad4(Ml), 1};
-    TcOperand Bt{b.siteA, D * Mr, Ml, pad4(Ml), 1};
-    CK(split_f64_t(in, 0, (long long)D * Mr, 0, Bt, st));
-    CK(heff_left_mix(Lp, Bt, W.lr, Ml, Mr, d, W.Dl, Yp, b.status, st));
-  } else {
-    left_x_tc(st, b, W.Dl, Ml, Ml, D, Mr, in);
-    CK(mix_split(W.lr, Ml, d, Mr, b.x32, (long long)Ml * D * Mr, (long long)W.Dl * Ml * D * Mr, Yp,
-                 0, st));
-  }
+  CK(mix_split(W.lr, Ml, d, Mr, b.x32, (long long)Ml * D * Mr, (long long)W.Dl * Ml * D * Mr, Yp, 0,
+               st));
   TcOperand Rp{b.envB, Mr, Mr, pad4(Mr), W.Dr};
   TcGemm g{};
   g.M = Ml * D; g.N = Mr; g.K = Mr; g.nred = W.Dr; g.nbatch = 1; g.a_red = 1; g.b_red = 1;
@@ -798,8 +790,13 @@ void Engine::gauge_qr_dev(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cplx* 
                       qr_gcap_, rank_tol_, src));
   if (timed) {
     CK(cudaEventRecord(qr_ev_[2 * qr_ev_n_ + 1], st_));
+    qr_ev_bulk_[qr_ev_n_] = m >= 4096 ? 1 : 0;
     ++qr_ev_n_;
     stats.qr_flops += 8.0 * m * (double)n * n;   // one Gram-Schmidt pass
+    if (m >= 4096) {
+      stats.qr_bulk_flops += 8.0 * m * (double)n * n;
+      stats.qr_bulk_n += 1;
+    }
   }
   toc(stats.t_qr, t0);
   stats.qrs += 1;
@@ -813,6 +810,7 @@ void Engine::harvest_qr_events() {
       float ms = 0.f;
       CK(cudaEventElapsedTime(&ms, qr_ev_[2 * i], qr_ev_[2 * i + 1]));
       stats.qr_ms += ms;
+      if (qr_ev_bulk_[i]) stats.qr_bulk_ms += ms;
     }
     qr_ev_n_ = 0;
   }
@@ -993,6 +991,16 @@ void Engine::set_graphs(bool on, int qr_cap) {
   if (on && fixed_k_ <= 0)
     throw Failure{TDMRG_ERR_ARG, "graph mode needs a fixed Krylov dimension (set_krylov fixed_k)"};
   clear_graphs();
+  if (on && twin_on_) {
+    // graph mode steps both states on this engine: take the second state back from the twin
+    CK(cudaStreamSynchronize(twin_->st_));
+    for (int k = 0; k < psi2_.L(); ++k)
+      CK(cudaMemcpyAsync(psi2_.A[k], twin_->psi1_.A[k], sizeof(cplx) * (size_t)psi2_.size(k),
+                         cudaMemcpyDeviceToDevice, st_));
+    build_right_envs(psi2_);
+    CK(cudaStreamSynchronize(st_));
+    twin_on_ = false;
+  }
   graphs_ = on;
   qr_gcap_ = qr_cap;
   if (on && st_ == 0) {
@@ -1453,6 +1461,9 @@ Stats Engine::total_stats() const {
     s.heff_ms += t.heff_ms;
     s.qr_ms += t.qr_ms;
     s.qr_flops += t.qr_flops;
+    s.qr_bulk_ms += t.qr_bulk_ms;
+    s.qr_bulk_flops += t.qr_bulk_flops;
+    s.qr_bulk_n += t.qr_bulk_n;
     s.lz_ms += t.lz_ms;
     s.t_site += t.t_site;
     s.t_qr += t.t_qr;

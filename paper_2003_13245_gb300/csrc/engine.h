@@ -123,6 +123,7 @@ struct Stats {
          qrs = 0, completions = 0, env_updates = 0;
   double heff_ms = 0;                 // event-timed duration of the site H_eff matvecs
   double qr_ms = 0, qr_flops = 0;     // event-timed gauge QRs and their algorithmic flops
+  double qr_bulk_ms = 0, qr_bulk_flops = 0, qr_bulk_n = 0;   // the same for QRs of m >= 4096
   double lz_ms = 0;                   // event-timed Lanczos orthogonalisation steps
   // host wall time per phase (filled only when profiling is on; the phase ends synchronise)
   double t_site = 0, t_qr = 0, t_env = 0, t_bond = 0, t_absorb = 0, t_observe = 0;
@@ -342,6 +343,7 @@ class Engine {
   static constexpr int QR_EV = 256;   // gauge-QR event pairs held before they are read
   cudaEvent_t qr_ev_[2 * QR_EV] = {};
   int qr_ev_n_ = 0;
+  unsigned char qr_ev_bulk_[QR_EV] = {};   // the QR of event pair i has m >= 4096
   cudaEvent_t lz_ev_[2 * QR_EV] = {};
   int lz_ev_n_ = 0;
   TcBufs tcb_{};

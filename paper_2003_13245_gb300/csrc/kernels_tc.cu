@@ -506,217 +506,6 @@ __global__ void planes_to_f64_kernel(const float* P, int nb, int rows, int K, in
 }
 
 // ---------------------------------------------------------------------------------------
-// First contraction of H_eff fused with the MPO mixing (mixed path):
-//   X_w[a][(u, q)] = sum_y L[w][a][y] A[y][(u, q)]          q = t * Mr + c (tcgen05, FP32)
-//   Y[v][(a, s, t)][c] = sum_{blocks w -> v} sum_u op[s][u] X_w[a][(u, q)]
-// written straight into the four split planes of the second contraction's A operand, so the
-// FP32 intermediate X never goes through memory.  A CTA owns 128 rows a and, for FQ(d) = 32 / d
-// consecutive q, all d levels u: its MMA tile is 128 x 32 with one TMEM accumulator pair per
-// MPO channel w (Dl <= 8: 64 columns each).  The pipeline runs over (k tile, w); B (the site
-// tile, 16 KB) is loaded with every A tile (64 KB of L_w) so that a stage is self-contained.
-// The epilogue reads each accumulator back per output channel v and applies the channel's
-// sparse d x d operators from shared memory (zero entries skipped).
-// ---------------------------------------------------------------------------------------
-constexpr int FN = 32;                                   // MMA N of the fused tile
-constexpr int F_B_PLANE = FN * BK * 4;                   // 4 KB: one plane of the B tile
-constexpr int F_STAGE = 4 * A_TILE + 4 * F_B_PLANE;      // 80 KB
-constexpr int F_NST = 2;
-constexpr int F_MAX_DL = 8;
-constexpr size_t F_SMEM_BYTES = F_NST * F_STAGE + 1024 + 256 +
-                                MIX_MAX_OPS * sizeof(float2) + 2 * (MIX_MAX_BLK + 1) * sizeof(int);
-
-__host__ __device__ constexpr uint32_t idesc_n(int negA, int n) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)negA << 13) | ((uint32_t)(n >> 3) << 17) |
-         ((uint32_t)(BM >> 4) << 24);
-}
-
-struct FusedArgs {
-  int Ml, Mr, d, Dl, Dout, nblk;
-  const int* start;       // Dout + 1
-  const int* chan;        // nblk
-  const float2* ops;      // nblk * d * d
-  float* Y;               // split planes [4][Dout][Ml * d * d][ld]
-  int ld;
-  long long plane;
-  int* status;
-};
-
-template <int D>
-__global__ void __launch_bounds__(128, 1)
-    heff_left_mix_kernel(const __grid_constant__ CUtensorMap tmL,
-                         const __grid_constant__ CUtensorMap tmB, FusedArgs g) {
-  constexpr int FQ = FN / D;                       // q values per tile
-  extern __shared__ unsigned char smem_raw[];
-  unsigned char* smem =
-      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + F_NST * F_STAGE);
-  uint64_t* empty = full + F_NST;
-  uint64_t* done = empty + F_NST;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
-  volatile int* s_fail = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  volatile int* s_issued = s_fail + 1;
-  float2* s_ops = reinterpret_cast<float2*>(smem + F_NST * F_STAGE + 256);
-  int* s_start = reinterpret_cast<int*>(s_ops + MIX_MAX_OPS);
-  int* s_chan = s_start + MIX_MAX_BLK + 1;
-
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int q0 = blockIdx.x * FQ, a0 = blockIdx.y * BM;
-  const int Dl = g.Dl;
-  const int ktiles = (g.Ml + BK - 1) / BK;
-  const int total = ktiles * Dl;
-  const uint32_t ncols = Dl <= 1 ? 64u : (Dl <= 2 ? 128u : (Dl <= 4 ? 256u : 512u));
-
-  for (int i = threadIdx.x; i < g.nblk * D * D; i += blockDim.x) s_ops[i] = g.ops[i];
-  for (int i = threadIdx.x; i <= g.Dout; i += blockDim.x) s_start[i] = g.start[i];
-  for (int i = threadIdx.x; i < g.nblk; i += blockDim.x) s_chan[i] = g.chan[i];
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < F_NST; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
-    }
-    mbar_init(done, 1);
-    *s_fail = 0;
-    *s_issued = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(tmem_slot)),
-                 "r"(ncols));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = *tmem_slot;
-
-  if (threadIdx.x == 0) {
-    // producer: stage t = (k tile t / Dl, channel t % Dl)
-    for (int t = 0; t < total; ++t) {
-      const int s = t % F_NST, use = t / F_NST;
-      if (t >= F_NST && !mbar_wait(&empty[s], (use - 1) & 1, g.status)) {
-        *s_fail = 1;
-        break;
-      }
-      const int k0 = (t / Dl) * BK, w = t % Dl;
-      unsigned char* st = smem + s * F_STAGE;
-      mbar_expect_tx(&full[s], 4 * A_TILE + 4 * D * FQ * BK * 4);
-      tma_load_4d(st, &tmL, k0, w * g.Ml + a0, 0, 0, &full[s]);
-      for (int p = 0; p < 4; ++p)
-        tma_load_4d(st + 4 * A_TILE + p * F_B_PLANE, &tmB, k0, q0, 0, p, &full[s]);
-      *s_issued = t + 1;
-    }
-  } else if (threadIdx.x == 32) {
-    // MMA issuer: Cr = Ar Br - Ai Bi, Ci = Ar Bi + Ai Br (no conjugation)
-    for (int t = 0; t < total; ++t) {
-      const int s = t % F_NST;
-      if (!mbar_wait(&full[s], (t / F_NST) & 1, g.status)) {
-        *s_fail = 1;
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int w = t % Dl;
-      const bool first = t < Dl;
-      const uint32_t d_re = tmem + (uint32_t)(w * 2 * FN), d_im = d_re + FN;
-      const uint32_t a0s = smem_u32(smem + s * F_STAGE);
-      const uint32_t b0s = a0s + 4 * A_TILE;
-#pragma unroll
-      for (int kk = 0; kk < BK / 8; ++kk) {
-        const uint32_t ko = kk * 32;
-        const uint64_t arh = sdesc(a0s + 0 * A_TILE + ko), arl = sdesc(a0s + 1 * A_TILE + ko);
-        const uint64_t aih = sdesc(a0s + 2 * A_TILE + ko), ail = sdesc(a0s + 3 * A_TILE + ko);
-        const uint64_t brh = sdesc(b0s + 0 * F_B_PLANE + ko), brl = sdesc(b0s + 1 * F_B_PLANE + ko);
-        const uint64_t bih = sdesc(b0s + 2 * F_B_PLANE + ko), bil = sdesc(b0s + 3 * F_B_PLANE + ko);
-        const uint32_t acc0 = (first && kk == 0) ? 0u : 1u;
-        mma_tf32(d_re, arh, brh, idesc_n(0, FN), acc0);
-        mma_tf32(d_re, arh, brl, idesc_n(0, FN), 1u);
-        mma_tf32(d_re, arl, brh, idesc_n(0, FN), 1u);
-        mma_tf32(d_re, aih, bih, idesc_n(1, FN), 1u);
-        mma_tf32(d_re, aih, bil, idesc_n(1, FN), 1u);
-        mma_tf32(d_re, ail, bih, idesc_n(1, FN), 1u);
-        mma_tf32(d_im, arh, bih, idesc_n(0, FN), acc0);
-        mma_tf32(d_im, arh, bil, idesc_n(0, FN), 1u);
-        mma_tf32(d_im, arl, bih, idesc_n(0, FN), 1u);
-        mma_tf32(d_im, aih, brh, idesc_n(0, FN), 1u);
-        mma_tf32(d_im, aih, brl, idesc_n(0, FN), 1u);
-        mma_tf32(d_im, ail, brh, idesc_n(0, FN), 1u);
-      }
-      mma_commit(&empty[s]);
-    }
-    mma_commit(done);
-  }
-  __syncwarp();
-  const bool waited = mbar_wait(done, 0, g.status);
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const bool ok = __syncthreads_and(waited ? 1 : 0) && !*s_fail;
-  if (ok) {
-    const int a = a0 + warp * 32 + lane;          // the row this thread owns
-    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-    const int Dd = D * D, Q = D * g.Mr;
-    for (int v = 0; v < g.Dout; ++v) {
-      float accr[D][FQ], acci[D][FQ];
-#pragma unroll
-      for (int s = 0; s < D; ++s)
-#pragma unroll
-        for (int q = 0; q < FQ; ++q) accr[s][q] = acci[s][q] = 0.f;
-      for (int blk = s_start[v]; blk < s_start[v + 1]; ++blk) {
-        const int w = s_chan[blk];
-        float xr[FN], xi[FN];
-        tmem_ld16(lane_addr + w * 2 * FN, xr);
-        tmem_ld16(lane_addr + w * 2 * FN + 16, xr + 16);
-        tmem_ld16(lane_addr + w * 2 * FN + FN, xi);
-        tmem_ld16(lane_addr + w * 2 * FN + FN + 16, xi + 16);
-        const float2* op = s_ops + blk * Dd;
-#pragma unroll
-        for (int s = 0; s < D; ++s)
-#pragma unroll
-          for (int u = 0; u < D; ++u) {
-            const float2 o = op[s * D + u];
-            if (o.x != 0.f || o.y != 0.f) {
-#pragma unroll
-              for (int q = 0; q < FQ; ++q) {
-                const float x_r = xr[u * FQ + q], x_i = xi[u * FQ + q];
-                accr[s][q] = fmaf(o.x, x_r, fmaf(-o.y, x_i, accr[s][q]));
-                acci[s][q] = fmaf(o.x, x_i, fmaf(o.y, x_r, acci[s][q]));
-              }
-            }
-          }
-      }
-      if (a < g.Ml) {
-#pragma unroll
-        for (int q = 0; q < FQ; ++q) {
-          const int qg = q0 + q;
-          if (qg >= Q) continue;
-          const int tt = qg / g.Mr, c = qg - tt * g.Mr;
-#pragma unroll
-          for (int s = 0; s < D; ++s) {
-            const long long o =
-                ((long long)v * g.Ml * Dd + (long long)a * Dd + s * D + tt) * g.ld + c;
-            const float rh = tf32_round(accr[s][q]), ih = tf32_round(acci[s][q]);
-            g.Y[o] = rh;
-            g.Y[g.plane + o] = tf32_round(accr[s][q] - rh);
-            g.Y[2 * g.plane + o] = ih;
-            g.Y[3 * g.plane + o] = tf32_round(acci[s][q] - ih);
-          }
-        }
-      }
-    }
-  } else if (threadIdx.x == 0) {
-    const int issued = *s_issued;
-    for (int s = 0; s < F_NST; ++s) {
-      int last = -1;
-      for (int t = s; t < issued; t += F_NST) last = t;
-      if (last >= 0) mbar_wait(&full[s], (last / F_NST) & 1, g.status);
-    }
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
-  }
-}
-
-// ---------------------------------------------------------------------------------------
 // split-K table: the split of each contraction shape (M, N, K, nred, nbatch) measured by the
 // tuning script shipped beside the library (tune_splitk.py) and read from
 // tc_splitk_table.txt next to libtdmrg.so (or the file named by TDMRG_SPLITK_TABLE); shapes
@@ -820,66 +609,6 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, const TcGemm& g, cud
     e = cudaGetLastError();
   }
   return e;
-}
-
-bool heff_left_mix_supported(int d, int Dl, const MixTable& T) {
-  return Dl >= 1 && Dl <= F_MAX_DL && d >= 2 && d <= 10 && T.nblk <= MIX_MAX_BLK &&
-         T.nblk * d * d <= MIX_MAX_OPS && T.Dout <= MIX_MAX_BLK;
-}
-
-template <int D>
-static cudaError_t launch_left_mix(const CUtensorMap& mL, const CUtensorMap& mB, const FusedArgs& a,
-                                   int Q, int Ml, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(heff_left_mix_kernel<D>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)F_SMEM_BYTES);
-  if (e != cudaSuccess) return e;
-  constexpr int FQ = FN / D;
-  dim3 grid((Q + FQ - 1) / FQ, (Ml + BM - 1) / BM, 1);
-  count_launch();
-  heff_left_mix_kernel<D><<<grid, 128, F_SMEM_BYTES, s>>>(mL, mB, a);
-  return cudaGetLastError();
-}
-
-cudaError_t heff_left_mix(const TcOperand& Lp, const TcOperand& Bt, const MixTable& T, int Ml,
-                          int Mr, int d, int Dl, const TcOperand& Yp, int* status,
-                          cudaStream_t s) {
-  cudaError_t e = get_encoder();
-  if (e != cudaSuccess) return e;
-  if (!heff_left_mix_supported(d, Dl, T) || !status) return cudaErrorInvalidValue;
-  const int Q = d * Mr, FQ = FN / d;
-  if (Lp.rows < Dl * Ml || Lp.K != Ml || Bt.rows < d * Q || Bt.K != Ml || Yp.K != Mr ||
-      Yp.rows < Ml * d * d || Yp.nb < T.Dout)
-    return cudaErrorInvalidValue;
-  CUtensorMap mL, mB;
-  if ((e = make_map(&mL, Lp, BM)) != cudaSuccess) return e;
-  // the site operand as {K, q, u, plane}: row u * Q + q of each plane
-  if ((Bt.ld % 4) != 0 || (reinterpret_cast<uintptr_t>(Bt.p) & 15) != 0) return cudaErrorInvalidValue;
-  cuuint64_t dims[4] = {(cuuint64_t)Ml, (cuuint64_t)Q, (cuuint64_t)d, 4};
-  cuuint64_t strides[3] = {(cuuint64_t)Bt.ld * 4, (cuuint64_t)Bt.ld * 4 * Q,
-                           (cuuint64_t)Bt.ld * 4 * Bt.rows * Bt.nb};
-  cuuint32_t box[4] = {BK, (cuuint32_t)FQ, (cuuint32_t)d, 1};
-  cuuint32_t es[4] = {1, 1, 1, 1};
-  CUresult r = g_encode(&mB, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void*)Bt.p, dims, strides, box,
-                        es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-  FusedArgs a;
-  a.Ml = Ml; a.Mr = Mr; a.d = d; a.Dl = Dl; a.Dout = T.Dout; a.nblk = T.nblk;
-  a.start = T.start; a.chan = T.chan; a.ops = T.ops32;
-  a.Y = Yp.p; a.ld = Yp.ld; a.plane = Yp.plane(); a.status = status;
-  switch (d) {
-    case 2: return launch_left_mix<2>(mL, mB, a, Q, Ml, s);
-    case 3: return launch_left_mix<3>(mL, mB, a, Q, Ml, s);
-    case 4: return launch_left_mix<4>(mL, mB, a, Q, Ml, s);
-    case 5: return launch_left_mix<5>(mL, mB, a, Q, Ml, s);
-    case 6: return launch_left_mix<6>(mL, mB, a, Q, Ml, s);
-    case 7: return launch_left_mix<7>(mL, mB, a, Q, Ml, s);
-    case 8: return launch_left_mix<8>(mL, mB, a, Q, Ml, s);
-    case 9: return launch_left_mix<9>(mL, mB, a, Q, Ml, s);
-    case 10: return launch_left_mix<10>(mL, mB, a, Q, Ml, s);
-    default: return cudaErrorInvalidValue;
-  }
 }
 
 void tc_record_shapes(bool on) {

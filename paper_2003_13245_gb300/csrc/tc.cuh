@@ -57,12 +57,5 @@ cudaError_t split_f64_t(const cplx* src, long long sb, long long kstride, int co
 cudaError_t mix_split(const MixTable& T, int Ma, int d, int Mb, const float* X, long long xs,
                       long long xplane, const TcOperand& dst, int trans, cudaStream_t s);
 cudaError_t planes_to_f64(const TcOperand& P, cplx* out, cudaStream_t s);
-// First contraction of H_eff fused with the MPO mixing: Yp (split planes, rows (a, s, t),
-// K = c, nb = T.Dout) = mix_T(L . A) with L as Lp (rows (w, a), K = Ml) and A^T as Bt (rows
-// (u, t, c), K = Ml).  Supported for 2 <= d <= 10 and Dl <= 8 (heff_left_mix_supported).
-bool heff_left_mix_supported(int d, int Dl, const MixTable& T);
-cudaError_t heff_left_mix(const TcOperand& Lp, const TcOperand& Bt, const MixTable& T, int Ml,
-                          int Mr, int d, int Dl, const TcOperand& Yp, int* status,
-                          cudaStream_t s);
 
 }  // namespace tdmrg

@@ -728,7 +728,7 @@ def run_hp_sweep(args):
 def run_isotope(args):
     """Frequency-scaling isotope scan (isotope approach 2: every w_m scaled by m^-1/2 with
     g_m^2 w_m fixed): mu(m) and the coherence length L(m) of Eq. 9 from batched TD-DMRG, and
-    the hopping-limit mu_FGR(m) from the batched Eq. 7 kernel, at three temperatures.
+    the hopping-limit mu_FGR(m) from the batched Eq. 7 kernel, at kBT = 0.625, 1 and 1.25.
     Synthetic chain: N = 8, modes (0.2, 1.5, 6) and (1.0, 0.8, 4), V = 0.5, M = 64, 3xTF32,
     fixed Krylov dimension 8, dt = 0.05."""
     import torch
@@ -738,7 +738,7 @@ def run_isotope(args):
     torch.cuda.set_device(0)
     N, omega, g, nmax, V, M, dt = 8, [0.2, 1.0], [1.5, 0.8], [6, 4], 0.5, 64, 0.05
     masses = [1.0, 13.0 / 12.0, 1.25, 1.5, 2.0]
-    temps = [0.8, 1.0, 1.2]
+    temps = [0.625, 1.0, 1.25]          # beta = 1.6, 1.0, 0.8: even multiples of dtau = 0.05
     specs, models, Ls = [], [], []
     t0 = time.perf_counter()
     for kT in temps:

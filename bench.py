@@ -644,6 +644,7 @@ def run_accuracy(args):
             m.close()
         err = np.abs(res["c64"]["C"] - res["c128"]["C"]) / abs(res["c128"]["C"][0])
         rows.append({"point": label, "V": V, "kT": kT, "M": M, "ct_err": float(err.max()),
+                     "ct_err_per_step": [float(x) for x in err],
                      "logZ_err": abs(res["c64"]["logz"] - res["c128"]["logz"]),
                      "C0": [res["c128"]["C"][0].real, res["c128"]["C"][0].imag],
                      "mixed_site_updates_per_s": res["c64"]["rate"],

@@ -33,7 +33,7 @@ WORKLOAD = dict(name="holstein-N16-2mode-M128", N=16, omega=[0.2, 1.0], g=[1.5, 
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 METRIC = "TDVP site-updates/s (real-time, both states, N=16 2-mode Holstein chain, M=128)"
 # DRAM bytes (read + write) of one 8192 x 128 gauge-QR launch, measured by ncu
-QR_BULK_TRAFFIC = 17413888 + 214784
+QR_BULK_TRAFFIC = 17378560 + 225792
 
 
 def parse():
@@ -365,7 +365,7 @@ def run_ours(args):
                                  "other and with FP64 work, so the in-sweep per-matvec rate "
                                  "is a shared-device figure",
                 "kernel": "H_eff matvec: split + tc_zgemm_kernel (tcgen05 kind::tf32) + "
-                          "mix_split_kernel + tc_zgemm_kernel, 3xTF32 complex",
+                          "MPO mixing into split planes + tc_zgemm_kernel, 3xTF32 complex",
                 "peak_source": "MEASURED_PEAKS bf16_tflops_sustained / 2 (TF32 dense), of measured",
                 "per_launch": "algorithmic flops 8*(Dl*Ml^2*d^2*Mr + Dr*Ml*d^2*Mr^2) per matvec "
                               "(1.50e10 at the d^2=64, M=128 site) / event-timed matvec duration; "

@@ -847,7 +847,8 @@ static cudaError_t qr_allow_smem() {
 }
 
 cudaError_t gauge_qr(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cplx* R,
-                     const QrScratch& W, int* status, cudaStream_t s, int gcap) {
+                     const QrScratch& W, int* status, cudaStream_t s, int gcap, double rank_tol,
+                     int* src) {
   int G = gauge_qr_grid(m);
   if (gcap > 0 && G > gcap) G = gcap;
   if (G > W.gmax || n > W.nmax) return cudaErrorInvalidValue;
@@ -864,9 +865,10 @@ cudaError_t gauge_qr(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cplx* R,
   a.Q = Q; a.R = R;
   a.part = W.part; a.partn = W.partn; a.bar = W.bar; a.status = status;
   a.wait = W.wait > 0 ? W.wait : kBarrierWaitCycles;
-  a.rank_tol = 1e-12;
+  a.rank_tol = rank_tol;
   a.complete_tol = 1e-2;
   a.acc_in = nullptr;
+  a.src_out = src;
   // cooperative launch through cudaLaunchKernelEx (also valid inside a stream capture)
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(G);

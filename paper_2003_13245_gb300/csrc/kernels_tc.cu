@@ -6,10 +6,12 @@
 // and a complex product as four such real products (12 MMAs per 8-deep k step).
 //
 // One CTA computes a 128 x 64 tile of C = sum_r op(A_r) op(B_r)^T (both operands K-major).
-// Thread 0 issues the TMA loads (SWIZZLE_128B, 32-float = 128-byte rows, all four planes of
+// Thread 0 issues the TMA loads (SWIZZLE_64B, 16-float = 64-byte rows, all four planes of
 // a tile in one 4-D box), thread 32 issues tcgen05.mma into two TMEM accumulators (re, im:
 // 64 columns each), and all four warps read TMEM back with tcgen05.ld for the epilogue.
-// Two pipeline stages of 96 KB; every wait is bounded and reports through `status`.
+// Stages of 48 KB: two per CTA when the grid has more CTAs than the GPU has SMs (two CTAs fit
+// on an SM, so one's epilogue overlaps the other's main loop), four when it has at most one
+// CTA per SM; every wait is bounded and reports through `status`.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <dlfcn.h>
@@ -31,14 +33,15 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int BN = 64;
-constexpr int BK = 32;                          // floats per 128-byte swizzle row
-constexpr int NST = 2;
-constexpr int A_TILE = BM * BK * 4;             // one plane: 16 KB
-constexpr int B_TILE = BN * BK * 4;             // one plane: 8 KB
-constexpr int STAGE = 4 * A_TILE + 4 * B_TILE;  // 96 KB
+constexpr int BK = 16;                          // floats per 64-byte swizzle row
+constexpr int A_TILE = BM * BK * 4;             // one plane: 8 KB
+constexpr int B_TILE = BN * BK * 4;             // one plane: 4 KB
+constexpr int STAGE = 4 * A_TILE + 4 * B_TILE;  // 48 KB
 constexpr int TMEM_COLS = 128;                  // re accumulator [0, 64), im [64, 128)
 constexpr long long WAIT_CYCLES = 4000000000LL; // about 2 s
-constexpr size_t SMEM_BYTES = NST * STAGE + 1024 + 256;
+// pipeline depth: two stages when two CTAs share an SM (grids larger than the GPU), four when
+// the grid leaves SMs with a single CTA
+constexpr size_t smem_bytes(int nst) { return (size_t)nst * STAGE + 1024 + 256; }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -89,14 +92,14 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
-// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms 1024 B apart
+// shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row atoms 512 B apart
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
   uint64_t d = 0;
   d |= (uint64_t)((addr & 0x3FFFF) >> 4);          // start address
   d |= (uint64_t)1 << 16;                          // leading byte offset (unused here)
-  d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset
+  d |= (uint64_t)((8 * BK * 4) >> 4) << 32;        // stride byte offset: 8-row atoms
   d |= (uint64_t)1 << 46;                          // descriptor version
-  d |= (uint64_t)2 << 61;                          // SWIZZLE_128B
+  d |= (uint64_t)4 << 61;                          // SWIZZLE_64B
   return d;
 }
 
@@ -142,7 +145,8 @@ __device__ __forceinline__ float tf32_round(float x) {
   return __uint_as_float(r);
 }
 
-__global__ void __launch_bounds__(128, 1)
+template <int NST>
+__global__ void __launch_bounds__(128, NST == 2 ? 2 : 1)
     tc_zgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     TcGemm g) {
   extern __shared__ unsigned char smem_raw[];
@@ -376,7 +380,7 @@ cudaError_t make_map(CUtensorMap* m, const TcOperand& op, int box_rows) {
   cuuint32_t box[4] = {BK, (cuuint32_t)box_rows, 1, 4};
   cuuint32_t es[4] = {1, 1, 1, 1};
   CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void*)op.p, dims, strides, box, es,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
@@ -490,6 +494,71 @@ __global__ void mix_split_kernel(int Dout, int Ma, int d, int Mb, const int* sta
   }
 }
 
+// The same mixing with one thread per column (wo, a, tau, b) computing all D output levels
+// sigma: the d input levels u of each block's channel are loaded once and reused for every
+// sigma (the per-element form above reloads them d times).
+template <int D>
+__global__ void __launch_bounds__(256) mix_split_cols_kernel(int Dout, int Ma, int Mb,
+                                                             const int* start, const int* chan,
+                                                             const float2* ops, int nblk,
+                                                             const float* X, long long xs,
+                                                             long long xplane, float* dst,
+                                                             int ld, int trans) {
+  __shared__ float2 s_ops[MIX_MAX_OPS];
+  __shared__ int s_start[MIX_MAX_BLK + 1];
+  __shared__ int s_chan[MIX_MAX_BLK];
+  for (int i = threadIdx.x; i < nblk * D * D; i += blockDim.x) s_ops[i] = ops[i];
+  for (int i = threadIdx.x; i <= Dout; i += blockDim.x) s_start[i] = start[i];
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) s_chan[i] = chan[i];
+  __syncthreads();
+  const long long total = (long long)Dout * Ma * D * Mb;
+  const int rows = trans == 1 ? Mb : (trans == 2 ? Ma : Ma * D * D);
+  const long long plane = (long long)Dout * rows * ld;
+  const long long ustride = (long long)D * Mb;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    long long r = e;
+    const int b = (int)(r % Mb); r /= Mb;
+    const int tau = (int)(r % D); r /= D;
+    const int a = (int)(r % Ma);
+    const int wo = (int)(r / Ma);
+    float ar[D], ai[D];
+#pragma unroll
+    for (int sg = 0; sg < D; ++sg) ar[sg] = ai[sg] = 0.f;
+    for (int blk = s_start[wo]; blk < s_start[wo + 1]; ++blk) {
+      const float* x = X + s_chan[blk] * xs + ((long long)a * D * D + tau) * Mb + b;
+      float xr[D], xi[D];
+#pragma unroll
+      for (int u = 0; u < D; ++u) {
+        xr[u] = x[u * ustride];
+        xi[u] = x[xplane + u * ustride];
+      }
+      const float2* op = s_ops + blk * D * D;
+#pragma unroll
+      for (int sg = 0; sg < D; ++sg)
+#pragma unroll
+        for (int u = 0; u < D; ++u) {
+          const float2 o = op[sg * D + u];
+          ar[sg] = fmaf(o.x, xr[u], fmaf(-o.y, xi[u], ar[sg]));
+          ai[sg] = fmaf(o.x, xi[u], fmaf(o.y, xr[u], ai[sg]));
+        }
+    }
+#pragma unroll
+    for (int sg = 0; sg < D; ++sg) {
+      const int ast = (a * D + sg) * D + tau;
+      long long o;
+      if (trans == 1) o = ((long long)wo * rows + b) * ld + ast;
+      else if (trans == 2) o = ((long long)wo * rows + a) * ld + (long long)(sg * D + tau) * Mb + b;
+      else o = ((long long)wo * rows + ast) * ld + b;
+      const float rh = tf32_round(ar[sg]), ih = tf32_round(ai[sg]);
+      dst[o] = rh;
+      dst[plane + o] = tf32_round(ar[sg] - rh);
+      dst[2 * plane + o] = ih;
+      dst[3 * plane + o] = tf32_round(ai[sg] - ih);
+    }
+  }
+}
+
 // split planes (natural operand layout [4][nb][rows][ld]) -> complex FP64 [nb][rows][K]
 __global__ void planes_to_f64_kernel(const float* P, int nb, int rows, int K, int ld,
                                      double2* out) {
@@ -568,13 +637,28 @@ int grid_for(long long total) {
 cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, const TcGemm& g, cudaStream_t s) {
   cudaError_t e = get_encoder();
   if (e != cudaSuccess) return e;
-  static bool attr = false;
-  if (!attr) {
-    e = cudaFuncSetAttribute(tc_zgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  // once per process (the library serves one device): SM count and the kernels' attributes
+  static std::once_flag once;
+  static int n_sms = 0;
+  static cudaError_t init_err = cudaSuccess;
+  std::call_once(once, [] {
+    int dev = 0, sms = 0;
+    cudaError_t r = cudaGetDevice(&dev);
+    if (r == cudaSuccess) r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // the largest shared-memory carveout, so that two 2-stage CTAs are resident per SM
+    if (r == cudaSuccess)
+      r = cudaFuncSetAttribute(tc_zgemm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem_bytes(2));
+    if (r == cudaSuccess)
+      r = cudaFuncSetAttribute(tc_zgemm_kernel<2>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared);
+    if (r == cudaSuccess)
+      r = cudaFuncSetAttribute(tc_zgemm_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem_bytes(4));
+    n_sms = sms;
+    init_err = r;
+  });
+  if (init_err != cudaSuccess) return init_err;
   if (g.M < 1 || g.N < 1 || g.K < 1 || g.nred < 1 || g.nbatch < 1 || !g.status)
     return cudaErrorInvalidValue;
   if (A.K != g.K || B.K != g.K || A.rows < g.M || B.rows < g.N) return cudaErrorInvalidValue;
@@ -601,7 +685,10 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, const TcGemm& g, cud
   if (ks > 1) gg.ksplit = ks;
   dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, g.nbatch * gg.ksplit);
   count_launch();
-  tc_zgemm_kernel<<<grid, 128, SMEM_BYTES, s>>>(ma, mb, gg);
+  if ((long long)grid.x * grid.y * grid.z <= n_sms)
+    tc_zgemm_kernel<4><<<grid, 128, smem_bytes(4), s>>>(ma, mb, gg);
+  else
+    tc_zgemm_kernel<2><<<grid, 128, smem_bytes(2), s>>>(ma, mb, gg);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (gg.ksplit > 1) {
     count_launch();
@@ -656,6 +743,27 @@ cudaError_t mix_split(const MixTable& T, int Ma, int d, int Mb, const float* X, 
   if (T.nblk > MIX_MAX_BLK || T.nblk * d * d > MIX_MAX_OPS || T.Dout > MIX_MAX_BLK)
     return cudaErrorInvalidValue;
   count_launch();
+  const long long cols = (long long)T.Dout * Ma * d * Mb;
+#define TDMRG_MIX_COLS(DD)                                                                    \
+  case DD:                                                                                   \
+    mix_split_cols_kernel<DD><<<grid_for(cols), 256, 0, s>>>(T.Dout, Ma, Mb, T.start, T.chan, \
+                                                             T.ops32, T.nblk, X, xs, xplane, \
+                                                             dst.p, dst.ld, trans);          \
+    return cudaGetLastError();
+  switch (d) {
+    TDMRG_MIX_COLS(2)
+    TDMRG_MIX_COLS(3)
+    TDMRG_MIX_COLS(4)
+    TDMRG_MIX_COLS(5)
+    TDMRG_MIX_COLS(6)
+    TDMRG_MIX_COLS(7)
+    TDMRG_MIX_COLS(8)
+    TDMRG_MIX_COLS(9)
+    TDMRG_MIX_COLS(10)
+    default:
+      break;
+  }
+#undef TDMRG_MIX_COLS
   mix_split_kernel<<<grid_for(total), 256, 0, s>>>(T.Dout, Ma, d, Mb, T.start, T.chan, T.ops32,
                                                    T.nblk, X, xs, xplane, dst.p, dst.ld, trans);
   return cudaGetLastError();

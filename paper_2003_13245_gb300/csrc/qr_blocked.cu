@@ -117,8 +117,7 @@ __global__ void __launch_bounds__(QB_THREADS) gauge_qr_blocked_kernel(QbArgs A) 
   const int T = blockDim.x;
   cplx* vb = reinterpret_cast<cplx*>(smem);                 // [QB][rows]
   cplx* H = vb + QB * rows;                                   // [n][QB] projection coefficients
-  cplx* Hacc = H + n * QB;                                    // [n][QB] accumulated
-  cplx* Gb = Hacc + n * QB;                                   // [QB][QB] Gram, then R of the block
+  cplx* Gb = H + n * QB;                                      // [QB][QB] Gram, then R of the block
   double* dvec = reinterpret_cast<double*>(Gb + QB * QB);     // vv[QB], hh[QB], diag0[QB], misc
   unsigned char* acc = reinterpret_cast<unsigned char*>(dvec + 4 * QB + 8);   // [n]
   unsigned char* accb = acc + n;                              // [QB]
@@ -158,7 +157,12 @@ __global__ void __launch_bounds__(QB_THREADS) gauge_qr_blocked_kernel(QbArgs A) 
       const int t = e / nr, r = e % nr;
       vb[t * rows + r] = qb_load(A.Y, r0 + r, j0 + t);
     }
-    for (int e = threadIdx.x; e < j0 * QB; e += T) Hacc[e] = make_double2(0.0, 0.0);
+    // the block's coefficients accumulate over the passes straight into R (CTA 0 only, each
+    // entry by the same thread; a block that stopped early leaves partial sums in the columns it
+    // did not finish, which the next block clears here)
+    if (blockIdx.x == 0)
+      for (int e = threadIdx.x; e < j0 * bsz; e += T)
+        A.R[(long long)(e / bsz) * n + j0 + e % bsz] = make_double2(0.0, 0.0);
     __syncthreads();
     // ---- projection passes against the accepted columns < j0
     for (int pass = 0; pass < 2 && j0 > 0; ++pass) {
@@ -194,7 +198,10 @@ __global__ void __launch_bounds__(QB_THREADS) gauge_qr_blocked_kernel(QbArgs A) 
         const int i = e / bsz, t = e % bsz;
         const cplx h = acc[i] ? __ldcg(&A.fin[i * QB + t]) : make_double2(0.0, 0.0);
         H[i * QB + t] = h;
-        Hacc[i * QB + t] = make_double2(Hacc[i * QB + t].x + h.x, Hacc[i * QB + t].y + h.y);
+        if (blockIdx.x == 0) {
+          cplx& r = A.R[(long long)i * n + j0 + t];
+          r = make_double2(r.x + h.x, r.y + h.y);
+        }
       }
       __syncthreads();
       // hh[t] = sum_i |h_it|^2 (one warp per column), vv[t] from fin
@@ -348,10 +355,6 @@ __global__ void __launch_bounds__(QB_THREADS) gauge_qr_blocked_kernel(QbArgs A) 
       }
     }
     if (blockIdx.x == 0) {
-      for (int e = threadIdx.x; e < j0 * done; e += T) {
-        const int i = e / done, t = e % done;
-        A.R[(long long)i * n + j0 + t] = Hacc[i * QB + t];
-      }
       for (int e = threadIdx.x; e < done * done; e += T) {
         const int s = e / done, t = e % done;
         if (s <= t) A.R[(long long)(j0 + s) * n + j0 + t] = Gb[s * QB + t];
@@ -392,10 +395,11 @@ cudaError_t gauge_qr_blocked(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cpl
   const long long PS = (long long)n * QB + QB + QB * QB;
   if ((long long)G * PS + PS > scratch_len) return cudaErrorInvalidValue;
   const int rows = (m + G - 1) / G;
-  const size_t smem = (size_t)QB * rows * sizeof(cplx) + 2 * (size_t)n * QB * sizeof(cplx) +
+  const size_t smem = (size_t)QB * rows * sizeof(cplx) + (size_t)n * QB * sizeof(cplx) +
                       QB * QB * sizeof(cplx) + (4 * QB + 8) * sizeof(double) + (size_t)n + QB +
                       64;
-  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  if (smem > 200 * 1024)
+    return gauge_qr(m, n, Y, p, E, Q, R, W, status, s, gcap, rank_tol, src);
   if (!g_qb_attr) {
     cudaError_t e = cudaFuncSetAttribute(gauge_qr_blocked_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);

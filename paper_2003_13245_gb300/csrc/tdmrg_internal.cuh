@@ -40,6 +40,7 @@ struct MixTable {
   const cplx* ops;       // d x d per block
   const float2* ops32;   // the same operators rounded to FP32 (mixed-precision path)
   int nblk;
+  int Din = 0;           // number of input channels (0: not recorded)
 };
 cudaError_t mpo_mix(const MixTable& T, int Ma, int d, int Mb, const cplx* X, long long xs,
                     cplx* Y, long long ys, const int* skip, cudaStream_t s);
@@ -121,7 +122,8 @@ struct QrScratch {
 constexpr long long kBarrierWaitCycles = 4000000000LL;
 // gcap > 0 caps the cooperative grid (several QRs of concurrent instances can then co-reside)
 cudaError_t gauge_qr(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cplx* R,
-                     const QrScratch& W, int* status, cudaStream_t s, int gcap = 0);
+                     const QrScratch& W, int* status, cudaStream_t s, int gcap = 0,
+                     double rank_tol = 1e-12, int* src = nullptr);
 int gauge_qr_grid(int m);
 // dynamic shared memory of the column-wise QR on a grid of G blocks (each block stages its
 // ceil(m / G) rows); launches above kQrMaxSmem are refused
@@ -134,7 +136,9 @@ cudaError_t gauge_qr_complete(int m, int n, int p, QrRef E, cplx* Q, const unsig
                               const QrScratch& W, int* status, cudaStream_t s, int gcap = 0,
                               int* src = nullptr);
 // blocked variant (16 columns per block); scratch: gauge_qr_blocked_scratch(n, gmax) complex
-// entries and n accepted flags; W supplies the barrier and the completion pass' scratch
+// entries and n accepted flags; W supplies the barrier and the completion pass' scratch.  When a
+// block's row slice and coefficients do not fit its shared memory (very tall or wide factors on
+// a capped grid) the column-wise kernel does the factorisation instead.
 long long gauge_qr_blocked_scratch(int n, int gmax);
 cudaError_t gauge_qr_blocked(int m, int n, QrRef Y, int p, QrRef E, cplx* Q, cplx* R,
                              cplx* scratch, long long scratch_len, unsigned char* acc,

@@ -56,7 +56,7 @@ def tune(shapes, reps):
     from paper_2003_13245_gb300 import binding
     rows = []
     for (M, N, K, nred, nbatch) in shapes:
-        kt = ((K + 31) // 32) * nred
+        kt = ((K + 15) // 16) * nred
         best = None
         for ks in CANDIDATES:
             if ks > kt:

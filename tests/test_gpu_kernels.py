@@ -103,6 +103,26 @@ def test_gauge_qr_matches_oracle(m, n, rank, p, blocked):
         assert np.abs(np.abs(np.einsum("ij,ij->j", Qg.conj(), Qr)) - 1).max() < 1e-6
 
 
+def test_gauge_qr_blocked_too_wide_for_shared_memory():
+    """A factor whose row slices and block coefficients exceed a block's shared memory
+    (24576 x 640 on 152 blocks) is factorised by the column-wise kernel instead: for a full-rank
+    Y the result is the QR with a real positive diagonal, which Q^H Q = 1, Q R = Y and R upper
+    triangular with diag(R) > 0 fix uniquely."""
+    from paper_2003_13245_gb300 import binding
+    rng = np.random.default_rng(24576)
+    m, n = 24576, 640
+    Y = random_complex(rng, (m, n))
+    Q = torch.zeros((m, n), dtype=torch.complex128, device="cuda")
+    R = torch.zeros((n, n), dtype=torch.complex128, device="cuda")
+    binding.kernel_gauge_qr_blocked(dev(Y), Q, R, None)
+    Qg, Rg = Q.cpu().numpy(), R.cpu().numpy()
+    assert np.abs(Qg.conj().T @ Qg - np.eye(n)).max() < 1e-12
+    assert np.abs(Qg @ Rg - Y).max() <= 1e-10 * np.abs(Y).max()
+    assert np.abs(np.tril(Rg, -1)).max() == 0.0
+    dg = np.diag(Rg)
+    assert np.all(dg.real > 0) and np.abs(dg.imag).max() == 0.0
+
+
 @pytest.mark.parametrize("tau", [-0.3j, -0.05, 0.05, -2.0j, 0.4 - 1.5j])
 def test_krylov_dense_matches_expm(tau):
     import scipy.linalg

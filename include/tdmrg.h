@@ -285,6 +285,14 @@ int tdmrg_host_mpo_site(int N, int modes, const double* omega, const double* g, 
  * the quadrature of the exponential VJPs' Frechet integrals. */
 int tdmrg_host_gauss_legendre(int n, double* s, double* w);
 
+/* The node count the Krylov-basis quadrature of the exponential VJPs uses (host only): the
+ * smallest n in [min(2, nmax), nmax] whose n-point Gauss-Legendre error bound on [0, 1],
+ * (n!)^4 / ((2n + 1) ((2n)!)^3) r^(2n) e^r, is at most eps, for the Frechet integrand
+ * s -> e^{sA} E e^{(1-s)A} with r = 2 |A| (its 2n-th derivative is at most r^(2n) e^r |E|);
+ * nmax when no smaller count meets it.  r >= 0, 1 <= nmax <= 64, eps > 0, else TDMRG_ERR_ARG.
+ * The count is written to *n_out. */
+int tdmrg_host_quadrature_nodes(double r, int nmax, double eps, int* n_out);
+
 /* exp(z_s T) e_1, s < nz, for the real symmetric tridiagonal Lanczos matrix T = tridiag(beta,
  * alpha, beta) (alpha[k] diagonal, beta[k-1] off-diagonal, 1 <= k <= 64), from one cyclic
  * Jacobi eigendecomposition of T on the host (no handle, no GPU): z[2 nz] interleaved complex,
@@ -551,25 +559,28 @@ int tdmrg_kernel_bond_exp(int M, int Dw, const void* L, const void* R, const voi
 int tdmrg_kernel_dfma_loop(int blocks, long long iters, double* sink, double* flops_out,
                            void* stream);
 
-/* Split-K tuning of the tensor-core contractions (no counterpart in the paper).  Every
+/* Tile tuning of the tensor-core contractions (no counterpart in the paper).  Every
  * contraction of the mixed-precision path is one tcgen05 GEMM of shape (M, N, K) summed over
- * nred operand pairs for nbatch outputs; its K loop may be split over CTAs.  The split of each
- * shape is read from tc_splitk_table.txt beside libtdmrg.so (or the file named by the
- * environment variable TDMRG_SPLITK_TABLE), lines "M N K nred nbatch ksplit"; shapes not listed
- * use an occupancy rule.  The table is written by paper_2003_13245_gb300/tune_splitk.py, which
- * records a workload's shapes and times every candidate split:
+ * nred operand pairs for nbatch outputs, computed in 128-row tiles of 64 or 128 columns; its K
+ * loop may be split over CTAs.  The split and the tile width of each shape are read from
+ * tc_splitk_table.txt beside libtdmrg.so (or the file named by the environment variable
+ * TDMRG_SPLITK_TABLE), lines "M N K nred nbatch ksplit [tile_n]" (tile_n 64 when absent);
+ * shapes not listed use 64-column tiles and an occupancy rule.  The table is written by
+ * paper_2003_13245_gb300/tune_splitk.py, which records a workload's shapes and times every
+ * candidate split and tile width:
  *   tdmrg_tune_record_shapes(1) starts recording the shapes tc_gemm sees (0 stops);
  *   tdmrg_tune_recorded_shapes writes up to `capacity` shapes as 5 ints each to shapes[] and
  *     their number to *count (host);
  *   tdmrg_tune_reload_table makes the next contraction read the table file again;
- *   tdmrg_kernel_tc_gemm_timed runs one shape with split ksplit (0: the table / rule) on
- *     synthetic operands, one warm-up then `reps` launches between CUDA events on `stream`,
- *     and writes the average milliseconds to *ms_out (allocates and frees its operands). */
+ *   tdmrg_kernel_tc_gemm_timed runs one shape with split ksplit and tile width tile_n (64 or
+ *     128; 0 for either: the table / rule) on synthetic operands, one warm-up then `reps`
+ *     launches between CUDA events on `stream`, and writes the average milliseconds to
+ *     *ms_out (allocates and frees its operands); TDMRG_ERR_ARG for another tile_n. */
 int tdmrg_tune_record_shapes(int on);
 int tdmrg_tune_recorded_shapes(int* shapes, int capacity, int* count);
 int tdmrg_tune_reload_table(void);
-int tdmrg_kernel_tc_gemm_timed(int M, int N, int K, int nred, int nbatch, int ksplit, int reps,
-                               double* ms_out, void* stream);
+int tdmrg_kernel_tc_gemm_timed(int M, int N, int K, int nred, int nbatch, int ksplit, int tile_n,
+                               int reps, double* ms_out, void* stream);
 
 /* Krylov exponential of a dense Hermitian matrix H (n x n, device) -- the site and bond
  * exponentials of Eq. S1 on an explicit matrix:

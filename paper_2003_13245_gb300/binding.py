@@ -58,7 +58,7 @@ _SIGS = {
     "tdmrg_tune_record_shapes": [_i],
     "tdmrg_tune_recorded_shapes": [_ip, _i, _ip],
     "tdmrg_tune_reload_table": [],
-    "tdmrg_kernel_tc_gemm_timed": [_i, _i, _i, _i, _i, _i, _i, _dp, _p],
+    "tdmrg_kernel_tc_gemm_timed": [_i, _i, _i, _i, _i, _i, _i, _i, _dp, _p],
     "tdmrg_fgr_mobility_batch": [_i, _i, _dp, _dp, _dp, _dp, _d, _i, _dp, _p],
     "tdmrg_coherence_length": [_i, _dp, _dp],
     "tdmrg_thermal_prepare": [_p, _d, _d, _i],
@@ -98,6 +98,7 @@ _SIGS = {
     "tdmrg_host_tridiag_exp": [_i, _dp, _dp, _i, _dp, _dp],
     "tdmrg_model_set_adjoint_krylov_basis": [_p, _i],
     "tdmrg_host_gauss_legendre": [_i, _dp, _dp],
+    "tdmrg_host_quadrature_nodes": [_d, _i, _d, ctypes.POINTER(ctypes.c_int)],
 }
 
 
@@ -414,12 +415,13 @@ def tune_reload_table():
     load().tdmrg_tune_reload_table()
 
 
-def kernel_tc_gemm_timed(M, N, K, nred, nbatch, ksplit, reps=10, stream=None):
-    """Average milliseconds of one tensor-core contraction shape with split ksplit."""
+def kernel_tc_gemm_timed(M, N, K, nred, nbatch, ksplit, reps=10, stream=None, tile_n=0):
+    """Average milliseconds of one tensor-core contraction shape with split ksplit and tile
+    width tile_n (64 or 128; 0: the table's)."""
     lib = load()
     ms = ctypes.c_double()
     _check(lib.tdmrg_kernel_tc_gemm_timed(int(M), int(N), int(K), int(nred), int(nbatch),
-                                          int(ksplit), int(reps), ctypes.byref(ms),
+                                          int(ksplit), int(tile_n), int(reps), ctypes.byref(ms),
                                           _stream_ptr(stream)))
     return ms.value
 
@@ -454,6 +456,13 @@ def host_gauss_legendre(n):
     sn, wn = np.zeros(int(n)), np.zeros(int(n))
     _check(load().tdmrg_host_gauss_legendre(int(n), _dptr(sn), _dptr(wn)))
     return sn, wn
+
+
+def host_quadrature_nodes(r, nmax=16, eps=1e-15):
+    """Node count of the Krylov-basis quadrature for the integrand bound r (host only)."""
+    n = ctypes.c_int()
+    _check(load().tdmrg_host_quadrature_nodes(float(r), int(nmax), float(eps), ctypes.byref(n)))
+    return n.value
 
 
 def host_tridiag_exp(alpha, beta, z):

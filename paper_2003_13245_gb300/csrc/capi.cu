@@ -668,6 +668,12 @@ int tdmrg_correlation_vjp(tdmrg_model* h, double beta, double dtau, int M, doubl
   });
 }
 
+int tdmrg_host_quadrature_nodes(double r, int nmax, double eps, int* n_out) {
+  if (!(r >= 0.0) || !std::isfinite(r) || nmax < 1 || nmax > 64 || !(eps > 0.0) || !n_out)
+    return fail(nullptr, TDMRG_ERR_ARG, "host_quadrature_nodes: need r >= 0, 1 <= nmax <= 64, eps > 0");
+  return guarded(nullptr, [&] { *n_out = tdmrg::gauss_legendre_nodes_for(r, nmax, eps); });
+}
+
 int tdmrg_host_gauss_legendre(int n, double* s, double* w) {
   if (n < 1 || n > 64 || !s || !w)
     return fail(nullptr, TDMRG_ERR_ARG, "host_gauss_legendre: need 1 <= n <= 64");
@@ -869,9 +875,10 @@ int tdmrg_tune_reload_table(void) {
   return TDMRG_OK;
 }
 
-int tdmrg_kernel_tc_gemm_timed(int M, int N, int K, int nred, int nbatch, int ksplit, int reps,
-                               double* ms_out, void* stream) {
-  if (M < 1 || N < 1 || K < 1 || nred < 1 || nbatch < 1 || ksplit < 0 || reps < 1 || !ms_out)
+int tdmrg_kernel_tc_gemm_timed(int M, int N, int K, int nred, int nbatch, int ksplit, int tile_n,
+                               int reps, double* ms_out, void* stream) {
+  if (M < 1 || N < 1 || K < 1 || nred < 1 || nbatch < 1 || ksplit < 0 || reps < 1 || !ms_out ||
+      (tile_n != 0 && tile_n != 64 && tile_n != 128))
     return fail(nullptr, TDMRG_ERR_ARG, "tc_gemm_timed: bad arguments");
   return guarded(nullptr, [&] {
     using tdmrg::pad4;
@@ -903,7 +910,7 @@ int tdmrg_kernel_tc_gemm_timed(int M, int N, int K, int nred, int nbatch, int ks
     g.M = M; g.N = N; g.K = K; g.nred = nred; g.nbatch = nbatch;
     g.a_red = nred > 1 ? 1 : 0; g.b_red = nred > 1 ? 1 : 0; g.b_bat = nbatch > 1 ? nred : 0;
     g.out_mode = 1; g.C = C; g.ldc = N; g.sbc = (long long)M * N; g.plane = mn;
-    g.status = st; g.ksplit = ksplit;
+    g.status = st; g.ksplit = ksplit; g.bn = tile_n;
     g.part_len = 4LL << 20;           // the engine's split-K scratch
     g.part = (float*)get(sizeof(float) * (size_t)g.part_len);
     CK(tdmrg::tc_gemm(A, B, g, s));   // warm-up

@@ -382,8 +382,8 @@ void Engine::upload_mpo(const std::vector<MpoSite>& W, DevMpo& out) {
     }
     CK(cudaMemcpy(d_lrs, ilr_start.data(), sizeof(int) * (h.Dr + 1), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d_rls, irl_start.data(), sizeof(int) * (h.Dl + 1), cudaMemcpyHostToDevice));
-    s.lr = MixTable{h.Dr, d_lrs, d_lrc, d_olr, d_flr, nb, h.Dl};
-    s.rl = MixTable{h.Dl, d_rls, d_rlc, d_orl, d_frl, nb, h.Dr};
+    s.lr = MixTable{h.Dr, d_lrs, d_lrc, d_olr, d_flr, nb};
+    s.rl = MixTable{h.Dl, d_rls, d_rlc, d_orl, d_frl, nb};
   }
 }
 

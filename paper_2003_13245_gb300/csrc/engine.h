@@ -243,8 +243,10 @@ class Engine {
   // vbar (true: the node vectors as basis combinations, small exponentials on the host).
   void set_adjoint_krylov_basis(bool on) { adjoint_basis_ = on; }
   // Krylov-basis reverse of y = exp(tau H) v: vbar = exp(conj(tau) H) ybar, and the node
-  // vectors a_q (rows of Aq) and b_q (rows of Bq), q < nodes, with Hbar = sum_q k_q a_q b_q^H,
-  // k_q = w_q conj(tau) returned in kq (step_adjoint.cu)
+  // vectors a_q (rows of Aq) and b_q (rows of Bq), q < kq.size() <= nodes, with
+  // Hbar = sum_q k_q a_q b_q^H, k_q = w_q conj(tau) returned in kq; the node count is the
+  // fewest whose Gauss-Legendre error bound meets 1e-15 for the two Lanczos matrices' norms
+  // (step_adjoint.cu)
   template <class F>
   void exp_vjp_nodes(long long n, const cplx* v, const cplx* ybar, double tr, double ti,
                      int nodes, cplx* vbar, cplx* Aq, cplx* Bq, cplx* basis,

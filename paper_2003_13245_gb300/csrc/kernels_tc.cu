@@ -32,16 +32,17 @@ namespace tdmrg {
 namespace {
 
 constexpr int BM = 128;
-constexpr int BN = 64;
 constexpr int BK = 16;                          // floats per 64-byte swizzle row
 constexpr int A_TILE = BM * BK * 4;             // one plane: 8 KB
-constexpr int B_TILE = BN * BK * 4;             // one plane: 4 KB
-constexpr int STAGE = 4 * A_TILE + 4 * B_TILE;  // 48 KB
-constexpr int TMEM_COLS = 128;                  // re accumulator [0, 64), im [64, 128)
+// tile width BN = 64 or 128 columns: one B plane BN * 64 bytes; a stage holds the four planes
+// of both operands (48 KB or 64 KB); TMEM holds the re accumulator in columns [0, BN) and the
+// im accumulator in [BN, 2 BN)
+__host__ __device__ constexpr int b_tile(int bn) { return bn * BK * 4; }
+__host__ __device__ constexpr int stage_bytes(int bn) { return 4 * A_TILE + 4 * b_tile(bn); }
 constexpr long long WAIT_CYCLES = 4000000000LL; // about 2 s
-// pipeline depth: two stages when two CTAs share an SM (grids larger than the GPU), four when
-// the grid leaves SMs with a single CTA
-constexpr size_t smem_bytes(int nst) { return (size_t)nst * STAGE + 1024 + 256; }
+// pipeline depth: with 64-column tiles two stages when two CTAs share an SM (grids larger than
+// the GPU), four when the grid leaves SMs with a single CTA; 128-column tiles take three
+constexpr size_t smem_bytes(int nst, int bn) { return (size_t)nst * stage_bytes(bn) + 1024 + 256; }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -103,9 +104,9 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
   return d;
 }
 
-// instruction descriptor: D f32, A/B tf32, both K-major, M = 128, N = BN
-__host__ __device__ constexpr uint32_t idesc(int negA) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)negA << 13) | ((uint32_t)(BN >> 3) << 17) |
+// instruction descriptor: D f32, A/B tf32, both K-major, M = 128, N = bn
+__host__ __device__ constexpr uint32_t idesc(int negA, int bn) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)negA << 13) | ((uint32_t)(bn >> 3) << 17) |
          ((uint32_t)(BM >> 4) << 24);
 }
 
@@ -145,10 +146,15 @@ __device__ __forceinline__ float tf32_round(float x) {
   return __uint_as_float(r);
 }
 
-template <int NST>
+template <int NST, int BN>
 __global__ void __launch_bounds__(128, NST == 2 ? 2 : 1)
     tc_zgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     TcGemm g) {
+  constexpr int B_TILE = b_tile(BN);
+  constexpr int STAGE = stage_bytes(BN);
+  constexpr int TMEM_COLS = 2 * BN;
+  // the epilogue stages the re and im tiles (rows padded to BN + 1 floats) in the free stages
+  static_assert(2 * BM * (BN + 1) * 4 <= NST * STAGE, "epilogue tile exceeds the stages");
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -232,21 +238,21 @@ __global__ void __launch_bounds__(128, NST == 2 ? 2 : 1)
         const uint64_t brh = sdesc(b0 + 0 * B_TILE + ko), brl = sdesc(b0 + 1 * B_TILE + ko);
         const uint64_t bih = sdesc(b0 + 2 * B_TILE + ko), bil = sdesc(b0 + 3 * B_TILE + ko);
         // real part
-        mma_tf32(d_re, arh, brh, idesc(0), first_re ? 0u : 1u);
+        mma_tf32(d_re, arh, brh, idesc(0, BN), first_re ? 0u : 1u);
         first_re = false;
-        mma_tf32(d_re, arh, brl, idesc(0), 1u);
-        mma_tf32(d_re, arl, brh, idesc(0), 1u);
-        mma_tf32(d_re, aih, bih, idesc(neg_ii), 1u);
-        mma_tf32(d_re, aih, bil, idesc(neg_ii), 1u);
-        mma_tf32(d_re, ail, bih, idesc(neg_ii), 1u);
+        mma_tf32(d_re, arh, brl, idesc(0, BN), 1u);
+        mma_tf32(d_re, arl, brh, idesc(0, BN), 1u);
+        mma_tf32(d_re, aih, bih, idesc(neg_ii, BN), 1u);
+        mma_tf32(d_re, aih, bil, idesc(neg_ii, BN), 1u);
+        mma_tf32(d_re, ail, bih, idesc(neg_ii, BN), 1u);
         // imaginary part
-        mma_tf32(d_im, arh, bih, idesc(neg_ri), first_im ? 0u : 1u);
+        mma_tf32(d_im, arh, bih, idesc(neg_ri, BN), first_im ? 0u : 1u);
         first_im = false;
-        mma_tf32(d_im, arh, bil, idesc(neg_ri), 1u);
-        mma_tf32(d_im, arl, bih, idesc(neg_ri), 1u);
-        mma_tf32(d_im, aih, brh, idesc(neg_ir), 1u);
-        mma_tf32(d_im, aih, brl, idesc(neg_ir), 1u);
-        mma_tf32(d_im, ail, brh, idesc(neg_ir), 1u);
+        mma_tf32(d_im, arh, bil, idesc(neg_ri, BN), 1u);
+        mma_tf32(d_im, arl, bih, idesc(neg_ri, BN), 1u);
+        mma_tf32(d_im, aih, brh, idesc(neg_ir, BN), 1u);
+        mma_tf32(d_im, aih, brl, idesc(neg_ir, BN), 1u);
+        mma_tf32(d_im, ail, brh, idesc(neg_ir, BN), 1u);
       }
       mma_commit(&empty[s]);
     }
@@ -496,14 +502,15 @@ __global__ void mix_split_kernel(int Dout, int Ma, int d, int Mb, const int* sta
 
 // The same mixing with one thread per column (wo, a, tau, b) computing all D output levels
 // sigma: the d input levels u of each block's channel are loaded once and reused for every
-// sigma (the per-element form above reloads them d times).
+// sigma (the per-element form above reloads them d times).  The column index is decomposed in
+// 32-bit arithmetic (the launcher checks that the columns number fewer than 2^31).
 template <int D>
-__global__ void __launch_bounds__(256) mix_split_cols_kernel(int Dout, int Ma, int Mb,
-                                                             const int* start, const int* chan,
-                                                             const float2* ops, int nblk,
-                                                             const float* X, long long xs,
-                                                             long long xplane, float* dst,
-                                                             int ld, int trans) {
+__global__ void __launch_bounds__(256, D >= 10 ? 2 : (D >= 8 ? 3 : 4)) mix_split_cols_kernel(int Dout, int Ma, int Mb,
+                                                                const int* start, const int* chan,
+                                                                const float2* ops, int nblk,
+                                                                const float* X, long long xs,
+                                                                long long xplane, float* dst,
+                                                                int ld, int trans) {
   __shared__ float2 s_ops[MIX_MAX_OPS];
   __shared__ int s_start[MIX_MAX_BLK + 1];
   __shared__ int s_chan[MIX_MAX_BLK];
@@ -511,17 +518,16 @@ __global__ void __launch_bounds__(256) mix_split_cols_kernel(int Dout, int Ma, i
   for (int i = threadIdx.x; i <= Dout; i += blockDim.x) s_start[i] = start[i];
   for (int i = threadIdx.x; i < nblk; i += blockDim.x) s_chan[i] = chan[i];
   __syncthreads();
-  const long long total = (long long)Dout * Ma * D * Mb;
+  const int total = Dout * Ma * D * Mb;
   const int rows = trans == 1 ? Mb : (trans == 2 ? Ma : Ma * D * D);
   const long long plane = (long long)Dout * rows * ld;
   const long long ustride = (long long)D * Mb;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    long long r = e;
-    const int b = (int)(r % Mb); r /= Mb;
-    const int tau = (int)(r % D); r /= D;
-    const int a = (int)(r % Ma);
-    const int wo = (int)(r / Ma);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    int r = e;
+    const int b = r % Mb; r /= Mb;
+    const int tau = r % D; r /= D;
+    const int a = r % Ma;
+    const int wo = r / Ma;
     float ar[D], ai[D];
 #pragma unroll
     for (int sg = 0; sg < D; ++sg) ar[sg] = ai[sg] = 0.f;
@@ -575,16 +581,22 @@ __global__ void planes_to_f64_kernel(const float* P, int nb, int rows, int K, in
 }
 
 // ---------------------------------------------------------------------------------------
-// split-K table: the split of each contraction shape (M, N, K, nred, nbatch) measured by the
-// tuning script shipped beside the library (tune_splitk.py) and read from
-// tc_splitk_table.txt next to libtdmrg.so (or the file named by TDMRG_SPLITK_TABLE); shapes
-// not in the table use the occupancy rule in tc_gemm.  Optionally every shape tc_gemm sees is
-// recorded, which is how the tuning script learns the shapes of a workload.
+// tile table: the split-K factor and the tile width (64 or 128 columns) of each contraction
+// shape (M, N, K, nred, nbatch), measured by the tuning script shipped beside the library
+// (tune_splitk.py) and read from tc_splitk_table.txt next to libtdmrg.so (or the file named
+// by TDMRG_SPLITK_TABLE); a line "M N K nred nbatch ksplit [width]" (width 64 when absent).
+// Shapes not in the table use 64-column tiles and the occupancy rule in tc_gemm.  Optionally
+// every shape tc_gemm sees is recorded, which is how the tuning script learns the shapes of a
+// workload.
 // ---------------------------------------------------------------------------------------
 using Shape = std::tuple<int, int, int, int, int>;
+struct TileChoice {
+  int ksplit = 0;
+  int bn = 0;
+};
 std::mutex g_tab_mu;
 bool g_tab_loaded = false;
-std::map<Shape, int> g_tab;
+std::map<Shape, TileChoice> g_tab;
 bool g_record = false;
 std::set<Shape> g_seen;
 
@@ -608,21 +620,26 @@ void load_table_locked() {
   char line[256];
   while (std::fgets(line, sizeof line, f)) {
     if (line[0] == '#') continue;
-    int M, N, K, r, b, ks;
-    if (std::sscanf(line, "%d %d %d %d %d %d", &M, &N, &K, &r, &b, &ks) == 6 && ks >= 1)
-      g_tab[Shape(M, N, K, r, b)] = ks;
+    int M, N, K, r, b, ks, bn = 64;
+    const int got = std::sscanf(line, "%d %d %d %d %d %d %d", &M, &N, &K, &r, &b, &ks, &bn);
+    if (got >= 6 && ks >= 1 && (bn == 64 || bn == 128)) {
+      TileChoice c;
+      c.ksplit = ks;
+      c.bn = got == 7 ? bn : 64;
+      g_tab[Shape(M, N, K, r, b)] = c;
+    }
   }
   std::fclose(f);
 }
 
-// the table's split for a shape, or 0 when the shape is not listed
-int table_split(const TcGemm& g) {
+// the table's choice for a shape ({0, 0} when the shape is not listed)
+TileChoice table_choice(const TcGemm& g) {
   std::lock_guard<std::mutex> lock(g_tab_mu);
   load_table_locked();
   const Shape key(g.M, g.N, g.K, g.nred, g.nbatch);
   if (g_record) g_seen.insert(key);
   const auto it = g_tab.find(key);
-  return it == g_tab.end() ? 0 : it->second;
+  return it == g_tab.end() ? TileChoice{} : it->second;
 }
 
 int grid_for(long long total) {
@@ -647,35 +664,43 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, const TcGemm& g, cud
     if (r == cudaSuccess) r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     // the largest shared-memory carveout, so that two 2-stage CTAs are resident per SM
     if (r == cudaSuccess)
-      r = cudaFuncSetAttribute(tc_zgemm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem_bytes(2));
+      r = cudaFuncSetAttribute(tc_zgemm_kernel<2, 64>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(2, 64));
     if (r == cudaSuccess)
-      r = cudaFuncSetAttribute(tc_zgemm_kernel<2>, cudaFuncAttributePreferredSharedMemoryCarveout,
+      r = cudaFuncSetAttribute(tc_zgemm_kernel<2, 64>,
+                               cudaFuncAttributePreferredSharedMemoryCarveout,
                                (int)cudaSharedmemCarveoutMaxShared);
     if (r == cudaSuccess)
-      r = cudaFuncSetAttribute(tc_zgemm_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem_bytes(4));
+      r = cudaFuncSetAttribute(tc_zgemm_kernel<4, 64>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(4, 64));
+    if (r == cudaSuccess)
+      r = cudaFuncSetAttribute(tc_zgemm_kernel<3, 128>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(3, 128));
     n_sms = sms;
     init_err = r;
   });
   if (init_err != cudaSuccess) return init_err;
   if (g.M < 1 || g.N < 1 || g.K < 1 || g.nred < 1 || g.nbatch < 1 || !g.status)
     return cudaErrorInvalidValue;
+  if (g.bn != 0 && g.bn != 64 && g.bn != 128) return cudaErrorInvalidValue;
   if (A.K != g.K || B.K != g.K || A.rows < g.M || B.rows < g.N) return cudaErrorInvalidValue;
   // the batch / reduction coordinate of each operand must stay inside its nb
   const int amax = (g.nred - 1) * g.a_red + (g.nbatch - 1) * g.a_bat;
   const int bmax = (g.nred - 1) * g.b_red + (g.nbatch - 1) * g.b_bat;
   if (amax >= A.nb || bmax >= B.nb) return cudaErrorInvalidValue;
+  // tile width and split-K: forced (timing), else the tuned table, else 64-column tiles and a
+  // split when the output tiles cannot fill the GPU and the K loop is long
+  const TileChoice tab = (g.ksplit > 0 && g.bn > 0) ? TileChoice{} : table_choice(g);
+  const int bn = g.bn > 0 ? g.bn : (tab.bn > 0 ? tab.bn : 64);
   CUtensorMap ma, mb;
   if ((e = make_map(&ma, A, BM)) != cudaSuccess) return e;
-  if ((e = make_map(&mb, B, BN)) != cudaSuccess) return e;
-  // split-K: a forced split (timing), else the tuned table, else split when the output
-  // tiles cannot fill the GPU and the K loop is long
+  if ((e = make_map(&mb, B, bn)) != cudaSuccess) return e;
   TcGemm gg = g;
   gg.ksplit = 1;
-  const long long tiles = (long long)((g.N + BN - 1) / BN) * ((g.M + BM - 1) / BM) * g.nbatch;
+  gg.bn = bn;
+  const long long tiles = (long long)((g.N + bn - 1) / bn) * ((g.M + BM - 1) / BM) * g.nbatch;
   const int all = ((g.K + BK - 1) / BK) * g.nred;
-  int ks = g.ksplit > 0 ? g.ksplit : table_split(g);
+  int ks = g.ksplit > 0 ? g.ksplit : tab.ksplit;
   if (ks == 0 && g.part && tiles < 76 && all >= 8) {
     ks = (int)((152 + tiles - 1) / tiles);
     if (ks > all / 4) ks = all / 4;
@@ -683,12 +708,14 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, const TcGemm& g, cud
   if (ks > all) ks = all;
   while (ks > 1 && (!g.part || 2LL * g.nbatch * ks * g.M * g.N > g.part_len)) --ks;
   if (ks > 1) gg.ksplit = ks;
-  dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, g.nbatch * gg.ksplit);
+  dim3 grid((g.N + bn - 1) / bn, (g.M + BM - 1) / BM, g.nbatch * gg.ksplit);
   count_launch();
-  if ((long long)grid.x * grid.y * grid.z <= n_sms)
-    tc_zgemm_kernel<4><<<grid, 128, smem_bytes(4), s>>>(ma, mb, gg);
+  if (bn == 128)
+    tc_zgemm_kernel<3, 128><<<grid, 128, smem_bytes(3, 128), s>>>(ma, mb, gg);
+  else if ((long long)grid.x * grid.y * grid.z <= n_sms)
+    tc_zgemm_kernel<4, 64><<<grid, 128, smem_bytes(4, 64), s>>>(ma, mb, gg);
   else
-    tc_zgemm_kernel<2><<<grid, 128, smem_bytes(2), s>>>(ma, mb, gg);
+    tc_zgemm_kernel<2, 64><<<grid, 128, smem_bytes(2, 64), s>>>(ma, mb, gg);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (gg.ksplit > 1) {
     count_launch();
@@ -746,6 +773,7 @@ cudaError_t mix_split(const MixTable& T, int Ma, int d, int Mb, const float* X, 
   const long long cols = (long long)T.Dout * Ma * d * Mb;
 #define TDMRG_MIX_COLS(DD)                                                                    \
   case DD:                                                                                   \
+    if (cols >= (1LL << 31) - 256LL * 152 * 32) break;                                       \
     mix_split_cols_kernel<DD><<<grid_for(cols), 256, 0, s>>>(T.Dout, Ma, Mb, T.start, T.chan, \
                                                              T.ops32, T.nblk, X, xs, xplane, \
                                                              dst.p, dst.ld, trans);          \

@@ -104,4 +104,16 @@ void gauss_legendre01(int n, std::vector<double>& s, std::vector<double>& w) {
   }
 }
 
+int gauss_legendre_nodes_for(double r, int nmax, double eps) {
+  const int n0 = nmax < 2 ? nmax : 2;
+  if (!(r > 0.0)) return n0;
+  const double lr = std::log(r), le = std::log(eps);
+  for (int n = n0; n < nmax; ++n) {
+    const double lc = 4.0 * std::lgamma(n + 1.0) - std::log(2.0 * n + 1.0) -
+                      3.0 * std::lgamma(2.0 * n + 1.0);
+    if (lc + 2.0 * n * lr + r <= le) return n;
+  }
+  return nmax;
+}
+
 }  // namespace tdmrg

@@ -249,10 +249,6 @@ template <class F>
 void Engine::exp_vjp_nodes(long long n, const cplx* v, const cplx* ybar, double tr, double ti,
                            int nodes, cplx* vbar, cplx* Aq, cplx* Bq, cplx* basis,
                            std::vector<Cx>& kq, F&& matvec) {
-  std::vector<double> sq, wq;
-  gauss_legendre01(nodes, sq, wq);
-  kq.resize(nodes);
-  for (int q = 0; q < nodes; ++q) kq[q] = wq[q] * std::conj(Cx(tr, ti));
   auto read_state = [&](int& k, double& b0, std::vector<double>& al, std::vector<double>& be) {
     LzState h;
     CK(cudaMemcpyAsync(&h, lz_, sizeof(LzState), cudaMemcpyDeviceToHost, st_));
@@ -273,6 +269,25 @@ void Engine::exp_vjp_nodes(long long n, const cplx* v, const cplx* ybar, double 
   // Lanczos of ybar with conj(tau): vbar, and its basis (left in V_) for the a_q
   krylov(n, ybar, vbar, tr, -ti, matvec);
   read_state(k2, b2, a2, e2);
+  // node count: at most `nodes`, the fewest for which the Gauss-Legendre error bound of the
+  // Frechet integrand s -> e^{s tau T1} (.) e^{(1-s) tau T2} stays below 1e-15 of its scale
+  // (r = |tau| (|T1| + |T2|), infinity norms of the two Lanczos matrices)
+  auto tnorm = [](const std::vector<double>& al, const std::vector<double>& be) {
+    double m = 0.0;
+    for (size_t i = 0; i < al.size(); ++i) {
+      double r = std::fabs(al[i]);
+      if (i > 0) r += std::fabs(be[i - 1]);
+      if (i < be.size()) r += std::fabs(be[i]);
+      m = std::max(m, r);
+    }
+    return m;
+  };
+  const double r = std::hypot(tr, ti) * (tnorm(a1, e1) + tnorm(a2, e2));
+  nodes = gauss_legendre_nodes_for(r, nodes, 1e-15);
+  std::vector<double> sq, wq;
+  gauss_legendre01(nodes, sq, wq);
+  kq.resize(nodes);
+  for (int q = 0; q < nodes; ++q) kq[q] = wq[q] * std::conj(Cx(tr, ti));
   std::vector<Cx> zb(nodes), za(nodes), cb((size_t)nodes * std::max(k1, 1)),
       ca((size_t)nodes * std::max(k2, 1));
   for (int q = 0; q < nodes; ++q) {
@@ -572,7 +587,7 @@ void Engine::step_vjp(int M, const cplx* const* A_in, double tr, double ti,
     const int gsz = W.Dl * W.Dr * D[k];
     const bool gram = np > 0 && dd[k] <= 16;
     if (gram) CK(cudaMemsetAsync(Gacc, 0, sizeof(cplx) * (size_t)gsz, st_));
-    for (int q = 0; q < nodes; ++q) {
+    for (int q = 0; q < (int)kq.size(); ++q) {
       const cplx* a = Aq + (size_t)q * n[k];
       const cplx* b = Bq + (size_t)q * n[k];
       const Cx kc = std::conj(kq[q]);                 // w_q tau
@@ -629,7 +644,7 @@ void Engine::step_vjp(int M, const cplx* const* A_in, double tr, double ti,
                   });
     CK(cudaMemsetAsync(Lbar, 0, sizeof(cplx) * (size_t)(Dw * mm), st_));
     CK(cudaMemsetAsync(Rbar, 0, sizeof(cplx) * (size_t)(Dw * mm), st_));
-    for (int q = 0; q < nodes; ++q) {
+    for (int q = 0; q < (int)kq.size(); ++q) {
       const cplx* a = Aq + (size_t)q * mm;
       const cplx* b = Bq + (size_t)q * mm;
       const cplx kk = {kq[q].real(), kq[q].imag()};  // w_q conj(tau)

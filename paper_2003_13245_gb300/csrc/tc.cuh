@@ -36,10 +36,11 @@ struct TcGemm {
   float* part;
   long long part_len;
   int ksplit;          // 0: tuned table / occupancy rule; > 0: forced (tc_gemm sets the one used)
+  int bn;              // tile width: 0 = tuned table (else 64); 64 or 128 = forced
 };
 
 // g.ksplit on input: 0 = the tuned table's split for the shape (else the occupancy rule),
-// > 0 = that split (capped by the K loop and the scratch)
+// > 0 = that split (capped by the K loop and the scratch); g.bn likewise for the tile width
 cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, const TcGemm& g, cudaStream_t s);
 // shapes (M, N, K, nred, nbatch) seen by tc_gemm while recording is on
 void tc_record_shapes(bool on);

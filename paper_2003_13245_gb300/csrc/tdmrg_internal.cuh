@@ -40,7 +40,6 @@ struct MixTable {
   const cplx* ops;       // d x d per block
   const float2* ops32;   // the same operators rounded to FP32 (mixed-precision path)
   int nblk;
-  int Din = 0;           // number of input channels (0: not recorded)
 };
 cudaError_t mpo_mix(const MixTable& T, int Ma, int d, int Mb, const cplx* X, long long xs,
                     cplx* Y, long long ys, const int* skip, cudaStream_t s);

@@ -1,13 +1,14 @@
-"""Split-K tuner of the tensor-core contractions (run on the GPU; writes the table the library
+"""Tile tuner of the tensor-core contractions (run on the GPU; writes the table the library
 reads).
 
 Every contraction of the mixed-precision path is one tcgen05 GEMM of shape (M, N, K) summed over
-nred operand pairs for nbatch outputs; when the output has few tiles its K loop is split over
-CTAs and a second kernel adds the partial sums.  This script runs short versions of the
-benchmark workloads with shape recording on (the contraction shapes depend only on the local
-dimensions, the bond dimensions and the MPO bond dimension, so four molecules per chain give
-every bulk shape of a long chain), times every recorded shape at each candidate split, and
-writes the fastest split per shape to tc_splitk_table.txt beside libtdmrg.so:
+nred operand pairs for nbatch outputs, computed in 128-row tiles of 64 or 128 columns; when the
+output has few tiles its K loop is split over CTAs and a second kernel adds the partial sums.
+This script runs short versions of the benchmark workloads with shape recording on (the
+contraction shapes depend only on the local dimensions, the bond dimensions and the MPO bond
+dimension, so four molecules per chain give every bulk shape of a long chain), times every
+recorded shape at each candidate (tile width, split), and writes the fastest per shape to
+tc_splitk_table.txt beside libtdmrg.so:
 
     python -m paper_2003_13245_gb300.tune_splitk [--out PATH] [--reps 10]
 """
@@ -58,16 +59,17 @@ def tune(shapes, reps):
     for (M, N, K, nred, nbatch) in shapes:
         kt = ((K + 15) // 16) * nred
         best = None
-        for ks in CANDIDATES:
-            if ks > kt:
-                break
-            ms = binding.kernel_tc_gemm_timed(M, N, K, nred, nbatch, ks, reps)
-            if best is None or ms < best[1]:
-                best = (ks, ms)
-        rule = binding.kernel_tc_gemm_timed(M, N, K, nred, nbatch, 0, reps)
-        rows.append((M, N, K, nred, nbatch, best[0], best[1], rule))
-        print("%6d %6d %5d %3d %3d  split %2d  %.4f ms  (rule %.4f ms)" %
-              (M, N, K, nred, nbatch, best[0], best[1], rule), flush=True)
+        for bn in ((64, 128) if N > 64 else (64,)):
+            for ks in CANDIDATES:
+                if ks > kt:
+                    break
+                ms = binding.kernel_tc_gemm_timed(M, N, K, nred, nbatch, ks, reps, tile_n=bn)
+                if best is None or ms < best[1]:
+                    best = (ks, ms, bn)
+        rule = binding.kernel_tc_gemm_timed(M, N, K, nred, nbatch, 0, reps, tile_n=64)
+        rows.append((M, N, K, nred, nbatch, best[0], best[1], rule, best[2]))
+        print("%6d %6d %5d %3d %3d  split %2d  tile %3d  %.4f ms  (rule %.4f ms)" %
+              (M, N, K, nred, nbatch, best[0], best[2], best[1], rule), flush=True)
     return rows
 
 
@@ -87,10 +89,11 @@ def main():
     rows = tune(record_shapes(), a.reps)
     name = torch.cuda.get_device_name(0)
     with open(a.out, "w") as f:
-        f.write("# split-K table of the tensor-core contractions, measured on %s by "
-                "tune_splitk.py\n# M N K nred nbatch ksplit   (best ms, occupancy-rule ms)\n" % name)
-        for M, N, K, r, b, ks, ms, rule in rows:
-            f.write("%d %d %d %d %d %d   # %.4f %.4f\n" % (M, N, K, r, b, ks, ms, rule))
+        f.write("# tile table of the tensor-core contractions, measured on %s by "
+                "tune_splitk.py\n# M N K nred nbatch ksplit tile_n   (best ms, ms of 64-column "
+                "tiles with the occupancy rule)\n" % name)
+        for M, N, K, r, b, ks, ms, rule, bn in rows:
+            f.write("%d %d %d %d %d %d %d   # %.4f %.4f\n" % (M, N, K, r, b, ks, bn, ms, rule))
     gain = sum(r[7] for r in rows) / max(sum(r[6] for r in rows), 1e-30)
     print("wrote %s (%d shapes; summed time of the rule / of the table: %.3f)" %
           (a.out, len(rows), gain))

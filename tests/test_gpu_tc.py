@@ -67,18 +67,22 @@ def test_heff_tc_matches_oracle(Ml, Mr, d, Dl, Dr):
     assert err < TOL, err
 
 
-@pytest.mark.parametrize("ksplit", [1, 3, 8])
-def test_splitk_table_is_applied_and_exact(ksplit, tmp_path, monkeypatch):
-    """A split-K table entry for a contraction shape changes only the summation order: with the
-    split forced through a table file, C = A B^T still matches FP64 to the 3xTF32 bound for its
+@pytest.mark.parametrize("ksplit,tile_n,M,N", [(1, 64, 128, 64), (3, 64, 128, 64),
+                                               (8, 64, 128, 64), (1, 128, 165, 197),
+                                               (3, 128, 165, 197), (2, None, 165, 197)])
+def test_splitk_table_is_applied_and_exact(ksplit, tile_n, M, N, tmp_path, monkeypatch):
+    """A tile-table entry for a contraction shape (split-K factor and tile width, 64 or 128
+    columns; a line without a width means 64) changes only the summation order: with the entry
+    forced through a table file, C = A B^T still matches FP64 to the 3xTF32 bound for its
     length: an FP32 sum of K products carries up to K 2^-24 of the sum of their moduli, which
     for random entries is about K 2^-24 of max|C| (2.4e-4 at K = 4096; an unsplit loop sums all
-    4096 products in one FP32 accumulator, measured 7e-5), and the timed entry point runs that
-    shape at every candidate split."""
+    4096 products in one FP32 accumulator, measured 7e-5), ragged row and column tiles
+    included, and the timed entry point runs that shape at every candidate."""
     from paper_2003_13245_gb300 import binding
-    M, N, K = 128, 64, 4096
+    K = 4096
     table = tmp_path / "table.txt"
-    table.write_text("# test\n%d %d %d 1 1 %d\n" % (M, N, K, ksplit))
+    table.write_text("# test\n%d %d %d 1 1 %d%s\n" % (M, N, K, ksplit,
+                                                      "" if tile_n is None else " %d" % tile_n))
     monkeypatch.setenv("TDMRG_SPLITK_TABLE", str(table))
     binding.tune_reload_table()
     try:
@@ -89,7 +93,8 @@ def test_splitk_table_is_applied_and_exact(ksplit, tmp_path, monkeypatch):
         binding.kernel_zgemm_tc(dev(A), dev(B), C, 0, 0)
         ref = A @ B.T
         assert np.abs(C.cpu().numpy() - ref).max() / np.abs(ref).max() < K * 2.0 ** -24
-        assert binding.kernel_tc_gemm_timed(M, N, K, 1, 1, ksplit, reps=2) > 0.0
+        assert binding.kernel_tc_gemm_timed(M, N, K, 1, 1, ksplit, reps=2,
+                                            tile_n=tile_n or 64) > 0.0
     finally:
         monkeypatch.delenv("TDMRG_SPLITK_TABLE")
         binding.tune_reload_table()

@@ -166,3 +166,27 @@ def test_host_gauss_legendre_rule(lib, n):
     assert np.abs(s - 0.5 * (x + 1)).max() < 1e-14 and np.abs(w - 0.5 * v).max() < 1e-14
     for deg in (0, n, 2 * n - 1):
         assert abs(np.sum(w * s ** deg) - 1.0 / (deg + 1)) < 1e-13
+
+
+@pytest.mark.parametrize("r", [0.0, 0.05, 0.5, 1.5, 4.0, 12.0])
+def test_host_quadrature_node_count_meets_its_bound(lib, r):
+    """The node count of the Krylov-basis quadrature, pinned by closed forms: with the count
+    chosen for the bound r, Gauss-Legendre integrates the scalar Frechet integrands
+    e^{s x} e^{(1-s) y} on [0, 1] with |x| + |y| = r to within 1e-15 e^{r/2} of
+    (e^x - e^y)/(x - y), for real (imaginary time) and imaginary (real time) exponents, and one
+    node fewer violates the bound (the count is the smallest)."""
+    from math import log, lgamma
+    from paper_2003_13245_gb300 import binding
+    eps = 1e-15
+    n = binding.host_quadrature_nodes(r, 64, eps)
+    assert 2 <= n <= 64
+    s, w = binding.host_gauss_legendre(n)
+    for x, y in ((0.5 * r, -0.5 * r), (0.5j * r, -0.5j * r), (0.3 * r, -0.7 * r)):
+        f = np.exp(s * x) * np.exp((1 - s) * y)
+        exact = (np.exp(x) - np.exp(y)) / (x - y) if r > 0 else 1.0
+        assert abs(np.sum(w * f) - exact) <= eps * np.exp(0.5 * r) + 4e-16 * n
+    if n > 2:
+        m = n - 1
+        lc = 4 * lgamma(m + 1) - log(2 * m + 1) - 3 * lgamma(2 * m + 1)
+        assert lc + 2 * m * log(r) + r > log(eps)
+    assert binding.host_quadrature_nodes(r, 3, eps) == min(n, 3)

@@ -100,11 +100,13 @@ def test_splitk_table_is_applied_and_exact(ksplit, tile_n, M, N, tmp_path, monke
         binding.tune_reload_table()
 
 
-@pytest.mark.parametrize("Ml,Mr,d,Dl,Dr", HEFF_CASES + [(128, 128, 6, 7, 7), (50, 130, 10, 8, 3)])
+@pytest.mark.parametrize("Ml,Mr,d,Dl,Dr", HEFF_CASES + [(128, 128, 6, 7, 7), (50, 130, 10, 8, 3),
+                                           (37, 64, 8, 7, 7), (20, 32, 4, 5, 3),
+                                           (50, 32, 2, 6, 6)])
 def test_sweep_heff_path_matches_oracle(Ml, Mr, d, Dl, Dr):
     """The H_eff product as the sweep runs it (tdmrg_kernel_heff_timed: split, L.A contraction,
-    MPO mixing into split planes, contraction with R, with the split-K table) against the
-    oracle, 3xTF32 bound; ragged row and column tiles."""
+    MPO mixing into split planes, contraction with R, with the tile table) against the oracle,
+    3xTF32 bound; ragged row and column tiles, local dimensions d = 2 .. 10."""
     from oracle import tdvp
     from paper_2003_13245_gb300 import binding
     rng = np.random.default_rng(3000 + Ml + Mr + d)

@@ -511,6 +511,9 @@ int tdmrg_kernel_gauge_qr(int m, int n, const void* Y, int p, const void* E, voi
  * and status handling as tdmrg_kernel_gauge_qr, computed 16 columns at a time (block
  * Gram-Schmidt projections, Gram-form factorisation inside the block with a cancellation
  * guard that restarts the block at any column whose residual lost more than half its norm).
+ * Each block stages ceil(m / blocks) rows of 16 columns and 16 n projection coefficients in at
+ * most 200 KB of shared memory; a factor that does not fit (e.g. 24576 x 640 on 152 SMs) is
+ * factorised by the column-wise kernel of tdmrg_kernel_gauge_qr instead (same result).
  * Allocates and frees its scratch; synchronises `stream`. */
 int tdmrg_kernel_gauge_qr_blocked(int m, int n, const void* Y, int p, const void* E, void* Q,
                                   void* R, int* status, void* stream);

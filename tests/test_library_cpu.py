@@ -72,6 +72,19 @@ def test_argument_errors_are_reported(lib):
     assert rc == -1
     rc = lib.tdmrg_kernel_bond_exp(257, 7, 1, 1, 1, 1, 0.0, -0.05, 1e-7, 32, None, None)
     assert rc == -1
+    # tile widths other than 0, 64 and 128 are rejected before any allocation
+    import ctypes
+    ms = ctypes.c_double()
+    for tile_n in (32, 96, -64):
+        rc = lib.tdmrg_kernel_tc_gemm_timed(128, 64, 256, 1, 1, 1, tile_n, 2, ctypes.byref(ms),
+                                            None)
+        assert rc == -1
+    # the quadrature node rule checks its bound, cap and tolerance
+    for args in ((-1.0, 16, 1e-15), (float("nan"), 16, 1e-15), (1.0, 0, 1e-15), (1.0, 65, 1e-15),
+                 (1.0, 16, 0.0)):
+        with pytest.raises(binding.TdmrgError) as e:
+            binding.host_quadrature_nodes(*args)
+        assert e.value.code == -1
 
 
 def _mpo_params(peierls):

@@ -5,13 +5,15 @@
 // x*y is taken as x_hi*y_hi + x_hi*y_lo + x_lo*y_hi with FP32 accumulation in tensor memory,
 // and a complex product as four such real products (12 MMAs per 8-deep k step).
 //
-// One CTA computes a 128 x 64 tile of C = sum_r op(A_r) op(B_r)^T (both operands K-major).
-// Thread 0 issues the TMA loads (SWIZZLE_64B, 16-float = 64-byte rows, all four planes of
-// a tile in one 4-D box), thread 32 issues tcgen05.mma into two TMEM accumulators (re, im:
-// 64 columns each), and all four warps read TMEM back with tcgen05.ld for the epilogue.
-// Stages of 48 KB: two per CTA when the grid has more CTAs than the GPU has SMs (two CTAs fit
-// on an SM, so one's epilogue overlaps the other's main loop), four when it has at most one
-// CTA per SM; every wait is bounded and reports through `status`.
+// One CTA computes a 128 x BN tile (BN = 64 or 128 columns, chosen per contraction shape by
+// the tile table) of C = sum_r op(A_r) op(B_r)^T (both operands K-major).  Thread 0 issues the
+// TMA loads (SWIZZLE_64B, 16-float = 64-byte rows, all four planes of a tile in one 4-D box),
+// thread 32 issues tcgen05.mma into two TMEM accumulators (re, im: BN columns each), and all
+// four warps read TMEM back with tcgen05.ld for the epilogue.  With 64-column tiles the stages
+// are 48 KB: two per CTA when the grid has more CTAs than the GPU has SMs (two CTAs fit on an
+// SM, so one's epilogue overlaps the other's main loop), four when it has at most one CTA per
+// SM; 128-column tiles take three 64 KB stages.  Every wait is bounded and reports through
+// `status`.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <dlfcn.h>

@@ -575,6 +575,9 @@ int tdmrg_kernel_dfma_loop(int blocks, long long iters, double* sink, double* fl
  *   tdmrg_tune_recorded_shapes writes up to `capacity` shapes as 5 ints each to shapes[] and
  *     their number to *count (host);
  *   tdmrg_tune_reload_table makes the next contraction read the table file again;
+ *   tdmrg_tune_table_lookup writes the table's split and tile width for one shape to *ksplit
+ *     and *tile_n (host only, no CUDA call; both 0 when the shape is not listed; a line with
+ *     a width other than 64 or 128, or a split below 1, is ignored);
  *   tdmrg_kernel_tc_gemm_timed runs one shape with split ksplit and tile width tile_n (64 or
  *     128; 0 for either: the table / rule) on synthetic operands, one warm-up then `reps`
  *     launches between CUDA events on `stream`, and writes the average milliseconds to
@@ -582,6 +585,7 @@ int tdmrg_kernel_dfma_loop(int blocks, long long iters, double* sink, double* fl
 int tdmrg_tune_record_shapes(int on);
 int tdmrg_tune_recorded_shapes(int* shapes, int capacity, int* count);
 int tdmrg_tune_reload_table(void);
+int tdmrg_tune_table_lookup(int M, int N, int K, int nred, int nbatch, int* ksplit, int* tile_n);
 int tdmrg_kernel_tc_gemm_timed(int M, int N, int K, int nred, int nbatch, int ksplit, int tile_n,
                                int reps, double* ms_out, void* stream);
 

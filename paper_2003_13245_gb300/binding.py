@@ -58,6 +58,7 @@ _SIGS = {
     "tdmrg_tune_record_shapes": [_i],
     "tdmrg_tune_recorded_shapes": [_ip, _i, _ip],
     "tdmrg_tune_reload_table": [],
+    "tdmrg_tune_table_lookup": [_i, _i, _i, _i, _i, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
     "tdmrg_kernel_tc_gemm_timed": [_i, _i, _i, _i, _i, _i, _i, _i, _dp, _p],
     "tdmrg_fgr_mobility_batch": [_i, _i, _dp, _dp, _dp, _dp, _d, _i, _dp, _p],
     "tdmrg_coherence_length": [_i, _dp, _dp],
@@ -413,6 +414,15 @@ def tune_recorded_shapes():
 
 def tune_reload_table():
     load().tdmrg_tune_reload_table()
+
+
+def tune_table_lookup(M, N, K, nred, nbatch):
+    """(ksplit, tile_n) of the tile table for one contraction shape, (0, 0) when not listed
+    (host only)."""
+    ks, bn = ctypes.c_int(), ctypes.c_int()
+    _check(load().tdmrg_tune_table_lookup(int(M), int(N), int(K), int(nred), int(nbatch),
+                                          ctypes.byref(ks), ctypes.byref(bn)))
+    return ks.value, bn.value
 
 
 def kernel_tc_gemm_timed(M, N, K, nred, nbatch, ksplit, reps=10, stream=None, tile_n=0):

@@ -875,6 +875,16 @@ int tdmrg_tune_reload_table(void) {
   return TDMRG_OK;
 }
 
+int tdmrg_tune_table_lookup(int M, int N, int K, int nred, int nbatch, int* ksplit, int* tile_n) {
+  if (!ksplit || !tile_n) return fail(nullptr, TDMRG_ERR_ARG, "tune_table_lookup: NULL output");
+  return guarded(nullptr, [&] {
+    int ks = 0, bn = 0;
+    if (!tdmrg::tc_table_lookup(M, N, K, nred, nbatch, &ks, &bn)) ks = bn = 0;
+    *ksplit = ks;
+    *tile_n = bn;
+  });
+}
+
 int tdmrg_kernel_tc_gemm_timed(int M, int N, int K, int nred, int nbatch, int ksplit, int tile_n,
                                int reps, double* ms_out, void* stream) {
   if (M < 1 || N < 1 || K < 1 || nred < 1 || nbatch < 1 || ksplit < 0 || reps < 1 || !ms_out ||

@@ -742,6 +742,16 @@ std::vector<std::array<int, 5>> tc_recorded_shapes() {
   return out;
 }
 
+bool tc_table_lookup(int M, int N, int K, int nred, int nbatch, int* ksplit, int* bn) {
+  std::lock_guard<std::mutex> lock(g_tab_mu);
+  load_table_locked();
+  const auto it = g_tab.find(Shape(M, N, K, nred, nbatch));
+  if (it == g_tab.end()) return false;
+  *ksplit = it->second.ksplit;
+  *bn = it->second.bn;
+  return true;
+}
+
 void tc_reload_table() {
   std::lock_guard<std::mutex> lock(g_tab_mu);
   g_tab.clear();

@@ -47,6 +47,8 @@ void tc_record_shapes(bool on);
 std::vector<std::array<int, 5>> tc_recorded_shapes();
 // forget the loaded split-K table (read again at the next tc_gemm)
 void tc_reload_table();
+// the table's entry for a shape (host only, no CUDA call): false when the shape is not listed
+bool tc_table_lookup(int M, int N, int K, int nred, int nbatch, int* ksplit, int* bn);
 // dst(b, row, k) = conj?(src[b*sb + row*rs + k*ks])
 cudaError_t split_f64(const cplx* src, long long sb, long long rs, long long ks, int conj,
                       const TcOperand& dst, cudaStream_t s);

@@ -203,3 +203,29 @@ def test_host_quadrature_node_count_meets_its_bound(lib, r):
         lc = 4 * lgamma(m + 1) - log(2 * m + 1) - 3 * lgamma(2 * m + 1)
         assert lc + 2 * m * log(r) + r > log(eps)
     assert binding.host_quadrature_nodes(r, 3, eps) == min(n, 3)
+
+
+def test_tile_table_parsing(lib, tmp_path, monkeypatch):
+    """The tile table read beside the library (or from TDMRG_SPLITK_TABLE): lines
+    "M N K nred nbatch ksplit [tile_n]" with the width 64 when absent, comments skipped, lines
+    with a width other than 64 / 128 or a split below 1 ignored, unlisted shapes (0, 0); and
+    the committed table lists the shapes of the c2 bulk-site H_eff contractions."""
+    from paper_2003_13245_gb300 import binding
+    table = tmp_path / "table.txt"
+    table.write_text("# comment\n128 64 4096 1 1 3\n165 197 4096 1 1 2 128   # ms\n"
+                     "10 10 10 1 1 2 96\n11 11 11 1 1 0 64\n")
+    monkeypatch.setenv("TDMRG_SPLITK_TABLE", str(table))
+    binding.tune_reload_table()
+    try:
+        assert binding.tune_table_lookup(128, 64, 4096, 1, 1) == (3, 64)
+        assert binding.tune_table_lookup(165, 197, 4096, 1, 1) == (2, 128)
+        assert binding.tune_table_lookup(10, 10, 10, 1, 1) == (0, 0)
+        assert binding.tune_table_lookup(11, 11, 11, 1, 1) == (0, 0)
+        assert binding.tune_table_lookup(1, 2, 3, 4, 5) == (0, 0)
+    finally:
+        monkeypatch.delenv("TDMRG_SPLITK_TABLE")
+        binding.tune_reload_table()
+    ks, bn = binding.tune_table_lookup(8192, 128, 128, 7, 1)     # second contraction, c2 bulk
+    assert ks >= 1 and bn in (64, 128)
+    ks, bn = binding.tune_table_lookup(896, 8192, 128, 1, 1)     # first contraction, c2 bulk
+    assert ks >= 1 and bn in (64, 128)
